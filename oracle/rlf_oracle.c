@@ -1,0 +1,501 @@
+/*
+ * FP64 CPU oracle for the RadioLensfit hot path (Rivi & Miller, arXiv 2203.14071).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this file.  The CUDA library shares no code,
+ * header, table or constant generator with it.
+ *
+ * Every routine is the plain definition of one step of the method, written in
+ * double precision with straightforward loops:
+ *   rlfo_model_vis      Eq. 1 with the shear matrix of Eq. 2 (Sec. 2.2)
+ *   rlfo_alpha_med      Eq. 4 scale-flux relation (Sec. 2.2)
+ *   rlfo_sky_model      sum of Eq. 1 over the catalogue (Sec. 2.2)
+ *   rlfo_extract_facet  residual isolation, phase shift and facet averaging
+ *                       (Sec. 2.3), facet size K * alpha (Sec. 2.3, Sec. 4.1)
+ *   rlfo_fit_facet      chi^2 likelihood, analytic flux marginal, numeric
+ *                       scalelength marginal, 5% threshold moments and the
+ *                       bad-fit cut (Sec. 2.4, Sec. 4.1)
+ *   rlfo_pipeline       the whole chain with the sky-model update in chunks
+ *                       (Sec. 2.2, Sec. 3.1)
+ * Readings where the paper is silent are stated beside the code that takes them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define RLFO_C 299792458.0
+#define RLFO_PI 3.14159265358979323846
+#define RLFO_ARCSEC (RLFO_PI / 648000.0)
+
+/* per-source estimate record written by rlfo_fit_facet */
+enum {
+    RLFO_E1 = 0, RLFO_E2, RLFO_SIG1, RLFO_SIG2, RLFO_ALPHA, RLFO_FLUX, RLFO_FLAG,
+    RLFO_E1_SMOOTH, RLFO_E2_SMOOTH, RLFO_LOGL_MAX, RLFO_THRESH_MARGIN, RLFO_MAP_INDEX,
+    RLFO_NC, RLFO_NEST
+};
+
+typedef struct {
+    double add, esp, psf_nat, beta, nu_ref_hz, sigma_jy;
+    double e_max, r_min_arcsec, r_max_arcsec, r_std;
+    double thresh_frac, var_sigma_min, var_det_min;
+    int32_t facet_n, n_e, n_alpha, flux_prior; /* flux_prior 0: S in [0, inf); 1: real line */
+    int32_t chunk, update_mode;                /* update_mode 0: good fits only; 1: all */
+} rlfo_params;
+
+int rlfo_nest(void) { return RLFO_NEST; }
+int rlfo_params_size(void) { return (int)sizeof(rlfo_params); }
+
+/* Eq. 4: ln(alpha_med / arcsec) = ADD + ESP ln(S / uJy).  Returns arcsec. */
+double rlfo_alpha_med(double flux_jy, double add, double esp)
+{
+    return exp(add + esp * log(flux_jy * 1.0e6));
+}
+
+/* |A^{-T} k|^2 with A the shear matrix of Eq. 2, inverted explicitly. */
+static double sheared_k2(double ku, double kv, double e1, double e2)
+{
+    double a11 = 1.0 - e1, a12 = -e2, a21 = -e2, a22 = 1.0 + e1;
+    double det = a11 * a22 - a12 * a21;
+    /* inverse of A */
+    double i11 = a22 / det, i12 = -a12 / det, i21 = -a21 / det, i22 = a11 / det;
+    /* transpose of the inverse applied to k */
+    double x = i11 * ku + i21 * kv;
+    double y = i12 * ku + i22 * kv;
+    return x * x + y * y;
+}
+
+/* the Eq. 1 brightness factor (1 + 4 pi^2 alpha^2 |A^{-T} k|^2)^{-3/2}; k in wavelengths */
+double rlfo_shape(double ku, double kv, double alpha_rad, double e1, double e2)
+{
+    double k2 = sheared_k2(ku, kv, e1, e2);
+    return pow(1.0 + 4.0 * RLFO_PI * RLFO_PI * alpha_rad * alpha_rad * k2, -1.5);
+}
+
+/* n - 1 = sqrt(1 - l^2 - m^2) - 1, written without cancellation */
+static double n_minus_1(double l, double m)
+{
+    double r2 = l * l + m * m;
+    return -r2 / (1.0 + sqrt(1.0 - r2));
+}
+
+/* Eq. 1: visibility of one source at baseline (u, v, w) metres and frequency freq. */
+void rlfo_model_vis(double u, double v, double w, double freq, double l, double m,
+                    double flux_jy, double alpha_rad, double e1, double e2,
+                    double beta, double nu_ref, double *re, double *im)
+{
+    double s = freq / RLFO_C;
+    double ku = u * s, kv = v * s, kw = w * s;
+    double amp = pow(freq / nu_ref, beta) * flux_jy * rlfo_shape(ku, kv, alpha_rad, e1, e2);
+    double ph = 2.0 * RLFO_PI * (ku * l + kv * m + kw * n_minus_1(l, m));
+    *re = amp * cos(ph);
+    *im = amp * sin(ph);
+}
+
+/*
+ * Sky model (Sec. 2.2): V[r, c] = sum_j Eq.1_j(u_r, v_r, w_r, nu_c).
+ * rows: optional list of row indices (NULL = every row); out is [n_out][n_chan][2];
+ * abs_out (optional) receives sum_j |term_j| per output, the scale of a
+ * cancellation-aware tolerance.
+ */
+void rlfo_sky_model(int64_t n_rows, int32_t n_chan, const double *u, const double *v,
+                    const double *w, const double *freq, const int64_t *rows, int64_t n_out,
+                    int32_t n_src, const double *l, const double *m, const double *flux,
+                    const double *alpha_rad, const double *e1, const double *e2,
+                    double beta, double nu_ref, double *out, double *abs_out, int n_threads)
+{
+    if (!rows) n_out = n_rows;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t o = 0; o < n_out; ++o) {
+        int64_t r = rows ? rows[o] : o;
+        for (int32_t c = 0; c < n_chan; ++c) {
+            double sr = 0.0, si = 0.0, sa = 0.0;
+            for (int32_t j = 0; j < n_src; ++j) {
+                double re, im;
+                rlfo_model_vis(u[r], v[r], w[r], freq[c], l[j], m[j], flux[j], alpha_rad[j],
+                               e1[j], e2[j], beta, nu_ref, &re, &im);
+                sr += re;
+                si += im;
+                sa += sqrt(re * re + im * im);
+            }
+            out[(o * n_chan + c) * 2 + 0] = sr;
+            out[(o * n_chan + c) * 2 + 1] = si;
+            if (abs_out) abs_out[o * n_chan + c] = sa;
+        }
+    }
+}
+
+/*
+ * Facet of one source (Sec. 2.3).
+ *   residual   R = D - V_sky + model_i     (every source but i removed)
+ *   shifted    x = R * exp(-2 pi i (u l + v m + w (n - 1)))
+ *   cell       (iu, iv) = floor(k / du) + N/2 on an N x N window centred on the
+ *              origin; visibilities outside the window are dropped (reading).
+ * acc is [4][N*N]: sum Re x, sum Im x, count, sum of the spectral factor
+ * (nu/nu_ref)^beta; cell index iv * N + iu.  abs_acc (optional) is sum |x|.
+ * The sky model is read either as complex64 (sky_f) or complex128 (sky_d).
+ * The source model added back uses the source's current sky-model shape
+ * (e1_cur, e2_cur) and scalelength alpha_sky_rad.
+ */
+void rlfo_extract_facet(int64_t n_rows, int32_t n_chan, const double *u, const double *v,
+                        const double *w, const double *freq, const float *data,
+                        const float *sky_f, const double *sky_d,
+                        double l, double m, double flux, double alpha_sky_rad,
+                        double e1_cur, double e2_cur, double beta, double nu_ref,
+                        double du, int32_t facet_n, double *acc, double *abs_acc)
+{
+    const int64_t nc = (int64_t)facet_n * facet_n;
+    memset(acc, 0, sizeof(double) * 4 * nc);
+    if (abs_acc) memset(abs_acc, 0, sizeof(double) * nc);
+    const double n1 = n_minus_1(l, m);
+    for (int64_t r = 0; r < n_rows; ++r) {
+        for (int32_t c = 0; c < n_chan; ++c) {
+            double s = freq[c] / RLFO_C;
+            double ku = u[r] * s, kv = v[r] * s, kw = w[r] * s;
+            double fu = floor(ku / du), fv = floor(kv / du);
+            if (fu < -facet_n / 2 || fu >= facet_n / 2 || fv < -facet_n / 2 || fv >= facet_n / 2)
+                continue;
+            int64_t iu = (int64_t)fu + facet_n / 2, iv = (int64_t)fv + facet_n / 2;
+            int64_t idx = (r * n_chan + c) * 2;
+            double skr = sky_f ? (double)sky_f[idx] : sky_d[idx];
+            double ski = sky_f ? (double)sky_f[idx + 1] : sky_d[idx + 1];
+            double mr, mi;
+            rlfo_model_vis(u[r], v[r], w[r], freq[c], l, m, flux, alpha_sky_rad, e1_cur, e2_cur,
+                           beta, nu_ref, &mr, &mi);
+            double rr = (double)data[idx] - skr + mr;
+            double ri = (double)data[idx + 1] - ski + mi;
+            double ph = -2.0 * RLFO_PI * (ku * l + kv * m + kw * n1);
+            double cr = cos(ph), ci = sin(ph);
+            double xr = rr * cr - ri * ci;
+            double xi = rr * ci + ri * cr;
+            int64_t cell = iv * facet_n + iu;
+            acc[0 * nc + cell] += xr;
+            acc[1 * nc + cell] += xi;
+            acc[2 * nc + cell] += 1.0;
+            acc[3 * nc + cell] += pow(freq[c] / nu_ref, beta);
+            if (abs_acc) abs_acc[cell] += sqrt(xr * xr + xi * xi);
+        }
+    }
+}
+
+/* ln erfc(x) + x^2 for x > 25: the asymptotic series of Abramowitz & Stegun 7.1.23 */
+static double log_erfc_scaled_tail(double x)
+{
+    double t = 1.0 / (2.0 * x * x);
+    /* 1 - 1/(2x^2) + 3/(2x^2)^2 - 15/(2x^2)^3 + 105/(2x^2)^4 */
+    double series = 1.0 - t + 3.0 * t * t - 15.0 * t * t * t + 105.0 * t * t * t * t;
+    return -log(x * sqrt(RLFO_PI)) + log(series);
+}
+
+/*
+ * Flux-marginalised log-likelihood (Sec. 2.4): chi^2 = C - 2 S b + S^2 a and a
+ * uniform flux prior give
+ *   S in [0, inf):  -C/2 + b^2/(2a) + ln sqrt(pi/(2a)) + ln erfc(-b/sqrt(2a))
+ *   S on the line:  -C/2 + b^2/(2a) + ln sqrt(2 pi/a)
+ * When x = -b/sqrt(2a) > 25 the b^2/(2a) = x^2 term cancels the leading -x^2 of
+ * ln erfc(x); that cancellation is done analytically.
+ */
+double rlfo_flux_marginal(double a, double b, double cc, int flux_prior)
+{
+    if (flux_prior == 1)
+        return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(2.0 * RLFO_PI / a);
+    double x = -b / sqrt(2.0 * a);
+    if (x > 25.0)
+        return -0.5 * cc + 0.5 * log(RLFO_PI / (2.0 * a)) + log_erfc_scaled_tail(x);
+    return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(RLFO_PI / (2.0 * a)) + log(erfc(x));
+}
+
+double rlfo_grid_e(const rlfo_params *p, int k)
+{
+    return -p->e_max + k * (2.0 * p->e_max / (p->n_e - 1));
+}
+
+/* scalelength nodes with quadratic spacing on [RMIN, RMAX] (Sec. 2.4, Sec. 4.2); arcsec */
+double rlfo_grid_alpha(const rlfo_params *p, int k)
+{
+    double t = (p->n_alpha > 1) ? (double)k / (p->n_alpha - 1) : 0.0;
+    return p->r_min_arcsec + (p->r_max_arcsec - p->r_min_arcsec) * t * t;
+}
+
+/*
+ * Likelihood grid of one facet (Sec. 2.4) on e1, e2 in {-e_max .. e_max} (n_e
+ * nodes, |e| < 1 only) x alpha nodes.  loglike/a_out/b_out are
+ * [n_e][n_e][n_alpha] (e1 outer, alpha inner); invalid points get -inf, 0, 0.
+ * The facet model of a cell is S * s_c * shape(k_c) at the cell centre, w = 0.
+ * Returns the number of non-empty cells.
+ */
+int rlfo_like_grid(const double *acc, double du, const rlfo_params *p,
+                   double *loglike, double *a_out, double *b_out)
+{
+    const int N = p->facet_n, ne = p->n_e, na = p->n_alpha;
+    const int64_t nc = (int64_t)N * N;
+    const double sig2 = p->sigma_jy * p->sigma_jy;
+    /* cell averages and weights: D_c = mean x, s_c = mean spectral factor, w_c = n_c / sigma^2 */
+    int ncell = 0;
+    double cc = 0.0;
+    double *cu = malloc(sizeof(double) * nc), *cv = malloc(sizeof(double) * nc);
+    double *cw = malloc(sizeof(double) * nc), *cs = malloc(sizeof(double) * nc);
+    double *cd = malloc(sizeof(double) * nc);
+    for (int iv = 0; iv < N; ++iv)
+        for (int iu = 0; iu < N; ++iu) {
+            int64_t cell = (int64_t)iv * N + iu;
+            double n = acc[2 * nc + cell];
+            if (n <= 0.0) continue;
+            double dr = acc[0 * nc + cell] / n, di = acc[1 * nc + cell] / n;
+            cu[ncell] = (iu - N / 2 + 0.5) * du;
+            cv[ncell] = (iv - N / 2 + 0.5) * du;
+            cw[ncell] = n / sig2;
+            cs[ncell] = acc[3 * nc + cell] / n;
+            cd[ncell] = dr;
+            cc += cw[ncell] * (dr * dr + di * di);
+            ++ncell;
+        }
+    for (int i1 = 0; i1 < ne; ++i1)
+        for (int i2 = 0; i2 < ne; ++i2) {
+            double e1 = rlfo_grid_e(p, i1), e2 = rlfo_grid_e(p, i2);
+            int valid = (e1 * e1 + e2 * e2 < 1.0);
+            for (int k = 0; k < na; ++k) {
+                int64_t g = ((int64_t)i1 * ne + i2) * na + k;
+                if (!valid || ncell == 0) {
+                    loglike[g] = -INFINITY;
+                    a_out[g] = 0.0;
+                    b_out[g] = 0.0;
+                    continue;
+                }
+                double al = rlfo_grid_alpha(p, k) * RLFO_ARCSEC;
+                double a = 0.0, b = 0.0;
+                for (int c = 0; c < ncell; ++c) {
+                    double M = rlfo_shape(cu[c], cv[c], al, e1, e2);
+                    a += cw[c] * cs[c] * cs[c] * M * M;
+                    b += cw[c] * cs[c] * M * cd[c];
+                }
+                a_out[g] = a;
+                b_out[g] = b;
+                loglike[g] = rlfo_flux_marginal(a, b, cc, p->flux_prior);
+            }
+        }
+    free(cu); free(cv); free(cw); free(cs); free(cd);
+    return ncell;
+}
+
+/* trapezoid weight times the log-normal scalelength prior (mean from Eq. 4, sigma R_STD) */
+double rlfo_alpha_weight(const rlfo_params *p, double flux_cat, int k)
+{
+    const int na = p->n_alpha;
+    double ak = rlfo_grid_alpha(p, k);
+    double q;
+    if (na == 1) q = 1.0;
+    else if (k == 0) q = 0.5 * (rlfo_grid_alpha(p, 1) - ak);
+    else if (k == na - 1) q = 0.5 * (ak - rlfo_grid_alpha(p, na - 2));
+    else q = 0.5 * (rlfo_grid_alpha(p, k + 1) - rlfo_grid_alpha(p, k - 1));
+    double mu = p->add + p->esp * log(flux_cat * 1.0e6);
+    double z = (log(ak) - mu) / p->r_std;
+    return q * exp(-0.5 * z * z) / (ak * p->r_std * sqrt(2.0 * RLFO_PI));
+}
+
+/*
+ * Estimate from a likelihood grid (Sec. 2.4): marginalise alpha numerically,
+ * keep the e points whose marginal is at least thresh_frac of its maximum, and
+ * return their likelihood-weighted mean and standard deviation; the bad-fit cut
+ * of Sec. 4.1 sets the flag.  Le_out (optional, [n_e*n_e]) receives the
+ * alpha-marginal L(e) relative to exp(max logL).
+ */
+void rlfo_estimate(const double *loglike, const double *a_out, const double *b_out,
+                   double flux_cat, int ncell, const rlfo_params *p, double *est, double *Le_out)
+{
+    const int ne = p->n_e, na = p->n_alpha;
+    double lmax = -INFINITY;
+    for (int64_t g = 0; g < (int64_t)ne * ne * na; ++g)
+        if (loglike[g] > lmax) lmax = loglike[g];
+    double *qp = malloc(sizeof(double) * na);
+    for (int k = 0; k < na; ++k) qp[k] = rlfo_alpha_weight(p, flux_cat, k);
+    double mu = p->add + p->esp * log(flux_cat * 1.0e6);
+
+    /* marginal over alpha: L(e) = sum_k q_k p(alpha_k) exp(logL(e, alpha_k) - lmax) */
+    double *Le = malloc(sizeof(double) * ne * ne);
+    double *Ae = malloc(sizeof(double) * ne * ne);
+    double Lmax = 0.0;
+    for (int e = 0; e < ne * ne; ++e) {
+        double s = 0.0, sa = 0.0;
+        for (int k = 0; k < na; ++k) {
+            double lg = loglike[(int64_t)e * na + k];
+            if (lg == -INFINITY) continue;
+            double t = qp[k] * exp(lg - lmax);
+            s += t;
+            sa += t * rlfo_grid_alpha(p, k);
+        }
+        Le[e] = s;
+        Ae[e] = sa;
+        if (s > Lmax) Lmax = s;
+        if (Le_out) Le_out[e] = s;
+    }
+
+    /* moments over the points above thresh_frac * Lmax, and over all points */
+    double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0;
+    double margin = INFINITY;
+    for (int e = 0; e < ne * ne; ++e) {
+        if (!(Le[e] > 0.0)) continue;
+        double e1 = rlfo_grid_e(p, e / ne), e2 = rlfo_grid_e(p, e % ne);
+        Ws += Le[e];
+        s1 += Le[e] * e1;
+        s2 += Le[e] * e2;
+        double dm = fabs(log(Le[e] / Lmax) - log(p->thresh_frac));
+        if (dm < margin) margin = dm;
+        if (Le[e] >= p->thresh_frac * Lmax) {
+            W += Le[e];
+            m1 += Le[e] * e1;
+            m2 += Le[e] * e2;
+            WA += Ae[e];
+        }
+    }
+    double e1m = 0, e2m = 0, c11 = 0, c22 = 0, c12 = 0, am = 0;
+    if (W > 0) {
+        e1m = m1 / W;
+        e2m = m2 / W;
+        am = WA / W;
+        for (int e = 0; e < ne * ne; ++e) {
+            if (!(Le[e] > 0.0) || Le[e] < p->thresh_frac * Lmax) continue;
+            double d1 = rlfo_grid_e(p, e / ne) - e1m, d2 = rlfo_grid_e(p, e % ne) - e2m;
+            c11 += Le[e] * d1 * d1;
+            c22 += Le[e] * d2 * d2;
+            c12 += Le[e] * d1 * d2;
+        }
+        c11 /= W;
+        c22 /= W;
+        c12 /= W;
+    }
+    /* maximum a posteriori grid point: logL + ln p(alpha); ties -> lowest flat index */
+    int64_t gmap = -1;
+    double best = -INFINITY;
+    for (int64_t g = 0; g < (int64_t)ne * ne * na; ++g) {
+        if (loglike[g] == -INFINITY) continue;
+        double ak = rlfo_grid_alpha(p, (int)(g % na));
+        double z = (log(ak) - mu) / p->r_std;
+        double lp = loglike[g] - 0.5 * z * z - log(ak);
+        if (lp > best) {
+            best = lp;
+            gmap = g;
+        }
+    }
+    double s1d = sqrt(c11), s2d = sqrt(c22);
+    double det = c11 * c22 - c12 * c12;
+    double sdet = det > 0 ? sqrt(det) : 0.0;
+    int bad = (W <= 0) || (s1d <= p->var_sigma_min) || (s2d <= p->var_sigma_min) ||
+              (sdet <= p->var_det_min);
+    est[RLFO_E1] = e1m;
+    est[RLFO_E2] = e2m;
+    est[RLFO_SIG1] = s1d;
+    est[RLFO_SIG2] = s2d;
+    est[RLFO_ALPHA] = am;
+    est[RLFO_FLUX] = (gmap >= 0 && a_out[gmap] > 0) ? b_out[gmap] / a_out[gmap] : 0.0;
+    est[RLFO_FLAG] = bad ? 1.0 : 0.0;
+    est[RLFO_E1_SMOOTH] = Ws > 0 ? s1 / Ws : 0.0;
+    est[RLFO_E2_SMOOTH] = Ws > 0 ? s2 / Ws : 0.0;
+    est[RLFO_LOGL_MAX] = lmax;
+    est[RLFO_THRESH_MARGIN] = margin;
+    est[RLFO_MAP_INDEX] = (double)gmap;
+    est[RLFO_NC] = (double)ncell;
+    free(qp); free(Le); free(Ae);
+}
+
+/* likelihood grid followed by the estimate */
+void rlfo_fit_facet(const double *acc, double du, double flux_cat, const rlfo_params *p,
+                    double *loglike, double *a_out, double *b_out, double *est)
+{
+    int ncell = rlfo_like_grid(acc, du, p, loglike, a_out, b_out);
+    rlfo_estimate(loglike, a_out, b_out, flux_cat, ncell, p, est, NULL);
+}
+
+/* facet cell size du = 1 / (K alpha) in wavelengths (Sec. 2.3); alpha in arcsec */
+double rlfo_facet_du(double flux_jy, double alpha_cat_arcsec, const rlfo_params *p)
+{
+    double a = alpha_cat_arcsec > 0 ? alpha_cat_arcsec : rlfo_alpha_med(flux_jy, p->add, p->esp);
+    return 1.0 / (p->psf_nat * a * RLFO_ARCSEC);
+}
+
+/*
+ * Whole chain (Sec. 2): circular sky model, then for each chunk of sources in
+ * catalogue order: extract every facet of the chunk from the current sky model,
+ * fit them, and replace their shapes in the sky model (good fits only, or all
+ * with update_mode 1).  chunk = 1 is the serial order; chunk = n_src extracts
+ * everything from the initial model (Sec. 3.1 on chunked updates).
+ * est is [n_src][RLFO_NEST]; sky_out (optional) receives the final sky model.
+ */
+int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double *v,
+                  const double *w, const double *freq, const float *data, int32_t n_src,
+                  const double *l, const double *m, const double *flux,
+                  const double *alpha_cat_arcsec, const rlfo_params *p, double *est,
+                  double *sky_out, int n_threads)
+{
+    const int64_t nv = n_rows * n_chan;
+    const int64_t nc = (int64_t)p->facet_n * p->facet_n;
+    const int ng = p->n_e * p->n_e * p->n_alpha;
+    double *sky = malloc(sizeof(double) * nv * 2);
+    double *alpha_sky = malloc(sizeof(double) * n_src);
+    double *e1c = calloc(n_src, sizeof(double)), *e2c = calloc(n_src, sizeof(double));
+    if (!sky || !alpha_sky || !e1c || !e2c) return 1;
+    for (int j = 0; j < n_src; ++j) {
+        double a = alpha_cat_arcsec && alpha_cat_arcsec[j] > 0 ? alpha_cat_arcsec[j]
+                                                               : rlfo_alpha_med(flux[j], p->add, p->esp);
+        alpha_sky[j] = a * RLFO_ARCSEC;
+    }
+    rlfo_sky_model(n_rows, n_chan, u, v, w, freq, NULL, 0, n_src, l, m, flux, alpha_sky, e1c, e2c,
+                   p->beta, p->nu_ref_hz, sky, NULL, n_threads);
+    int chunk = p->chunk > 0 ? p->chunk : n_src;
+    for (int first = 0; first < n_src; first += chunk) {
+        int cnt = (first + chunk <= n_src) ? chunk : n_src - first;
+#ifdef _OPENMP
+        if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (int t = 0; t < cnt; ++t) {
+            int i = first + t;
+            double *acc = malloc(sizeof(double) * 4 * nc);
+            double *lg = malloc(sizeof(double) * ng * 3);
+            double du = rlfo_facet_du(flux[i], alpha_cat_arcsec ? alpha_cat_arcsec[i] : 0.0, p);
+            rlfo_extract_facet(n_rows, n_chan, u, v, w, freq, data, NULL, sky, l[i], m[i], flux[i],
+                               alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, du, p->facet_n,
+                               acc, NULL);
+            rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, est + (int64_t)i * RLFO_NEST);
+            free(acc);
+            free(lg);
+        }
+        /* sky update: V += model_i(e_new) - model_i(e_cur) for the chunk */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int64_t r = 0; r < n_rows; ++r)
+            for (int32_t c = 0; c < n_chan; ++c)
+                for (int t = 0; t < cnt; ++t) {
+                    int i = first + t;
+                    const double *e = est + (int64_t)i * RLFO_NEST;
+                    if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
+                    double nr, ni, orr, oi;
+                    rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
+                                   e[RLFO_E1], e[RLFO_E2], p->beta, p->nu_ref_hz, &nr, &ni);
+                    rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
+                                   e1c[i], e2c[i], p->beta, p->nu_ref_hz, &orr, &oi);
+                    sky[(r * n_chan + c) * 2 + 0] += nr - orr;
+                    sky[(r * n_chan + c) * 2 + 1] += ni - oi;
+                }
+        for (int t = 0; t < cnt; ++t) {
+            int i = first + t;
+            const double *e = est + (int64_t)i * RLFO_NEST;
+            if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
+            e1c[i] = e[RLFO_E1];
+            e2c[i] = e[RLFO_E2];
+        }
+    }
+    if (sky_out) memcpy(sky_out, sky, sizeof(double) * nv * 2);
+    free(sky);
+    free(alpha_sky);
+    free(e1c);
+    free(e2c);
+    return 0;
+}
