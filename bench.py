@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Throughput of the RadioLensfit hot path on GB300.
+
+One step is one pass of the whole chain over the workload: sky model of the
+catalogue, extraction of every facet, likelihood fit of every facet, sky-model
+update with the measured shapes (rlf_run).  Default workload: 197 antennas
+(19306 baselines) x 240 time steps x 8 channels = 37,067,520 visibilities and 200
+sources (chunk = all sources, mixed precision).  Inputs are synthetic and
+resident in HBM before the timed region (they exceed L2, so no flush is
+needed); the data visibilities are made with the library's own sky-model call at
+the catalogue's true shapes and scalelengths plus seeded Gaussian noise.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+ARC = math.pi / 648000.0
+METRIC = "source fits/sec (end-to-end: sky model + facet extraction + likelihood fit + sky update)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--chunk", type=int, default=0, help="sources per extract/fit/update step (0: all)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--update-mode", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--components", action="store_true", help="also time each entry point alone")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU arm: the FP64 oracle on a bounded sample
+
+
+def oracle_sample_step(wl, obs, cat, params, rows_stride=4, n_threads=1):
+    """Per-source CPU cost of the chain, measured on one source (index 0).
+
+    Extraction and the sky-model/update passes are timed on every
+    `rows_stride`-th row and scaled by the row ratio; the fit runs on the full
+    facet of that subset.  Returns seconds per source at the full workload:
+        t_extract + t_fit + t_update + t_sky_model / n_src
+    """
+    import oracle
+    rows = np.arange(0, obs.n_rows, rows_stride)
+    u, v, w = obs.u[rows], obs.v[rows], obs.w[rows]
+    scale = obs.n_rows / rows.size
+    rng = np.random.default_rng(5)
+    data = rng.standard_normal((rows.size, obs.n_chan, 2)).astype(np.float32) * np.float32(1e-5)
+    sky = np.zeros_like(data)
+    i = 0
+    al = oracle.alpha_med(cat.flux_jy[i]) * ARC
+    du = oracle.facet_du(cat.flux_jy[i], 0.0, params)
+    t0 = time.perf_counter()
+    acc = oracle.extract_facet(u, v, w, obs.freq_hz, data, sky, cat.l[i], cat.m[i], cat.flux_jy[i], al,
+                               0.0, 0.0, du, params)
+    t1 = time.perf_counter()
+    oracle.fit_facet(acc, du, cat.flux_jy[i], params)
+    t2 = time.perf_counter()
+    # one source's sky-model term on the subset: the sky model costs n_src of these per pass,
+    # the update two of them (new and old shape) per source
+    oracle.sky_model(u, v, w, obs.freq_hz, cat.l[:1], cat.m[:1], cat.flux_jy[:1], np.array([al]),
+                     np.zeros(1), np.zeros(1), nu_ref=wl.nu_ref_hz, n_threads=n_threads)
+    t3 = time.perf_counter()
+    t_term = (t3 - t2) * scale
+    return (t1 - t0) * scale + (t2 - t1) + 2 * t_term + t_term
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    wl = synth.workload(args.workload)
+    obs = synth.make_observation(wl)
+    cat = synth.make_catalogue(wl)
+    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample_step(wl, obs, cat, params)
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        per.append(oracle_sample_step(wl, obs, cat, params))
+    wall = time.perf_counter() - t0
+    sec_per_source = float(np.mean(per))
+    value = 1.0 / sec_per_source
+    sample = ("source 0 of %d: facet extraction and one-source sky-model term on every 4th row (scaled x4), "
+              "fit of that facet; per-source cost = extract + fit + update (2 terms) + sky model (1 term)"
+              % cat.n_src)
+    line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_per_source * cat.n_src * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "n_vis": obs.n_rows * obs.n_chan, "n_src": cat.n_src},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "fits/s", "cores": 1, "sample": sample,
+                             "wall_s": wall},
+            "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_14071_gb300 as rlf
+    from paper_2203_14071_gb300 import build_ext
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        build_ext.build()
+    if world > 1:
+        dist.barrier()
+    rlf.lib()
+
+    wl = synth.workload(args.workload)
+    obs_np = synth.make_observation(wl)
+    cat_np = synth.make_catalogue(wl)
+    n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
+    n_vis = R * C
+    prec = rlf.PREC_MIXED if args.precision == "mixed" else rlf.PREC_FP64
+    t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz)
+    zeros = torch.zeros(n_src, dtype=torch.float64, device=dev)
+    cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
+    truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
+    params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=args.chunk,
+                                precision=prec, update_mode=args.update_mode)
+
+    # observed data: the true sky (library sky model at the catalogue's true shapes) plus noise
+    ws = rlf.alloc_workspace(R, C, n_src, params, rlf.WS_RUN, device=dev)
+    data = torch.empty(n_vis * 2, dtype=torch.float32, device=dev)
+    rlf.sky_model(obs, truth, params, data, ws)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    data += torch.randn(n_vis * 2, generator=gen, device=dev, dtype=torch.float32) * wl.sigma_jy
+    sky = torch.empty_like(data)
+    out = rlf.Results(n_src, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rlf.run(obs, data, cat, params, out, sky, ws, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    code, status = rlf.read_status(ws, stream)
+    if code != rlf.RLF_OK:
+        raise RuntimeError(f"device status {status}: {rlf.strerror(code)}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+
+    # per-kernel timing of the dominant phases (same stream, CUDA events), and e2e
+    comp = component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, args, n_src)
+    clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    e2e = None if args.no_e2e else e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, args)
+    res = out.numpy()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = rlf.peaks_measure(stream)
+    value = n_src * world / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == rlf.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_ant": obs_np.n_ant, "n_baselines": obs_np.n_bl,
+                   "n_time": obs_np.n_time, "n_chan": C, "n_vis": n_vis, "n_src": n_src,
+                   "facet_n": params.facet_n, "grid": [params.n_e, params.n_e, params.n_alpha],
+                   "chunk": args.chunk if args.chunk > 0 else n_src, "precision": args.precision,
+                   "update_mode": args.update_mode, "l2": "inputs larger than L2 (no flush)"},
+        "sky_model_gvis_s": comp["sky_gvis_s"],
+        "phases_ms": comp["phases_ms"],
+        "gpu_launches": comp["launches_per_step"] * args.steps,
+        "clocks": clocks.summary(),
+        "measured_unit_peaks": peaks,
+        "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2))},
+    }
+    line["roofline"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, obs_np, cat_np)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, args, n_src):
+    """Each entry point timed alone with CUDA events on the launching stream."""
+    reps = max(3, args.steps)
+    facets = torch.empty(rlf.facets_size(n_src, params) // 8, dtype=torch.float64, device=dev)
+    ws_fit = rlf.alloc_workspace(obs.n_rows, obs.n_chan, n_src, params, rlf.WS_FIT, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    sky_ms = timed(lambda: rlf.sky_model(obs, cat, params, sky, ws, stream))
+    ext_ms = timed(lambda: rlf.extract_facets(obs, data, sky, cat, 0, n_src, params, facets, ws, stream))
+    fit_ms = timed(lambda: rlf.fit_sources(facets, cat, 0, n_src, params, out, ws_fit, stream))
+    upd_ms = timed(lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream))
+    chunk = params.chunk if params.chunk > 0 else n_src
+    n_chunks = (n_src + chunk - 1) // chunk
+    # rlf_run: memset + 2 copies + prepare + sky; per chunk: memset + prepare + extract + compact + grid
+    # + estimate + prepare + update  (memsets/copies are not kernels of ours)
+    launches = 2 + n_chunks * 7
+    return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
+            "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches}
+
+
+def roofline(comp, peaks, params, n_vis, n_src, R, C):
+    """Roofline of the dominant phase.  The path is ALU bound (no dense contraction,
+    HBM traffic far below the compute time); the limiting unit and its per-unit
+    op counts are stated in the design doc."""
+    ph = comp["phases_ms"]
+    name = max(ph, key=ph.get)
+    t = ph[name] * 1e-3
+    if name in ("sky_model", "update", "extract"):
+        # FP64 phase argument and reduction: per (row, source) 3 FMA-class ops for the
+        # argument and 2 x (multiply, round, subtract) for the channel-0 and channel-step
+        # phases = 9 FP64 ops; the sky update evaluates the phase once per source too
+        units = R * n_src
+        ops = 9.0 * units
+        return {"kernel": name, "bound": "alu", "unit": "FP64 Gop/s", "achieved": ops / t / 1e9,
+                "peak": peaks["fp64_fma_per_s"] / 1e9, "frac": ops / t / peaks["fp64_fma_per_s"],
+                "traffic": None, "note": "peak = measured FP64 FMA rate (rlf_peaks_measure)"}
+    # fit: one MUFU rsqrt per (grid point, cell)
+    G = params.n_e * params.n_e * params.n_alpha
+    return {"kernel": name, "bound": "alu", "unit": "MUFU Gop/s", "achieved": None, "peak":
+            peaks["mufu_rsqrt_per_s"] / 1e9, "frac": None, "traffic": None, "grid_points": G}
+
+
+def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, args):
+    """Same step through the public API with host buffers: pinned host inputs copied in,
+    the fitted shapes copied back, every step."""
+    n = cat.n_src
+    h_data = data.cpu().pin_memory()
+    h_uvw = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (obs_np.u, obs_np.v, obs_np.w)]
+    d_uvw = [torch.empty_like(x, device=dev) for x in h_uvw]
+    d_data = torch.empty_like(data)
+    obs = rlf.Observation(d_uvw[0], d_uvw[1], d_uvw[2], obs_np.freq_hz)
+    h_out = torch.empty((2, n), dtype=torch.float64).pin_memory()
+
+    def step():
+        for h, d in zip(h_uvw, d_uvw):
+            d.copy_(h, non_blocking=True)
+        d_data.copy_(h_data, non_blocking=True)
+        rlf.run(obs, d_data, cat, params, out, sky, ws, stream)
+        h_out[0].copy_(out.e1, non_blocking=True)
+        h_out[1].copy_(out.e2, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.steps
+    h2d = h_data.numel() * 4 + sum(x.numel() * 8 for x in h_uvw)
+    return {"value": n / (ms * 1e-3), "unit": "fits/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 2 * n * 8}
+
+
+def cpu_baseline(wl, obs_np, cat_np):
+    import oracle
+    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy)
+    oracle.build()
+    t0 = time.perf_counter()
+    sec = oracle_sample_step(wl, obs_np, cat_np, params)
+    wall = time.perf_counter() - t0
+    return {"value": 1.0 / sec, "unit": "fits/s", "cores": 1, "kind": "oracle", "wall_s": wall,
+            "sample": "source 0: facet extraction and one-source sky-model term on every 4th row (x4), "
+                      "fit of that facet; per source = extract + fit + update + sky model / n_src"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * rlf.h - C ABI of the GB300 (sm_103a) RadioLensfit hot path.
+ *
+ * The library implements the data-parallel core of RadioLensfit
+ * (Rivi & Miller, arXiv 2203.14071):
+ *   - the analytic sky model: the sum over the catalogue of the exponential-disk
+ *     visibility of Eq. 1 with the shear matrix of Eq. 2 (Sec. 2.2);
+ *   - per-source isolation of the residual visibilities, phase shift to the
+ *     source and averaging into a facet of cell size 1/(K alpha) (Sec. 2.3);
+ *   - the chi^2 likelihood of each facet on an (e1, e2, alpha) grid with the
+ *     flux marginalised analytically and alpha numerically, reduced to the
+ *     ellipticity estimate and its spread (Sec. 2.4), and the sky-model update
+ *     with the measured shapes (Sec. 2.2, Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers documented as "device" point to GPU global memory owned by the
+ *     caller; the library never frees them and never allocates device memory.
+ *     Scratch space is the caller-provided workspace (see rlf_workspace_size).
+ *   - Pointers documented as "host" point to ordinary CPU memory and are read
+ *     before the call returns.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Work is
+ *     enqueued on it and the call returns without waiting for the GPU, except
+ *     where noted.
+ *   - Visibilities are complex64, stored as interleaved float pairs (re, im),
+ *     row-major [n_rows][n_chan] (channel fastest), in Jy.
+ *   - Argument errors found on the host return RLF_EINVAL / RLF_EUNSUPPORTED /
+ *     RLF_ENOSPACE before anything is enqueued.  Per-source value errors
+ *     (flux <= 0 or not finite, |e| >= 1, l^2 + m^2 >= 1) are found on the GPU:
+ *     the source contributes nothing, its fit flag gets RLF_FLAG_INVALID and the
+ *     workspace status word gets RLF_DEV_INVALID_SOURCE (read it with
+ *     rlf_read_status).  A CUDA launch failure returns RLF_ECUDA.
+ */
+#ifndef RLF_H
+#define RLF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RLF_OK = 0,
+    RLF_EINVAL = 1,        /* null pointer, non-positive size, bad parameter */
+    RLF_ECUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    RLF_ENOSPACE = 3,      /* workspace or facet buffer smaller than required */
+    RLF_ETIMEOUT = 4,      /* a bounded device wait gave up (status word) */
+    RLF_ENUMERIC = 5,      /* a non-finite likelihood was produced (status word) */
+    RLF_EUNSUPPORTED = 6   /* valid request outside the implemented limits */
+} rlf_status;
+
+/* arithmetic of the path */
+enum {
+    RLF_PREC_FP64 = 0,     /* every step in double precision */
+    RLF_PREC_MIXED = 1     /* FP32 model and sums of products; FP64 phase argument and its
+                              range reduction, cell-index decisions, likelihood accumulation
+                              and the marginal normalisation */
+};
+
+/* bits of the per-source fit flag */
+enum {
+    RLF_FLAG_BAD = 1,      /* Sec. 4.1 cut: sigma(e_i) or sqrt(det cov) not above its minimum */
+    RLF_FLAG_INVALID = 2,  /* the source's input values are out of range */
+    RLF_FLAG_EMPTY = 4     /* the facet holds no visibility */
+};
+
+/* bits of the device status word */
+enum {
+    RLF_DEV_INVALID_SOURCE = 1,
+    RLF_DEV_NONFINITE = 2,
+    RLF_DEV_TIMEOUT = 4
+};
+
+/* workspace users for rlf_workspace_size */
+enum { RLF_WS_SKY = 0, RLF_WS_EXTRACT = 1, RLF_WS_FIT = 2, RLF_WS_RUN = 3 };
+
+/* Largest channel count and facet side handled by one call. */
+#define RLF_MAX_CHAN 128
+#define RLF_MAX_FACET_N 64
+
+/* Observation: baselines in metres (Sec. 2.2: (u, v, w) with w towards the phase centre). */
+typedef struct {
+    int64_t n_rows;          /* number of (baseline, time) rows, > 0 */
+    int32_t n_chan;          /* channels, 1 .. RLF_MAX_CHAN */
+    int32_t reserved;
+    const double *u;         /* device [n_rows], metres */
+    const double *v;         /* device [n_rows], metres */
+    const double *w;         /* device [n_rows], metres */
+    const double *freq_hz;   /* host [n_chan], channel centres, strictly increasing */
+} rlf_uvw;
+
+/* Catalogue (Sec. 2.1): ordered by decreasing flux or SNR by the caller. */
+typedef struct {
+    int32_t n_src;           /* > 0 */
+    int32_t reserved;
+    const double *l;         /* device [n_src], direction cosine */
+    const double *m;         /* device [n_src], direction cosine */
+    const double *flux_jy;   /* device [n_src], integrated flux at nu_ref, > 0 */
+    const double *alpha_arcsec; /* device [n_src] catalogue scalelength, <= 0 entries (or a
+                                   NULL pointer) use the Eq. 4 median for the flux */
+    const double *e1;        /* device [n_src], shape currently in the sky model */
+    const double *e2;        /* device [n_src] */
+} rlf_sources;
+
+/* Algorithm parameters; rlf_params_default gives the paper's values. */
+typedef struct {
+    double add, esp;         /* Eq. 4 intercept and slope (ADD = -0.93, ESP = 0.33) */
+    double psf_nat;          /* facet field-of-view factor K (Sec. 2.3, K = 38 in Sec. 4.1) */
+    double beta;             /* spectral index (-0.7, Sec. 2.2) */
+    double nu_ref_hz;        /* reference frequency of the fluxes */
+    double sigma_jy;         /* noise standard deviation per visibility component */
+    double e_max;            /* grid e1, e2 in [-e_max, e_max] */
+    double r_min_arcsec, r_max_arcsec; /* scalelength range [RMIN, RMAX] (Sec. 4.2) */
+    double r_std;            /* log-normal prior width R_STD (Sec. 2.4) */
+    double thresh_frac;      /* fraction of the maximum kept by the estimator (0.05) */
+    double var_sigma_min;    /* bad fit if sigma(e_i) <= this (5e-3, Sec. 4.1) */
+    double var_det_min;      /* bad fit if sqrt(det cov) <= this (5e-5, Sec. 4.1) */
+    int32_t facet_n;         /* facet side in cells, even, 2 .. RLF_MAX_FACET_N */
+    int32_t n_e;             /* grid nodes per ellipticity component, 2 .. 64 */
+    int32_t n_alpha;         /* scalelength nodes, 1 .. 64 */
+    int32_t flux_prior;      /* 0: uniform on S >= 0; 1: uniform on the real line */
+    int32_t chunk;           /* sources per extract/fit/update step of rlf_run; <= 0: all */
+    int32_t update_mode;     /* 0: update the sky model with good fits only; 1: with all */
+    int32_t precision;       /* RLF_PREC_FP64 or RLF_PREC_MIXED */
+    int32_t reserved;
+} rlf_params;
+
+/* Per-source results, each a device array of `count` entries. */
+typedef struct {
+    double *e1, *e2;         /* likelihood-weighted mean over the kept grid points */
+    double *sig1, *sig2;     /* their standard deviations */
+    double *alpha_arcsec;    /* posterior mean scalelength over the kept points */
+    double *flux_jy;         /* b/a at the maximum a posteriori grid point */
+    double *e1_smooth, *e2_smooth; /* mean over every grid point (no threshold) */
+    int32_t *flag;           /* RLF_FLAG_* bits */
+} rlf_fit_out;
+
+/* Fill *p with the paper's defaults: ADD, ESP, K = 38, beta = -0.7, RMIN 0.3",
+ * RMAX 3.5", R_STD 0.3136, 5% threshold, 5e-3 / 5e-5 cuts, 21 x 21 e nodes on
+ * [-0.8, 0.8], 20 alpha nodes, 64 x 64 facets, RLF_PREC_MIXED, chunk = all. */
+void rlf_params_default(rlf_params *p);
+
+/* Bytes of workspace needed by entry point `which` (RLF_WS_*) for these sizes;
+ * RLF_WS_RUN covers every entry point.  0 for invalid arguments. */
+size_t rlf_workspace_size(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params *p,
+                          int32_t which);
+
+/* Bytes of a facet buffer holding `count` facets: count * 4 * facet_n^2 doubles. */
+size_t rlf_facets_size(int32_t count, const rlf_params *p);
+
+/*
+ * Sky model, Sec. 2.2 (Eq. 1 summed over the catalogue, Eq. 2 shear):
+ *   vis_sky[r, c] = sum_j (nu_c/nu_ref)^beta S_j (1 + 4 pi^2 alpha_j^2 |A_j^{-T} k|^2)^{-3/2}
+ *                   * exp(2 pi i (u l_j + v m_j + w (n_j - 1)) nu_c / c)
+ * with k = (u, v) nu_c / c, alpha_j the catalogue scalelength or the Eq. 4 median
+ * and A_j built from the sources' current (e1, e2).  vis_sky (device
+ * [n_rows][n_chan][2] float) is overwritten.
+ */
+rlf_status rlf_sky_model(const rlf_uvw *uvw, const rlf_sources *src, const rlf_params *p,
+                         float *vis_sky, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Sky-model update, Sec. 2.2 and Sec. 3.1: for each source i in
+ * [first, first + count) selected by update_mode (all, or flag[i - first] has no
+ * RLF_FLAG_BAD / RLF_FLAG_INVALID / RLF_FLAG_EMPTY bit),
+ *   vis_sky += model_i(e_new) - model_i(e_old)
+ * where e_old is src->e1/e2 and e_new is e1_new/e2_new (device [count]).
+ * flag (device [count]) may be NULL, which updates every source in the range.
+ */
+rlf_status rlf_sky_update(const rlf_uvw *uvw, const rlf_sources *src, int32_t first,
+                          int32_t count, const double *e1_new, const double *e2_new,
+                          const int32_t *flag, const rlf_params *p, float *vis_sky,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Facet extraction, Sec. 2.3, for sources [first, first + count):
+ *   x = (D - V_sky + model_i) exp(-2 pi i (u l_i + v m_i + w (n_i - 1)) nu / c)
+ * averaged in cells of side du_i = 1 / (K alpha_i) wavelengths on a facet_n x
+ * facet_n window centred on the origin; cell (iu, iv) = floor(k / du_i) + facet_n/2,
+ * visibilities outside the window are dropped.  model_i uses the source's
+ * current (e1, e2).  facets (device) receives, per source, 4 planes of
+ * facet_n^2 doubles: sum Re x, sum Im x, count, sum (nu/nu_ref)^beta; cell
+ * index iv * facet_n + iu.  facets_bytes must be >= rlf_facets_size(count, p).
+ */
+rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const float *vis_sky,
+                              const rlf_sources *src, int32_t first, int32_t count,
+                              const rlf_params *p, double *facets, size_t facets_bytes,
+                              void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Source fitting, Sec. 2.4, for the `count` facets in `facets` (sources
+ * [first, first + count)).  With D_c = mean x, s_c = mean spectral factor and
+ * w_c = n_c / sigma^2 per non-empty cell and M_c the Eq. 1 brightness factor at
+ * the cell centre (w = 0):
+ *   a = sum w_c s_c^2 M_c^2,  b = sum w_c s_c M_c Re D_c,  C = sum w_c |D_c|^2
+ *   logL = -C/2 + b^2/(2a) + ln sqrt(pi/(2a)) + ln erfc(-b / sqrt(2a))
+ * on e1, e2 nodes -e_max + k 2 e_max/(n_e - 1) with |e| < 1 and alpha nodes
+ * RMIN + (RMAX - RMIN)(k/(n_alpha - 1))^2.  alpha is marginalised with
+ * trapezoid weights and a log-normal prior (mean ln alpha from Eq. 4, width
+ * R_STD); the e points at or above thresh_frac of the maximum give the mean and
+ * spread; the Sec. 4.1 cut sets RLF_FLAG_BAD.  Results go to *out.
+ */
+rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t first,
+                           int32_t count, const rlf_params *p, const rlf_fit_out *out,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * The whole chain, Sec. 2: circular sky model from the catalogue shapes in src
+ * (normally zero), then for each chunk of p->chunk sources in catalogue order:
+ * extract their facets from the current sky model, fit them, and replace their
+ * shapes in the sky model (update_mode).  chunk = 1 is the serial order;
+ * chunk = n_src extracts every facet from the initial model (Sec. 3.1).
+ * vis_sky (device, [n_rows][n_chan][2]) ends holding the final sky model; out
+ * holds n_src results.  The workspace must be rlf_workspace_size(..., RLF_WS_RUN).
+ */
+rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
+                   const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
+                   void *workspace, size_t ws_bytes, void *stream);
+
+/* Copy the workspace's device status word (RLF_DEV_* bits) to *status_out and clear it.
+ * Waits for `stream`.  Returns RLF_ETIMEOUT / RLF_ENUMERIC when those bits are set. */
+rlf_status rlf_read_status(void *workspace, int32_t *status_out, void *stream);
+
+/* Static text for a status code. */
+const char *rlf_strerror(rlf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLF_H */

@@ -1,0 +1,278 @@
+"""GB300 (sm_103a) RadioLensfit hot path: Python binding of librlf.so.
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of ``csrc/`` behind the C ABI declared in ``include/rlf.h``; PyTorch
+supplies device memory and streams.  Importing this package does not need a
+GPU, but calling a compute entry point does, and there is no CPU fallback: if
+``_build/librlf.so`` is missing the calls raise.
+
+Names follow the C ABI without the ``rlf_`` prefix:
+``sky_model``, ``sky_update``, ``extract_facets``, ``fit_sources``, ``run``,
+``workspace_size``, ``facets_size``, ``params_default``, ``read_status``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librlf.so")
+INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+HEADER = os.path.join(INCLUDE, "rlf.h")
+
+RLF_OK, RLF_EINVAL, RLF_ECUDA, RLF_ENOSPACE, RLF_ETIMEOUT, RLF_ENUMERIC, RLF_EUNSUPPORTED = range(7)
+PREC_FP64, PREC_MIXED = 0, 1
+FLAG_BAD, FLAG_INVALID, FLAG_EMPTY = 1, 2, 4
+DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
+WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
+MAX_CHAN, MAX_FACET_N = 128, 64
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class RlfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class Uvw(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_chan", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("u", _vp), ("v", _vp), ("w", _vp), ("freq_hz", _vp)]
+
+
+class Sources(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int32), ("reserved", ctypes.c_int32), ("l", _vp), ("m", _vp),
+                ("flux_jy", _vp), ("alpha_arcsec", _vp), ("e1", _vp), ("e2", _vp)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("add", ctypes.c_double), ("esp", ctypes.c_double), ("psf_nat", ctypes.c_double),
+                ("beta", ctypes.c_double), ("nu_ref_hz", ctypes.c_double), ("sigma_jy", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("r_min_arcsec", ctypes.c_double),
+                ("r_max_arcsec", ctypes.c_double), ("r_std", ctypes.c_double),
+                ("thresh_frac", ctypes.c_double), ("var_sigma_min", ctypes.c_double),
+                ("var_det_min", ctypes.c_double), ("facet_n", ctypes.c_int32), ("n_e", ctypes.c_int32),
+                ("n_alpha", ctypes.c_int32), ("flux_prior", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("update_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+                ("mufu_rsqrt_per_s", ctypes.c_double), ("mufu_sin_per_s", ctypes.c_double),
+                ("sm_count", ctypes.c_int)]
+
+
+class FitOut(ctypes.Structure):
+    _fields_ = [("e1", _vp), ("e2", _vp), ("sig1", _vp), ("sig2", _vp), ("alpha_arcsec", _vp),
+                ("flux_jy", _vp), ("e1_smooth", _vp), ("e2_smooth", _vp), ("flag", _vp)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load librlf.so (built by build_ext.build()); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run paper_2203_14071_gb300.build_ext.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            i32, i64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+            P = ctypes.POINTER
+            L.rlf_params_default.argtypes = [P(Params)]
+            L.rlf_params_default.restype = None
+            L.rlf_workspace_size.argtypes = [i64, i32, i32, P(Params), i32]
+            L.rlf_workspace_size.restype = sz
+            L.rlf_facets_size.argtypes = [i32, P(Params)]
+            L.rlf_facets_size.restype = sz
+            L.rlf_strerror.argtypes = [ctypes.c_int]
+            L.rlf_strerror.restype = ctypes.c_char_p
+            L.rlf_sky_model.argtypes = [P(Uvw), P(Sources), P(Params), _vp, _vp, sz, _vp]
+            L.rlf_sky_update.argtypes = [P(Uvw), P(Sources), i32, i32, _vp, _vp, _vp, P(Params), _vp, _vp,
+                                         sz, _vp]
+            L.rlf_extract_facets.argtypes = [P(Uvw), _vp, _vp, P(Sources), i32, i32, P(Params), _vp, sz,
+                                             _vp, sz, _vp]
+            L.rlf_fit_sources.argtypes = [_vp, P(Sources), i32, i32, P(Params), P(FitOut), _vp, sz, _vp]
+            L.rlf_run.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp]
+            L.rlf_read_status.argtypes = [_vp, P(ctypes.c_int32), _vp]
+            L.rlf_peaks_measure.argtypes = [_vp, sz, _vp, P(Peaks)]
+            L.rlf_peaks_measure.restype = ctypes.c_int
+            for f in ("rlf_sky_model", "rlf_sky_update", "rlf_extract_facets", "rlf_fit_sources", "rlf_run",
+                      "rlf_read_status"):
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions the headers in include/ declare."""
+    names = set()
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(rlf_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def strerror(code: int) -> str:
+    return lib().rlf_strerror(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != RLF_OK:
+        raise RlfError(code, where)
+
+
+def params_default(**overrides) -> Params:
+    p = Params()
+    lib().rlf_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def workspace_size(n_rows: int, n_chan: int, n_src: int, params: Params, which: int = WS_RUN) -> int:
+    return int(lib().rlf_workspace_size(n_rows, n_chan, n_src, ctypes.byref(params), which))
+
+
+def facets_size(count: int, params: Params) -> int:
+    return int(lib().rlf_facets_size(count, ctypes.byref(params)))
+
+
+# ---- marshalling helpers (torch tensors -> raw pointers) -------------------------------
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Observation:
+    """Device baselines plus the host channel table, as the C ABI wants them."""
+
+    def __init__(self, u, v, w, freq_hz):
+        self.u, self.v, self.w = u, v, w
+        self.freq_hz = np.ascontiguousarray(freq_hz, dtype=np.float64)
+        self.struct = Uvw(n_rows=int(u.shape[0]), n_chan=int(self.freq_hz.shape[0]), reserved=0,
+                          u=_ptr(u), v=_ptr(v), w=_ptr(w),
+                          freq_hz=self.freq_hz.ctypes.data_as(ctypes.c_void_p).value)
+
+    @property
+    def n_rows(self):
+        return self.struct.n_rows
+
+    @property
+    def n_chan(self):
+        return self.struct.n_chan
+
+
+class Catalogue:
+    """Device catalogue arrays (float64), sorted by decreasing flux."""
+
+    def __init__(self, l, m, flux_jy, e1, e2, alpha_arcsec=None):
+        self.l, self.m, self.flux_jy, self.e1, self.e2, self.alpha_arcsec = l, m, flux_jy, e1, e2, alpha_arcsec
+        self.struct = Sources(n_src=int(l.shape[0]), reserved=0, l=_ptr(l), m=_ptr(m), flux_jy=_ptr(flux_jy),
+                              alpha_arcsec=_ptr(alpha_arcsec), e1=_ptr(e1), e2=_ptr(e2))
+
+    @property
+    def n_src(self):
+        return self.struct.n_src
+
+
+class Results:
+    """Device result arrays for `count` sources."""
+
+    FIELDS = ("e1", "e2", "sig1", "sig2", "alpha_arcsec", "flux_jy", "e1_smooth", "e2_smooth")
+
+    def __init__(self, count: int, device):
+        import torch
+        for f in self.FIELDS:
+            setattr(self, f, torch.zeros(count, dtype=torch.float64, device=device))
+        self.flag = torch.zeros(count, dtype=torch.int32, device=device)
+        self.struct = FitOut(**{f: _ptr(getattr(self, f)) for f in self.FIELDS}, flag=_ptr(self.flag))
+
+    def numpy(self):
+        d = {f: getattr(self, f).cpu().numpy() for f in self.FIELDS}
+        d["flag"] = self.flag.cpu().numpy()
+        return d
+
+
+def sky_model(obs: Observation, cat: Catalogue, params: Params, vis_sky, workspace, stream=None):
+    _check(lib().rlf_sky_model(ctypes.byref(obs.struct), ctypes.byref(cat.struct), ctypes.byref(params),
+                               _ptr(vis_sky), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                               _stream(stream)), "rlf_sky_model")
+
+
+def sky_update(obs: Observation, cat: Catalogue, first: int, count: int, e1_new, e2_new, flag,
+               params: Params, vis_sky, workspace, stream=None):
+    _check(lib().rlf_sky_update(ctypes.byref(obs.struct), ctypes.byref(cat.struct), first, count,
+                                _ptr(e1_new), _ptr(e2_new), _ptr(flag), ctypes.byref(params), _ptr(vis_sky),
+                                _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                _stream(stream)), "rlf_sky_update")
+
+
+def extract_facets(obs: Observation, vis_data, vis_sky, cat: Catalogue, first: int, count: int,
+                   params: Params, facets, workspace, stream=None):
+    _check(lib().rlf_extract_facets(ctypes.byref(obs.struct), _ptr(vis_data), _ptr(vis_sky),
+                                    ctypes.byref(cat.struct), first, count, ctypes.byref(params), _ptr(facets),
+                                    facets.numel() * facets.element_size(), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream(stream)),
+           "rlf_extract_facets")
+
+
+def fit_sources(facets, cat: Catalogue, first: int, count: int, params: Params, out: Results, workspace,
+                stream=None):
+    _check(lib().rlf_fit_sources(_ptr(facets), ctypes.byref(cat.struct), first, count, ctypes.byref(params),
+                                 ctypes.byref(out.struct), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)),
+           "rlf_fit_sources")
+
+
+def run(obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results, vis_sky, workspace,
+        stream=None):
+    _check(lib().rlf_run(ctypes.byref(obs.struct), _ptr(vis_data), ctypes.byref(cat.struct),
+                         ctypes.byref(params), ctypes.byref(out.struct), _ptr(vis_sky), _ptr(workspace),
+                         workspace.numel() * workspace.element_size(), _stream(stream)), "rlf_run")
+
+
+def read_status(workspace, stream=None) -> tuple[int, int]:
+    v = ctypes.c_int32(0)
+    code = lib().rlf_read_status(_ptr(workspace), ctypes.byref(v), _stream(stream))
+    return code, int(v.value)
+
+
+def alloc_workspace(n_rows: int, n_chan: int, n_src: int, params: Params, which: int = WS_RUN, device="cuda"):
+    import torch
+    n = workspace_size(n_rows, n_chan, n_src, params, which)
+    if n == 0:
+        raise RlfError(RLF_EINVAL, "rlf_workspace_size")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def peaks_measure(stream=None) -> dict:
+    """Measured FP32/FP64 FMA and MUFU rsqrt/sin throughputs (per second) on the current GPU."""
+    import torch
+    out = Peaks()
+    scratch = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+    code = lib().rlf_peaks_measure(_ptr(scratch), scratch.numel(), _stream(stream), ctypes.byref(out))
+    if code != 0:
+        raise RuntimeError(f"rlf_peaks_measure failed ({code})")
+    return {f: getattr(out, f) for f, _ in Peaks._fields_}

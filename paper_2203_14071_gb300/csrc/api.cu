@@ -1,0 +1,337 @@
+// C ABI entry points (include/rlf.h): argument checks, the channel table,
+// workspace carve-up and the whole-chain driver.  Host code only; the work is
+// in sky.cu, extract.cu and fit.cu.
+#include <cmath>
+#include <cstring>
+
+#include "rlf_internal.cuh"
+
+namespace rlf {
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool params_ok(const rlf_params &p)
+{
+    if (!(p.facet_n >= 2 && p.facet_n <= RLF_MAX_FACET_N && p.facet_n % 2 == 0)) return false;
+    if (!(p.n_e >= 2 && p.n_e <= kMaxNe)) return false;
+    if (!(p.n_alpha >= 1 && p.n_alpha <= 64)) return false;
+    if (!(p.sigma_jy > 0 && std::isfinite(p.sigma_jy))) return false;
+    if (!(p.psf_nat > 0 && std::isfinite(p.psf_nat))) return false;
+    if (!(p.r_min_arcsec > 0 && p.r_max_arcsec >= p.r_min_arcsec && std::isfinite(p.r_max_arcsec))) return false;
+    if (!(p.r_std > 0 && std::isfinite(p.r_std))) return false;
+    if (!(p.thresh_frac > 0 && p.thresh_frac <= 1)) return false;
+    if (!(p.e_max > 0 && p.e_max <= 1)) return false;
+    if (!(p.nu_ref_hz > 0 && std::isfinite(p.nu_ref_hz))) return false;
+    if (!std::isfinite(p.beta) || !std::isfinite(p.add) || !std::isfinite(p.esp)) return false;
+    if (p.precision != RLF_PREC_FP64 && p.precision != RLF_PREC_MIXED) return false;
+    if (p.flux_prior != 0 && p.flux_prior != 1) return false;
+    if (p.update_mode != 0 && p.update_mode != 1) return false;
+    return true;
+}
+
+rlf_status check_uvw(const rlf_uvw *uvw)
+{
+    if (!uvw || !uvw->u || !uvw->v || !uvw->w || !uvw->freq_hz) return RLF_EINVAL;
+    if (uvw->n_rows <= 0 || uvw->n_chan <= 0) return RLF_EINVAL;
+    if (uvw->n_chan > RLF_MAX_CHAN) return RLF_EUNSUPPORTED;
+    for (int k = 0; k < uvw->n_chan; ++k) {
+        if (!(uvw->freq_hz[k] > 0 && std::isfinite(uvw->freq_hz[k]))) return RLF_EINVAL;
+        if (k > 0 && !(uvw->freq_hz[k] > uvw->freq_hz[k - 1])) return RLF_EINVAL;
+    }
+    return RLF_OK;
+}
+
+rlf_status check_src(const rlf_sources *src, int32_t first, int32_t count)
+{
+    if (!src || !src->l || !src->m || !src->flux_jy || !src->e1 || !src->e2) return RLF_EINVAL;
+    if (src->n_src <= 0 || first < 0 || count <= 0 || (int64_t)first + count > src->n_src) return RLF_EINVAL;
+    return RLF_OK;
+}
+
+ChanTable make_chan_table(const rlf_uvw &uvw, const rlf_params &p)
+{
+    ChanTable ch;
+    std::memset(&ch, 0, sizeof(ch));
+    ch.n = uvw.n_chan;
+    for (int k = 0; k < ch.n; ++k) {
+        ch.s[k] = uvw.freq_hz[k] / kC;
+        ch.spec[k] = std::pow(uvw.freq_hz[k] / p.nu_ref_hz, p.beta);
+    }
+    ch.s0 = ch.s[0];
+    ch.ds = ch.n > 1 ? (ch.s[ch.n - 1] - ch.s[0]) / (ch.n - 1) : 0.0;
+    ch.uniform = 1;
+    for (int k = 0; k < ch.n; ++k)
+        if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;
+    return ch;
+}
+
+rlf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RLF_OK : RLF_ECUDA; }
+
+int32_t fit_capacity(int32_t n_src, const rlf_params &p, int32_t which)
+{
+    if (which == RLF_WS_RUN) return (p.chunk > 0 && p.chunk < n_src) ? p.chunk : n_src;
+    return n_src;
+}
+
+}  // namespace
+
+size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params &p,
+                        int32_t which, void *base, Workspace *ws)
+{
+    (void)n_rows;
+    (void)n_chan;
+    const size_t NN = (size_t)p.facet_n * p.facet_n;
+    const size_t ng = (size_t)p.n_e * p.n_e * p.n_alpha;
+    const size_t cap = (size_t)fit_capacity(n_src, p, which);
+    const bool fit = which == RLF_WS_FIT || which == RLF_WS_RUN;
+    const bool run = which == RLF_WS_RUN;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t o_status = take(64 * sizeof(int32_t));
+    const size_t o_table = take((size_t)n_src * sizeof(SrcRow));
+    const size_t o_upd = take((which == RLF_WS_SKY || run) ? (size_t)n_src * sizeof(SrcRow) : 0);
+    const size_t o_cells = take(fit ? 5 * cap * NN * sizeof(double) : 0);
+    const size_t o_ncell = take(fit ? cap * sizeof(int32_t) : 0);
+    const size_t o_cc = take(fit ? cap * sizeof(double) : 0);
+    const size_t o_ga = take(fit ? cap * ng * sizeof(double) : 0);
+    const size_t o_gb = take(fit ? cap * ng * sizeof(double) : 0);
+    const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
+    const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
+    const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
+    const size_t total = off + 256;   // slack for aligning an arbitrary base pointer
+    if (ws && base) {
+        char *b = reinterpret_cast<char *>(align_up(reinterpret_cast<size_t>(base), 256));
+        ws->status = reinterpret_cast<int32_t *>(b + o_status);
+        ws->table = reinterpret_cast<SrcRow *>(b + o_table);
+        ws->upd = reinterpret_cast<SrcRow *>(b + o_upd);
+        ws->cells = b + o_cells;
+        ws->ncell = reinterpret_cast<int32_t *>(b + o_ncell);
+        ws->cc = reinterpret_cast<double *>(b + o_cc);
+        ws->ga = reinterpret_cast<double *>(b + o_ga);
+        ws->gb = reinterpret_cast<double *>(b + o_gb);
+        ws->gl = reinterpret_cast<double *>(b + o_gl);
+        ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
+        ws->facets = reinterpret_cast<double *>(b + o_fac);
+        ws->bytes = total;
+    }
+    return total;
+}
+
+}  // namespace rlf
+
+using namespace rlf;
+
+extern "C" {
+
+void rlf_params_default(rlf_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->add = -0.93;
+    p->esp = 0.33;
+    p->psf_nat = 38.0;
+    p->beta = -0.7;
+    p->nu_ref_hz = 1.4e9;
+    p->sigma_jy = 1e-6;
+    p->e_max = 0.8;
+    p->r_min_arcsec = 0.3;
+    p->r_max_arcsec = 3.5;
+    p->r_std = 0.3136;
+    p->thresh_frac = 0.05;
+    p->var_sigma_min = 5e-3;
+    p->var_det_min = 5e-5;
+    p->facet_n = 64;
+    p->n_e = 21;
+    p->n_alpha = 20;
+    p->flux_prior = 0;
+    p->chunk = 0;
+    p->update_mode = 0;
+    p->precision = RLF_PREC_MIXED;
+}
+
+size_t rlf_workspace_size(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params *p,
+                          int32_t which)
+{
+    if (!p || !params_ok(*p) || n_src <= 0 || which < RLF_WS_SKY || which > RLF_WS_RUN) return 0;
+    return workspace_layout(n_rows, n_chan, n_src, *p, which, nullptr, nullptr);
+}
+
+size_t rlf_facets_size(int32_t count, const rlf_params *p)
+{
+    if (!p || count <= 0 || !params_ok(*p)) return 0;
+    return (size_t)count * 4 * p->facet_n * p->facet_n * sizeof(double);
+}
+
+const char *rlf_strerror(rlf_status s)
+{
+    switch (s) {
+    case RLF_OK: return "ok";
+    case RLF_EINVAL: return "invalid argument";
+    case RLF_ECUDA: return "CUDA error";
+    case RLF_ENOSPACE: return "workspace or buffer too small";
+    case RLF_ETIMEOUT: return "bounded device wait timed out";
+    case RLF_ENUMERIC: return "non-finite likelihood";
+    case RLF_EUNSUPPORTED: return "request outside the implemented limits";
+    }
+    return "unknown status";
+}
+
+rlf_status rlf_sky_model(const rlf_uvw *uvw, const rlf_sources *src, const rlf_params *p,
+                         float *vis_sky, void *workspace, size_t ws_bytes, void *stream)
+{
+    rlf_status s = check_uvw(uvw);
+    if (s != RLF_OK) return s;
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    if ((s = check_src(src, 0, src ? src->n_src : 0)) != RLF_OK) return s;
+    if (!vis_sky || !workspace) return RLF_EINVAL;
+    Workspace ws;
+    if (workspace_layout(uvw->n_rows, uvw->n_chan, src->n_src, *p, RLF_WS_SKY, workspace, &ws) > ws_bytes)
+        return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ChanTable ch = make_chan_table(*uvw, *p);
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, 0, src->n_src, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
+                           nullptr, *p, ws.table, ws.status, st);
+    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, src->n_src, false, p->precision, vis_sky, st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_sky_update(const rlf_uvw *uvw, const rlf_sources *src, int32_t first,
+                          int32_t count, const double *e1_new, const double *e2_new,
+                          const int32_t *flag, const rlf_params *p, float *vis_sky,
+                          void *workspace, size_t ws_bytes, void *stream)
+{
+    rlf_status s = check_uvw(uvw);
+    if (s != RLF_OK) return s;
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    if ((s = check_src(src, first, count)) != RLF_OK) return s;
+    if (!vis_sky || !workspace || !e1_new || !e2_new) return RLF_EINVAL;
+    Workspace ws;
+    if (workspace_layout(uvw->n_rows, uvw->n_chan, src->n_src, *p, RLF_WS_SKY, workspace, &ws) > ws_bytes)
+        return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ChanTable ch = make_chan_table(*uvw, *p);
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, first, count, src->e1, src->e2, e1_new, e2_new, flag,
+                           flag ? p->update_mode : 1, nullptr, nullptr, *p, ws.upd, ws.status, st);
+    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.upd, count, true, p->precision, vis_sky, st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const float *vis_sky,
+                              const rlf_sources *src, int32_t first, int32_t count,
+                              const rlf_params *p, double *facets, size_t facets_bytes,
+                              void *workspace, size_t ws_bytes, void *stream)
+{
+    rlf_status s = check_uvw(uvw);
+    if (s != RLF_OK) return s;
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    if ((s = check_src(src, first, count)) != RLF_OK) return s;
+    if (!vis_data || !vis_sky || !facets || !workspace) return RLF_EINVAL;
+    if (facets_bytes < rlf_facets_size(count, p)) return RLF_ENOSPACE;
+    Workspace ws;
+    if (workspace_layout(uvw->n_rows, uvw->n_chan, src->n_src, *p, RLF_WS_EXTRACT, workspace, &ws) > ws_bytes)
+        return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ChanTable ch = make_chan_table(*uvw, *p);
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
+                           nullptr, *p, ws.table, ws.status, st);
+    if (e == cudaSuccess) e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, facets, st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t first,
+                           int32_t count, const rlf_params *p, const rlf_fit_out *out,
+                           void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    rlf_status s = check_src(src, first, count);
+    if (s != RLF_OK) return s;
+    if (!facets || !workspace || !out || !out->e1 || !out->e2 || !out->sig1 || !out->sig2 ||
+        !out->alpha_arcsec || !out->flux_jy || !out->e1_smooth || !out->e2_smooth || !out->flag)
+        return RLF_EINVAL;
+    Workspace ws;
+    if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
+                           nullptr, *p, ws.table, ws.status, st);
+    if (e == cudaSuccess) e = launch_fit(facets, ws.table, count, *p, ws, *out, 0, st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
+                   const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
+                   void *workspace, size_t ws_bytes, void *stream)
+{
+    rlf_status s = check_uvw(uvw);
+    if (s != RLF_OK) return s;
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    if ((s = check_src(src, 0, src ? src->n_src : 0)) != RLF_OK) return s;
+    if (!vis_data || !vis_sky || !workspace || !out || !out->e1 || !out->e2 || !out->sig1 ||
+        !out->sig2 || !out->alpha_arcsec || !out->flux_jy || !out->e1_smooth || !out->e2_smooth ||
+        !out->flag)
+        return RLF_EINVAL;
+    const int32_t n = src->n_src;
+    Workspace ws;
+    if (workspace_layout(uvw->n_rows, uvw->n_chan, n, *p, RLF_WS_RUN, workspace, &ws) > ws_bytes)
+        return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ChanTable ch = make_chan_table(*uvw, *p);
+    const int32_t chunk = fit_capacity(n, *p, RLF_WS_RUN);
+    double *e1c = ws.e_cur, *e2c = ws.e_cur + n;
+
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(e1c, src->e1, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(e2c, src->e2, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    // the sky model of the catalogue's current shapes (circular for a fresh catalogue)
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, *p,
+                           ws.table, ws.status, st);
+    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, n, false, p->precision, vis_sky, st);
+    for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
+        const int32_t cnt = first + chunk <= n ? chunk : n - first;
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.facets, st);
+        if (e != cudaSuccess) break;
+        e = launch_fit(ws.facets, ws.table + first, cnt, *p, ws, *out, first, st);
+        if (e != cudaSuccess) break;
+        // replace the chunk's shapes in the sky model (good fits, or all with update_mode 1)
+        e = launch_prepare(*src, first, cnt, e1c, e2c, out->e1 + first, out->e2 + first, out->flag + first,
+                           p->update_mode, e1c, e2c, *p, ws.upd, ws.status, st);
+        if (e != cudaSuccess) break;
+        e = launch_sky(*uvw, ch, ws.upd, cnt, true, p->precision, vis_sky, st);
+    }
+    return cuda_status(e);
+}
+
+rlf_status rlf_read_status(void *workspace, int32_t *status_out, void *stream)
+{
+    if (!workspace || !status_out) return RLF_EINVAL;
+    Workspace ws;
+    rlf_params p;
+    rlf_params_default(&p);
+    workspace_layout(0, 1, 1, p, RLF_WS_SKY, workspace, &ws);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return RLF_ECUDA;
+    *status_out = v;
+    if (v & RLF_DEV_TIMEOUT) return RLF_ETIMEOUT;
+    if (v & RLF_DEV_NONFINITE) return RLF_ENUMERIC;
+    return RLF_OK;
+}
+
+}  // extern "C"

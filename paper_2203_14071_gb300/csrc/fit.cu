@@ -1,0 +1,455 @@
+// Source fitting (Sec. 2.4): facet compaction, the likelihood grid over
+// (e1, e2, alpha) with the flux marginalised analytically, the numerical alpha
+// marginal and the thresholded estimate with the bad-fit cut of Sec. 4.1.
+//
+//   compact_kernel    one CTA per facet: the non-empty cells in increasing cell
+//                     order, as (uu, uv, vv) in units of du^2 (exact for the
+//                     half-integer cell centres), A = w s^2, B = w s Re D, and
+//                     C = sum w |D|^2 in FP64.
+//   grid_kernel       CTA = (facet, tile of (e point, alpha group)); cells are
+//                     staged through shared memory; each thread evaluates its
+//                     alpha nodes for every cell: one quadratic form per cell,
+//                     then per alpha one FMA, one rsqrt and the a, b products.
+//                     Mixed precision sums the products in FP32 over a tile of
+//                     cells and adds the tile sums to FP64 accumulators.
+//   estimate_kernel   one CTA per facet, FP64 throughout: logL, alpha marginal,
+//                     threshold, moments, MAP point, flags.
+#include <cfloat>
+#include <cmath>
+#include <type_traits>
+
+#include "rlf_internal.cuh"
+
+namespace rlf {
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ table, int32_t N,
+               double inv_sigma2, size_t plane, T *__restrict__ cells, int32_t *__restrict__ ncell,
+               double *__restrict__ cc_out)
+{
+    __shared__ int32_t warp_tot[kThreads / 32];
+    __shared__ double warp_cc[kThreads / 32];
+    const int s = blockIdx.x;
+    const int NN = N * N;
+    const double *f = facets + (size_t)s * 4 * NN;
+    const int per = (NN + kThreads - 1) / kThreads;
+    const int c0 = threadIdx.x * per;
+    int mine = 0;
+    double cc = 0.0;
+    for (int i = 0; i < per; ++i) {
+        const int c = c0 + i;
+        if (c < NN && f[2 * NN + c] > 0.0) {
+            ++mine;
+            const double n = f[2 * NN + c];
+            const double dr = f[c] / n, di = f[NN + c] / n;
+            cc += n * inv_sigma2 * (dr * dr + di * di);
+        }
+    }
+    // exclusive scan of the per-thread counts (warp shuffles, then the warp totals)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    double ccw = cc;
+    for (int o = 16; o > 0; o >>= 1) ccw += __shfl_down_sync(0xffffffffu, ccw, o);
+    if (lane == 31) warp_tot[wid] = incl;
+    if (lane == 0) warp_cc[wid] = ccw;
+    __syncthreads();
+    int base = 0;
+    for (int i = 0; i < wid; ++i) base += warp_tot[i];
+    int pos = base + incl - mine;
+    const double du = table[s].du;
+    (void)du;
+    T *uu = cells + (size_t)s * NN;
+    T *uv = uu + plane;
+    T *vv = uv + plane;
+    T *A = vv + plane;
+    T *B = A + plane;
+    for (int i = 0; i < per; ++i) {
+        const int c = c0 + i;
+        if (c < NN && f[2 * NN + c] > 0.0) {
+            const double n = f[2 * NN + c];
+            const double dr = f[c] / n;
+            const double sbar = f[3 * NN + c] / n;
+            const double wc = n * inv_sigma2;
+            const int iu = c % N, iv = c / N;
+            const double cu = iu - N / 2 + 0.5, cv = iv - N / 2 + 0.5;
+            uu[pos] = (T)(cu * cu);
+            uv[pos] = (T)(cu * cv);
+            vv[pos] = (T)(cv * cv);
+            A[pos] = (T)(wc * sbar * sbar);
+            B[pos] = (T)(wc * sbar * dr);
+            ++pos;
+        }
+    }
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        double ct = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            tot += warp_tot[i];
+            ct += warp_cc[i];
+        }
+        ncell[s] = tot;
+        cc_out[s] = ct;
+    }
+}
+
+__device__ __forceinline__ double grid_e(const GridConst &g, int k)
+{
+    return -g.e_max + k * (2.0 * g.e_max / (g.n_e - 1));
+}
+
+__device__ __forceinline__ double grid_alpha(const GridConst &g, int k)
+{
+    const double t = g.n_alpha > 1 ? (double)k / (g.n_alpha - 1) : 0.0;
+    return g.r_min + (g.r_max - g.r_min) * t * t;
+}
+
+template <typename T, int AG>
+__global__ void __launch_bounds__(kThreads)
+grid_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
+            const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
+            const GridConst gc, double *__restrict__ ga, double *__restrict__ gb)
+{
+    __shared__ T sm[5][kCellTile];
+    const int s = blockIdx.x / tiles_per_src;
+    const int tile = blockIdx.x % tiles_per_src;
+    const int pair = tile * kThreads + threadIdx.x;
+    const int ne2 = gc.n_e * gc.n_e;
+    const int e_idx = pair / gc.n_ag;
+    const int ag = pair % gc.n_ag;
+    const int i1 = e_idx / gc.n_e, i2 = e_idx % gc.n_e;
+    bool on = e_idx < ne2;
+    double e1 = 0.0, e2 = 0.0;
+    if (on) {
+        e1 = grid_e(gc, i1);
+        e2 = grid_e(gc, i2);
+        on = e1 * e1 + e2 * e2 < 1.0;
+    }
+    const double du = table[s].du;
+    T p11 = 0, p12 = 0, p22 = 0;
+    T calpha[AG];
+    int nk = 0;
+    if (on) {
+        const double det = 1.0 - e1 * e1 - e2 * e2;
+        const double id2 = 1.0 / (det * det);
+        p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+        p12 = (T)(4.0 * e2 * id2);
+        p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+    }
+#pragma unroll
+    for (int j = 0; j < AG; ++j) {
+        const int k = ag * AG + j;
+        if (k < gc.n_alpha) {
+            const double al = grid_alpha(gc, k) * kArcsec * du;
+            calpha[j] = (T)(4.0 * kPi * kPi * al * al);
+            nk = j + 1;
+        } else {
+            calpha[j] = T(0);
+        }
+    }
+    double da[AG], db[AG];
+#pragma unroll
+    for (int j = 0; j < AG; ++j) da[j] = db[j] = 0.0;
+
+    const int nc = ncell[s];
+    const T *cu = cells + (size_t)s * NN;
+    for (int c0 = 0; c0 < nc; c0 += kCellTile) {
+        const int nt = min(kCellTile, nc - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nt; j += kThreads) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
+        }
+        __syncthreads();
+        if (!on) continue;
+        T pa[AG], pb[AG];
+#pragma unroll
+        for (int j = 0; j < AG; ++j) pa[j] = pb[j] = T(0);
+        for (int c = 0; c < nt; ++c) {
+            const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+            const T A = sm[3][c], B = sm[4][c];
+#pragma unroll
+            for (int j = 0; j < AG; ++j) {
+                const T x = calpha[j] * Q + T(1);
+                T M;
+                if constexpr (std::is_same<T, float>::value) {
+                    const T r = rsqrtf(x);
+                    M = r * r * r;
+                } else {
+                    M = T(1) / (x * sqrt(x));
+                }
+                const T AM = A * M;
+                pa[j] += AM * M;
+                pb[j] += B * M;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < AG; ++j) {
+            da[j] += (double)pa[j];
+            db[j] += (double)pb[j];
+        }
+    }
+    if (e_idx < ne2) {
+        const size_t base = ((size_t)s * ne2 + e_idx) * gc.n_alpha + (size_t)ag * AG;
+        for (int j = 0; j < nk; ++j) {
+            ga[base + j] = on ? da[j] : 0.0;
+            gb[base + j] = on ? db[j] : 0.0;
+        }
+    }
+}
+
+// block reductions over kThreads threads (fixed tree order)
+__device__ double block_sum(double x, double *scratch)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) t += scratch[i];
+    return t;
+}
+
+__device__ double block_max(double x, double *scratch)
+{
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = x;
+    __syncthreads();
+    double t = -INFINITY;
+    for (int i = 0; i < kThreads / 32; ++i) t = fmax(t, scratch[i]);
+    return t;
+}
+
+// argmax with ties to the lowest index
+__device__ void block_argmax(double &v, long long &idx, double *sv, long long *si)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sv[wid] = v;
+        si[wid] = idx;
+    }
+    __syncthreads();
+    v = -INFINITY;
+    idx = 0x7fffffffffffffffLL;
+    for (int i = 0; i < kThreads / 32; ++i)
+        if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
+            v = sv[i];
+            idx = si[i];
+        }
+}
+
+// flux-marginalised log-likelihood (Sec. 2.4); for b < 0 the erfc factor is
+// written through erfcx so that b^2/(2a) cancels analytically
+__device__ double flux_marginal(double a, double b, double cc, int flux_prior)
+{
+    if (flux_prior == 1) return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(2.0 * kPi / a);
+    const double x = -b / sqrt(2.0 * a);
+    if (x > 0.0) return -0.5 * cc + 0.5 * log(kPi / (2.0 * a)) + log(erfcx(x));
+    return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(kPi / (2.0 * a)) + log(erfc(x));
+}
+
+__global__ void __launch_bounds__(kThreads)
+estimate_kernel(const double *__restrict__ ga, const double *__restrict__ gb, double *__restrict__ gl,
+                const int32_t *__restrict__ ncell, const double *__restrict__ ccv,
+                const SrcRow *__restrict__ table, const GridConst gc, rlf_fit_out out,
+                int32_t out_offset, int32_t *__restrict__ status)
+{
+    __shared__ double red[kThreads / 32];
+    __shared__ long long redi[kThreads / 32];
+    __shared__ double qp[64], alph[64], lnp[64];
+    __shared__ double Le[kMaxNe * kMaxNe], Ae[kMaxNe * kMaxNe];
+    const int s = blockIdx.x;
+    const int ne = gc.n_e, na = gc.n_alpha, ne2 = ne * ne;
+    const long long ng = (long long)ne2 * na;
+    const SrcRow S = table[s];
+    const int nc = ncell[s];
+    const double cc = ccv[s];
+    const double *a = ga + (size_t)s * ng;
+    const double *b = gb + (size_t)s * ng;
+    double *lg = gl + (size_t)s * ng;
+
+    if (threadIdx.x < na) {
+        const int k = threadIdx.x;
+        const double ak = grid_alpha(gc, k);
+        double q;
+        if (na == 1) q = 1.0;
+        else if (k == 0) q = 0.5 * (grid_alpha(gc, 1) - ak);
+        else if (k == na - 1) q = 0.5 * (ak - grid_alpha(gc, na - 2));
+        else q = 0.5 * (grid_alpha(gc, k + 1) - grid_alpha(gc, k - 1));
+        const double z = (log(ak) - S.mu) / gc.r_std;
+        qp[k] = q * exp(-0.5 * z * z) / (ak * gc.r_std * sqrt(2.0 * kPi));
+        alph[k] = ak;
+        lnp[k] = -0.5 * z * z - log(ak);
+    }
+    // logL on every valid point
+    double lmax = -INFINITY;
+    bool bad_num = false;
+    for (long long g = threadIdx.x; g < ng; g += kThreads) {
+        const int e_idx = (int)(g / na);
+        const double e1 = grid_e(gc, e_idx / ne), e2 = grid_e(gc, e_idx % ne);
+        double v = -INFINITY;
+        if (nc > 0 && e1 * e1 + e2 * e2 < 1.0) {
+            v = flux_marginal(a[g], b[g], cc, gc.flux_prior);
+            if (!isfinite(v)) bad_num = true;
+        }
+        lg[g] = v;
+        lmax = fmax(lmax, v);
+    }
+    if (bad_num) atomicOr(status, RLF_DEV_NONFINITE);
+    lmax = block_max(lmax, red);
+    __syncthreads();
+    // alpha marginal per e point
+    double Lm = 0.0;
+    for (int e = threadIdx.x; e < ne2; e += kThreads) {
+        double sL = 0.0, sA = 0.0;
+        for (int k = 0; k < na; ++k) {
+            const double v = lg[(size_t)e * na + k];
+            if (v == -INFINITY) continue;
+            const double t = qp[k] * exp(v - lmax);
+            sL += t;
+            sA += t * alph[k];
+        }
+        Le[e] = sL;
+        Ae[e] = sA;
+        Lm = fmax(Lm, sL);
+    }
+    const double Lmax = block_max(Lm, red);
+    __syncthreads();
+    // moments above the threshold and over every point
+    double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0;
+    for (int e = threadIdx.x; e < ne2; e += kThreads) {
+        const double L = Le[e];
+        if (!(L > 0.0)) continue;
+        const double e1 = grid_e(gc, e / ne), e2 = grid_e(gc, e % ne);
+        Ws += L;
+        s1 += L * e1;
+        s2 += L * e2;
+        if (L >= gc.thresh_frac * Lmax) {
+            W += L;
+            m1 += L * e1;
+            m2 += L * e2;
+            WA += Ae[e];
+        }
+    }
+    W = block_sum(W, red);
+    m1 = block_sum(m1, red);
+    m2 = block_sum(m2, red);
+    WA = block_sum(WA, red);
+    Ws = block_sum(Ws, red);
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    const double e1m = W > 0 ? m1 / W : 0.0, e2m = W > 0 ? m2 / W : 0.0;
+    double c11 = 0, c22 = 0, c12 = 0;
+    for (int e = threadIdx.x; e < ne2; e += kThreads) {
+        const double L = Le[e];
+        if (!(L > 0.0) || L < gc.thresh_frac * Lmax) continue;
+        const double d1 = grid_e(gc, e / ne) - e1m, d2 = grid_e(gc, e % ne) - e2m;
+        c11 += L * d1 * d1;
+        c22 += L * d2 * d2;
+        c12 += L * d1 * d2;
+    }
+    c11 = block_sum(c11, red);
+    c22 = block_sum(c22, red);
+    c12 = block_sum(c12, red);
+    // MAP grid point: logL + ln p(alpha), ties to the lowest flat index
+    double best = -INFINITY;
+    long long gbest = 0x7fffffffffffffffLL;
+    for (long long g = threadIdx.x; g < ng; g += kThreads) {
+        const double v = lg[g];
+        if (v == -INFINITY) continue;
+        const double lp = v + lnp[g % na];
+        if (lp > best || (lp == best && g < gbest)) {
+            best = lp;
+            gbest = g;
+        }
+    }
+    block_argmax(best, gbest, red, redi);
+    if (threadIdx.x == 0) {
+        if (W > 0) {
+            c11 /= W;
+            c22 /= W;
+            c12 /= W;
+        }
+        const double sd1 = sqrt(c11), sd2 = sqrt(c22);
+        const double det = c11 * c22 - c12 * c12;
+        const double sdet = det > 0 ? sqrt(det) : 0.0;
+        int flag = 0;
+        if (!(W > 0) || sd1 <= gc.var_sigma_min || sd2 <= gc.var_sigma_min || sdet <= gc.var_det_min)
+            flag |= RLF_FLAG_BAD;
+        if (S.invalid) flag |= RLF_FLAG_INVALID;
+        if (nc == 0) flag |= RLF_FLAG_EMPTY;
+        const int o = out_offset + s;
+        double fl = 0.0;
+        if (best > -INFINITY && a[gbest] > 0) fl = b[gbest] / a[gbest];
+        out.e1[o] = e1m;
+        out.e2[o] = e2m;
+        out.sig1[o] = sd1;
+        out.sig2[o] = sd2;
+        out.alpha_arcsec[o] = W > 0 ? WA / W : 0.0;
+        out.flux_jy[o] = fl;
+        out.e1_smooth[o] = Ws > 0 ? s1 / Ws : 0.0;
+        out.e2_smooth[o] = Ws > 0 ? s2 / Ws : 0.0;
+        out.flag[o] = flag;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
+                       const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
+                       int32_t out_offset, cudaStream_t st)
+{
+    const int N = p.facet_n, NN = N * N;
+    GridConst gc;
+    gc.n_e = p.n_e;
+    gc.n_alpha = p.n_alpha;
+    gc.n_ag = (p.n_alpha + kAlphaPerThread - 1) / kAlphaPerThread;
+    gc.flux_prior = p.flux_prior;
+    gc.e_max = p.e_max;
+    gc.r_min = p.r_min_arcsec;
+    gc.r_max = p.r_max_arcsec;
+    gc.r_std = p.r_std;
+    gc.inv_sigma2 = 1.0 / (p.sigma_jy * p.sigma_jy);
+    gc.thresh_frac = p.thresh_frac;
+    gc.var_sigma_min = p.var_sigma_min;
+    gc.var_det_min = p.var_det_min;
+    const size_t plane = (size_t)count * NN;
+    const int pairs = p.n_e * p.n_e * gc.n_ag;
+    const int tiles = (pairs + kThreads - 1) / kThreads;
+    if (p.precision == RLF_PREC_MIXED) {
+        float *cells = static_cast<float *>(ws.cells);
+        compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
+                                                          ws.ncell, ws.cc);
+        grid_kernel<float, kAlphaPerThread><<<count * tiles, kThreads, 0, st>>>(
+            cells, ws.ncell, table, plane, NN, tiles, gc, ws.ga, ws.gb);
+    } else {
+        double *cells = static_cast<double *>(ws.cells);
+        compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
+                                                           ws.ncell, ws.cc);
+        grid_kernel<double, kAlphaPerThread><<<count * tiles, kThreads, 0, st>>>(
+            cells, ws.ncell, table, plane, NN, tiles, gc, ws.ga, ws.gb);
+    }
+    estimate_kernel<<<count, kThreads, 0, st>>>(ws.ga, ws.gb, ws.gl, ws.ncell, ws.cc, table, gc, out,
+                                                out_offset, ws.status);
+    return cudaGetLastError();
+}
+
+}  // namespace rlf

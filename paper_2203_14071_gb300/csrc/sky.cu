@@ -1,0 +1,349 @@
+// Per-source constants and the sky model (Sec. 2.2, Eq. 1, Eq. 2, Eq. 4).
+//
+// Sky model layout: one thread owns one (row, channel group) output and walks
+// the catalogue, which every CTA stages through shared memory in tiles; rows
+// are visited with a grid-stride loop so the staging is amortised over many
+// rows.  Mixed precision keeps the phase argument u l + v m + w (n - 1) and its
+// range reduction in FP64 once per (row, source) and steps it across the
+// channels of the group by an FP32 complex rotation; the brightness factor
+// (1 + x)^{-3/2} is one MUFU rsqrt and two multiplies per term.
+#include <cmath>
+
+#include "rlf_internal.cuh"
+
+namespace rlf {
+
+namespace {
+
+struct PrepConst {
+    double add, esp, psf_nat;
+    int32_t update, update_mode;
+};
+
+__device__ inline void shape_coeffs(double e1, double e2, double alpha_rad, double q[3])
+{
+    // |A^{-T} k|^2 for A = [[1 - e1, -e2], [-e2, 1 + e1]] (Eq. 2):
+    // ((1 + e1)^2 + e2^2) u^2 + 4 e2 u v + ((1 - e1)^2 + e2^2) v^2, over det(A)^2
+    const double det = 1.0 - e1 * e1 - e2 * e2;
+    const double c = 4.0 * kPi * kPi * alpha_rad * alpha_rad / (det * det);
+    q[0] = c * ((1.0 + e1) * (1.0 + e1) + e2 * e2);
+    q[1] = c * 4.0 * e2;
+    q[2] = c * ((1.0 - e1) * (1.0 - e1) + e2 * e2);
+}
+
+__global__ void prepare_kernel(rlf_sources src, int32_t first, int32_t count,
+                               const double *__restrict__ e1, const double *__restrict__ e2,
+                               const double *__restrict__ e1n, const double *__restrict__ e2n,
+                               const int32_t *__restrict__ flag, double *__restrict__ e1c,
+                               double *__restrict__ e2c, PrepConst pc,
+                               SrcRow *__restrict__ out, int32_t *__restrict__ status)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int i = first + t;
+    const double l = src.l[i], m = src.m[i], S = src.flux_jy[i];
+    const double acat = src.alpha_arcsec ? src.alpha_arcsec[i] : 0.0;
+    const double a1 = e1[i], a2 = e2[i];
+    bool ok = isfinite(l) && isfinite(m) && (l * l + m * m < 1.0) && isfinite(S) && S > 0.0 &&
+              isfinite(a1) && isfinite(a2) && (a1 * a1 + a2 * a2 < 1.0) && isfinite(acat);
+    double b1 = 0.0, b2 = 0.0;
+    bool selected = true;
+    if (pc.update) {
+        b1 = e1n[t];
+        b2 = e2n[t];
+        ok = ok && isfinite(b1) && isfinite(b2) && (b1 * b1 + b2 * b2 < 1.0);
+        if (pc.update_mode == 0 && flag) selected = (flag[t] & (RLF_FLAG_BAD | RLF_FLAG_INVALID | RLF_FLAG_EMPTY)) == 0;
+    }
+    SrcRow row;
+    const double lnS = log(S * 1.0e6);
+    // Eq. 4 median scalelength unless the catalogue gives one (Sec. 2.3)
+    const double alpha_as = acat > 0.0 ? acat : exp(pc.add + pc.esp * lnS);
+    row.l = l;
+    row.m = m;
+    const double r2 = l * l + m * m;
+    row.n1 = -r2 / (1.0 + sqrt(1.0 - r2));
+    row.alpha_rad = alpha_as * kArcsec;
+    row.du = 1.0 / (pc.psf_nat * alpha_as * kArcsec);
+    row.mu = pc.add + pc.esp * lnS;
+    row.flux = (ok && selected) ? S : 0.0;
+    row.invalid = ok ? 0 : 1;
+    row.pad = 0;
+    if (ok) {
+        shape_coeffs(a1, a2, row.alpha_rad, row.q);
+        if (pc.update) shape_coeffs(b1, b2, row.alpha_rad, row.qn);
+        else row.qn[0] = row.qn[1] = row.qn[2] = 0.0;
+    } else {
+        row.q[0] = row.q[1] = row.q[2] = 0.0;
+        row.qn[0] = row.qn[1] = row.qn[2] = 0.0;
+        atomicOr(status, RLF_DEV_INVALID_SOURCE);
+    }
+    out[t] = row;
+    // the shapes now in the sky model (the whole-chain driver keeps them)
+    if (pc.update && e1c && ok && selected) {
+        e1c[i] = b1;
+        e2c[i] = b2;
+    }
+}
+
+struct SkySrc {
+    double l, m, n1;
+    float flux, q0, q1, q2, qn0, qn1, qn2, pad;
+};
+
+// Mixed precision sky model / update.  CG channels per thread.
+template <int CG, bool kUpdate, bool kUniform>
+__global__ void __launch_bounds__(kThreads)
+sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
+                 const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
+                 const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis)
+{
+    __shared__ SkySrc sm[kSkyTile];
+    const int C = ch.n;
+    const int n_groups = (C + CG - 1) / CG;
+    const int lanes = kThreads / n_groups;
+    const int g = threadIdx.x % n_groups;
+    const int lane = threadIdx.x / n_groups;
+    const bool thread_on = lane < lanes;
+    const int k0 = g * CG;
+
+    float f2[CG], spec[CG];
+    double sk[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+        const int k = k0 + c;
+        const double s = k < C ? ch.s[k] : 0.0;
+        sk[c] = s;
+        f2[c] = (float)(s * s);
+        spec[c] = k < C ? (float)ch.spec[k] : 0.0f;
+    }
+    const double s_k0 = sk[0];
+    const double ds = ch.ds;
+    constexpr float kTwoPi = 6.28318530717958647692f;
+
+    for (int64_t rb = (int64_t)blockIdx.x * lanes; rb < n_rows; rb += (int64_t)gridDim.x * lanes) {
+        const int64_t r = rb + lane;
+        const bool act = thread_on && r < n_rows;
+        double ud = 0.0, vd = 0.0, wd = 0.0;
+        if (act) {
+            ud = u[r];
+            vd = v[r];
+            wd = w[r];
+        }
+        const float uu = (float)(ud * ud), uv = (float)(ud * vd), vv = (float)(vd * vd);
+        float are[CG], aim[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) are[c] = aim[c] = 0.0f;
+
+        for (int t0 = 0; t0 < n_src; t0 += kSkyTile) {
+            const int nt = min(kSkyTile, n_src - t0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < nt; j += kThreads) {
+                const SrcRow &R = table[t0 + j];
+                SkySrc s;
+                s.l = R.l;
+                s.m = R.m;
+                s.n1 = R.n1;
+                s.flux = (float)R.flux;
+                s.q0 = (float)R.q[0];
+                s.q1 = (float)R.q[1];
+                s.q2 = (float)R.q[2];
+                s.qn0 = (float)R.qn[0];
+                s.qn1 = (float)R.qn[1];
+                s.qn2 = (float)R.qn[2];
+                s.pad = 0.0f;
+                sm[j] = s;
+            }
+            __syncthreads();
+            if (!act) continue;
+            for (int j = 0; j < nt; ++j) {
+                const SkySrc &S = sm[j];
+                if (S.flux == 0.0f) continue;
+                // phase argument in metres and its reduction to [-1/2, 1/2] cycles, FP64
+                const double ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
+                const float q = fmaf(S.q2, vv, fmaf(S.q1, uv, S.q0 * uu));
+                float qn = 0.0f;
+                if (kUpdate) qn = fmaf(S.qn2, vv, fmaf(S.qn1, uv, S.qn0 * uu));
+                float sn, cs, sd = 0.0f, cd = 1.0f;
+                if (kUniform) {
+                    const double t = ph * s_k0;
+                    __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
+                    if (CG > 1) {
+                        const double td = ph * ds;
+                        __sincosf((float)(td - rint(td)) * kTwoPi, &sd, &cd);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    if (!kUniform) {
+                        const double t = ph * sk[c];
+                        __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
+                    }
+                    const float x = fmaf(q, f2[c], 1.0f);
+                    const float rr = rsqrtf(x);
+                    float M = rr * rr * rr;
+                    if (kUpdate) {
+                        const float xn = fmaf(qn, f2[c], 1.0f);
+                        const float rn = rsqrtf(xn);
+                        M = rn * rn * rn - M;
+                    }
+                    const float a = S.flux * M;
+                    are[c] = fmaf(a, cs, are[c]);
+                    aim[c] = fmaf(a, sn, aim[c]);
+                    if (kUniform && c + 1 < CG) {
+                        const float cn = cs * cd - sn * sd;
+                        sn = fmaf(cs, sd, sn * cd);
+                        cs = cn;
+                    }
+                }
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < CG; ++c) {
+                const int k = k0 + c;
+                if (k < C) {
+                    float2 o = make_float2(are[c] * spec[c], aim[c] * spec[c]);
+                    if (kUpdate) {
+                        const float2 p = vis[r * C + k];
+                        o.x += p.x;
+                        o.y += p.y;
+                    }
+                    vis[r * C + k] = o;
+                }
+            }
+        }
+    }
+}
+
+// FP64 sky model / update: every operation in double precision.
+template <bool kUpdate>
+__global__ void __launch_bounds__(kThreads)
+sky_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
+                const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
+                const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis)
+{
+    __shared__ SrcRow sm[kSkyTile / 2];
+    constexpr int kTile = kSkyTile / 2;
+    const int C = ch.n;
+    const int64_t n_out = n_rows * C;
+    for (int64_t ob = (int64_t)blockIdx.x * kThreads; ob < n_out; ob += (int64_t)gridDim.x * kThreads) {
+        const int64_t o = ob + threadIdx.x;
+        const bool act = o < n_out;
+        const int64_t r = act ? o / C : 0;
+        const int k = act ? (int)(o % C) : 0;
+        const double ud = act ? u[r] : 0.0, vd = act ? v[r] : 0.0, wd = act ? w[r] : 0.0;
+        const double s = ch.s[k];
+        const double f2 = s * s;
+        double are = 0.0, aim = 0.0;
+        for (int t0 = 0; t0 < n_src; t0 += kTile) {
+            const int nt = min(kTile, n_src - t0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < nt; j += kThreads) sm[j] = table[t0 + j];
+            __syncthreads();
+            if (!act) continue;
+            for (int j = 0; j < nt; ++j) {
+                const SrcRow &S = sm[j];
+                if (S.flux == 0.0) continue;
+                const double t = fma(wd, S.n1, fma(vd, S.m, ud * S.l)) * s;
+                double sn, cs;
+                sincospi(2.0 * (t - rint(t)), &sn, &cs);
+                const double q = (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * f2;
+                const double x = 1.0 + q;
+                double M = 1.0 / (x * sqrt(x));
+                if (kUpdate) {
+                    const double xn = 1.0 + (S.qn[0] * ud * ud + S.qn[1] * ud * vd + S.qn[2] * vd * vd) * f2;
+                    M = 1.0 / (xn * sqrt(xn)) - M;
+                }
+                are += S.flux * M * cs;
+                aim += S.flux * M * sn;
+            }
+        }
+        if (act) {
+            const double sp = ch.spec[k];
+            float2 out = make_float2((float)(are * sp), (float)(aim * sp));
+            if (kUpdate) {
+                const float2 p = vis[o];
+                out.x = (float)((double)p.x + are * sp);
+                out.y = (float)((double)p.y + aim * sp);
+            }
+            vis[o] = out;
+        }
+    }
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+template <int CG, bool kUpdate>
+void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
+                  float *vis, cudaStream_t st)
+{
+    const int n_groups = (ch.n + CG - 1) / CG;
+    const int lanes = kThreads / n_groups;
+    const int64_t blocks_needed = (uvw.n_rows + lanes - 1) / lanes;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
+    if (ch.uniform)
+        sky_mixed_kernel<CG, kUpdate, true><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
+    else
+        sky_mixed_kernel<CG, kUpdate, false><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
+}
+
+template <bool kUpdate>
+void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table,
+                     int32_t n_src, float *vis, cudaStream_t st)
+{
+    if (ch.n == 1) launch_mixed<1, kUpdate>(uvw, ch, table, n_src, vis, st);
+    else if (ch.n == 2) launch_mixed<2, kUpdate>(uvw, ch, table, n_src, vis, st);
+    else if (ch.n <= 4) launch_mixed<4, kUpdate>(uvw, ch, table, n_src, vis, st);
+    else launch_mixed<8, kUpdate>(uvw, ch, table, n_src, vis, st);
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
+                           const double *e1, const double *e2, const double *e1n,
+                           const double *e2n, const int32_t *flag, int32_t update_mode,
+                           double *e1_commit, double *e2_commit,
+                           const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st)
+{
+    PrepConst pc{p.add, p.esp, p.psf_nat, e1n != nullptr, update_mode};
+    const int grid = (count + kThreads - 1) / kThreads;
+    prepare_kernel<<<grid, kThreads, 0, st>>>(src, first, count, e1, e2, e1n, e2n, flag, e1_commit,
+                                              e2_commit, pc, out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
+                       bool update, int32_t precision, float *vis, cudaStream_t st)
+{
+    if (precision == RLF_PREC_MIXED) {
+        if (update) launch_mixed_cg<true>(uvw, ch, table, n_src, vis, st);
+        else launch_mixed_cg<false>(uvw, ch, table, n_src, vis, st);
+    } else {
+        const int64_t n_out = uvw.n_rows * ch.n;
+        const int64_t need = (n_out + kThreads - 1) / kThreads;
+        const int64_t cap = (int64_t)sm_count() * 8;
+        const int grid = (int)(need < cap ? need : cap);
+        if (update)
+            sky_fp64_kernel<true><<<grid, kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table,
+                                                             n_src, reinterpret_cast<float2 *>(vis));
+        else
+            sky_fp64_kernel<false><<<grid, kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table,
+                                                              n_src, reinterpret_cast<float2 *>(vis));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rlf

@@ -1,0 +1,311 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small workloads are compared element by element; the 37M-visibility, 200-source
+workload is run in full on the GPU, in the launch configuration the benchmark
+times, and compared on sampled rows and sources that the oracle computes one by
+one.  Tolerances:
+  visibilities  per value |dV| <= 1e-5 sum_j |term_j| and normwise 1e-5 (mixed),
+                1e-10 (FP64 path)
+  facets        counts exact; sums within 3e-5 sum |x| (mixed), 1e-9 (FP64)
+  fits          |de1|, |de2| <= 1e-4
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+PRECS = {"mixed": 1, "fp64": 0}
+VIS_TOL = {"mixed": 1e-5, "fp64": 1e-10}
+FACET_TOL = {"mixed": 3e-5, "fp64": 1e-9}
+
+
+@pytest.fixture(scope="module")
+def rlf():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2203_14071_gb300 as m
+    from paper_2203_14071_gb300 import build_ext
+    build_ext.build()
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def small():
+    return small_case(True)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _sky_gpu(rlf, case, prec, e1, e2, alpha=None, vis_out=None):
+    torch = _torch()
+    obs, cat = cases.to_device(case, e1, e2, alpha)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=case.wl.nu_ref_hz)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_SKY)
+    vis = vis_out if vis_out is not None else torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32,
+                                                           device="cuda")
+    rlf.sky_model(obs, cat, p, vis, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK and status == 0
+    return vis.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+
+
+def _check_vis(got, ref, ab, tol):
+    g = got[..., 0] + 1j * got[..., 1]
+    err = np.abs(g - ref)
+    assert np.all(err <= tol * ab + 1e-30), float(np.max(err / (ab + 1e-300)))
+    assert np.linalg.norm(g - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_sky_model_small_full(rlf, small, prec):
+    c = small
+    al = c.cat.alpha_arcsec
+    got = _sky_gpu(rlf, c, prec, c.cat.e1, c.cat.e2, alpha=al)
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                               al * cases.ARC, c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz, with_abs=True)
+    _check_vis(got, ref, ab, VIS_TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("n_chan,uniform", [(1, True), (2, True), (3, True), (8, True), (13, True), (5, False)])
+def test_sky_model_channels_and_tiles(rlf, prec, n_chan, uniform):
+    # 300 sources: three shared-memory tiles with a ragged last one; channel groups with ragged tails
+    wl = synth.tiny(seed=30 + n_chan, n_ant=20, n_time=13, n_chan=n_chan, n_src=300, r_max_m=20000.0)
+    c = cases.build(wl, with_data=False)
+    if not uniform:
+        c.obs.freq_hz = c.obs.freq_hz * (1 + 0.01 * np.arange(n_chan) ** 2 / n_chan ** 2)
+    got = _sky_gpu(rlf, c, prec, c.cat.e1, c.cat.e2)
+    al = c.alpha_med_rad()
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy, al,
+                               c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz, with_abs=True)
+    _check_vis(got, ref, ab, VIS_TOL[prec])
+
+
+def test_sky_update_equals_model_of_new_shapes(rlf):
+    torch = _torch()
+    wl = synth.tiny(seed=41, n_ant=16, n_time=11, n_chan=4, n_src=37, r_max_m=8000.0)
+    c = cases.build(wl, with_data=False)
+    obs, cat = cases.to_device(c)  # circular shapes
+    p = rlf.params_default(nu_ref_hz=wl.nu_ref_hz)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_SKY)
+    vis = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.sky_model(obs, cat, p, vis, ws)
+    first, count = 5, 20
+    e1n = torch.from_numpy(c.cat.e1[first:first + count].copy()).cuda()
+    e2n = torch.from_numpy(c.cat.e2[first:first + count].copy()).cuda()
+    flag = torch.zeros(count, dtype=torch.int32, device="cuda")
+    flag[3] = rlf.FLAG_BAD    # a bad fit stays circular in the paper's update rule
+    rlf.sky_update(obs, cat, first, count, e1n, e2n, flag, p, vis, ws)
+    got = vis.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    e1 = np.zeros(c.cat.n_src)
+    e2 = np.zeros(c.cat.n_src)
+    sel = np.arange(first, first + count) != first + 3
+    e1[first:first + count][sel] = c.cat.e1[first:first + count][sel]
+    e2[first:first + count][sel] = c.cat.e2[first:first + count][sel]
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                               c.alpha_med_rad(), e1, e2, nu_ref=wl.nu_ref_hz, with_abs=True)
+    _check_vis(got, ref, ab, 2e-5)
+
+
+def _extract_gpu(rlf, case, prec, e1, e2, data, sky, first=0, count=None, facet_n=64):
+    torch = _torch()
+    count = case.cat.n_src - first if count is None else count
+    obs, cat = cases.to_device(case, e1, e2)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=case.wl.nu_ref_hz, facet_n=facet_n)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_EXTRACT)
+    fac = torch.empty(rlf.facets_size(count, p) // 8, dtype=torch.float64, device="cuda")
+    rlf.extract_facets(obs, cases.vis_tensor(data), cases.vis_tensor(sky), cat, first, count, p, fac, ws)
+    torch.cuda.synchronize()
+    return fac.view(count, 4, facet_n * facet_n).cpu().numpy()
+
+
+def _check_facet(got, ref, ab, tol):
+    assert np.array_equal(got[2], ref[2]), np.argwhere(got[2] != ref[2])[:5]
+    assert np.all(np.abs(got[0] - ref[0]) <= tol * ab + 1e-300)
+    assert np.all(np.abs(got[1] - ref[1]) <= tol * ab + 1e-300)
+    assert np.all(np.abs(got[3] - ref[3]) <= 1e-5 * ref[3] + 1e-300)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_extract_small_full(rlf, small, prec):
+    c = small
+    e1 = c.cat.e1 * 0.5   # shapes currently in the sky model (non-zero: the added-back model uses them)
+    e2 = c.cat.e2 * 0.5
+    al = c.alpha_med_rad()
+    sky = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy, al, e1, e2,
+                           nu_ref=c.wl.nu_ref_hz)
+    sky2 = np.stack([sky.real, sky.imag], -1).astype(np.float32)
+    got = _extract_gpu(rlf, c, prec, e1, e2, c.data, sky2)
+    p = c.oracle_params()
+    for i in range(c.cat.n_src):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p)
+        ref, ab = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, sky2, c.cat.l[i], c.cat.m[i],
+                                       c.cat.flux_jy[i], al[i], e1[i], e2[i], du, p, with_abs=True)
+        assert ref[2].sum() > 1000
+        _check_facet(got[i], ref, ab, FACET_TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_extract_multichannel_ragged(rlf, prec):
+    wl = synth.tiny(seed=52, n_ant=24, n_time=17, n_chan=11, n_src=6, r_max_m=6000.0)
+    c = cases.build(wl, snr10=True)
+    got = _extract_gpu(rlf, c, prec, None, None, c.data, c.sky0, first=2, count=3, facet_n=16)
+    p = c.oracle_params(facet_n=16)
+    al = c.alpha_med_rad()
+    for t in range(3):
+        i = 2 + t
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p)
+        ref, ab = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i],
+                                       c.cat.m[i], c.cat.flux_jy[i], al[i], 0.0, 0.0, du, p, with_abs=True)
+        assert ref[2].sum() > 100
+        _check_facet(got[t], ref, ab, FACET_TOL[prec])
+
+
+def _fit_gpu(rlf, case, prec, facets_np, first=0, **pk):
+    torch = _torch()
+    count = facets_np.shape[0]
+    obs, cat = cases.to_device(case)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=case.wl.nu_ref_hz, sigma_jy=case.sigma, **pk)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+    out = rlf.Results(count, "cuda")
+    fac = torch.from_numpy(np.ascontiguousarray(facets_np)).cuda()
+    rlf.fit_sources(fac, cat, first, count, p, out, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    return out.numpy()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("snr10", [True, False])
+def test_fit_small_from_oracle_facets(rlf, prec, snr10):
+    c = small_case(snr10)
+    p = c.oracle_params()
+    al = c.alpha_med_rad()
+    facets, ests = [], []
+    for i in range(c.cat.n_src):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p)
+        acc = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i], c.cat.m[i],
+                                   c.cat.flux_jy[i], al[i], 0.0, 0.0, du, p)
+        facets.append(acc)
+        ests.append(oracle.fit_facet(acc, du, c.cat.flux_jy[i], p).est)
+    got = _fit_gpu(rlf, c, prec, np.stack(facets))
+    for i, est in enumerate(ests):
+        assert cases.est_matches(got, i, est) <= 1e-4, (i, got["e1"][i], est[oracle.E1])
+        assert got["flag"][i] & 1 == int(est[oracle.FLAG])
+        if est[oracle.THRESH_MARGIN] > 1e-3:
+            assert abs(got["sig1"][i] - est[oracle.SIG1]) <= 1e-4 + 1e-3 * est[oracle.SIG1]
+            assert abs(got["alpha_arcsec"][i] - est[oracle.ALPHA]) <= 1e-3
+        assert abs(got["flux_jy"][i] - est[oracle.FLUX]) <= 1e-4 * abs(est[oracle.FLUX])
+
+
+_SMALL = {}
+
+
+def small_case(snr10: bool):
+    if snr10 not in _SMALL:
+        _SMALL[snr10] = cases.build(synth.workload("small"), snr10=snr10)
+    return _SMALL[snr10]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("chunk,update_mode", [(1, 1), (0, 1), (3, 0)])
+def test_run_small_pipeline(rlf, prec, chunk, update_mode):
+    torch = _torch()
+    c = small_case(True)
+    p_or = c.oracle_params(chunk=chunk, update_mode=update_mode)
+    est = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m, c.cat.flux_jy,
+                          None, p_or)
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, chunk=chunk,
+                           update_mode=update_mode)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.run(obs, cases.vis_tensor(c.data), cat, p, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    got = out.numpy()
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(got, i, est[i]) <= 1e-4, (i, got["e1"][i], est[i, oracle.E1], got["e2"][i],
+                                                           est[i, oracle.E2])
+
+
+def test_invalid_and_empty_sources_are_flagged(rlf):
+    torch = _torch()
+    wl = synth.tiny(seed=61, n_ant=12, n_time=9, n_chan=2, n_src=4, r_max_m=3000.0)
+    c = cases.build(wl, snr10=True)
+    obs, cat = cases.to_device(c)
+    cat.flux_jy[1] = -1.0                 # invalid flux
+    cat.e1[2] = 0.9
+    cat.e2[2] = 0.6                       # |e| >= 1
+    # K = 1e6 makes the cells ~0.1 wavelength wide: no baseline falls in the facet window
+    p = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=c.sigma, facet_n=8, psf_nat=1.0e6)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.run(obs, cases.vis_tensor(c.data), cat, p, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert status & rlf.DEV_INVALID_SOURCE
+    f = out.numpy()["flag"]
+    assert f[1] & rlf.FLAG_INVALID and f[2] & rlf.FLAG_INVALID
+    for i in (0, 3):
+        assert not (f[i] & rlf.FLAG_INVALID) and f[i] & rlf.FLAG_EMPTY
+
+
+# ---- full-size workload (37M visibilities, 200 sources), sampled ----------------------------
+
+@pytest.fixture(scope="module")
+def mid():
+    wl = synth.workload("mid")
+    return cases.build(wl, with_data=False)
+
+
+def test_sky_model_mid_sampled(rlf, mid):
+    c = mid
+    got = _sky_gpu(rlf, c, "mixed", c.cat.e1, c.cat.e2)
+    rng = np.random.default_rng(123)
+    rows = np.sort(rng.choice(c.obs.n_rows, 1500, replace=False))
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                               c.alpha_med_rad(), c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz, rows=rows,
+                               with_abs=True, n_threads=0)
+    _check_vis(got[rows], ref, ab, 1e-5)
+
+
+def test_extract_and_fit_mid_sampled(rlf, mid):
+    # data = an arbitrary sky array plus noise; the sources' current shapes are non-zero, so
+    # every facet holds that source's model plus noise and the fit has a known answer
+    torch = _torch()
+    c = mid
+    R, C = c.obs.n_rows, c.obs.n_chan
+    rng = np.random.default_rng(7)
+    sky = (rng.standard_normal((R, C, 2), dtype=np.float32) * np.float32(1e-4))
+    sigma = 3e-3
+    data = sky + synth.noise(R, C, sigma, 99)
+    e1, e2 = c.cat.e1, c.cat.e2
+    got_f = _extract_gpu(rlf, c, "mixed", e1, e2, data, sky)
+    # fit the GPU facets on the GPU
+    obs, cat = cases.to_device(c, e1, e2)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=sigma)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+    out = rlf.Results(cat.n_src, "cuda")
+    rlf.fit_sources(torch.from_numpy(got_f).cuda(), cat, 0, cat.n_src, p, out, ws)
+    res = out.numpy()
+    po = c.oracle_params(sigma_jy=sigma)
+    al = c.alpha_med_rad()
+    for i in (0, 117, c.cat.n_src - 1):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, po)
+        ref, ab = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, data, sky, c.cat.l[i], c.cat.m[i],
+                                       c.cat.flux_jy[i], al[i], e1[i], e2[i], du, po, with_abs=True)
+        _check_facet(got_f[i], ref, ab, FACET_TOL["mixed"])
+        est = oracle.fit_facet(ref, du, c.cat.flux_jy[i], po).est
+        assert cases.est_matches(res, i, est) <= 1e-4, (i, res["e1"][i], est[oracle.E1])
