@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--chunk", type=int, default=0, help="sources per extract/fit/update step (0: all)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="split", choices=["split", "mixed", "fp64"])
     ap.add_argument("--update-mode", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,9 +216,9 @@ def main():
     cat_np = synth.make_catalogue(wl)
     n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
     n_vis = R * C
-    prec = rlf.PREC_MIXED if args.precision == "mixed" else rlf.PREC_FP64
+    prec = {"split": rlf.PREC_MIXED_SPLIT, "mixed": rlf.PREC_MIXED, "fp64": rlf.PREC_FP64}[args.precision]
     t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
-    obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz)
+    obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz, obs_np.n_bl)
     zeros = torch.zeros(n_src, dtype=torch.float64, device=dev)
     cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
     truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
@@ -281,7 +281,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if prec == rlf.PREC_MIXED else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {0: "f64", 1: "f32+f64", 2: "f32 (phase as f32 pairs)"}[prec], "data": "synthetic",
         "config": {"workload": args.workload, "n_ant": obs_np.n_ant, "n_baselines": obs_np.n_bl,
                    "n_time": obs_np.n_time, "n_chan": C, "n_vis": n_vis, "n_src": n_src,
                    "facet_n": params.facet_n, "grid": [params.n_e, params.n_e, params.n_alpha],
@@ -364,7 +364,7 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
     h_uvw = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (obs_np.u, obs_np.v, obs_np.w)]
     d_uvw = [torch.empty_like(x, device=dev) for x in h_uvw]
     d_data = torch.empty_like(data)
-    obs = rlf.Observation(d_uvw[0], d_uvw[1], d_uvw[2], obs_np.freq_hz)
+    obs = rlf.Observation(d_uvw[0], d_uvw[1], d_uvw[2], obs_np.freq_hz, obs_np.n_bl)
     h_out = torch.empty((2, n), dtype=torch.float64).pin_memory()
 
     def step():

@@ -53,9 +53,13 @@ typedef enum {
 /* arithmetic of the path */
 enum {
     RLF_PREC_FP64 = 0,     /* every step in double precision */
-    RLF_PREC_MIXED = 1     /* FP32 model and sums of products; FP64 phase argument and its
+    RLF_PREC_MIXED = 1,    /* FP32 model and sums of products; FP64 phase argument and its
                               range reduction, cell-index decisions, likelihood accumulation
                               and the marginal normalisation */
+    RLF_PREC_MIXED_SPLIT = 2 /* as RLF_PREC_MIXED, but the phase argument and its range
+                              reduction are carried as pairs of floats with error-free FP32
+                              products and sums (about 48 significant bits), which GB300 runs
+                              at its FP32 rate instead of its much lower FP64 rate */
 };
 
 /* bits of the per-source fit flag */
@@ -83,7 +87,9 @@ enum { RLF_WS_SKY = 0, RLF_WS_EXTRACT = 1, RLF_WS_FIT = 2, RLF_WS_RUN = 3 };
 typedef struct {
     int64_t n_rows;          /* number of (baseline, time) rows, > 0 */
     int32_t n_chan;          /* channels, 1 .. RLF_MAX_CHAN */
-    int32_t reserved;
+    int32_t n_baselines;     /* rows are time-major with this many baselines per time step
+                                (the Measurement Set order); 0 if unknown.  Only speed
+                                depends on it: extraction walks each baseline's time series */
     const double *u;         /* device [n_rows], metres */
     const double *v;         /* device [n_rows], metres */
     const double *w;         /* device [n_rows], metres */
@@ -122,7 +128,7 @@ typedef struct {
     int32_t flux_prior;      /* 0: uniform on S >= 0; 1: uniform on the real line */
     int32_t chunk;           /* sources per extract/fit/update step of rlf_run; <= 0: all */
     int32_t update_mode;     /* 0: update the sky model with good fits only; 1: with all */
-    int32_t precision;       /* RLF_PREC_FP64 or RLF_PREC_MIXED */
+    int32_t precision;       /* RLF_PREC_FP64, RLF_PREC_MIXED or RLF_PREC_MIXED_SPLIT */
     int32_t reserved;
 } rlf_params;
 

@@ -25,7 +25,7 @@ INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 HEADER = os.path.join(INCLUDE, "rlf.h")
 
 RLF_OK, RLF_EINVAL, RLF_ECUDA, RLF_ENOSPACE, RLF_ETIMEOUT, RLF_ENUMERIC, RLF_EUNSUPPORTED = range(7)
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_SPLIT = 0, 1, 2
 FLAG_BAD, FLAG_INVALID, FLAG_EMPTY = 1, 2, 4
 DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
 WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
@@ -42,7 +42,7 @@ class RlfError(RuntimeError):
 
 
 class Uvw(ctypes.Structure):
-    _fields_ = [("n_rows", ctypes.c_int64), ("n_chan", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_chan", ctypes.c_int32), ("n_baselines", ctypes.c_int32),
                 ("u", _vp), ("v", _vp), ("w", _vp), ("freq_hz", _vp)]
 
 
@@ -168,10 +168,10 @@ def _stream(stream) -> int | None:
 class Observation:
     """Device baselines plus the host channel table, as the C ABI wants them."""
 
-    def __init__(self, u, v, w, freq_hz):
+    def __init__(self, u, v, w, freq_hz, n_baselines: int = 0):
         self.u, self.v, self.w = u, v, w
         self.freq_hz = np.ascontiguousarray(freq_hz, dtype=np.float64)
-        self.struct = Uvw(n_rows=int(u.shape[0]), n_chan=int(self.freq_hz.shape[0]), reserved=0,
+        self.struct = Uvw(n_rows=int(u.shape[0]), n_chan=int(self.freq_hz.shape[0]), n_baselines=int(n_baselines),
                           u=_ptr(u), v=_ptr(v), w=_ptr(w),
                           freq_hz=self.freq_hz.ctypes.data_as(ctypes.c_void_p).value)
 

@@ -25,7 +25,8 @@ bool params_ok(const rlf_params &p)
     if (!(p.e_max > 0 && p.e_max <= 1)) return false;
     if (!(p.nu_ref_hz > 0 && std::isfinite(p.nu_ref_hz))) return false;
     if (!std::isfinite(p.beta) || !std::isfinite(p.add) || !std::isfinite(p.esp)) return false;
-    if (p.precision != RLF_PREC_FP64 && p.precision != RLF_PREC_MIXED) return false;
+    if (p.precision != RLF_PREC_FP64 && p.precision != RLF_PREC_MIXED && p.precision != RLF_PREC_MIXED_SPLIT)
+        return false;
     if (p.flux_prior != 0 && p.flux_prior != 1) return false;
     if (p.update_mode != 0 && p.update_mode != 1) return false;
     return true;
@@ -34,7 +35,7 @@ bool params_ok(const rlf_params &p)
 rlf_status check_uvw(const rlf_uvw *uvw)
 {
     if (!uvw || !uvw->u || !uvw->v || !uvw->w || !uvw->freq_hz) return RLF_EINVAL;
-    if (uvw->n_rows <= 0 || uvw->n_chan <= 0) return RLF_EINVAL;
+    if (uvw->n_rows <= 0 || uvw->n_chan <= 0 || uvw->n_baselines < 0) return RLF_EINVAL;
     if (uvw->n_chan > RLF_MAX_CHAN) return RLF_EUNSUPPORTED;
     for (int k = 0; k < uvw->n_chan; ++k) {
         if (!(uvw->freq_hz[k] > 0 && std::isfinite(uvw->freq_hz[k]))) return RLF_EINVAL;
@@ -59,8 +60,17 @@ ChanTable make_chan_table(const rlf_uvw &uvw, const rlf_params &p)
         ch.s[k] = uvw.freq_hz[k] / kC;
         ch.spec[k] = std::pow(uvw.freq_hz[k] / p.nu_ref_hz, p.beta);
     }
+    for (int k = 0; k < ch.n; ++k) {
+        ch.s_hi[k] = (float)ch.s[k];
+        ch.s_lo[k] = (float)(ch.s[k] - (double)ch.s_hi[k]);
+    }
+    double mean = 0.0;
+    for (int k = 0; k < ch.n; ++k) mean += ch.spec[k];
+    ch.spec_off = mean / ch.n;
     ch.s0 = ch.s[0];
     ch.ds = ch.n > 1 ? (ch.s[ch.n - 1] - ch.s[0]) / (ch.n - 1) : 0.0;
+    ch.ds_hi = (float)ch.ds;
+    ch.ds_lo = (float)(ch.ds - (double)ch.ds_hi);
     ch.uniform = 1;
     for (int k = 0; k < ch.n; ++k)
         if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;
@@ -80,7 +90,6 @@ int32_t fit_capacity(int32_t n_src, const rlf_params &p, int32_t which)
 size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params &p,
                         int32_t which, void *base, Workspace *ws)
 {
-    (void)n_rows;
     (void)n_chan;
     const size_t NN = (size_t)p.facet_n * p.facet_n;
     const size_t ng = (size_t)p.n_e * p.n_e * p.n_alpha;
@@ -104,6 +113,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
+    const bool ext = which == RLF_WS_EXTRACT || run;
+    const size_t o_split = take(ext ? 6 * (size_t)(n_rows > 0 ? n_rows : 0) * sizeof(float) : 0);
     const size_t total = off + 256;   // slack for aligning an arbitrary base pointer
     if (ws && base) {
         char *b = reinterpret_cast<char *>(align_up(reinterpret_cast<size_t>(base), 256));
@@ -118,6 +129,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->gl = reinterpret_cast<double *>(b + o_gl);
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
         ws->facets = reinterpret_cast<double *>(b + o_fac);
+        ws->uvw_split = reinterpret_cast<float *>(b + o_split);
         ws->bytes = total;
     }
     return total;
@@ -246,7 +258,9 @@ rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const f
     if (e == cudaSuccess)
         e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                            nullptr, *p, ws.table, ws.status, st);
-    if (e == cudaSuccess) e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, facets, st);
+    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
+    if (e == cudaSuccess)
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, facets, st);
     return cuda_status(e);
 }
 
@@ -300,9 +314,10 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
         e = launch_prepare(*src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, *p,
                            ws.table, ws.status, st);
     if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, n, false, p->precision, vis_sky, st);
+    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.facets, st);
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.uvw_split, ws.facets, st);
         if (e != cudaSuccess) break;
         e = launch_fit(ws.facets, ws.table + first, cnt, *p, ws, *out, first, st);
         if (e != cudaSuccess) break;

@@ -2,16 +2,25 @@
 // averaging of the shifted visibilities into a facet_n x facet_n uv grid of
 // cell side du = 1 / (K alpha).
 //
-// One CTA owns (source, chunk of rows) and accumulates a private copy of the
-// facet in shared memory (4 planes: sum Re x, sum Im x, count, sum of the
-// spectral factor) with shared-memory atomics; at the end the non-empty cells
-// are added to the FP64 facet in global memory.  blockIdx.x runs over the
-// sources so the CTAs that read the same row chunk run together and share it
-// through L2.
-//
 // The residual of source i is D - V_sky + model_i; model_i carries the phase
 // exp(+2 pi i phi_i), so after the shift it is the real number S s M(k) and
 // x = (D - V_sky) exp(-2 pi i phi_i) + S s M(k).
+//
+// Mixed-precision kernel (extract_rl_kernel).  A CTA owns (source, block of
+// baselines, chunk of time steps) and keeps a private copy of the facet in
+// shared memory.  Each thread walks one baseline's time series for a group of
+// channels.  A baseline's uv track moves slowly (a few per cent of a cell per
+// 60 s step at the facet sizes of the method), so consecutive visibilities of
+// one channel usually fall in the same cell: the thread sums that run in
+// registers and adds it to shared memory only when the cell changes.  At the
+// end the non-empty cells are added to the FP64 facet in global memory.
+// blockIdx.x runs over the sources, so the CTAs reading the same rows run
+// together and share them through L2.
+//
+// Shared-memory planes: sum Re x, sum Im x (FP32), count (int32), and the sum of
+// spec - spec_off (FP32, spec_off the band mean; the flush adds count * spec_off
+// back in FP64, which keeps the rounding of cells with 1e5 visibilities far
+// below 1e-6 relative).
 //
 // Cell index: both coordinates are computed in FP32 (u * (nu/c/du)); when the
 // value lies within the FP32 error bound of a cell edge the index is recomputed
@@ -32,139 +41,257 @@ __device__ __forceinline__ bool near_edge(float t)
     return fabsf(t - rintf(t)) <= 1.0e-6f * fmaxf(fabsf(t), 1.0f);
 }
 
-template <bool kMixed, int CG, bool kUniform>
-__global__ void __launch_bounds__(kThreads)
-extract_kernel(const double *__restrict__ u, const double *__restrict__ v,
-               const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
-               const float2 *__restrict__ data, const float2 *__restrict__ sky,
-               const SrcRow *__restrict__ table, int32_t N, int64_t rows_per_chunk,
-               double *__restrict__ facets)
+__global__ void split_uvw_kernel(const double *__restrict__ u, const double *__restrict__ v,
+                                 const double *__restrict__ w, int64_t n, float *__restrict__ out)
 {
-    using Acc = typename std::conditional<kMixed, float, double>::type;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        split_double(u[i], h, l);
+        out[i] = h;
+        out[n + i] = l;
+        split_double(v[i], h, l);
+        out[2 * n + i] = h;
+        out[3 * n + i] = l;
+        split_double(w[i], h, l);
+        out[4 * n + i] = h;
+        out[5 * n + i] = l;
+    }
+}
+
+template <int CG, bool kUniform, bool kSplit>
+__global__ void __launch_bounds__(kThreads, 2)
+extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
+                  const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
+                  int32_t stride, int32_t t_per_chunk, const ChanTable ch,
+                  const float2 *__restrict__ data, const float2 *__restrict__ sky,
+                  const SrcRow *__restrict__ table, int32_t N, double *__restrict__ facets)
+{
     extern __shared__ __align__(16) unsigned char smraw[];
-    Acc *acc = reinterpret_cast<Acc *>(smraw);
     const int NN = N * N;
+    float *sre = reinterpret_cast<float *>(smraw);
+    float *sim = sre + NN;
+    int *scnt = reinterpret_cast<int *>(sim + NN);
+    float *ssp = reinterpret_cast<float *>(scnt + NN);
     const int s = blockIdx.x;
     const SrcRow S = table[s];
 
-    for (int i = threadIdx.x; i < 4 * NN; i += kThreads) acc[i] = Acc(0);
+    for (int i = threadIdx.x; i < NN; i += kThreads) {
+        sre[i] = 0.0f;
+        sim[i] = 0.0f;
+        scnt[i] = 0;
+        ssp[i] = 0.0f;
+    }
     __syncthreads();
 
     const int C = ch.n;
     const int n_groups = (C + CG - 1) / CG;
-    const int lanes = kThreads / n_groups;
-    const int g = threadIdx.x % n_groups;
-    const int lane = threadIdx.x / n_groups;
+    const int bpc = kThreads / n_groups;           // baselines per CTA
+    const int g = threadIdx.x / bpc;
+    const int bl = blockIdx.y * bpc + threadIdx.x % bpc;
     const int k0 = g * CG;
     const int half = N / 2;
     const double du = S.du;
     constexpr float kTwoPi = 6.28318530717958647692f;
 
-    if (S.flux > 0.0 && lane < lanes) {
-        double sk[CG];
-        float sdu[CG], f2[CG], spec[CG];
+    if (S.flux > 0.0 && g < n_groups && bl < stride) {
+        // per-channel constants used for every visibility stay in registers; the
+        // rest is read from the kernel-parameter bank when needed
+        float sdu[CG], f2[CG], fspec[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
-            const int k = k0 + c;
-            sk[c] = k < C ? ch.s[k] : 0.0;
-            sdu[c] = (float)(sk[c] / du);
-            f2[c] = (float)(sk[c] * sk[c]);
-            spec[c] = k < C ? (float)ch.spec[k] : 0.0f;
+            const int k = min(k0 + c, C - 1);
+            sdu[c] = (float)(ch.s[k] / du);
+            f2[c] = (float)(ch.s[k] * ch.s[k]);
+            fspec[c] = (float)(S.flux * ch.spec[k]);
         }
-        const float sflux = (float)S.flux;
         const float q0 = (float)S.q[0], q1 = (float)S.q[1], q2 = (float)S.q[2];
-        const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
-        const int64_t r1 = min(n_rows, r0 + rows_per_chunk);
-        for (int64_t r = r0 + lane; r < r1; r += lanes) {
-            const double ud = u[r], vd = v[r], wd = w[r];
-            const double ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
-            if (kMixed) {
-                const float uf = (float)ud, vf = (float)vd;
-                const float uu = (float)(ud * ud), uv = (float)(ud * vd), vv = (float)(vd * vd);
-                const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
-                float sn = 0.0f, cs = 1.0f, sd = 0.0f, cd = 1.0f;
-                if (kUniform) {
-                    const double t = ph * sk[0];
-                    __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
+        float lh, ll, mh, ml, nh, nl;
+        split_double(S.l, lh, ll);
+        split_double(S.m, mh, ml);
+        split_double(S.n1, nh, nl);
+
+        int run_cell[CG], run_n[CG];
+        float run_re[CG], run_im[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+            run_cell[c] = -1;
+            run_n[c] = 0;
+            run_re[c] = run_im[c] = 0.0f;
+        }
+        auto flush = [&](int c) {
+            const int cell = run_cell[c];
+            atomicAdd(&sre[cell], run_re[c]);
+            atomicAdd(&sim[cell], run_im[c]);
+            atomicAdd(&scnt[cell], run_n[c]);
+            atomicAdd(&ssp[cell], (float)run_n[c] * (float)(ch.spec[k0 + c] - ch.spec_off));
+        };
+
+        const int64_t n_time = (n_rows + stride - 1) / stride;
+        const int64_t t0 = (int64_t)blockIdx.z * t_per_chunk;
+        const int64_t t1 = min(n_time, t0 + t_per_chunk);
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t r = t * stride + bl;
+            if (r >= n_rows) break;
+            float uh, ul, vh, vl, wh, wl;
+            double ph = 0.0;
+            if (kSplit) {
+                uh = us[r];
+                ul = us[n_rows + r];
+                vh = us[2 * n_rows + r];
+                vl = us[3 * n_rows + r];
+                wh = us[4 * n_rows + r];
+                wl = us[5 * n_rows + r];
+            } else {
+                const double ud = u[r], vd = v[r], wd = w[r];
+                ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
+                uh = (float)ud;
+                vh = (float)vd;
+                ul = vl = wh = wl = 0.0f;
+            }
+            const float uu = uh * uh, uv = uh * vh, vv = vh * vh;
+            const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
+            float P = 0.0f, E = 0.0f;
+            if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
+            float sn = 0.0f, cs = 1.0f, sd = 0.0f, cd = 1.0f;
+            if (kUniform) {
+                float f0, fd = 0.0f;
+                if (kSplit) {
+                    f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
+                    if (CG > 1) fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
+                } else {
+                    const double tt = ph * ch.s[k0];
+                    f0 = (float)(tt - rint(tt));
                     if (CG > 1) {
                         const double td = ph * ch.ds;
-                        __sincosf((float)(td - rint(td)) * kTwoPi, &sd, &cd);
+                        fd = (float)(td - rint(td));
                     }
                 }
+                __sincosf(f0 * kTwoPi, &sn, &cs);
+                if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
+            }
 #pragma unroll
-                for (int c = 0; c < CG; ++c) {
-                    const int k = k0 + c;
-                    if (!kUniform) {
-                        const double t = ph * sk[c];
-                        __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
+            for (int c = 0; c < CG; ++c) {
+                const int k = k0 + c;
+                if (!kUniform) {
+                    const int kk = min(k, C - 1);
+                    float f;
+                    if (kSplit) {
+                        f = frac_cycles(P, E, ch.s_hi[kk], ch.s_lo[kk]);
+                    } else {
+                        const double tt = ph * ch.s[kk];
+                        f = (float)(tt - rint(tt));
                     }
-                    if (k < C) {
-                        const float tu = uf * sdu[c], tv = vf * sdu[c];
-                        if (fabsf(tu) < half + 1.0f && fabsf(tv) < half + 1.0f) {
-                            int iu = (int)floorf(tu), iv = (int)floorf(tv);
-                            if (near_edge(tu)) iu = (int)floor((ud * sk[c]) / du);
-                            if (near_edge(tv)) iv = (int)floor((vd * sk[c]) / du);
-                            iu += half;
-                            iv += half;
-                            if (iu >= 0 && iu < N && iv >= 0 && iv < N) {
-                                const float2 dv = data[r * C + k];
-                                const float2 sv = sky[r * C + k];
-                                const float rr = dv.x - sv.x, ri = dv.y - sv.y;
-                                // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn)
-                                float xr = fmaf(rr, cs, ri * sn);
-                                const float xi = fmaf(ri, cs, -rr * sn);
-                                const float rq = rsqrtf(fmaf(q, f2[c], 1.0f));
-                                xr = fmaf(sflux * spec[c], rq * rq * rq, xr);
-                                const int cell = iv * N + iu;
-                                atomicAdd(&acc[cell], xr);
-                                atomicAdd(&acc[NN + cell], xi);
-                                atomicAdd(&acc[2 * NN + cell], 1.0f);
-                                atomicAdd(&acc[3 * NN + cell], spec[c]);
-                            }
-                        }
+                    __sincosf(f * kTwoPi, &sn, &cs);
+                }
+                if (k < C) {
+                    int cell = -1;
+                    const float tu = uh * sdu[c], tv = vh * sdu[c];
+                    if (fabsf(tu) < half + 1.0f && fabsf(tv) < half + 1.0f) {
+                        int iu = (int)floorf(tu), iv = (int)floorf(tv);
+                        if (near_edge(tu)) iu = (int)floor((u[r] * ch.s[k]) / du);
+                        if (near_edge(tv)) iv = (int)floor((v[r] * ch.s[k]) / du);
+                        iu += half;
+                        iv += half;
+                        if (iu >= 0 && iu < N && iv >= 0 && iv < N) cell = iv * N + iu;
                     }
-                    if (kUniform && c + 1 < CG) {
-                        const float cn = cs * cd - sn * sd;
-                        sn = fmaf(cs, sd, sn * cd);
-                        cs = cn;
+                    if (cell != run_cell[c]) {
+                        if (run_n[c] > 0) flush(c);
+                        run_cell[c] = cell;
+                        run_n[c] = 0;
+                        run_re[c] = run_im[c] = 0.0f;
+                    }
+                    if (cell >= 0) {
+                        const float2 dv = data[r * C + k];
+                        const float2 sv = sky[r * C + k];
+                        const float rr = dv.x - sv.x, ri = dv.y - sv.y;
+                        // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn)
+                        float xr = fmaf(rr, cs, ri * sn);
+                        const float xi = fmaf(ri, cs, -rr * sn);
+                        const float rq = rsqrtf(fmaf(q, f2[c], 1.0f));
+                        xr = fmaf(fspec[c], rq * rq * rq, xr);
+                        run_re[c] += xr;
+                        run_im[c] += xi;
+                        run_n[c] += 1;
                     }
                 }
-            } else {
-#pragma unroll
-                for (int c = 0; c < CG; ++c) {
-                    const int k = k0 + c;
-                    if (k >= C) continue;
-                    const double ku = ud * sk[c], kv = vd * sk[c];
-                    const double fu = floor(ku / du), fv = floor(kv / du);
-                    if (fu < -half || fu >= half || fv < -half || fv >= half) continue;
-                    const int iu = (int)fu + half, iv = (int)fv + half;
-                    const float2 dv = data[r * C + k];
-                    const float2 sv = sky[r * C + k];
-                    const double rr = (double)dv.x - (double)sv.x, ri = (double)dv.y - (double)sv.y;
-                    const double t = ph * sk[c];
-                    double sn, cs;
-                    sincospi(2.0 * (t - rint(t)), &sn, &cs);
-                    double xr = rr * cs + ri * sn;
-                    const double xi = ri * cs - rr * sn;
-                    const double x = 1.0 + (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * sk[c] * sk[c];
-                    xr += S.flux * ch.spec[k] / (x * sqrt(x));
-                    const int cell = iv * N + iu;
-                    atomicAdd(&acc[cell], (Acc)xr);
-                    atomicAdd(&acc[NN + cell], (Acc)xi);
-                    atomicAdd(&acc[2 * NN + cell], Acc(1));
-                    atomicAdd(&acc[3 * NN + cell], (Acc)ch.spec[k]);
+                if (kUniform && c + 1 < CG) {
+                    const float cn = cs * cd - sn * sd;
+                    sn = fmaf(cs, sd, sn * cd);
+                    cs = cn;
                 }
             }
+        }
+#pragma unroll
+        for (int c = 0; c < CG; ++c)
+            if (run_n[c] > 0) flush(c);
+    }
+    __syncthreads();
+    double *f = facets + (size_t)s * 4 * NN;
+    for (int i = threadIdx.x; i < NN; i += kThreads) {
+        const int n = scnt[i];
+        if (n != 0) {
+            atomicAdd(&f[i], (double)sre[i]);
+            atomicAdd(&f[NN + i], (double)sim[i]);
+            atomicAdd(&f[2 * NN + i], (double)n);
+            atomicAdd(&f[3 * NN + i], (double)ssp[i] + (double)n * ch.spec_off);
+        }
+    }
+}
+
+// FP64 extraction: every operation in double precision, one visibility at a time.
+__global__ void __launch_bounds__(kThreads)
+extract_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
+                    const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
+                    const float2 *__restrict__ data, const float2 *__restrict__ sky,
+                    const SrcRow *__restrict__ table, int32_t N, int64_t rows_per_chunk,
+                    double *__restrict__ facets)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double *acc = reinterpret_cast<double *>(smraw);
+    const int NN = N * N;
+    const int s = blockIdx.x;
+    const SrcRow S = table[s];
+    for (int i = threadIdx.x; i < 4 * NN; i += kThreads) acc[i] = 0.0;
+    __syncthreads();
+    const int C = ch.n;
+    const int half = N / 2;
+    const double du = S.du;
+    if (S.flux > 0.0) {
+        const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+        const int64_t r1 = min(n_rows, r0 + rows_per_chunk);
+        for (int64_t o = r0 * C + threadIdx.x; o < r1 * C; o += kThreads) {
+            const int64_t r = o / C;
+            const int k = (int)(o % C);
+            const double ud = u[r], vd = v[r], wd = w[r];
+            const double ku = ud * ch.s[k], kv = vd * ch.s[k];
+            const double fu = floor(ku / du), fv = floor(kv / du);
+            if (fu < -half || fu >= half || fv < -half || fv >= half) continue;
+            const int iu = (int)fu + half, iv = (int)fv + half;
+            const float2 dv = data[o];
+            const float2 sv = sky[o];
+            const double rr = (double)dv.x - (double)sv.x, ri = (double)dv.y - (double)sv.y;
+            const double t = fma(wd, S.n1, fma(vd, S.m, ud * S.l)) * ch.s[k];
+            double sn, cs;
+            sincospi(2.0 * (t - rint(t)), &sn, &cs);
+            double xr = rr * cs + ri * sn;
+            const double xi = ri * cs - rr * sn;
+            const double x = 1.0 + (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * ch.s[k] * ch.s[k];
+            xr += S.flux * ch.spec[k] / (x * sqrt(x));
+            const int cell = iv * N + iu;
+            atomicAdd(&acc[cell], xr);
+            atomicAdd(&acc[NN + cell], xi);
+            atomicAdd(&acc[2 * NN + cell], 1.0);
+            atomicAdd(&acc[3 * NN + cell], ch.spec[k]);
         }
     }
     __syncthreads();
     double *f = facets + (size_t)s * 4 * NN;
     for (int i = threadIdx.x; i < NN; i += kThreads) {
-        if (acc[2 * NN + i] != Acc(0)) {
-            atomicAdd(&f[i], (double)acc[i]);
-            atomicAdd(&f[NN + i], (double)acc[NN + i]);
-            atomicAdd(&f[2 * NN + i], (double)acc[2 * NN + i]);
-            atomicAdd(&f[3 * NN + i], (double)acc[3 * NN + i]);
+        if (acc[2 * NN + i] != 0.0) {
+            atomicAdd(&f[i], acc[i]);
+            atomicAdd(&f[NN + i], acc[NN + i]);
+            atomicAdd(&f[2 * NN + i], acc[2 * NN + i]);
+            atomicAdd(&f[3 * NN + i], acc[3 * NN + i]);
         }
     }
 }
@@ -181,65 +308,97 @@ int sm_count_x()
     return n;
 }
 
-template <bool kMixed, int CG>
-cudaError_t launch_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                      const SrcRow *table, int32_t count, int32_t N, double *facets,
+template <int CG, bool kSplit>
+cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
+                      const SrcRow *table, int32_t count, int32_t N, const float *us, double *facets,
                       cudaStream_t st)
 {
-    const size_t acc_bytes = kMixed ? sizeof(float) : sizeof(double);
-    const size_t smem = 4 * (size_t)N * N * acc_bytes;
-    auto kern = ch.uniform ? extract_kernel<kMixed, CG, true> : extract_kernel<kMixed, CG, false>;
+    const size_t smem = 4 * (size_t)N * N * sizeof(float);
+    auto kern = ch.uniform ? extract_rl_kernel<CG, true, kSplit> : extract_rl_kernel<CG, false, kSplit>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    // Row chunks: enough CTAs for several waves, and a chunk of rows small enough
-    // (about 16 MB of visibilities and baselines) that the CTAs of all sources
-    // reading it at the same time find it in L2.
+    // rows are walked as [time][stride]; stride = baselines per time step when known
+    const int32_t stride = uvw.n_baselines > 0 ? uvw.n_baselines : 1024;
     const int n_groups = (ch.n + CG - 1) / CG;
-    const int64_t lanes = kThreads / n_groups;
+    const int bpc = kThreads / n_groups;
+    const int64_t bl_blocks = (stride + bpc - 1) / bpc;
+    const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
+    // enough CTAs for about four waves; split the time axis only when the
+    // (source, baseline block) pairs alone are too few
     const int64_t target = (int64_t)sm_count_x() * per_sm * 4;
+    int64_t t_chunks = (target + count * bl_blocks - 1) / (count * bl_blocks);
+    if (t_chunks < 1) t_chunks = 1;
+    if (t_chunks > n_time) t_chunks = n_time;
+    if (t_chunks > 65535) t_chunks = 65535;
+    const int64_t t_per_chunk = (n_time + t_chunks - 1) / t_chunks;
+    t_chunks = (n_time + t_per_chunk - 1) / t_per_chunk;
+    if (bl_blocks > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid(count, (unsigned)bl_blocks, (unsigned)t_chunks);
+    kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)t_per_chunk, ch,
+                                       reinterpret_cast<const float2 *>(data),
+                                       reinterpret_cast<const float2 *>(sky), table, N, facets);
+    return cudaGetLastError();
+}
+
+template <bool kSplit>
+cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
+                         const SrcRow *table, int32_t count, int32_t N, const float *us, double *facets,
+                         cudaStream_t st)
+{
+    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
+    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
+    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
+    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
+}
+
+cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
+                        const SrcRow *table, int32_t count, int32_t N, double *facets, cudaStream_t st)
+{
+    const size_t smem = 4 * (size_t)N * N * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(extract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t target = (int64_t)sm_count_x() * 4;
     int64_t n_chunks = (target + count - 1) / count;
-    const double bytes = (double)uvw.n_rows * (16.0 * ch.n + 24.0);
-    const int64_t by_l2 = (int64_t)(bytes / 16.0e6) + 1;
-    if (by_l2 > n_chunks) n_chunks = by_l2;
-    const int64_t max_chunks = (uvw.n_rows + lanes - 1) / lanes;
+    const int64_t max_chunks = (uvw.n_rows * uvw.n_chan + kThreads - 1) / kThreads;
     if (n_chunks > max_chunks) n_chunks = max_chunks;
     if (n_chunks < 1) n_chunks = 1;
     if (n_chunks > 65535) n_chunks = 65535;
     const int64_t rows_per_chunk = (uvw.n_rows + n_chunks - 1) / n_chunks;
     dim3 grid(count, (unsigned)n_chunks);
-    kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch,
-                                       reinterpret_cast<const float2 *>(data),
-                                       reinterpret_cast<const float2 *>(sky), table, N,
-                                       rows_per_chunk, facets);
+    extract_fp64_kernel<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch,
+                                                     reinterpret_cast<const float2 *>(data),
+                                                     reinterpret_cast<const float2 *>(sky), table, N,
+                                                     rows_per_chunk, facets);
     return cudaGetLastError();
-}
-
-template <bool kMixed>
-cudaError_t launch_prec(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
-                        const float *sky, const SrcRow *table, int32_t count, int32_t N,
-                        double *facets, cudaStream_t st)
-{
-    if (ch.n == 1) return launch_cg<kMixed, 1>(uvw, ch, data, sky, table, count, N, facets, st);
-    if (ch.n == 2) return launch_cg<kMixed, 2>(uvw, ch, data, sky, table, count, N, facets, st);
-    if (ch.n <= 4) return launch_cg<kMixed, 4>(uvw, ch, data, sky, table, count, N, facets, st);
-    return launch_cg<kMixed, 8>(uvw, ch, data, sky, table, count, N, facets, st);
 }
 
 }  // namespace
 
+cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st)
+{
+    const int64_t need = (uvw.n_rows + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count_x() * 8;
+    split_uvw_kernel<<<(int)(need < cap ? need : cap), kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, double *facets, cudaStream_t st)
+                           const rlf_params &p, const float *uvw_split, double *facets,
+                           cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(facets, 0, (size_t)count * 4 * p.facet_n * p.facet_n * sizeof(double), st);
     if (e != cudaSuccess) return e;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_prec<true>(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
-    return launch_prec<false>(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
+        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, facets, st);
+    if (p.precision == RLF_PREC_MIXED_SPLIT)
+        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, facets, st);
+    return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
 }
 
 }  // namespace rlf

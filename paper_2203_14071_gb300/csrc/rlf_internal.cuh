@@ -37,9 +37,64 @@ struct ChanTable {
     int32_t n;              // channels
     int32_t uniform;        // s[k] = s0 + k ds to 1e-12 relative
     double s0, ds;          // nu / c of channel 0 and its step, 1/m
+    double spec_off;        // mean spectral factor: FP32 sums accumulate spec - spec_off
     double s[RLF_MAX_CHAN];     // nu_k / c (host division, the value the cell index uses)
     double spec[RLF_MAX_CHAN];  // (nu_k / nu_ref)^beta
+    float s_hi[RLF_MAX_CHAN], s_lo[RLF_MAX_CHAN];  // s as a float pair, s_hi + s_lo
+    float ds_hi, ds_lo;                             // ds as a float pair
 };
+
+// ---- error-free FP32 transformations (float-float arithmetic) -------------------------
+// A value carried as hi + lo with |lo| <= ulp(hi)/2 has about 48 significant bits.
+// two_prod: a * b = p + e exactly (FMA residual).  two_sum: a + b = s + e exactly
+// (Knuth).  The __f*_rn intrinsics are never contracted or reassociated.
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// phase argument u l + v m + w (n - 1) in metres as P + E, from float-pair inputs.
+// Products are exact (two_prod); the cross terms hi*lo carry about 2^-24 of the
+// product and are summed in FP32; lo*lo terms (2^-48 of the product) are dropped.
+__device__ __forceinline__ void phase_metres(float uh, float ul, float vh, float vl, float wh, float wl,
+                                             float lh, float ll, float mh, float ml, float nh, float nl,
+                                             float &P, float &E)
+{
+    float p1, e1, p2, e2, p3, e3;
+    two_prod(uh, lh, p1, e1);
+    two_prod(vh, mh, p2, e2);
+    two_prod(wh, nh, p3, e3);
+    const float cross = fmaf(uh, ll, ul * lh) + fmaf(vh, ml, vl * mh) + fmaf(wh, nl, wl * nh);
+    float s12, t12, t;
+    two_sum(p1, p2, s12, t12);
+    two_sum(s12, p3, P, t);
+    E = ((e1 + e2) + e3) + (t12 + t) + cross;
+}
+
+// fractional part in [-1/2, 1/2] of (P + E) * (sh + sl) cycles
+__device__ __forceinline__ float frac_cycles(float P, float E, float sh, float sl)
+{
+    float q, eq;
+    two_prod(P, sh, q, eq);
+    const float r = __fsub_rn(q, rintf(q));          // exact
+    const float f = r + (eq + fmaf(P, sl, E * sh));
+    return f - rintf(f);
+}
+
+__device__ __forceinline__ void split_double(double x, float &hi, float &lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
 
 // Grid constants of the likelihood (Sec. 2.4).
 struct GridConst {
@@ -62,6 +117,7 @@ struct Workspace {
     double *ga, *gb, *gl;   // [cap][n_e^2][n_alpha]
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
+    float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
     size_t bytes;
 };
 
@@ -76,9 +132,11 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st);
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st);
+cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, double *facets, cudaStream_t st);
+                           const rlf_params &p, const float *uvw_split, double *facets,
+                           cudaStream_t st);
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
                        int32_t out_offset, cudaStream_t st);

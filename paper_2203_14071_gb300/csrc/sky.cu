@@ -6,7 +6,9 @@
 // rows.  Mixed precision keeps the phase argument u l + v m + w (n - 1) and its
 // range reduction in FP64 once per (row, source) and steps it across the
 // channels of the group by an FP32 complex rotation; the brightness factor
-// (1 + x)^{-3/2} is one MUFU rsqrt and two multiplies per term.
+// (1 + x)^{-3/2} is one MUFU rsqrt and two multiplies per term.  The split
+// variant carries the phase argument as a float pair (error-free FP32 products
+// and sums), which GB300 executes at its FP32 rate.
 #include <cmath>
 
 #include "rlf_internal.cuh"
@@ -87,11 +89,13 @@ __global__ void prepare_kernel(rlf_sources src, int32_t first, int32_t count,
 
 struct SkySrc {
     double l, m, n1;
+    float lh, ll, mh, ml, nh, nl;       // direction cosines as float pairs (split phase)
     float flux, q0, q1, q2, qn0, qn1, qn2, pad;
 };
 
-// Mixed precision sky model / update.  CG channels per thread.
-template <int CG, bool kUpdate, bool kUniform>
+// Mixed precision sky model / update.  CG channels per thread.  kSplit selects
+// the float-pair phase argument instead of the FP64 one.
+template <int CG, bool kUpdate, bool kUniform, bool kSplit>
 __global__ void __launch_bounds__(kThreads)
 sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                  const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
@@ -106,7 +110,7 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
     const bool thread_on = lane < lanes;
     const int k0 = g * CG;
 
-    float f2[CG], spec[CG];
+    float f2[CG], spec[CG], shi[CG], slo[CG];
     double sk[CG];
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
@@ -115,6 +119,8 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
         sk[c] = s;
         f2[c] = (float)(s * s);
         spec[c] = k < C ? (float)ch.spec[k] : 0.0f;
+        shi[c] = k < C ? ch.s_hi[k] : 0.0f;
+        slo[c] = k < C ? ch.s_lo[k] : 0.0f;
     }
     const double s_k0 = sk[0];
     const double ds = ch.ds;
@@ -128,6 +134,12 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
             ud = u[r];
             vd = v[r];
             wd = w[r];
+        }
+        float uh = 0, ul = 0, vh = 0, vl = 0, wh = 0, wl = 0;
+        if (kSplit) {
+            split_double(ud, uh, ul);
+            split_double(vd, vh, vl);
+            split_double(wd, wh, wl);
         }
         const float uu = (float)(ud * ud), uv = (float)(ud * vd), vv = (float)(vd * vd);
         float are[CG], aim[CG];
@@ -143,6 +155,9 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                 s.l = R.l;
                 s.m = R.m;
                 s.n1 = R.n1;
+                split_double(R.l, s.lh, s.ll);
+                split_double(R.m, s.mh, s.ml);
+                split_double(R.n1, s.nh, s.nl);
                 s.flux = (float)R.flux;
                 s.q0 = (float)R.q[0];
                 s.q1 = (float)R.q[1];
@@ -158,25 +173,42 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
             for (int j = 0; j < nt; ++j) {
                 const SkySrc &S = sm[j];
                 if (S.flux == 0.0f) continue;
-                // phase argument in metres and its reduction to [-1/2, 1/2] cycles, FP64
-                const double ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
                 const float q = fmaf(S.q2, vv, fmaf(S.q1, uv, S.q0 * uu));
                 float qn = 0.0f;
                 if (kUpdate) qn = fmaf(S.qn2, vv, fmaf(S.qn1, uv, S.qn0 * uu));
+                // phase argument and its reduction to [-1/2, 1/2] cycles
+                double ph = 0.0;
+                float P = 0.0f, E = 0.0f;
+                if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, S.lh, S.ll, S.mh, S.ml, S.nh, S.nl, P, E);
+                else ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
                 float sn, cs, sd = 0.0f, cd = 1.0f;
                 if (kUniform) {
-                    const double t = ph * s_k0;
-                    __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
-                    if (CG > 1) {
-                        const double td = ph * ds;
-                        __sincosf((float)(td - rint(td)) * kTwoPi, &sd, &cd);
+                    float f0, fd = 0.0f;
+                    if (kSplit) {
+                        f0 = frac_cycles(P, E, shi[0], slo[0]);
+                        if (CG > 1) fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
+                    } else {
+                        const double t = ph * s_k0;
+                        f0 = (float)(t - rint(t));
+                        if (CG > 1) {
+                            const double td = ph * ds;
+                            fd = (float)(td - rint(td));
+                        }
                     }
+                    __sincosf(f0 * kTwoPi, &sn, &cs);
+                    if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
                 }
 #pragma unroll
                 for (int c = 0; c < CG; ++c) {
                     if (!kUniform) {
-                        const double t = ph * sk[c];
-                        __sincosf((float)(t - rint(t)) * kTwoPi, &sn, &cs);
+                        float f;
+                        if (kSplit) {
+                            f = frac_cycles(P, E, shi[c], slo[c]);
+                        } else {
+                            const double t = ph * sk[c];
+                            f = (float)(t - rint(t));
+                        }
+                        __sincosf(f * kTwoPi, &sn, &cs);
                     }
                     const float x = fmaf(q, f2[c], 1.0f);
                     const float rr = rsqrtf(x);
@@ -283,7 +315,7 @@ int sm_count()
     return n;
 }
 
-template <int CG, bool kUpdate>
+template <int CG, bool kUpdate, bool kSplit>
 void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                   float *vis, cudaStream_t st)
 {
@@ -293,21 +325,21 @@ void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, 
     const int64_t cap = (int64_t)sm_count() * 8;
     const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
     if (ch.uniform)
-        sky_mixed_kernel<CG, kUpdate, true><<<grid, kThreads, 0, st>>>(
+        sky_mixed_kernel<CG, kUpdate, true, kSplit><<<grid, kThreads, 0, st>>>(
             uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
     else
-        sky_mixed_kernel<CG, kUpdate, false><<<grid, kThreads, 0, st>>>(
+        sky_mixed_kernel<CG, kUpdate, false, kSplit><<<grid, kThreads, 0, st>>>(
             uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
 }
 
-template <bool kUpdate>
+template <bool kUpdate, bool kSplit>
 void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table,
                      int32_t n_src, float *vis, cudaStream_t st)
 {
-    if (ch.n == 1) launch_mixed<1, kUpdate>(uvw, ch, table, n_src, vis, st);
-    else if (ch.n == 2) launch_mixed<2, kUpdate>(uvw, ch, table, n_src, vis, st);
-    else if (ch.n <= 4) launch_mixed<4, kUpdate>(uvw, ch, table, n_src, vis, st);
-    else launch_mixed<8, kUpdate>(uvw, ch, table, n_src, vis, st);
+    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
+    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
+    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
+    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
 }
 
 }  // namespace
@@ -329,8 +361,11 @@ cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *ta
                        bool update, int32_t precision, float *vis, cudaStream_t st)
 {
     if (precision == RLF_PREC_MIXED) {
-        if (update) launch_mixed_cg<true>(uvw, ch, table, n_src, vis, st);
-        else launch_mixed_cg<false>(uvw, ch, table, n_src, vis, st);
+        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, st);
+        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, st);
+    } else if (precision == RLF_PREC_MIXED_SPLIT) {
+        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, st);
+        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, st);
     } else {
         const int64_t n_out = uvw.n_rows * ch.n;
         const int64_t need = (n_out + kThreads - 1) / kThreads;

@@ -63,7 +63,7 @@ def to_device(case: Case, e1=None, e2=None, alpha_arcsec=None, device="cuda"):
 
     import paper_2203_14071_gb300 as rlf
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
-    obs = rlf.Observation(t(case.obs.u), t(case.obs.v), t(case.obs.w), case.obs.freq_hz)
+    obs = rlf.Observation(t(case.obs.u), t(case.obs.v), t(case.obs.w), case.obs.freq_hz, case.obs.n_bl)
     z = np.zeros(case.cat.n_src)
     cat = rlf.Catalogue(t(case.cat.l), t(case.cat.m), t(case.cat.flux_jy), t(z if e1 is None else e1),
                         t(z if e2 is None else e2), None if alpha_arcsec is None else t(alpha_arcsec))

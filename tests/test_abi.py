@@ -76,7 +76,7 @@ def _fake_structs(n_rows=10, n_chan=2, n_src=3, freq=None):
     # pointers that are never dereferenced: the host checks reject the call first
     fake = 0x1000
     freq = np.array([1.0e9, 1.1e9][:n_chan] if freq is None else freq, dtype=np.float64)
-    uvw = rlf.Uvw(n_rows=n_rows, n_chan=n_chan, reserved=0, u=fake, v=fake, w=fake,
+    uvw = rlf.Uvw(n_rows=n_rows, n_chan=n_chan, n_baselines=0, u=fake, v=fake, w=fake,
                   freq_hz=freq.ctypes.data_as(ctypes.c_void_p).value)
     src = rlf.Sources(n_src=n_src, reserved=0, l=fake, m=fake, flux_jy=fake, alpha_arcsec=None, e1=fake, e2=fake)
     return uvw, src, freq
@@ -104,7 +104,7 @@ def test_host_argument_checks(L):
     assert f(ctypes.byref(uvw2), ctypes.byref(src), ctypes.byref(p), 0x3000, ws, 1 << 40, None) == rlf.RLF_EUNSUPPORTED
     # parameters out of range
     for bad in (dict(facet_n=65), dict(facet_n=7), dict(n_e=1), dict(n_e=33), dict(sigma_jy=0.0),
-                dict(precision=3), dict(r_min_arcsec=2.0, r_max_arcsec=1.0), dict(thresh_frac=0.0)):
+                dict(precision=4), dict(r_min_arcsec=2.0, r_max_arcsec=1.0), dict(thresh_frac=0.0)):
         pb = rlf.params_default(**bad)
         assert f(ctypes.byref(uvw), ctypes.byref(src), ctypes.byref(pb), 0x3000, ws, 1 << 40, None) == rlf.RLF_EINVAL
     # source range checks
