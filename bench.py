@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--update-mode", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--components", action="store_true", help="also time each entry point alone")
+    ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
+    ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update"],
+                    help="run only this entry point --steps times after one warm-up (for ncu captures)")
     return ap.parse_args()
 
 
@@ -213,7 +215,7 @@ def main():
 
     wl = synth.workload(args.workload)
     obs_np = synth.make_observation(wl)
-    cat_np = synth.make_catalogue(wl)
+    cat_np = synth.make_catalogue(wl, args.n_src if args.n_src > 0 else None)
     n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
     n_vis = R * C
     prec = {"split": rlf.PREC_MIXED_SPLIT, "mixed": rlf.PREC_MIXED, "fp64": rlf.PREC_FP64}[args.precision]
@@ -238,6 +240,10 @@ def main():
 
     def step():
         rlf.run(obs, data, cat, params, out, sky, ws, stream)
+
+    if args.only:
+        profile_only(args, rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, n_src)
+        return
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -302,6 +308,27 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def profile_only(args, rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, n_src):
+    """One entry point alone (after the chain ran once), for profiler captures."""
+    facets = torch.empty(rlf.facets_size(n_src, params) // 8, dtype=torch.float64, device=dev)
+    ws_fit = rlf.alloc_workspace(obs.n_rows, obs.n_chan, n_src, params, rlf.WS_FIT, device=dev)
+    rlf.run(obs, data, cat, params, out, sky, ws, stream)
+    rlf.extract_facets(obs, data, sky, cat, 0, n_src, params, facets, ws, stream)
+    calls = {"sky_model": lambda: rlf.sky_model(obs, cat, params, sky, ws, stream),
+             "extract": lambda: rlf.extract_facets(obs, data, sky, cat, 0, n_src, params, facets, ws, stream),
+             "fit": lambda: rlf.fit_sources(facets, cat, 0, n_src, params, out, ws_fit, stream),
+             "update": lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream)}
+    fn = calls[args.only]
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"only": args.only, "n_src": n_src, "ms_per_call": a.elapsed_time(b) / args.steps}))
 
 
 def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, args, n_src):

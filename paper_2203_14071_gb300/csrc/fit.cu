@@ -434,7 +434,7 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
     const size_t plane = (size_t)count * NN;
     const int pairs = p.n_e * p.n_e * gc.n_ag;
     const int tiles = (pairs + kThreads - 1) / kThreads;
-    if (p.precision == RLF_PREC_MIXED) {
+    if (p.precision != RLF_PREC_FP64) {
         float *cells = static_cast<float *>(ws.cells);
         compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                           ws.ncell, ws.cc);
