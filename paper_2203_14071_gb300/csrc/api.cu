@@ -90,7 +90,6 @@ int32_t fit_capacity(int32_t n_src, const rlf_params &p, int32_t which)
 size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params &p,
                         int32_t which, void *base, Workspace *ws)
 {
-    (void)n_chan;
     const size_t NN = (size_t)p.facet_n * p.facet_n;
     const size_t ng = (size_t)p.n_e * p.n_e * p.n_alpha;
     const size_t cap = (size_t)fit_capacity(n_src, p, which);
@@ -114,7 +113,9 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
     const bool ext = which == RLF_WS_EXTRACT || run;
-    const size_t o_split = take(ext ? 6 * (size_t)(n_rows > 0 ? n_rows : 0) * sizeof(float) : 0);
+    const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
+    const size_t o_split = take(ext ? 6 * rows * sizeof(float) : 0);
+    const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
     const size_t total = off + 256;   // slack for aligning an arbitrary base pointer
     if (ws && base) {
         char *b = reinterpret_cast<char *>(align_up(reinterpret_cast<size_t>(base), 256));
@@ -130,6 +131,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
         ws->facets = reinterpret_cast<double *>(b + o_fac);
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
+        ws->resid = reinterpret_cast<float *>(b + o_resid);
         ws->bytes = total;
     }
     return total;
@@ -260,7 +262,7 @@ rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const f
                            nullptr, *p, ws.table, ws.status, st);
     if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
     if (e == cudaSuccess)
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, facets, st);
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, ws.resid, facets, st);
     return cuda_status(e);
 }
 
@@ -317,7 +319,8 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
     if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.uvw_split, ws.facets, st);
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.uvw_split, ws.resid,
+                           ws.facets, st);
         if (e != cudaSuccess) break;
         e = launch_fit(ws.facets, ws.table + first, cnt, *p, ws, *out, first, st);
         if (e != cudaSuccess) break;

@@ -35,10 +35,29 @@ namespace rlf {
 
 namespace {
 
-__device__ __forceinline__ bool near_edge(float t)
+// floor(t) for |t| < 2^22: y = t - 1/2 is rounded to the nearest integer by adding
+// 1.5 * 2^23 (the integer lands in the low mantissa bits); d = y - round(y) is
+// exact.  Away from a cell edge round(t - 1/2) = floor(t).  With t = fl(u) *
+// fl(nu/c/du) - 1/2 formed by one FMA, |error of t| <= 3 * 2^-24 |t| < 6e-6 for
+// |t| <= 33 (every facet window here); `edge` flags values within 1e-5 of a
+// cell edge, where the caller takes the FP64 decision instead.
+__device__ __forceinline__ int cell_floor(float uh, float sdu, bool &edge)
 {
-    // |error| of t = fl(fl(u) * fl(s/du)) is below 3 * 2^-24 |t|; keep a 5x margin
-    return fabsf(t - rintf(t)) <= 1.0e-6f * fmaxf(fabsf(t), 1.0f);
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    const float y = fmaf(uh, sdu, -0.5f);
+    const float m = __fadd_rn(y, kMagic);
+    const float d = __fsub_rn(y, __fsub_rn(m, kMagic));
+    edge = fabsf(d) > 0.5f - 1.0e-5f;
+    return __float_as_int(m) - 0x4B400000;
+}
+
+__global__ void residual_kernel(const float4 *__restrict__ d, const float4 *__restrict__ s, int64_t n4,
+                                float4 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = d[i], b = s[i];
+        out[i] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    }
 }
 
 __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__restrict__ v,
@@ -58,8 +77,9 @@ __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__r
     }
 }
 
-template <int CG, bool kUniform, bool kSplit>
-__global__ void __launch_bounds__(kThreads, 2)
+// kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
+template <int CG, bool kUniform, bool kSplit, bool kResid>
+__global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
 extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                   const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
                   int32_t stride, int32_t t_per_chunk, const ChanTable ch,
@@ -184,16 +204,14 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     __sincosf(f * kTwoPi, &sn, &cs);
                 }
                 if (k < C) {
-                    int cell = -1;
-                    const float tu = uh * sdu[c], tv = vh * sdu[c];
-                    if (fabsf(tu) < half + 1.0f && fabsf(tv) < half + 1.0f) {
-                        int iu = (int)floorf(tu), iv = (int)floorf(tv);
-                        if (near_edge(tu)) iu = (int)floor((u[r] * ch.s[k]) / du);
-                        if (near_edge(tv)) iv = (int)floor((v[r] * ch.s[k]) / du);
-                        iu += half;
-                        iv += half;
-                        if (iu >= 0 && iu < N && iv >= 0 && iv < N) cell = iv * N + iu;
-                    }
+                    bool eu, ev;
+                    int iu = cell_floor(uh, sdu[c], eu);
+                    int iv = cell_floor(vh, sdu[c], ev);
+                    if (eu) iu = (int)floor((u[r] * ch.s[k]) / du);
+                    if (ev) iv = (int)floor((v[r] * ch.s[k]) / du);
+                    iu += half;
+                    iv += half;
+                    const int cell = ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) ? iv * N + iu : -1;
                     if (cell != run_cell[c]) {
                         if (run_n[c] > 0) flush(c);
                         run_cell[c] = cell;
@@ -201,9 +219,17 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                         run_re[c] = run_im[c] = 0.0f;
                     }
                     if (cell >= 0) {
-                        const float2 dv = data[r * C + k];
-                        const float2 sv = sky[r * C + k];
-                        const float rr = dv.x - sv.x, ri = dv.y - sv.y;
+                        float rr, ri;
+                        if (kResid) {
+                            const float2 dv = data[r * C + k];
+                            rr = dv.x;
+                            ri = dv.y;
+                        } else {
+                            const float2 dv = data[r * C + k];
+                            const float2 sv = sky[r * C + k];
+                            rr = dv.x - sv.x;
+                            ri = dv.y - sv.y;
+                        }
                         // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn)
                         float xr = fmaf(rr, cs, ri * sn);
                         const float xi = fmaf(ri, cs, -rr * sn);
@@ -314,7 +340,9 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
                       cudaStream_t st)
 {
     const size_t smem = 4 * (size_t)N * N * sizeof(float);
-    auto kern = ch.uniform ? extract_rl_kernel<CG, true, kSplit> : extract_rl_kernel<CG, false, kSplit>;
+    const bool resid = sky == nullptr;
+    auto kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true> : extract_rl_kernel<CG, true, kSplit, false>)
+                           : (resid ? extract_rl_kernel<CG, false, kSplit, true> : extract_rl_kernel<CG, false, kSplit, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -389,11 +417,26 @@ cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st)
 
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, double *facets,
+                           const rlf_params &p, const float *uvw_split, float *resid, double *facets,
                            cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(facets, 0, (size_t)count * 4 * p.facet_n * p.facet_n * sizeof(double), st);
     if (e != cudaSuccess) return e;
+    // several sources read every visibility: form D - V_sky once (one streaming pass)
+    if (p.precision != RLF_PREC_FP64 && resid && count >= 3) {
+        const int64_t n2 = uvw.n_rows * uvw.n_chan;   // complex values
+        if (n2 % 2 == 0) {
+            const int64_t n4 = n2 / 2;
+            const int64_t need = (n4 + kThreads - 1) / kThreads;
+            const int64_t cap = (int64_t)sm_count_x() * 16;
+            residual_kernel<<<(int)(need < cap ? need : cap), kThreads, 0, st>>>(
+                reinterpret_cast<const float4 *>(data), reinterpret_cast<const float4 *>(sky), n4,
+                reinterpret_cast<float4 *>(resid));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            data = resid;
+            sky = nullptr;
+        }
+    }
     if (p.precision == RLF_PREC_MIXED)
         return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, facets, st);
     if (p.precision == RLF_PREC_MIXED_SPLIT)

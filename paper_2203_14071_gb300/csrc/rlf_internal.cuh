@@ -118,6 +118,7 @@ struct Workspace {
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
+    float *resid;           // [n_rows][n_chan][2]: D - V_sky for batched extraction
     size_t bytes;
 };
 
@@ -135,7 +136,7 @@ cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *ta
 cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, double *facets,
+                           const rlf_params &p, const float *uvw_split, float *resid, double *facets,
                            cudaStream_t st);
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
