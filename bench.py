@@ -295,12 +295,13 @@ def main():
                    "update_mode": args.update_mode, "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
         "phases_ms": comp["phases_ms"],
+        "mean_cells_per_facet": comp["mean_cells_per_facet"],
         "gpu_launches": comp["launches_per_step"] * args.steps,
         "clocks": clocks.summary(),
         "measured_unit_peaks": peaks,
         "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2))},
     }
-    line["roofline"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
+    line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -351,6 +352,12 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     sky_ms = timed(lambda: rlf.sky_model(obs, cat, params, sky, ws, stream))
     ext_ms = timed(lambda: rlf.extract_facets(obs, data, sky, cat, 0, n_src, params, facets, ws, stream))
     fit_ms = timed(lambda: rlf.fit_sources(facets, cat, 0, n_src, params, out, ws_fit, stream))
+    # likelihood evaluations of the fit: valid grid points x non-empty cells, per source
+    nn = params.facet_n * params.facet_n
+    n_cells = (facets.view(n_src, 4, nn)[:, 2, :] > 0).sum(dim=1).double()
+    ge = -params.e_max + np.arange(params.n_e) * (2.0 * params.e_max / (params.n_e - 1))
+    n_valid = int((np.add.outer(ge ** 2, ge ** 2) < 1.0).sum()) * params.n_alpha
+    fit_evals = float(n_cells.sum().item()) * n_valid
     upd_ms = timed(lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream))
     chunk = params.chunk if params.chunk > 0 else n_src
     n_chunks = (n_src + chunk - 1) // chunk
@@ -358,29 +365,44 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     # + estimate + prepare + update  (memsets/copies are not kernels of ours)
     launches = 2 + n_chunks * 7
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
-            "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches}
+            "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches,
+            "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item())}
+
+
+# Algorithmic operation counts per unit of work: FP32 ops and
+# MUFU ops per unit, plus per (row, source) overheads of the phase argument.
+OPS = {
+    "sky_model": {"fp32": 10.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
+    "update": {"fp32": 13.0, "mufu": 2.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
+    "extract": {"fp32": 16.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gpair/s"},
+    "fit": {"fp32": 6.0, "mufu": 1.0, "fp32_rs": 0.0, "mufu_rs": 0.0, "unit": "Geval/s"},
+}
+
+
+def roofline_one(name, t_ms, units, row_src, peaks):
+    """ALU roofline: the shortest time the FP32 and MUFU budgets allow for the
+    algorithmic op counts, against the measured unit rates."""
+    o = OPS[name]
+    fp32_rate = max(peaks["fp32_fma_per_s"], peaks.get("fp32x2_fma_per_s", 0.0))
+    mufu_rate = min(peaks["mufu_rsqrt_per_s"], peaks["mufu_sin_per_s"])
+    t_fp32 = (o["fp32"] * units + o["fp32_rs"] * row_src) / fp32_rate
+    t_mufu = (o["mufu"] * units + o["mufu_rs"] * row_src) / mufu_rate
+    t_min = max(t_fp32, t_mufu)
+    t = t_ms * 1e-3
+    return {"kernel": name, "bound": "alu", "limiting_unit": "fp32" if t_fp32 >= t_mufu else "mufu",
+            "unit": o["unit"], "achieved": units / t / 1e9, "peak": units / t_min / 1e9, "frac": t_min / t,
+            "units_per_launch": units, "traffic": None,
+            "peak_basis": "measured FP32 %.3g FMA/s and MUFU %.3g op/s (rlf_peaks_measure)" % (fp32_rate, mufu_rate)}
 
 
 def roofline(comp, peaks, params, n_vis, n_src, R, C):
-    """Roofline of the dominant phase.  The path is ALU bound (no dense contraction,
-    HBM traffic far below the compute time); the limiting unit and its per-unit
-    op counts are stated in the design doc."""
     ph = comp["phases_ms"]
-    name = max(ph, key=ph.get)
-    t = ph[name] * 1e-3
-    if name in ("sky_model", "update", "extract"):
-        # FP64 phase argument and reduction: per (row, source) 3 FMA-class ops for the
-        # argument and 2 x (multiply, round, subtract) for the channel-0 and channel-step
-        # phases = 9 FP64 ops; the sky update evaluates the phase once per source too
-        units = R * n_src
-        ops = 9.0 * units
-        return {"kernel": name, "bound": "alu", "unit": "FP64 Gop/s", "achieved": ops / t / 1e9,
-                "peak": peaks["fp64_fma_per_s"] / 1e9, "frac": ops / t / peaks["fp64_fma_per_s"],
-                "traffic": None, "note": "peak = measured FP64 FMA rate (rlf_peaks_measure)"}
-    # fit: one MUFU rsqrt per (grid point, cell)
-    G = params.n_e * params.n_e * params.n_alpha
-    return {"kernel": name, "bound": "alu", "unit": "MUFU Gop/s", "achieved": None, "peak":
-            peaks["mufu_rsqrt_per_s"] / 1e9, "frac": None, "traffic": None, "grid_points": G}
+    out = {}
+    for name in ("sky_model", "update", "extract"):
+        out[name] = roofline_one(name, ph[name], float(n_vis) * n_src, float(R) * n_src, peaks)
+    out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks)
+    dom = max(ph, key=ph.get)
+    return out[dom], out
 
 
 def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, args):

@@ -64,7 +64,8 @@ class Params(ctypes.Structure):
 
 
 class Peaks(ctypes.Structure):
-    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp32x2_fma_per_s", ctypes.c_double),
+                ("fp64_fma_per_s", ctypes.c_double),
                 ("mufu_rsqrt_per_s", ctypes.c_double), ("mufu_sin_per_s", ctypes.c_double),
                 ("sm_count", ctypes.c_int)]
 

@@ -88,6 +88,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
+    (void)sky;
     float *sre = reinterpret_cast<float *>(smraw);
     float *sim = sre + NN;
     int *scnt = reinterpret_cast<int *>(sim + NN);
@@ -149,18 +150,57 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
         const int64_t n_time = (n_rows + stride - 1) / stride;
         const int64_t t0 = (int64_t)blockIdx.z * t_per_chunk;
         const int64_t t1 = min(n_time, t0 + t_per_chunk);
+        // the residual of a row's channel group is read as float4 pairs when the
+        // layout allows (even channel count, groups of >= 2 channels)
+        const bool vec = kResid && CG >= 2 && (C % 2 == 0);
+        // split baselines of the next row are fetched one iteration ahead
+        float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
+        if (kSplit && t0 < t1) {
+            const int64_t r = t0 * stride + bl;
+            if (r < n_rows) {
+                nuh = us[r];
+                nul = us[n_rows + r];
+                nvh = us[2 * n_rows + r];
+                nvl = us[3 * n_rows + r];
+                nwh = us[4 * n_rows + r];
+                nwl = us[5 * n_rows + r];
+            }
+        }
         for (int64_t t = t0; t < t1; ++t) {
             const int64_t r = t * stride + bl;
             if (r >= n_rows) break;
+            float2 rv[CG];
+            if (vec) {
+                const float4 *src4 = reinterpret_cast<const float4 *>(data + (r * C + k0));
+#pragma unroll
+                for (int j = 0; j < CG / 2; ++j) {
+                    if (k0 + 2 * j < C) {
+                        const float4 q4 = src4[j];
+                        rv[2 * j] = make_float2(q4.x, q4.y);
+                        rv[2 * j + 1] = make_float2(q4.z, q4.w);
+                    } else {
+                        rv[2 * j] = rv[2 * j + 1] = make_float2(0.0f, 0.0f);
+                    }
+                }
+            }
             float uh, ul, vh, vl, wh, wl;
             double ph = 0.0;
             if (kSplit) {
-                uh = us[r];
-                ul = us[n_rows + r];
-                vh = us[2 * n_rows + r];
-                vl = us[3 * n_rows + r];
-                wh = us[4 * n_rows + r];
-                wl = us[5 * n_rows + r];
+                uh = nuh;
+                ul = nul;
+                vh = nvh;
+                vl = nvl;
+                wh = nwh;
+                wl = nwl;
+                const int64_t rn = r + stride;
+                if (t + 1 < t1 && rn < n_rows) {
+                    nuh = us[rn];
+                    nul = us[n_rows + rn];
+                    nvh = us[2 * n_rows + rn];
+                    nvl = us[3 * n_rows + rn];
+                    nwh = us[4 * n_rows + rn];
+                    nwl = us[5 * n_rows + rn];
+                }
             } else {
                 const double ud = u[r], vd = v[r], wd = w[r];
                 ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
@@ -220,7 +260,10 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     }
                     if (cell >= 0) {
                         float rr, ri;
-                        if (kResid) {
+                        if (vec) {
+                            rr = rv[c].x;
+                            ri = rv[c].y;
+                        } else if (kResid) {
                             const float2 dv = data[r * C + k];
                             rr = dv.x;
                             ri = dv.y;

@@ -11,7 +11,8 @@
 //                     alpha nodes for every cell: one quadratic form per cell,
 //                     then per alpha one FMA, one rsqrt and the a, b products.
 //                     Mixed precision sums the products in FP32 over a tile of
-//                     cells and adds the tile sums to FP64 accumulators.
+//                     cells and adds the tile sums to FP64 accumulators; two
+//                     scalelength nodes share each paired (f32x2) instruction.
 //   estimate_kernel   one CTA per facet, FP64 throughout: logL, alpha marginal,
 //                     threshold, moments, MAP point, flags.
 #include <cfloat>
@@ -168,31 +169,65 @@ grid_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
         }
         __syncthreads();
         if (!on) continue;
-        T pa[AG], pb[AG];
+        if constexpr (std::is_same<T, float>::value && AG % 2 == 0) {
+            // two scalelength nodes per paired FP32 instruction
+            f32x2 c2[AG / 2], pa2[AG / 2], pb2[AG / 2];
+            const f32x2 one2 = pk2(1.0f, 1.0f), zero2 = pk2(0.0f, 0.0f);
 #pragma unroll
-        for (int j = 0; j < AG; ++j) pa[j] = pb[j] = T(0);
-        for (int c = 0; c < nt; ++c) {
-            const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
-            const T A = sm[3][c], B = sm[4][c];
+            for (int j = 0; j < AG / 2; ++j) {
+                c2[j] = pk2(calpha[2 * j], calpha[2 * j + 1]);
+                pa2[j] = pb2[j] = zero2;
+            }
+            for (int c = 0; c < nt; ++c) {
+                const float Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                const f32x2 Q2 = pk2(Q, Q), A2 = pk2(sm[3][c], sm[3][c]), B2 = pk2(sm[4][c], sm[4][c]);
+#pragma unroll
+                for (int j = 0; j < AG / 2; ++j) {
+                    float x0, x1;
+                    up2(fma2(c2[j], Q2, one2), x0, x1);
+                    const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
+                    const f32x2 M2 = mul2(mul2(r2, r2), r2);
+                    pa2[j] = fma2(mul2(A2, M2), M2, pa2[j]);
+                    pb2[j] = fma2(B2, M2, pb2[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < AG / 2; ++j) {
+                float a0, a1, b0, b1;
+                up2(pa2[j], a0, a1);
+                up2(pb2[j], b0, b1);
+                da[2 * j] += (double)a0;
+                da[2 * j + 1] += (double)a1;
+                db[2 * j] += (double)b0;
+                db[2 * j + 1] += (double)b1;
+            }
+        } else {
+            T pa[AG], pb[AG];
+#pragma unroll
+            for (int j = 0; j < AG; ++j) pa[j] = pb[j] = T(0);
+            for (int c = 0; c < nt; ++c) {
+                const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                const T A = sm[3][c], B = sm[4][c];
+#pragma unroll
+                for (int j = 0; j < AG; ++j) {
+                    const T x = calpha[j] * Q + T(1);
+                    T M;
+                    if constexpr (std::is_same<T, float>::value) {
+                        const T r = rsqrtf(x);
+                        M = r * r * r;
+                    } else {
+                        M = T(1) / (x * sqrt(x));
+                    }
+                    const T AM = A * M;
+                    pa[j] += AM * M;
+                    pb[j] += B * M;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < AG; ++j) {
-                const T x = calpha[j] * Q + T(1);
-                T M;
-                if constexpr (std::is_same<T, float>::value) {
-                    const T r = rsqrtf(x);
-                    M = r * r * r;
-                } else {
-                    M = T(1) / (x * sqrt(x));
-                }
-                const T AM = A * M;
-                pa[j] += AM * M;
-                pb[j] += B * M;
+                da[j] += (double)pa[j];
+                db[j] += (double)pb[j];
             }
-        }
-#pragma unroll
-        for (int j = 0; j < AG; ++j) {
-            da[j] += (double)pa[j];
-            db[j] += (double)pb[j];
         }
     }
     if (e_idx < ne2) {

@@ -24,6 +24,30 @@ __global__ void fma32_kernel(float *out, int iters, float a, float b)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void fma32x2_kernel(float *out, int iters, float a, float b)
+{
+    unsigned long long x[kChains];
+    unsigned long long av, bv;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a), "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b), "f"(b));
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        const float x0 = threadIdx.x * 1e-3f + c, x1 = x0 + 0.5f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(x0), "f"(x1));
+    }
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(av), "l"(bv));
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        float x0, x1;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(x[c]));
+        s += x0 + x1;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void fma64_kernel(double *out, int iters, double a, double b)
 {
     double x[kChains];
@@ -103,6 +127,8 @@ extern "C" int rlf_peaks_measure(void *scratch, size_t scratch_bytes, void *stre
     double ms;
     ms = time_ms([&] { fma32_kernel<<<blocks, kThreads, 0, st>>>(f, it32, 0.999999f, 1e-7f); }, st);
     out->fp32_fma_per_s = threads * it32 * kChains / (ms * 1e-3);
+    ms = time_ms([&] { fma32x2_kernel<<<blocks, kThreads, 0, st>>>(f, it32, 0.999999f, 1e-7f); }, st);
+    out->fp32x2_fma_per_s = 2.0 * threads * it32 * kChains / (ms * 1e-3);
     ms = time_ms([&] { fma64_kernel<<<blocks, kThreads, 0, st>>>(d, it64, 0.999999, 1e-7); }, st);
     out->fp64_fma_per_s = threads * it64 * kChains / (ms * 1e-3);
     ms = time_ms([&] { rsqrt_kernel<<<blocks, kThreads, 0, st>>>(f, itmu); }, st);
