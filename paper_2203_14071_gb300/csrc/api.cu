@@ -116,6 +116,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
     const size_t o_split = take(ext ? 6 * rows * sizeof(float) : 0);
     const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
+    const size_t o_part = take(ext ? (size_t)kMaxPartials * 4 * NN * sizeof(float) : 0);
     const size_t total = off + 256;   // slack for aligning an arbitrary base pointer
     if (ws && base) {
         char *b = reinterpret_cast<char *>(align_up(reinterpret_cast<size_t>(base), 256));
@@ -132,6 +133,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->facets = reinterpret_cast<double *>(b + o_fac);
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
         ws->resid = reinterpret_cast<float *>(b + o_resid);
+        ws->partial = reinterpret_cast<float *>(b + o_part);
         ws->bytes = total;
     }
     return total;
@@ -262,7 +264,7 @@ rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const f
                            nullptr, *p, ws.table, ws.status, st);
     if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
     if (e == cudaSuccess)
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, ws.resid, facets, st);
+        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, ws.resid, ws.partial, facets, st);
     return cuda_status(e);
 }
 
@@ -320,7 +322,7 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
         e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.uvw_split, ws.resid,
-                           ws.facets, st);
+                           ws.partial, ws.facets, st);
         if (e != cudaSuccess) break;
         e = launch_fit(ws.facets, ws.table + first, cnt, *p, ws, *out, first, st);
         if (e != cudaSuccess) break;

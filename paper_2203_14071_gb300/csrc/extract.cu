@@ -6,16 +6,18 @@
 // exp(+2 pi i phi_i), so after the shift it is the real number S s M(k) and
 // x = (D - V_sky) exp(-2 pi i phi_i) + S s M(k).
 //
-// Mixed-precision kernel (extract_rl_kernel).  A CTA owns (source, block of
-// baselines, chunk of time steps) and keeps a private copy of the facet in
-// shared memory.  Each thread walks one baseline's time series for a group of
-// channels.  A baseline's uv track moves slowly (a few per cent of a cell per
-// 60 s step at the facet sizes of the method), so consecutive visibilities of
-// one channel usually fall in the same cell: the thread sums that run in
-// registers and adds it to shared memory only when the cell changes.  At the
-// end the non-empty cells are added to the FP64 facet in global memory.
-// blockIdx.x runs over the sources, so the CTAs reading the same rows run
-// together and share them through L2.
+// Mixed-precision kernel (extract_rl_kernel).  A CTA owns (source, part) and
+// keeps a private copy of the facet in shared memory; the part is an
+// interleaved share of the blocks of baselines.  Each thread walks one
+// baseline's whole time series for a group of channels.  A baseline's uv track
+// moves slowly (a few per cent of a cell per 60 s step at the facet sizes of the
+// method), so consecutive visibilities of one channel usually fall in the same
+// cell: the thread sums that run in registers and adds it to shared memory only
+// when the cell changes.  At the end the CTA stores its partial facet with
+// plain coalesced stores, and facet_reduce_kernel sums the parts of each cell in
+// FP64 in a fixed order (no global atomics; the facets are bitwise
+// reproducible).  blockIdx.x runs over the sources, so the CTAs reading the same
+// baselines run together and share them through L2.
 //
 // Shared-memory planes: sum Re x, sum Im x (FP32), count (int32), and the sum of
 // spec - spec_off (FP32, spec_off the band mean; the flush adds count * spec_off
@@ -82,9 +84,9 @@ template <int CG, bool kUniform, bool kSplit, bool kResid>
 __global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
 extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                   const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
-                  int32_t stride, int32_t t_per_chunk, const ChanTable ch,
+                  int32_t stride, int32_t n_parts, const ChanTable ch,
                   const float2 *__restrict__ data, const float2 *__restrict__ sky,
-                  const SrcRow *__restrict__ table, int32_t N, double *__restrict__ facets)
+                  const SrcRow *__restrict__ table, int32_t N, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
@@ -106,15 +108,15 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
 
     const int C = ch.n;
     const int n_groups = (C + CG - 1) / CG;
-    const int bpc = kThreads / n_groups;           // baselines per CTA
+    const int bpc = kThreads / n_groups;           // baselines per block
     const int g = threadIdx.x / bpc;
-    const int bl = blockIdx.y * bpc + threadIdx.x % bpc;
+    const int lane_b = threadIdx.x % bpc;
     const int k0 = g * CG;
     const int half = N / 2;
     const double du = S.du;
     constexpr float kTwoPi = 6.28318530717958647692f;
 
-    if (S.flux > 0.0 && g < n_groups && bl < stride) {
+    if (S.flux > 0.0 && g < n_groups) {
         // per-channel constants used for every visibility stay in registers; the
         // rest is read from the kernel-parameter bank when needed
         float sdu[CG], f2[CG], fspec[CG];
@@ -133,12 +135,6 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
 
         int run_cell[CG], run_n[CG];
         float run_re[CG], run_im[CG];
-#pragma unroll
-        for (int c = 0; c < CG; ++c) {
-            run_cell[c] = -1;
-            run_n[c] = 0;
-            run_re[c] = run_im[c] = 0.0f;
-        }
         auto flush = [&](int c) {
             const int cell = run_cell[c];
             atomicAdd(&sre[cell], run_re[c]);
@@ -147,12 +143,20 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
             atomicAdd(&ssp[cell], (float)run_n[c] * (float)(ch.spec[k0 + c] - ch.spec_off));
         };
 
-        const int64_t n_time = (n_rows + stride - 1) / stride;
-        const int64_t t0 = (int64_t)blockIdx.z * t_per_chunk;
-        const int64_t t1 = min(n_time, t0 + t_per_chunk);
+        const int64_t t0 = 0, t1 = (n_rows + stride - 1) / stride;
+        const int n_blocks = (stride + bpc - 1) / bpc;
         // the residual of a row's channel group is read as float4 pairs when the
         // layout allows (even channel count, groups of >= 2 channels)
         const bool vec = kResid && CG >= 2 && (C % 2 == 0);
+        for (int blk = blockIdx.y; blk < n_blocks; blk += n_parts) {
+        const int bl = blk * bpc + lane_b;
+        if (bl >= stride) continue;
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+            run_cell[c] = -1;
+            run_n[c] = 0;
+            run_re[c] = run_im[c] = 0.0f;
+        }
         // split baselines of the next row are fetched one iteration ahead
         float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
         if (kSplit && t0 < t1) {
@@ -293,18 +297,40 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
 #pragma unroll
         for (int c = 0; c < CG; ++c)
             if (run_n[c] > 0) flush(c);
-    }
-    __syncthreads();
-    double *f = facets + (size_t)s * 4 * NN;
-    for (int i = threadIdx.x; i < NN; i += kThreads) {
-        const int n = scnt[i];
-        if (n != 0) {
-            atomicAdd(&f[i], (double)sre[i]);
-            atomicAdd(&f[NN + i], (double)sim[i]);
-            atomicAdd(&f[2 * NN + i], (double)n);
-            atomicAdd(&f[3 * NN + i], (double)ssp[i] + (double)n * ch.spec_off);
         }
     }
+    __syncthreads();
+    // this CTA's partial facet: plain stores; planes Re, Im, count (int bits), spec - spec_off
+    float *o = partial + ((size_t)s * n_parts + blockIdx.y) * 4 * NN;
+    for (int i = threadIdx.x; i < NN; i += kThreads) {
+        o[i] = sre[i];
+        o[NN + i] = sim[i];
+        o[2 * NN + i] = __int_as_float(scnt[i]);
+        o[3 * NN + i] = ssp[i];
+    }
+}
+
+// Sum of the parts of every cell in FP64, in part order.
+__global__ void facet_reduce_kernel(const float *__restrict__ partial, int32_t n_parts, int32_t NN,
+                                    double spec_off, double *__restrict__ facets)
+{
+    const int s = blockIdx.y;
+    const int cell = blockIdx.x * kThreads + threadIdx.x;
+    if (cell >= NN) return;
+    double re = 0.0, im = 0.0, sp = 0.0;
+    long long n = 0;
+    for (int p = 0; p < n_parts; ++p) {
+        const float *q = partial + ((size_t)s * n_parts + p) * 4 * NN;
+        re += (double)q[cell];
+        im += (double)q[NN + cell];
+        n += __float_as_int(q[2 * NN + cell]);
+        sp += (double)q[3 * NN + cell];
+    }
+    double *f = facets + (size_t)s * 4 * NN;
+    f[cell] = re;
+    f[NN + cell] = im;
+    f[2 * NN + cell] = (double)n;
+    f[3 * NN + cell] = sp + (double)n * spec_off;
 }
 
 // FP64 extraction: every operation in double precision, one visibility at a time.
@@ -379,8 +405,8 @@ int sm_count_x()
 
 template <int CG, bool kSplit>
 cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                      const SrcRow *table, int32_t count, int32_t N, const float *us, double *facets,
-                      cudaStream_t st)
+                      const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
+                      double *facets, cudaStream_t st)
 {
     const size_t smem = 4 * (size_t)N * N * sizeof(float);
     const bool resid = sky == nullptr;
@@ -396,34 +422,39 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
     const int32_t stride = uvw.n_baselines > 0 ? uvw.n_baselines : 1024;
     const int n_groups = (ch.n + CG - 1) / CG;
     const int bpc = kThreads / n_groups;
-    const int64_t bl_blocks = (stride + bpc - 1) / bpc;
-    const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
-    // enough CTAs for about four waves; split the time axis only when the
-    // (source, baseline block) pairs alone are too few
-    const int64_t target = (int64_t)sm_count_x() * per_sm * 4;
-    int64_t t_chunks = (target + count * bl_blocks - 1) / (count * bl_blocks);
-    if (t_chunks < 1) t_chunks = 1;
-    if (t_chunks > n_time) t_chunks = n_time;
-    if (t_chunks > 65535) t_chunks = 65535;
-    const int64_t t_per_chunk = (n_time + t_chunks - 1) / t_chunks;
-    t_chunks = (n_time + t_per_chunk - 1) / t_per_chunk;
-    if (bl_blocks > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid(count, (unsigned)bl_blocks, (unsigned)t_chunks);
-    kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)t_per_chunk, ch,
-                                       reinterpret_cast<const float2 *>(data),
-                                       reinterpret_cast<const float2 *>(sky), table, N, facets);
-    return cudaGetLastError();
+    const int64_t n_blocks = (stride + bpc - 1) / bpc;
+    const int NN = N * N;
+    const int64_t slots = (int64_t)sm_count_x() * per_sm;
+    // sources are handled in batches whose partial facets fit the workspace
+    for (int32_t first = 0; first < count; first += kMaxPartials) {
+        const int32_t cnt = count - first < kMaxPartials ? count - first : kMaxPartials;
+        // parts per source: about two waves of CTAs, at most one part per baseline block
+        int64_t parts = (2 * slots + cnt - 1) / cnt;
+        if (parts > n_blocks) parts = n_blocks;
+        if (parts > kMaxPartials / cnt) parts = kMaxPartials / cnt;
+        if (parts < 1) parts = 1;
+        dim3 grid(cnt, (unsigned)parts);
+        kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
+                                           reinterpret_cast<const float2 *>(data),
+                                           reinterpret_cast<const float2 *>(sky), table + first, N, partial);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dim3 rgrid((NN + kThreads - 1) / kThreads, cnt);
+        facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
+                                                        facets + (size_t)first * 4 * NN);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <bool kSplit>
 cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                         const SrcRow *table, int32_t count, int32_t N, const float *us, double *facets,
-                         cudaStream_t st)
+                         const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
+                         double *facets, cudaStream_t st)
 {
-    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
-    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
-    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
-    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, facets, st);
+    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
+    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
+    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
+    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
 }
 
 cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
@@ -460,11 +491,14 @@ cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st)
 
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, float *resid, double *facets,
-                           cudaStream_t st)
+                           const rlf_params &p, const float *uvw_split, float *resid, float *partial,
+                           double *facets, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(facets, 0, (size_t)count * 4 * p.facet_n * p.facet_n * sizeof(double), st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (p.precision == RLF_PREC_FP64) {
+        e = cudaMemsetAsync(facets, 0, (size_t)count * 4 * p.facet_n * p.facet_n * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+    }
     // several sources read every visibility: form D - V_sky once (one streaming pass)
     if (p.precision != RLF_PREC_FP64 && resid && count >= 3) {
         const int64_t n2 = uvw.n_rows * uvw.n_chan;   // complex values
@@ -481,9 +515,9 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
         }
     }
     if (p.precision == RLF_PREC_MIXED)
-        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, facets, st);
+        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, partial, facets, st);
     if (p.precision == RLF_PREC_MIXED_SPLIT)
-        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, facets, st);
+        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, partial, facets, st);
     return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
 }
 

@@ -18,6 +18,7 @@ constexpr int kSkyTile = 128;                            // sources staged per s
 constexpr int kCellTile = 128;                           // facet cells staged per tile in the fit
 constexpr int kAlphaPerThread = 4;                       // scalelength nodes per fit thread
 constexpr int kMaxNe = 32;                               // grid nodes per e component (estimator smem)
+constexpr int kMaxPartials = 2048;                       // (source, part) partial facets per extraction batch
 
 // Per-source constants derived on the device from the catalogue (Sec. 2.2, 2.3).
 struct SrcRow {
@@ -156,6 +157,7 @@ struct Workspace {
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
     float *resid;           // [n_rows][n_chan][2]: D - V_sky for batched extraction
+    float *partial;         // [kMaxPartials][4][N*N]: per-CTA partial facets of the extraction
     size_t bytes;
 };
 
@@ -173,8 +175,8 @@ cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *ta
 cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, float *resid, double *facets,
-                           cudaStream_t st);
+                           const rlf_params &p, const float *uvw_split, float *resid, float *partial,
+                           double *facets, cudaStream_t st);
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
                        int32_t out_offset, cudaStream_t st);
