@@ -80,6 +80,16 @@ __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__r
 }
 
 // kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
+// Flush queue: a lane whose run of equal cells ends appends the run to its
+// warp's queue (ballot + popc, no divergence); when 32 entries are waiting the
+// warp adds them to the shared-memory facet with all lanes active.
+struct RunEntry {
+    int cell, n;
+    float re, im, sp;
+};
+constexpr int kQueue = 64;   // entries per warp
+
+// kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
 template <int CG, bool kUniform, bool kSplit, bool kResid>
 __global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
 extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
@@ -95,8 +105,12 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     float *sim = sre + NN;
     int *scnt = reinterpret_cast<int *>(sim + NN);
     float *ssp = reinterpret_cast<float *>(scnt + NN);
+    RunEntry *queue = reinterpret_cast<RunEntry *>(ssp + NN);
     const int s = blockIdx.x;
     const SrcRow S = table[s];
+    const int lane = threadIdx.x & 31;
+    RunEntry *wq = queue + (threadIdx.x >> 5) * kQueue;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     for (int i = threadIdx.x; i < NN; i += kThreads) {
         sre[i] = 0.0f;
@@ -111,153 +125,180 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     const int bpc = kThreads / n_groups;           // baselines per block
     const int g = threadIdx.x / bpc;
     const int lane_b = threadIdx.x % bpc;
-    const int k0 = g * CG;
+    const bool group_on = g < n_groups;
+    const int k0 = group_on ? g * CG : 0;
     const int half = N / 2;
     const double du = S.du;
     constexpr float kTwoPi = 6.28318530717958647692f;
+    int qn = 0;                                    // warp-uniform queue length
 
-    if (S.flux > 0.0 && g < n_groups) {
+    auto drain32 = [&]() {
+        __syncwarp();
+        const RunEntry e = wq[lane];
+        atomicAdd(&sre[e.cell], e.re);
+        atomicAdd(&sim[e.cell], e.im);
+        atomicAdd(&scnt[e.cell], e.n);
+        atomicAdd(&ssp[e.cell], e.sp);
+        __syncwarp();
+        const int rest = qn - 32;
+        if (lane < rest) wq[lane] = wq[32 + lane];
+        __syncwarp();
+        qn = rest;
+    };
+    // every lane of the warp calls push with its own predicate
+    auto push = [&](bool pf, int cell, int n, float re, float im, float sp) {
+        const unsigned m = __ballot_sync(0xffffffffu, pf);
+        if (m == 0u) return;
+        if (pf) {
+            RunEntry e;
+            e.cell = cell;
+            e.n = n;
+            e.re = re;
+            e.im = im;
+            e.sp = sp;
+            wq[qn + __popc(m & lt_mask)] = e;
+        }
+        qn += __popc(m);
+        if (qn >= 32) drain32();
+    };
+
+    if (S.flux > 0.0) {
         // per-channel constants used for every visibility stay in registers; the
         // rest is read from the kernel-parameter bank when needed
-        float sdu[CG], f2[CG], fspec[CG];
+        float sdu[CG], f2[CG], fspec[CG], dsp[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
             const int k = min(k0 + c, C - 1);
             sdu[c] = (float)(ch.s[k] / du);
             f2[c] = (float)(ch.s[k] * ch.s[k]);
             fspec[c] = (float)(S.flux * ch.spec[k]);
+            dsp[c] = (float)(ch.spec[k] - ch.spec_off);
         }
         const float q0 = (float)S.q[0], q1 = (float)S.q[1], q2 = (float)S.q[2];
         float lh, ll, mh, ml, nh, nl;
         split_double(S.l, lh, ll);
         split_double(S.m, mh, ml);
         split_double(S.n1, nh, nl);
-
-        int run_cell[CG], run_n[CG];
-        float run_re[CG], run_im[CG];
-        auto flush = [&](int c) {
-            const int cell = run_cell[c];
-            atomicAdd(&sre[cell], run_re[c]);
-            atomicAdd(&sim[cell], run_im[c]);
-            atomicAdd(&scnt[cell], run_n[c]);
-            atomicAdd(&ssp[cell], (float)run_n[c] * (float)(ch.spec[k0 + c] - ch.spec_off));
-        };
-
-        const int64_t t0 = 0, t1 = (n_rows + stride - 1) / stride;
+        const int64_t n_time = (n_rows + stride - 1) / stride;
         const int n_blocks = (stride + bpc - 1) / bpc;
         // the residual of a row's channel group is read as float4 pairs when the
         // layout allows (even channel count, groups of >= 2 channels)
         const bool vec = kResid && CG >= 2 && (C % 2 == 0);
+
+        int run_cell[CG], run_n[CG];
+        float run_re[CG], run_im[CG];
+        // every lane runs every iteration (the queue's ballots need the whole warp);
+        // lanes without a visibility carry the predicate row_on = false
         for (int blk = blockIdx.y; blk < n_blocks; blk += n_parts) {
-        const int bl = blk * bpc + lane_b;
-        if (bl >= stride) continue;
-#pragma unroll
-        for (int c = 0; c < CG; ++c) {
-            run_cell[c] = -1;
-            run_n[c] = 0;
-            run_re[c] = run_im[c] = 0.0f;
-        }
-        // split baselines of the next row are fetched one iteration ahead
-        float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
-        if (kSplit && t0 < t1) {
-            const int64_t r = t0 * stride + bl;
-            if (r < n_rows) {
-                nuh = us[r];
-                nul = us[n_rows + r];
-                nvh = us[2 * n_rows + r];
-                nvl = us[3 * n_rows + r];
-                nwh = us[4 * n_rows + r];
-                nwl = us[5 * n_rows + r];
-            }
-        }
-        for (int64_t t = t0; t < t1; ++t) {
-            const int64_t r = t * stride + bl;
-            if (r >= n_rows) break;
-            float2 rv[CG];
-            if (vec) {
-                const float4 *src4 = reinterpret_cast<const float4 *>(data + (r * C + k0));
-#pragma unroll
-                for (int j = 0; j < CG / 2; ++j) {
-                    if (k0 + 2 * j < C) {
-                        const float4 q4 = src4[j];
-                        rv[2 * j] = make_float2(q4.x, q4.y);
-                        rv[2 * j + 1] = make_float2(q4.z, q4.w);
-                    } else {
-                        rv[2 * j] = rv[2 * j + 1] = make_float2(0.0f, 0.0f);
-                    }
-                }
-            }
-            float uh, ul, vh, vl, wh, wl;
-            double ph = 0.0;
-            if (kSplit) {
-                uh = nuh;
-                ul = nul;
-                vh = nvh;
-                vl = nvl;
-                wh = nwh;
-                wl = nwl;
-                const int64_t rn = r + stride;
-                if (t + 1 < t1 && rn < n_rows) {
-                    nuh = us[rn];
-                    nul = us[n_rows + rn];
-                    nvh = us[2 * n_rows + rn];
-                    nvl = us[3 * n_rows + rn];
-                    nwh = us[4 * n_rows + rn];
-                    nwl = us[5 * n_rows + rn];
-                }
-            } else {
-                const double ud = u[r], vd = v[r], wd = w[r];
-                ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
-                uh = (float)ud;
-                vh = (float)vd;
-                ul = vl = wh = wl = 0.0f;
-            }
-            const float uu = uh * uh, uv = uh * vh, vv = vh * vh;
-            const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
-            float P = 0.0f, E = 0.0f;
-            if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
-            float sn = 0.0f, cs = 1.0f, sd = 0.0f, cd = 1.0f;
-            if (kUniform) {
-                float f0, fd = 0.0f;
-                if (kSplit) {
-                    f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
-                    if (CG > 1) fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
-                } else {
-                    const double tt = ph * ch.s[k0];
-                    f0 = (float)(tt - rint(tt));
-                    if (CG > 1) {
-                        const double td = ph * ch.ds;
-                        fd = (float)(td - rint(td));
-                    }
-                }
-                __sincosf(f0 * kTwoPi, &sn, &cs);
-                if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
-            }
+            const int bl = blk * bpc + lane_b;
+            const bool lane_on = group_on && bl < stride;
 #pragma unroll
             for (int c = 0; c < CG; ++c) {
-                const int k = k0 + c;
-                if (!kUniform) {
-                    const int kk = min(k, C - 1);
-                    float f;
-                    if (kSplit) {
-                        f = frac_cycles(P, E, ch.s_hi[kk], ch.s_lo[kk]);
-                    } else {
-                        const double tt = ph * ch.s[kk];
-                        f = (float)(tt - rint(tt));
+                run_cell[c] = -1;
+                run_n[c] = 0;
+                run_re[c] = run_im[c] = 0.0f;
+            }
+            // split baselines of the next row are fetched one iteration ahead
+            float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
+            if (kSplit && lane_on && bl < n_rows) {
+                nuh = us[bl];
+                nul = us[n_rows + bl];
+                nvh = us[2 * n_rows + bl];
+                nvl = us[3 * n_rows + bl];
+                nwh = us[4 * n_rows + bl];
+                nwl = us[5 * n_rows + bl];
+            }
+            for (int64_t t = 0; t < n_time; ++t) {
+                const int64_t r = t * stride + bl;
+                const bool row_on = lane_on && r < n_rows;
+                float2 rv[CG];
+                if (vec && row_on) {
+                    const float4 *src4 = reinterpret_cast<const float4 *>(data + (r * C + k0));
+#pragma unroll
+                    for (int j = 0; j < CG / 2; ++j) {
+                        if (k0 + 2 * j < C) {
+                            const float4 q4 = src4[j];
+                            rv[2 * j] = make_float2(q4.x, q4.y);
+                            rv[2 * j + 1] = make_float2(q4.z, q4.w);
+                        } else {
+                            rv[2 * j] = rv[2 * j + 1] = make_float2(0.0f, 0.0f);
+                        }
                     }
-                    __sincosf(f * kTwoPi, &sn, &cs);
                 }
-                if (k < C) {
-                    bool eu, ev;
-                    int iu = cell_floor(uh, sdu[c], eu);
-                    int iv = cell_floor(vh, sdu[c], ev);
-                    if (eu) iu = (int)floor((u[r] * ch.s[k]) / du);
-                    if (ev) iv = (int)floor((v[r] * ch.s[k]) / du);
-                    iu += half;
-                    iv += half;
-                    const int cell = ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) ? iv * N + iu : -1;
-                    if (cell != run_cell[c]) {
-                        if (run_n[c] > 0) flush(c);
+                float uh = 0, ul = 0, vh = 0, vl = 0, wh = 0, wl = 0;
+                double ph = 0.0;
+                if (kSplit) {
+                    uh = nuh;
+                    ul = nul;
+                    vh = nvh;
+                    vl = nvl;
+                    wh = nwh;
+                    wl = nwl;
+                    const int64_t rn = r + stride;
+                    if (lane_on && t + 1 < n_time && rn < n_rows) {
+                        nuh = us[rn];
+                        nul = us[n_rows + rn];
+                        nvh = us[2 * n_rows + rn];
+                        nvl = us[3 * n_rows + rn];
+                        nwh = us[4 * n_rows + rn];
+                        nwl = us[5 * n_rows + rn];
+                    }
+                } else if (row_on) {
+                    const double ud = u[r], vd = v[r], wd = w[r];
+                    ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
+                    uh = (float)ud;
+                    vh = (float)vd;
+                }
+                const float uu = uh * uh, uv = uh * vh, vv = vh * vh;
+                const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
+                float P = 0.0f, E = 0.0f;
+                if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
+                float sn = 0.0f, cs = 1.0f, sd = 0.0f, cd = 1.0f;
+                if (kUniform) {
+                    float f0, fd = 0.0f;
+                    if (kSplit) {
+                        f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
+                        if (CG > 1) fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
+                    } else {
+                        const double tt = ph * ch.s[k0];
+                        f0 = (float)(tt - rint(tt));
+                        if (CG > 1) {
+                            const double td = ph * ch.ds;
+                            fd = (float)(td - rint(td));
+                        }
+                    }
+                    __sincosf(f0 * kTwoPi, &sn, &cs);
+                    if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
+                }
+#pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    const int k = k0 + c;
+                    if (!kUniform) {
+                        const int kk = min(k, C - 1);
+                        float f;
+                        if (kSplit) {
+                            f = frac_cycles(P, E, ch.s_hi[kk], ch.s_lo[kk]);
+                        } else {
+                            const double tt = ph * ch.s[kk];
+                            f = (float)(tt - rint(tt));
+                        }
+                        __sincosf(f * kTwoPi, &sn, &cs);
+                    }
+                    int cell = -1;
+                    if (row_on && k < C) {
+                        bool eu, ev;
+                        int iu = cell_floor(uh, sdu[c], eu);
+                        int iv = cell_floor(vh, sdu[c], ev);
+                        if (eu) iu = (int)floor((u[r] * ch.s[k]) / du);
+                        if (ev) iv = (int)floor((v[r] * ch.s[k]) / du);
+                        iu += half;
+                        iv += half;
+                        if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
+                    }
+                    const bool change = cell != run_cell[c];
+                    push(change && run_n[c] > 0, run_cell[c], run_n[c], run_re[c], run_im[c],
+                         (float)run_n[c] * dsp[c]);
+                    if (change) {
                         run_cell[c] = cell;
                         run_n[c] = 0;
                         run_re[c] = run_im[c] = 0.0f;
@@ -286,18 +327,26 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                         run_im[c] += xi;
                         run_n[c] += 1;
                     }
-                }
-                if (kUniform && c + 1 < CG) {
-                    const float cn = cs * cd - sn * sd;
-                    sn = fmaf(cs, sd, sn * cd);
-                    cs = cn;
+                    if (kUniform && c + 1 < CG) {
+                        const float cn = cs * cd - sn * sd;
+                        sn = fmaf(cs, sd, sn * cd);
+                        cs = cn;
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int c = 0; c < CG; ++c)
-            if (run_n[c] > 0) flush(c);
+            for (int c = 0; c < CG; ++c)
+                push(run_n[c] > 0, run_cell[c], run_n[c], run_re[c], run_im[c], (float)run_n[c] * dsp[c]);
         }
+    }
+    // the queue's remainder
+    __syncwarp();
+    if (lane < qn) {
+        const RunEntry e = wq[lane];
+        atomicAdd(&sre[e.cell], e.re);
+        atomicAdd(&sim[e.cell], e.im);
+        atomicAdd(&scnt[e.cell], e.n);
+        atomicAdd(&ssp[e.cell], e.sp);
     }
     __syncthreads();
     // this CTA's partial facet: plain stores; planes Re, Im, count (int bits), spec - spec_off
@@ -408,7 +457,7 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
                       const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
                       double *facets, cudaStream_t st)
 {
-    const size_t smem = 4 * (size_t)N * N * sizeof(float);
+    const size_t smem = 4 * (size_t)N * N * sizeof(float) + (kThreads / 32) * kQueue * sizeof(RunEntry);
     const bool resid = sky == nullptr;
     auto kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true> : extract_rl_kernel<CG, true, kSplit, false>)
                            : (resid ? extract_rl_kernel<CG, false, kSplit, true> : extract_rl_kernel<CG, false, kSplit, false>);
