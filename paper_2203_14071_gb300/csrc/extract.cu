@@ -79,7 +79,6 @@ __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__r
     }
 }
 
-// kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
 // Flush queue: a lane whose run of equal cells ends appends the run to its
 // warp's queue (ballot + popc, no divergence); when 32 entries are waiting the
 // warp adds them to the shared-memory facet with all lanes active.
@@ -88,6 +87,40 @@ struct RunEntry {
     float re, im, sp;
 };
 constexpr int kQueue = 64;   // entries per warp
+
+// Add the first 32 queued runs to the shared-memory facet with the whole warp, move
+// the rest to the front; returns the new queue length.  Kept out of line: it runs
+// once per 32 runs and inlining it into every channel iteration bloats the code.
+__device__ __noinline__ int drain_queue(RunEntry *wq, int qn, int lane, float *sre, float *sim, int *scnt,
+                                        float *ssp)
+{
+    __syncwarp();
+    const RunEntry e = wq[lane];
+    atomicAdd(&sre[e.cell], e.re);
+    atomicAdd(&sim[e.cell], e.im);
+    atomicAdd(&scnt[e.cell], e.n);
+    atomicAdd(&ssp[e.cell], e.sp);
+    __syncwarp();
+    const int rest = qn - 32;
+    if (lane < rest) wq[lane] = wq[32 + lane];
+    __syncwarp();
+    return rest;
+}
+
+// Both cell coordinates at once with paired FP32 instructions (see cell_floor).
+__device__ __forceinline__ void cell_floor2(float uh, float vh, float sdu, int &iu, int &iv, bool &edge)
+{
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    const f32x2 y = fma2(pk2(uh, vh), pk2(sdu, sdu), pk2(-0.5f, -0.5f));
+    const f32x2 m = add2(y, pk2(kMagic, kMagic));
+    const f32x2 d = add2(y, add2(m, pk2(-kMagic, -kMagic)) ^ 0x8000000080000000ull);
+    float du_, dv_, mu_, mv_;
+    up2(d, du_, dv_);
+    up2(m, mu_, mv_);
+    edge = fmaxf(fabsf(du_), fabsf(dv_)) > 0.5f - 1.0e-5f;
+    iu = __float_as_int(mu_) - 0x4B400000;
+    iv = __float_as_int(mv_) - 0x4B400000;
+}
 
 // kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
 template <int CG, bool kUniform, bool kSplit, bool kResid>
@@ -132,19 +165,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     constexpr float kTwoPi = 6.28318530717958647692f;
     int qn = 0;                                    // warp-uniform queue length
 
-    auto drain32 = [&]() {
-        __syncwarp();
-        const RunEntry e = wq[lane];
-        atomicAdd(&sre[e.cell], e.re);
-        atomicAdd(&sim[e.cell], e.im);
-        atomicAdd(&scnt[e.cell], e.n);
-        atomicAdd(&ssp[e.cell], e.sp);
-        __syncwarp();
-        const int rest = qn - 32;
-        if (lane < rest) wq[lane] = wq[32 + lane];
-        __syncwarp();
-        qn = rest;
-    };
+    auto drain32 = [&]() { qn = drain_queue(wq, qn, lane, sre, sim, scnt, ssp); };
     // every lane of the warp calls push with its own predicate
     auto push = [&](bool pf, int cell, int n, float re, float im, float sp) {
         const unsigned m = __ballot_sync(0xffffffffu, pf);
@@ -286,11 +307,13 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     }
                     int cell = -1;
                     if (row_on && k < C) {
-                        bool eu, ev;
-                        int iu = cell_floor(uh, sdu[c], eu);
-                        int iv = cell_floor(vh, sdu[c], ev);
-                        if (eu) iu = (int)floor((u[r] * ch.s[k]) / du);
-                        if (ev) iv = (int)floor((v[r] * ch.s[k]) / du);
+                        int iu, iv;
+                        bool edge;
+                        cell_floor2(uh, vh, sdu[c], iu, iv, edge);
+                        if (edge) {
+                            iu = (int)floor((u[r] * ch.s[k]) / du);
+                            iv = (int)floor((v[r] * ch.s[k]) / du);
+                        }
                         iu += half;
                         iv += half;
                         if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
