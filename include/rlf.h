@@ -224,6 +224,31 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
                    const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
                    void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Sky model without any caller-provided device memory.  There is no counterpart
+ * in the paper: it is the same computation as rlf_sky_model for callers that
+ * cannot allocate device memory (code running where cudaMalloc is not allowed or
+ * not wanted, e.g. inside another framework's memory pool, a real-time loop that
+ * must not allocate after start-up, or a plugin handed only its input and output
+ * buffers).  The per-source table that rlf_sky_model keeps in the workspace lives
+ * here in a fixed device array inside the library (about 460 KB on every GPU that
+ * loads the library, held until the process exits).
+ *   - At most RLF_STATIC_MAX_SRC sources; more returns RLF_ENOSPACE and enqueues
+ *     nothing.  Other arguments as for rlf_sky_model.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - Calls share the array: calls that overlap on the GPU (other streams, or
+ *     other host threads without ordering) race on it.  Each call rewrites what it
+ *     reads, so earlier contents do not matter.
+ *   - Per-source value errors are not reported (there is no workspace status to
+ *     read): such sources contribute nothing, as in rlf_sky_model.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.
+ */
+#define RLF_STATIC_MAX_SRC 4096
+rlf_status rlf_sky_model_static(const rlf_uvw *uvw, const rlf_sources *src, const rlf_params *p,
+                                float *vis_sky, void *stream);
+
 /* Copy the workspace's device status word (RLF_DEV_* bits) to *status_out and clear it.
  * Waits for `stream`.  Returns RLF_ETIMEOUT / RLF_ENUMERIC when those bits are set. */
 rlf_status rlf_read_status(void *workspace, int32_t *status_out, void *stream);

@@ -29,7 +29,7 @@ PREC_FP64, PREC_MIXED, PREC_MIXED_SPLIT = 0, 1, 2
 FLAG_BAD, FLAG_INVALID, FLAG_EMPTY = 1, 2, 4
 DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
 WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
-MAX_CHAN, MAX_FACET_N = 128, 64
+MAX_CHAN, MAX_FACET_N, STATIC_MAX_SRC = 128, 64, 4096
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -106,6 +106,8 @@ def lib():
             L.rlf_fit_sources.argtypes = [_vp, P(Sources), i32, i32, P(Params), P(FitOut), _vp, sz, _vp]
             L.rlf_run.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp]
             L.rlf_read_status.argtypes = [_vp, P(ctypes.c_int32), _vp]
+            L.rlf_sky_model_static.argtypes = [P(Uvw), P(Sources), P(Params), _vp, _vp]
+            L.rlf_sky_model_static.restype = ctypes.c_int
             L.rlf_peaks_measure.argtypes = [_vp, sz, _vp, P(Peaks)]
             L.rlf_peaks_measure.restype = ctypes.c_int
             for f in ("rlf_sky_model", "rlf_sky_update", "rlf_extract_facets", "rlf_fit_sources", "rlf_run",
@@ -252,6 +254,12 @@ def run(obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results
     _check(lib().rlf_run(ctypes.byref(obs.struct), _ptr(vis_data), ctypes.byref(cat.struct),
                          ctypes.byref(params), ctypes.byref(out.struct), _ptr(vis_sky), _ptr(workspace),
                          workspace.numel() * workspace.element_size(), _stream(stream)), "rlf_run")
+
+
+def sky_model_static(obs: Observation, cat: Catalogue, params: Params, vis_sky, stream=None):
+    """rlf_sky_model_static: the sky model with no workspace (for callers that cannot allocate)."""
+    _check(lib().rlf_sky_model_static(ctypes.byref(obs.struct), ctypes.byref(cat.struct), ctypes.byref(params),
+                                      _ptr(vis_sky), _stream(stream)), "rlf_sky_model_static")
 
 
 def read_status(workspace, stream=None) -> tuple[int, int]:
