@@ -129,6 +129,11 @@ typedef struct {
     int32_t chunk;           /* sources per extract/fit/update step of rlf_run; <= 0: all */
     int32_t update_mode;     /* 0: update the sky model with good fits only; 1: with all */
     int32_t precision;       /* RLF_PREC_FP64, RLF_PREC_MIXED or RLF_PREC_MIXED_SPLIT */
+    /* launch shapes (0: library default); rlf_autotune fills them by timing */
+    int32_t tune_fit_ag;        /* scalelength nodes per likelihood thread: 2, 4 or 8 (default 4) */
+    int32_t tune_fit_blocks;    /* CTAs per SM of the persistent fit (default: all that fit) */
+    int32_t tune_extract_waves; /* CTA waves per extraction batch (default 2) */
+    int32_t tune_sky_blocks;    /* CTAs per SM of the sky-model kernels (default 8) */
     int32_t reserved;
 } rlf_params;
 
@@ -223,6 +228,39 @@ rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t
 rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
                    const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
                    void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * The whole chain as a captured CUDA graph (the batched form: one graph holds the
+ * sky model, every extraction, the persistent fit and the update; with chunk =
+ * n_src that is one launch per step).  rlf_graph_create records rlf_run's work on
+ * `stream` (a non-default cudaStream_t, required) into a graph and instantiates it;
+ * every pointer, size, parameter and host channel value is baked in, so later
+ * launches recompute the chain on the current contents of the same buffers.
+ * rlf_graph_launch enqueues one replay on `stream`.  The graph object is host
+ * memory owned by the library; free it with rlf_graph_destroy.  Sec. 2 and Sec. 3.1
+ * define the chain; the graph is an execution form, not a change of the method.
+ */
+typedef struct rlf_graph_s rlf_graph;
+rlf_status rlf_graph_create(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
+                            const rlf_params *p, const rlf_fit_out *out, float *vis_sky, void *workspace,
+                            size_t ws_bytes, void *stream, rlf_graph **graph_out);
+rlf_status rlf_graph_launch(rlf_graph *graph, void *stream);
+void rlf_graph_destroy(rlf_graph *graph);
+
+/*
+ * Autotuner of the launch shapes (the tune_* fields of rlf_params) for this
+ * workload: times the sky model over CTAs per SM {4, 8, 12, 16}, the extraction
+ * of the first chunk over {1, 2, 3, 4} CTA waves, and the persistent fit over
+ * scalelength nodes per thread {2, 4, 8} x CTAs per SM {1, 2, 3} (median of 3
+ * runs each, CUDA events on `stream`), and writes the fastest choices into *p.
+ * Arguments as for rlf_run; vis_sky, out and the workspace are overwritten.
+ * phase_ms (host [3], may be NULL) receives the best sky, extraction and fit
+ * times.  Waits for `stream`.  The results depend on these fields only through the
+ * rounding of the extraction's partial sums (their grouping follows the wave count).
+ */
+rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src, rlf_params *p,
+                        const rlf_fit_out *out, float *vis_sky, void *workspace, size_t ws_bytes, void *stream,
+                        float *phase_ms);
 
 /*
  * Sky model without any caller-provided device memory.  There is no counterpart

@@ -60,6 +60,8 @@ class Params(ctypes.Structure):
                 ("var_det_min", ctypes.c_double), ("facet_n", ctypes.c_int32), ("n_e", ctypes.c_int32),
                 ("n_alpha", ctypes.c_int32), ("flux_prior", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("update_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tune_fit_ag", ctypes.c_int32), ("tune_fit_blocks", ctypes.c_int32),
+                ("tune_extract_waves", ctypes.c_int32), ("tune_sky_blocks", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -106,6 +108,16 @@ def lib():
             L.rlf_fit_sources.argtypes = [_vp, P(Sources), i32, i32, P(Params), P(FitOut), _vp, sz, _vp]
             L.rlf_run.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp]
             L.rlf_read_status.argtypes = [_vp, P(ctypes.c_int32), _vp]
+            L.rlf_graph_create.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp,
+                                           P(_vp)]
+            L.rlf_graph_create.restype = ctypes.c_int
+            L.rlf_graph_launch.argtypes = [_vp, _vp]
+            L.rlf_graph_launch.restype = ctypes.c_int
+            L.rlf_graph_destroy.argtypes = [_vp]
+            L.rlf_graph_destroy.restype = None
+            L.rlf_autotune.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp,
+                                       P(ctypes.c_float)]
+            L.rlf_autotune.restype = ctypes.c_int
             L.rlf_sky_model_static.argtypes = [P(Uvw), P(Sources), P(Params), _vp, _vp]
             L.rlf_sky_model_static.restype = ctypes.c_int
             L.rlf_peaks_measure.argtypes = [_vp, sz, _vp, P(Peaks)]
@@ -260,6 +272,79 @@ def sky_model_static(obs: Observation, cat: Catalogue, params: Params, vis_sky, 
     """rlf_sky_model_static: the sky model with no workspace (for callers that cannot allocate)."""
     _check(lib().rlf_sky_model_static(ctypes.byref(obs.struct), ctypes.byref(cat.struct), ctypes.byref(params),
                                       _ptr(vis_sky), _stream(stream)), "rlf_sky_model_static")
+
+
+class Graph:
+    """rlf_graph_create / rlf_graph_launch / rlf_graph_destroy: the whole chain as a CUDA graph.
+
+    The graph records the buffers it was created with; keep them alive and update
+    their contents in place between launches."""
+
+    def __init__(self, obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results, vis_sky,
+                 workspace, stream):
+        self._keep = (obs, vis_data, cat, params, out, vis_sky, workspace)
+        self.handle = ctypes.c_void_p()
+        _check(lib().rlf_graph_create(ctypes.byref(obs.struct), _ptr(vis_data), ctypes.byref(cat.struct),
+                                      ctypes.byref(params), ctypes.byref(out.struct), _ptr(vis_sky),
+                                      _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                      _stream(stream), ctypes.byref(self.handle)), "rlf_graph_create")
+
+    def launch(self, stream=None):
+        _check(lib().rlf_graph_launch(self.handle, _stream(stream)), "rlf_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().rlf_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TUNE_FIELDS = ("tune_sky_blocks", "tune_extract_waves", "tune_fit_ag", "tune_fit_blocks")
+
+
+def tuning_key(obs: Observation, n_src: int, params: Params) -> str:
+    """Cache key: workload shape, grid, precision, chunk and the GPU's SM count."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return "rows%d_chan%d_bl%d_src%d_N%d_e%d_a%d_prec%d_chunk%d_sm%d" % (
+        obs.n_rows, obs.n_chan, obs.struct.n_baselines, n_src, params.facet_n, params.n_e, params.n_alpha,
+        params.precision, params.chunk, sms)
+
+
+def autotune(obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results, vis_sky, workspace,
+             cache_path: str | None = None, stream=None) -> dict:
+    """rlf_autotune with a JSON cache keyed by tuning_key(); fills params.tune_* in place."""
+    import json
+    key = tuning_key(obs, cat.n_src, params)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        for f in TUNE_FIELDS:
+            setattr(params, f, int(cache[key][f]))
+        return dict(cache[key], cached=True)
+    ms = (ctypes.c_float * 3)()
+    _check(lib().rlf_autotune(ctypes.byref(obs.struct), _ptr(vis_data), ctypes.byref(cat.struct),
+                              ctypes.byref(params), ctypes.byref(out.struct), _ptr(vis_sky), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream(stream), ms), "rlf_autotune")
+    entry = {f: int(getattr(params, f)) for f in TUNE_FIELDS}
+    entry["phase_ms"] = [float(x) for x in ms]
+    if cache_path:
+        cache[key] = entry
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        tmp = cache_path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return dict(entry, cached=False)
 
 
 def read_status(workspace, stream=None) -> tuple[int, int]:

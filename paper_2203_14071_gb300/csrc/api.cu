@@ -3,6 +3,7 @@
 // in sky.cu, extract.cu and fit.cu.
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "rlf_internal.cuh"
 
@@ -29,6 +30,8 @@ bool params_ok(const rlf_params &p)
         return false;
     if (p.flux_prior != 0 && p.flux_prior != 1) return false;
     if (p.update_mode != 0 && p.update_mode != 1) return false;
+    if (p.tune_fit_ag != 0 && p.tune_fit_ag != 2 && p.tune_fit_ag != 4 && p.tune_fit_ag != 8) return false;
+    if (p.tune_fit_blocks < 0 || p.tune_extract_waves < 0 || p.tune_sky_blocks < 0) return false;
     return true;
 }
 
@@ -106,6 +109,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_upd = take((which == RLF_WS_SKY || run) ? (size_t)n_src * sizeof(SrcRow) : 0);
     const size_t o_cells = take(fit ? 5 * cap * NN * sizeof(double) : 0);
     const size_t o_ncell = take(fit ? cap * sizeof(int32_t) : 0);
+    const size_t o_order = take(fit ? cap * sizeof(int32_t) : 0);
+    const size_t o_count = take(fit ? (cap + 1) * sizeof(int32_t) : 0);
     const size_t o_cc = take(fit ? cap * sizeof(double) : 0);
     const size_t o_ga = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_gb = take(fit ? cap * ng * sizeof(double) : 0);
@@ -125,6 +130,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->upd = reinterpret_cast<SrcRow *>(b + o_upd);
         ws->cells = b + o_cells;
         ws->ncell = reinterpret_cast<int32_t *>(b + o_ncell);
+        ws->order = reinterpret_cast<int32_t *>(b + o_order);
+        ws->counters = reinterpret_cast<int32_t *>(b + o_count);
         ws->cc = reinterpret_cast<double *>(b + o_cc);
         ws->ga = reinterpret_cast<double *>(b + o_ga);
         ws->gb = reinterpret_cast<double *>(b + o_gb);
@@ -215,7 +222,7 @@ rlf_status rlf_sky_model(const rlf_uvw *uvw, const rlf_sources *src, const rlf_p
     if (e == cudaSuccess)
         e = launch_prepare(*src, 0, src->n_src, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                            nullptr, *p, ws.table, ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, src->n_src, false, p->precision, vis_sky, st);
+    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, src->n_src, false, p->precision, vis_sky, st, p->tune_sky_blocks);
     return cuda_status(e);
 }
 
@@ -238,7 +245,7 @@ rlf_status rlf_sky_update(const rlf_uvw *uvw, const rlf_sources *src, int32_t fi
     if (e == cudaSuccess)
         e = launch_prepare(*src, first, count, src->e1, src->e2, e1_new, e2_new, flag,
                            flag ? p->update_mode : 1, nullptr, nullptr, *p, ws.upd, ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.upd, count, true, p->precision, vis_sky, st);
+    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.upd, count, true, p->precision, vis_sky, st, p->tune_sky_blocks);
     return cuda_status(e);
 }
 
@@ -289,9 +296,13 @@ rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t
     return cuda_status(e);
 }
 
-rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
-                   const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
-                   void *workspace, size_t ws_bytes, void *stream)
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by rlf_run, rlf_graph_create and rlf_autotune.
+rlf_status check_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src, const rlf_params *p,
+                     const rlf_fit_out *out, const float *vis_sky, void *workspace, size_t ws_bytes, Workspace *ws)
 {
     rlf_status s = check_uvw(uvw);
     if (s != RLF_OK) return s;
@@ -301,38 +312,233 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
         !out->sig2 || !out->alpha_arcsec || !out->flux_jy || !out->e1_smooth || !out->e2_smooth ||
         !out->flag)
         return RLF_EINVAL;
-    const int32_t n = src->n_src;
-    Workspace ws;
-    if (workspace_layout(uvw->n_rows, uvw->n_chan, n, *p, RLF_WS_RUN, workspace, &ws) > ws_bytes)
+    if (workspace_layout(uvw->n_rows, uvw->n_chan, src->n_src, *p, RLF_WS_RUN, workspace, ws) > ws_bytes)
         return RLF_ENOSPACE;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const ChanTable ch = make_chan_table(*uvw, *p);
-    const int32_t chunk = fit_capacity(n, *p, RLF_WS_RUN);
+    return RLF_OK;
+}
+
+// The whole chain on stream st (arguments already checked).
+cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sources &src, const rlf_params &p,
+                      const rlf_fit_out &out, float *vis_sky, const Workspace &ws, cudaStream_t st)
+{
+    const int32_t n = src.n_src;
+    const ChanTable ch = make_chan_table(uvw, p);
+    const int32_t chunk = fit_capacity(n, p, RLF_WS_RUN);
     double *e1c = ws.e_cur, *e2c = ws.e_cur + n;
 
     cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(e1c, src->e1, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(e2c, src->e2, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(e1c, src.e1, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(e2c, src.e2, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     // the sky model of the catalogue's current shapes (circular for a fresh catalogue)
     if (e == cudaSuccess)
-        e = launch_prepare(*src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, *p,
-                           ws.table, ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, n, false, p->precision, vis_sky, st);
-    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
+        e = launch_prepare(src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
+                           ws.status, st);
+    if (e == cudaSuccess) e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
+    if (e == cudaSuccess && p.precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(uvw, ws.uvw_split, st);
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table + first, cnt, *p, ws.uvw_split, ws.resid,
+        e = launch_extract(uvw, ch, vis_data, vis_sky, ws.table + first, cnt, p, ws.uvw_split, ws.resid,
                            ws.partial, ws.facets, st);
         if (e != cudaSuccess) break;
-        e = launch_fit(ws.facets, ws.table + first, cnt, *p, ws, *out, first, st);
+        e = launch_fit(ws.facets, ws.table + first, cnt, p, ws, out, first, st);
         if (e != cudaSuccess) break;
         // replace the chunk's shapes in the sky model (good fits, or all with update_mode 1)
-        e = launch_prepare(*src, first, cnt, e1c, e2c, out->e1 + first, out->e2 + first, out->flag + first,
-                           p->update_mode, e1c, e2c, *p, ws.upd, ws.status, st);
+        e = launch_prepare(src, first, cnt, e1c, e2c, out.e1 + first, out.e2 + first, out.flag + first,
+                           p.update_mode, e1c, e2c, p, ws.upd, ws.status, st);
         if (e != cudaSuccess) break;
-        e = launch_sky(*uvw, ch, ws.upd, cnt, true, p->precision, vis_sky, st);
+        e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
     }
-    return cuda_status(e);
+    return e;
+}
+
+// Median of `reps` timings of fn on st (CUDA events), in ms; negative on error.
+template <typename F>
+float time_median(F fn, cudaStream_t st, int reps)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.0f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.0f;
+    }
+    float t[8];
+    reps = reps < 1 ? 1 : (reps > 8 ? 8 : reps);
+    bool ok = fn() == cudaSuccess;   // warm-up
+    for (int i = 0; i < reps && ok; ++i) {
+        ok = cudaEventRecord(a, st) == cudaSuccess && fn() == cudaSuccess && cudaEventRecord(b, st) == cudaSuccess &&
+             cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t[i], a, b) == cudaSuccess;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok) return -1.0f;
+    for (int i = 1; i < reps; ++i)
+        for (int j = i; j > 0 && t[j] < t[j - 1]; --j) {
+            const float x = t[j];
+            t[j] = t[j - 1];
+            t[j - 1] = x;
+        }
+    return t[reps / 2];
+}
+
+}  // namespace
+
+struct rlf_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
+                   const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
+                   void *workspace, size_t ws_bytes, void *stream)
+{
+    Workspace ws;
+    const rlf_status s = check_run(uvw, vis_data, src, p, out, vis_sky, workspace, ws_bytes, &ws);
+    if (s != RLF_OK) return s;
+    return cuda_status(run_chain(*uvw, vis_data, *src, *p, *out, vis_sky, ws, static_cast<cudaStream_t>(stream)));
+}
+
+rlf_status rlf_graph_create(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
+                            const rlf_params *p, const rlf_fit_out *out, float *vis_sky, void *workspace,
+                            size_t ws_bytes, void *stream, rlf_graph **graph_out)
+{
+    if (!graph_out || !stream) return RLF_EINVAL;
+    *graph_out = nullptr;
+    Workspace ws;
+    const rlf_status s = check_run(uvw, vis_data, src, p, out, vis_sky, workspace, ws_bytes, &ws);
+    if (s != RLF_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RLF_ECUDA;
+    const cudaError_t e = run_chain(*uvw, vis_data, *src, *p, *out, vis_sky, ws, st);
+    const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return RLF_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return RLF_ECUDA;
+    }
+    rlf_graph *h = new (std::nothrow) rlf_graph{g, exec};
+    if (!h) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(g);
+        return RLF_ECUDA;
+    }
+    *graph_out = h;
+    return RLF_OK;
+}
+
+rlf_status rlf_graph_launch(rlf_graph *graph, void *stream)
+{
+    if (!graph) return RLF_EINVAL;
+    return cuda_status(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+}
+
+void rlf_graph_destroy(rlf_graph *graph)
+{
+    if (!graph) return;
+    cudaGraphExecDestroy(graph->exec);
+    cudaGraphDestroy(graph->graph);
+    delete graph;
+}
+
+rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src, rlf_params *p,
+                        const rlf_fit_out *out, float *vis_sky, void *workspace, size_t ws_bytes, void *stream,
+                        float *phase_ms)
+{
+    Workspace ws;
+    rlf_status s = check_run(uvw, vis_data, src, p, out, vis_sky, workspace, ws_bytes, &ws);
+    if (s != RLF_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int32_t n = src->n_src;
+    const int32_t chunk = fit_capacity(n, *p, RLF_WS_RUN);
+    const ChanTable ch = make_chan_table(*uvw, *p);
+    const int reps = 3;
+    rlf_params q = *p;
+    // the sky model of the catalogue and the split baselines, inputs of the timed steps
+    cudaError_t e = launch_prepare(*src, 0, n, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr, nullptr, q,
+                                   ws.table, ws.status, st);
+    if (e == cudaSuccess && q.precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
+    if (e != cudaSuccess) return RLF_ECUDA;
+    float best[3] = {0, 0, 0};
+    // 1. sky-model CTAs per SM
+    {
+        const int cand[] = {4, 8, 12, 16};
+        float bt = 0;
+        int bc = 8;
+        for (int c : cand) {
+            const float t = time_median([&] { return launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, c); },
+                                        st, reps);
+            if (t < 0) return RLF_ECUDA;
+            if (bt == 0 || t < bt) {
+                bt = t;
+                bc = c;
+            }
+        }
+        q.tune_sky_blocks = bc;
+        best[0] = bt;
+        if ((e = launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, bc)) != cudaSuccess) return RLF_ECUDA;
+    }
+    // 2. extraction waves (first chunk of sources)
+    {
+        const int cand[] = {1, 2, 3, 4};
+        float bt = 0;
+        int bc = 2;
+        for (int c : cand) {
+            q.tune_extract_waves = c;
+            const float t = time_median([&] {
+                return launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws.uvw_split, ws.resid,
+                                      ws.partial, ws.facets, st);
+            }, st, reps);
+            if (t < 0) return RLF_ECUDA;
+            if (bt == 0 || t < bt) {
+                bt = t;
+                bc = c;
+            }
+        }
+        q.tune_extract_waves = bc;
+        best[1] = bt;
+        if (launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws.uvw_split, ws.resid, ws.partial,
+                           ws.facets, st) != cudaSuccess)
+            return RLF_ECUDA;
+    }
+    // 3. likelihood: scalelength nodes per thread x CTAs per SM
+    {
+        const int ags[] = {2, 4, 8};
+        const int blocks[] = {1, 2, 3};
+        float bt = 0;
+        int ba = 4, bb = 0;
+        for (int a : ags)
+            for (int b : blocks) {
+                q.tune_fit_ag = a;
+                q.tune_fit_blocks = b;
+                const float t = time_median([&] { return launch_fit(ws.facets, ws.table, chunk, q, ws, *out, 0, st); },
+                                            st, reps);
+                if (t < 0) return RLF_ECUDA;
+                if (bt == 0 || t < bt) {
+                    bt = t;
+                    ba = a;
+                    bb = b;
+                }
+            }
+        q.tune_fit_ag = ba;
+        q.tune_fit_blocks = bb;
+        best[2] = bt;
+    }
+    p->tune_sky_blocks = q.tune_sky_blocks;
+    p->tune_extract_waves = q.tune_extract_waves;
+    p->tune_fit_ag = q.tune_fit_ag;
+    p->tune_fit_blocks = q.tune_fit_blocks;
+    if (phase_ms) {
+        phase_ms[0] = best[0];
+        phase_ms[1] = best[1];
+        phase_ms[2] = best[2];
+    }
+    return RLF_OK;
 }
 
 rlf_status rlf_read_status(void *workspace, int32_t *status_out, void *stream)

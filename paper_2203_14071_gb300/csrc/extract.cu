@@ -37,22 +37,6 @@ namespace rlf {
 
 namespace {
 
-// floor(t) for |t| < 2^22: y = t - 1/2 is rounded to the nearest integer by adding
-// 1.5 * 2^23 (the integer lands in the low mantissa bits); d = y - round(y) is
-// exact.  Away from a cell edge round(t - 1/2) = floor(t).  With t = fl(u) *
-// fl(nu/c/du) - 1/2 formed by one FMA, |error of t| <= 3 * 2^-24 |t| < 6e-6 for
-// |t| <= 33 (every facet window here); `edge` flags values within 1e-5 of a
-// cell edge, where the caller takes the FP64 decision instead.
-__device__ __forceinline__ int cell_floor(float uh, float sdu, bool &edge)
-{
-    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-    const float y = fmaf(uh, sdu, -0.5f);
-    const float m = __fadd_rn(y, kMagic);
-    const float d = __fsub_rn(y, __fsub_rn(m, kMagic));
-    edge = fabsf(d) > 0.5f - 1.0e-5f;
-    return __float_as_int(m) - 0x4B400000;
-}
-
 __global__ void residual_kernel(const float4 *__restrict__ d, const float4 *__restrict__ s, int64_t n4,
                                 float4 *__restrict__ out)
 {
@@ -107,7 +91,13 @@ __device__ __noinline__ int drain_queue(RunEntry *wq, int qn, int lane, float *s
     return rest;
 }
 
-// Both cell coordinates at once with paired FP32 instructions (see cell_floor).
+// Cell index of both coordinates, with paired FP32 instructions: floor(t) for
+// |t| < 2^22 as round(t - 1/2), where the rounding to an integer is done by adding
+// 1.5 * 2^23 (the integer lands in the low mantissa bits) and d = y - round(y) is
+// exact.  Away from a cell edge round(t - 1/2) = floor(t).  With t = fl(u) *
+// fl(nu/c/du) formed by one FMA, |error of t| <= 3 * 2^-24 |t| < 6e-6 for
+// |t| <= 33 (every facet window here); `edge` flags values within 1e-5 of a
+// cell edge, where the caller takes the FP64 decision instead.
 __device__ __forceinline__ void cell_floor2(float uh, float vh, float sdu, int &iu, int &iv, bool &edge)
 {
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
@@ -478,7 +468,7 @@ int sm_count_x()
 template <int CG, bool kSplit>
 cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
                       const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
-                      double *facets, cudaStream_t st)
+                      double *facets, int waves, cudaStream_t st)
 {
     const size_t smem = 4 * (size_t)N * N * sizeof(float) + (kThreads / 32) * kQueue * sizeof(RunEntry);
     const bool resid = sky == nullptr;
@@ -500,8 +490,8 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
     // sources are handled in batches whose partial facets fit the workspace
     for (int32_t first = 0; first < count; first += kMaxPartials) {
         const int32_t cnt = count - first < kMaxPartials ? count - first : kMaxPartials;
-        // parts per source: about two waves of CTAs, at most one part per baseline block
-        int64_t parts = (2 * slots + cnt - 1) / cnt;
+        // parts per source: about `waves` waves of CTAs, at most one part per baseline block
+        int64_t parts = ((int64_t)waves * slots + cnt - 1) / cnt;
         if (parts > n_blocks) parts = n_blocks;
         if (parts > kMaxPartials / cnt) parts = kMaxPartials / cnt;
         if (parts < 1) parts = 1;
@@ -521,12 +511,12 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
 template <bool kSplit>
 cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
                          const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
-                         double *facets, cudaStream_t st)
+                         double *facets, int waves, cudaStream_t st)
 {
-    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
-    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
-    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
-    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, st);
+    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
+    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
+    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
+    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
 }
 
 cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
@@ -586,10 +576,12 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
             sky = nullptr;
         }
     }
+    const int waves = p.tune_extract_waves > 0 ? p.tune_extract_waves : 2;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, partial, facets, st);
+        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, partial, facets, waves, st);
     if (p.precision == RLF_PREC_MIXED_SPLIT)
-        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, partial, facets, st);
+        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, partial, facets, waves,
+                                  st);
     return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
 }
 

@@ -6,14 +6,18 @@
 //                     order, as (uu, uv, vv) in units of du^2 (exact for the
 //                     half-integer cell centres), A = w s^2, B = w s Re D, and
 //                     C = sum w |D|^2 in FP64.
-//   grid_kernel       CTA = (facet, tile of (e point, alpha group)); cells are
+//   fit_persistent_kernel  one launch for every facet: CTAs take work items
+//                     (facet in largest-first order, tile of grid pairs) from an
+//                     atomic counter; the CTA finishing a facet's last tile runs its
+//                     estimate (fused tail).
+//   grid_tile         work item = (facet, tile of (e point, alpha group)); cells are
 //                     staged through shared memory; each thread evaluates its
 //                     alpha nodes for every cell: one quadratic form per cell,
 //                     then per alpha one FMA, one rsqrt and the a, b products.
 //                     Mixed precision sums the products in FP32 over a tile of
 //                     cells and adds the tile sums to FP64 accumulators; two
 //                     scalelength nodes share each paired (f32x2) instruction.
-//   estimate_kernel   one CTA per facet, FP64 throughout: logL, alpha marginal,
+//   estimate_source   one CTA per facet, FP64 throughout: logL, alpha marginal,
 //                     threshold, moments, MAP point, flags.
 #include <cfloat>
 #include <cmath>
@@ -111,15 +115,14 @@ __device__ __forceinline__ double grid_alpha(const GridConst &g, int k)
     return g.r_min + (g.r_max - g.r_min) * t * t;
 }
 
+// One work item of the likelihood grid: facet s, threads over (e point, alpha group)
+// pairs tile * kThreads .. tile * kThreads + kThreads - 1.  Writes a, b in FP64.
 template <typename T, int AG>
-__global__ void __launch_bounds__(kThreads)
-grid_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
-            const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
-            const GridConst gc, double *__restrict__ ga, double *__restrict__ gb)
+__device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const int32_t *__restrict__ ncell,
+                          const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst &gc,
+                          double *__restrict__ ga, double *__restrict__ gb)
 {
     __shared__ T sm[5][kCellTile];
-    const int s = blockIdx.x / tiles_per_src;
-    const int tile = blockIdx.x % tiles_per_src;
     const int pair = tile * kThreads + threadIdx.x;
     const int ne2 = gc.n_e * gc.n_e;
     const int e_idx = pair / gc.n_ag;
@@ -301,17 +304,17 @@ __device__ double flux_marginal(double a, double b, double cc, int flux_prior)
     return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(kPi / (2.0 * a)) + log(erfc(x));
 }
 
-__global__ void __launch_bounds__(kThreads)
-estimate_kernel(const double *__restrict__ ga, const double *__restrict__ gb, double *__restrict__ gl,
-                const int32_t *__restrict__ ncell, const double *__restrict__ ccv,
-                const SrcRow *__restrict__ table, const GridConst gc, rlf_fit_out out,
-                int32_t out_offset, int32_t *__restrict__ status)
+// Estimate of facet s from its complete a, b grid (block-wide, FP64).
+__device__ void estimate_source(int s, const double *__restrict__ ga, const double *__restrict__ gb,
+                                double *__restrict__ gl, const int32_t *__restrict__ ncell,
+                                const double *__restrict__ ccv, const SrcRow *__restrict__ table,
+                                const GridConst &gc, const rlf_fit_out &out, int32_t out_offset,
+                                int32_t *__restrict__ status)
 {
     __shared__ double red[kThreads / 32];
     __shared__ long long redi[kThreads / 32];
     __shared__ double qp[64], alph[64], lnp[64];
     __shared__ double Le[kMaxNe * kMaxNe], Ae[kMaxNe * kMaxNe];
-    const int s = blockIdx.x;
     const int ne = gc.n_e, na = gc.n_alpha, ne2 = ne * ne;
     const long long ng = (long long)ne2 * na;
     const SrcRow S = table[s];
@@ -446,6 +449,103 @@ estimate_kernel(const double *__restrict__ ga, const double *__restrict__ gb, do
     }
 }
 
+
+// Largest facets first (LPT order): rank of facet i = number of facets with more
+// cells, ties by index.  order[rank] = i.
+__global__ void lpt_order_kernel(const int32_t *__restrict__ ncell, int32_t count, int32_t *__restrict__ order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int ni = ncell[i];
+    int rank = 0;
+    for (int j = 0; j < count; ++j) {
+        const int nj = ncell[j];
+        rank += (nj > ni) || (nj == ni && j < i);
+    }
+    order[rank] = i;
+}
+
+// Persistent likelihood fit: every CTA takes work items (facet in LPT order,
+// tile of grid pairs) from an atomic counter until none is left; the CTA that
+// completes a facet's last tile (per-facet atomic counter after a fence) runs
+// that facet's estimate.  Nothing waits on another CTA.
+template <typename T, int AG>
+__global__ void __launch_bounds__(kThreads, 3)
+fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
+                      const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
+                      int32_t count, const int32_t *__restrict__ order, int32_t *__restrict__ counters,
+                      const GridConst gc, double *__restrict__ ga, double *__restrict__ gb,
+                      double *__restrict__ gl, const double *__restrict__ ccv, rlf_fit_out out,
+                      int32_t out_offset, int32_t *__restrict__ status)
+{
+    __shared__ int s_item, s_last;
+    int32_t *item_counter = counters;
+    int32_t *src_done = counters + 1;
+    const int total = count * tiles_per_src;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int s = order[item / tiles_per_src];
+        const int tile = item % tiles_per_src;
+        grid_tile<T, AG>(s, tile, cells, ncell, table, plane, NN, gc, ga, gb);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&src_done[s], 1) == tiles_per_src - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            estimate_source(s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset, status);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T, int AG>
+cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                              GridConst gc, const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
+                              int32_t out_offset, cudaStream_t st)
+{
+    gc.n_ag = (gc.n_alpha + AG - 1) / AG;
+    const int pairs = gc.n_e * gc.n_e * gc.n_ag;
+    const int tiles = (pairs + kThreads - 1) / kThreads;
+    auto kern = fit_persistent_kernel<T, AG>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (p.tune_fit_blocks > 0 && p.tune_fit_blocks < per_sm) per_sm = p.tune_fit_blocks;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (int64_t)count * tiles;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > items) grid = items;
+    if ((e = cudaMemsetAsync(ws.counters, 0, (size_t)(count + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
+    lpt_order_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.ncell, count, ws.order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kern<<<(int)grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, ws.order, ws.counters,
+                                         gc, ws.ga, ws.gb, ws.gl, ws.cc, out, out_offset, ws.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_persistent_ag(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                                 const GridConst &gc, const rlf_params &p, const Workspace &ws,
+                                 const rlf_fit_out &out, int32_t out_offset, cudaStream_t st)
+{
+    switch (p.tune_fit_ag) {
+    case 2: return launch_persistent<T, 2>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    case 8: return launch_persistent<T, 8>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    default: return launch_persistent<T, 4>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
@@ -456,7 +556,7 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
     GridConst gc;
     gc.n_e = p.n_e;
     gc.n_alpha = p.n_alpha;
-    gc.n_ag = (p.n_alpha + kAlphaPerThread - 1) / kAlphaPerThread;
+    gc.n_ag = 0;
     gc.flux_prior = p.flux_prior;
     gc.e_max = p.e_max;
     gc.r_min = p.r_min_arcsec;
@@ -467,24 +567,20 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
     gc.var_sigma_min = p.var_sigma_min;
     gc.var_det_min = p.var_det_min;
     const size_t plane = (size_t)count * NN;
-    const int pairs = p.n_e * p.n_e * gc.n_ag;
-    const int tiles = (pairs + kThreads - 1) / kThreads;
     if (p.precision != RLF_PREC_FP64) {
         float *cells = static_cast<float *>(ws.cells);
         compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                           ws.ncell, ws.cc);
-        grid_kernel<float, kAlphaPerThread><<<count * tiles, kThreads, 0, st>>>(
-            cells, ws.ncell, table, plane, NN, tiles, gc, ws.ga, ws.gb);
-    } else {
-        double *cells = static_cast<double *>(ws.cells);
-        compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
-                                                           ws.ncell, ws.cc);
-        grid_kernel<double, kAlphaPerThread><<<count * tiles, kThreads, 0, st>>>(
-            cells, ws.ncell, table, plane, NN, tiles, gc, ws.ga, ws.gb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_persistent_ag<float>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
     }
-    estimate_kernel<<<count, kThreads, 0, st>>>(ws.ga, ws.gb, ws.gl, ws.ncell, ws.cc, table, gc, out,
-                                                out_offset, ws.status);
-    return cudaGetLastError();
+    double *cells = static_cast<double *>(ws.cells);
+    compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
+                                                       ws.ncell, ws.cc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_persistent<double, 4>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
 }
 
 }  // namespace rlf

@@ -16,7 +16,6 @@ constexpr double kArcsec = kPi / 648000.0;               // arcsec -> rad
 constexpr int kThreads = 256;                            // threads per CTA of every kernel
 constexpr int kSkyTile = 128;                            // sources staged per shared-memory tile
 constexpr int kCellTile = 128;                           // facet cells staged per tile in the fit
-constexpr int kAlphaPerThread = 4;                       // scalelength nodes per fit thread
 constexpr int kMaxNe = 32;                               // grid nodes per e component (estimator smem)
 constexpr int kMaxPartials = 2048;                       // (source, part) partial facets per extraction batch
 
@@ -151,6 +150,8 @@ struct Workspace {
     SrcRow *upd;            // [n_src] update table
     void *cells;            // [5][cap][N*N] T
     int32_t *ncell;         // [cap]
+    int32_t *order;         // [cap] facets in largest-first order
+    int32_t *counters;      // [cap + 1] work-item counter, per-facet finished tiles
     double *cc;             // [cap]
     double *ga, *gb, *gl;   // [cap][n_e^2][n_alpha]
     double *e_cur;          // [2][n_src]
@@ -171,7 +172,8 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            double *e1_commit, double *e2_commit,
                            const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st);
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                       bool update, int32_t precision, float *vis, cudaStream_t st);
+                       bool update, int32_t precision, float *vis, cudaStream_t st,
+                       int32_t blocks_per_sm = 0);
 cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,

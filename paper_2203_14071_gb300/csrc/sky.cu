@@ -317,12 +317,12 @@ int sm_count()
 
 template <int CG, bool kUpdate, bool kSplit>
 void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                  float *vis, cudaStream_t st)
+                  float *vis, int blocks_per_sm, cudaStream_t st)
 {
     const int n_groups = (ch.n + CG - 1) / CG;
     const int lanes = kThreads / n_groups;
     const int64_t blocks_needed = (uvw.n_rows + lanes - 1) / lanes;
-    const int64_t cap = (int64_t)sm_count() * 8;
+    const int64_t cap = (int64_t)sm_count() * blocks_per_sm;
     const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
     if (ch.uniform)
         sky_mixed_kernel<CG, kUpdate, true, kSplit><<<grid, kThreads, 0, st>>>(
@@ -334,12 +334,12 @@ void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, 
 
 template <bool kUpdate, bool kSplit>
 void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table,
-                     int32_t n_src, float *vis, cudaStream_t st)
+                     int32_t n_src, float *vis, int bps, cudaStream_t st)
 {
-    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
-    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
-    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
-    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, st);
+    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
+    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
+    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
+    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
 }
 
 }  // namespace
@@ -358,14 +358,15 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
 }
 
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                       bool update, int32_t precision, float *vis, cudaStream_t st)
+                       bool update, int32_t precision, float *vis, cudaStream_t st, int32_t blocks_per_sm)
 {
+    const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
     if (precision == RLF_PREC_MIXED) {
-        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, st);
-        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, st);
+        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, bps, st);
+        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, bps, st);
     } else if (precision == RLF_PREC_MIXED_SPLIT) {
-        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, st);
-        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, st);
+        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, bps, st);
+        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, bps, st);
     } else {
         const int64_t n_out = uvw.n_rows * ch.n;
         const int64_t need = (n_out + kThreads - 1) / kThreads;

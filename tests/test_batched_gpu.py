@@ -1,0 +1,170 @@
+"""Batched form: one persistent likelihood launch for every facet, the whole chain
+captured as a CUDA graph, and the launch-shape autotuner; all checked against the
+FP64 oracle.  The 148,270,080-visibility, 1000-source workload runs in full on
+the GPU and is compared on sampled rows and sources."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rlf():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2203_14071_gb300 as m
+    from paper_2203_14071_gb300 import build_ext
+    build_ext.build()
+    m.lib()
+    return m
+
+
+def _run_setup(rlf, c, **pk):
+    import torch
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, precision=rlf.PREC_MIXED_SPLIT, **pk)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    data = cases.vis_tensor(c.data)
+    return obs, cat, p, ws, out, sky, data
+
+
+def test_graph_replay_equals_run_and_oracle(rlf):
+    import torch
+    c = cases.build(synth.workload("small"), snr10=True)
+    obs, cat, p, ws, out, sky, data = _run_setup(rlf, c, update_mode=1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        rlf.run(obs, data, cat, p, out, sky, ws, stream)
+        stream.synchronize()
+        ref = out.numpy()
+        ref_sky = sky.clone()
+        g = rlf.Graph(obs, data, cat, p, out, sky, ws, stream)
+        for _ in range(2):
+            out.e1.zero_()
+            out.e2.zero_()
+            sky.zero_()
+            g.launch(stream)
+            stream.synchronize()
+            got = out.numpy()
+            for f in ("e1", "e2", "sig1", "sig2", "flag"):
+                assert np.array_equal(got[f], ref[f]), f
+            assert torch.equal(sky, ref_sky)
+        g.close()
+    est = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m, c.cat.flux_jy, None,
+                          c.oracle_params(chunk=0, update_mode=1))
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(ref, i, est[i]) <= 1e-4
+
+
+def test_persistent_fit_ragged_facets(rlf):
+    # facets of very different cell counts (one empty) fitted in one persistent launch
+    import torch
+    c = cases.build(synth.workload("small"), snr10=True)
+    p_or = c.oracle_params()
+    al = c.alpha_med_rad()
+    rng = np.random.default_rng(4)
+    facets, ests = [], []
+    for i in range(c.cat.n_src):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p_or)
+        acc = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i],
+                                   c.cat.m[i], c.cat.flux_jy[i], al[i], 0.0, 0.0, du, p_or)
+        keep = rng.random(acc.shape[1]) < (i + 1) / c.cat.n_src       # 10 % .. 100 % of the cells
+        if i == 3:
+            keep[:] = False                                            # an empty facet
+        acc[:, ~keep] = 0.0
+        facets.append(acc)
+        ests.append(oracle.fit_facet(acc, du, c.cat.flux_jy[i], p_or).est)
+    obs, cat = cases.to_device(c)
+    for ag in (2, 4, 8):
+        p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, tune_fit_ag=ag, tune_fit_blocks=1)
+        ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+        out = rlf.Results(cat.n_src, "cuda")
+        rlf.fit_sources(torch.from_numpy(np.stack(facets)).cuda(), cat, 0, cat.n_src, p, out, ws)
+        got = out.numpy()
+        for i, est in enumerate(ests):
+            if i == 3:
+                assert got["flag"][i] & rlf.FLAG_EMPTY
+                continue
+            assert cases.est_matches(got, i, est) <= 1e-4, (ag, i)
+
+
+def test_autotune_and_cache(rlf, tmp_path):
+    import torch
+    wl = synth.tiny(seed=81, n_ant=40, n_time=30, n_chan=8, n_src=24, r_max_m=6000.0)
+    c = cases.build(wl, snr10=True)
+    obs, cat, p, ws, out, sky, data = _run_setup(rlf, c, update_mode=1)
+    cache = str(tmp_path / "tune.json")
+    r1 = rlf.autotune(obs, data, cat, p, out, sky, ws, cache_path=cache)
+    assert not r1["cached"]
+    assert p.tune_sky_blocks in (4, 8, 12, 16) and p.tune_extract_waves in (1, 2, 3, 4)
+    assert p.tune_fit_ag in (2, 4, 8) and p.tune_fit_blocks in (1, 2, 3)
+    assert all(t > 0 for t in r1["phase_ms"])
+    p2 = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=c.sigma, precision=rlf.PREC_MIXED_SPLIT,
+                            update_mode=1)
+    r2 = rlf.autotune(obs, data, cat, p2, out, sky, ws, cache_path=cache)
+    assert r2["cached"] and all(getattr(p2, f) == getattr(p, f) for f in rlf.TUNE_FIELDS)
+    assert rlf.tuning_key(obs, cat.n_src, p) in json.load(open(cache))
+    # the tuned shapes give the oracle's answers
+    rlf.run(obs, data, cat, p, out, sky, ws)
+    got = out.numpy()
+    est = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m, c.cat.flux_jy, None,
+                          c.oracle_params(chunk=0, update_mode=1, facet_n=64))
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(got, i, est[i]) <= 1e-4, i
+
+
+def test_batched_workload_full_size_sampled(rlf):
+    # 148M visibilities, 1000 sources: sky model, every facet and every fit on the GPU
+    # (the chain's launch configuration); the oracle checks sampled rows and sources
+    import torch
+    c = cases.build(synth.workload("batched"), with_data=False)
+    R, C = c.obs.n_rows, c.obs.n_chan
+    e1, e2 = c.cat.e1, c.cat.e2
+    obs, cat = cases.to_device(c, e1, e2)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, precision=rlf.PREC_MIXED_SPLIT)
+    ws = rlf.alloc_workspace(R, C, cat.n_src, p, rlf.WS_SKY)
+    sky = torch.empty(R * C * 2, dtype=torch.float32, device="cuda")
+    rlf.sky_model(obs, cat, p, sky, ws)
+    rows = np.sort(np.random.default_rng(5).choice(R, 300, replace=False))
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                               c.alpha_med_rad(), e1, e2, nu_ref=c.wl.nu_ref_hz, rows=rows, with_abs=True)
+    got = sky.view(R, C, 2)[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    g = got[..., 0] + 1j * got[..., 1]
+    assert np.all(np.abs(g - ref) <= 1e-5 * ab + 2.0 ** -24 * np.sqrt(2) * np.abs(ref))
+    del sky, ws
+    # extraction + persistent fit of all 1000 facets from an arbitrary residual
+    sigma = 3e-3
+    rng = np.random.default_rng(8)
+    skyr = rng.standard_normal((R, C, 2), dtype=np.float32) * np.float32(1e-4)
+    data = skyr + synth.noise(R, C, sigma, 98)
+    pe = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, precision=rlf.PREC_MIXED_SPLIT, sigma_jy=sigma)
+    wse = rlf.alloc_workspace(R, C, cat.n_src, pe, rlf.WS_EXTRACT)
+    fac = torch.empty(rlf.facets_size(cat.n_src, pe) // 8, dtype=torch.float64, device="cuda")
+    rlf.extract_facets(obs, cases.vis_tensor(data), cases.vis_tensor(skyr), cat, 0, cat.n_src, pe, fac, wse)
+    del wse
+    wsf = rlf.alloc_workspace(R, C, cat.n_src, pe, rlf.WS_FIT)
+    out = rlf.Results(cat.n_src, "cuda")
+    rlf.fit_sources(fac, cat, 0, cat.n_src, pe, out, wsf)
+    res = out.numpy()
+    got_f = fac.view(cat.n_src, 4, -1)
+    po = c.oracle_params(sigma_jy=sigma)
+    al = c.alpha_med_rad()
+    for i in (0, 731):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, po)
+        refc, abc = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, data, skyr, c.cat.l[i], c.cat.m[i],
+                                         c.cat.flux_jy[i], al[i], e1[i], e2[i], du, po, with_abs=True)
+        gf = got_f[i].cpu().numpy()
+        assert np.array_equal(gf[2], refc[2])
+        assert np.all(np.abs(gf[0] - refc[0]) <= 3e-5 * abc + 1e-300)
+        assert np.all(np.abs(gf[1] - refc[1]) <= 3e-5 * abc + 1e-300)
+        est = oracle.fit_facet(refc, du, c.cat.flux_jy[i], po).est
+        assert cases.est_matches(res, i, est) <= 1e-4, (i, res["e1"][i], est[oracle.E1])
