@@ -15,8 +15,8 @@
 // cell: the thread sums that run in registers and adds it to shared memory only
 // when the cell changes.  At the end the CTA stores its partial facet with
 // plain coalesced stores, and facet_reduce_kernel sums the parts of each cell in
-// FP64 in a fixed order (no global atomics; the facets are bitwise
-// reproducible).  blockIdx.x runs over the sources, so the CTAs reading the same
+// FP64 in a fixed order (no global atomics).  Inside a CTA the warps' shared-memory
+// additions land in varying order, so repeated runs agree to FP32 rounding.  blockIdx.x runs over the sources, so the CTAs reading the same
 // baselines run together and share them through L2.
 //
 // Shared-memory planes: sum Re x, sum Im x (FP32), count (int32), and the sum of
