@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--precision", default="split", choices=["split", "mixed", "fp64"])
     ap.add_argument("--update-mode", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time rlf_run calls instead of the captured graph")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--no-batched", action="store_true", help="skip the extra 148M-visibility workload line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
     ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update"],
@@ -190,6 +193,58 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 
+TUNE_CACHE = os.path.join(ROOT, "paper_2203_14071_gb300", "_build", "tune_cache.json")
+
+
+def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
+    """Device inputs of a workload: baselines, catalogue (circular shapes), and data =
+    the library's sky model at the true shapes and scalelengths plus seeded noise."""
+    wl = synth.workload(name)
+    obs_np = synth.make_observation(wl)
+    cat_np = synth.make_catalogue(wl, n_src if n_src else (args.n_src if args.n_src > 0 else None))
+    R, C, n = obs_np.n_rows, obs_np.n_chan, cat_np.n_src
+    t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz, obs_np.n_bl)
+    zeros = torch.zeros(n, dtype=torch.float64, device=dev)
+    cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
+    truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
+    params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=args.chunk,
+                                precision=prec, update_mode=args.update_mode)
+    ws = rlf.alloc_workspace(R, C, n, params, rlf.WS_RUN, device=dev)
+    data = torch.empty(R * C * 2, dtype=torch.float32, device=dev)
+    rlf.sky_model(obs, truth, params, data, ws, stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    data += torch.randn(R * C * 2, generator=gen, device=dev, dtype=torch.float32) * wl.sigma_jy
+    sky = torch.empty_like(data)
+    out = rlf.Results(n, dev)
+    return {"wl": wl, "obs_np": obs_np, "cat_np": cat_np, "obs": obs, "cat": cat, "truth": truth,
+            "params": params, "ws": ws, "data": data, "sky": sky, "out": out}
+
+
+def batched_line(rlf, torch, dev, args, prec, rank, stream):
+    """The 148M-visibility, 1000-source workload (all facets per step, one graph)."""
+    W = setup_workload(rlf, torch, dev, "batched", args, prec, rank, stream, n_src=0)
+    p = W["params"]
+    tune = rlf.autotune(W["obs"], W["data"], W["cat"], p, W["out"], W["sky"], W["ws"], TUNE_CACHE, stream)
+    g = rlf.Graph(W["obs"], W["data"], W["cat"], p, W["out"], W["sky"], W["ws"], stream)
+    g.launch(stream)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 2
+    a.record(stream)
+    for _ in range(steps):
+        g.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    g.close()
+    n = W["cat_np"].n_src
+    nv = W["obs_np"].n_rows * W["obs_np"].n_chan
+    return {"workload": "batched", "n_vis": nv, "n_src": n, "ms_per_step": ms, "fits_per_s": n / (ms * 1e-3),
+            "tuning": {f: int(getattr(p, f)) for f in rlf.TUNE_FIELDS}, "steps": steps}
+
+
 
 def main():
     args = parse()
@@ -213,37 +268,27 @@ def main():
         dist.barrier()
     rlf.lib()
 
-    wl = synth.workload(args.workload)
-    obs_np = synth.make_observation(wl)
-    cat_np = synth.make_catalogue(wl, args.n_src if args.n_src > 0 else None)
+    stream = torch.cuda.Stream(dev)    # a non-default stream: the chain is captured as a CUDA graph
+    torch.cuda.set_stream(stream)
+    prec = {"split": rlf.PREC_MIXED_SPLIT, "mixed": rlf.PREC_MIXED, "fp64": rlf.PREC_FP64}[args.precision]
+    W = setup_workload(rlf, torch, dev, args.workload, args, prec, rank, stream)
+    obs_np, cat_np, obs, cat, params, ws, data, sky, out = (W[k] for k in (
+        "obs_np", "cat_np", "obs", "cat", "params", "ws", "data", "sky", "out"))
     n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
     n_vis = R * C
-    prec = {"split": rlf.PREC_MIXED_SPLIT, "mixed": rlf.PREC_MIXED, "fp64": rlf.PREC_FP64}[args.precision]
-    t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
-    obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz, obs_np.n_bl)
-    zeros = torch.zeros(n_src, dtype=torch.float64, device=dev)
-    cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
-    truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
-    params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=args.chunk,
-                                precision=prec, update_mode=args.update_mode)
-
-    # observed data: the true sky (library sky model at the catalogue's true shapes) plus noise
-    ws = rlf.alloc_workspace(R, C, n_src, params, rlf.WS_RUN, device=dev)
-    data = torch.empty(n_vis * 2, dtype=torch.float32, device=dev)
-    rlf.sky_model(obs, truth, params, data, ws)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(1234 + rank)
-    data += torch.randn(n_vis * 2, generator=gen, device=dev, dtype=torch.float32) * wl.sigma_jy
-    sky = torch.empty_like(data)
-    out = rlf.Results(n_src, dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
-        rlf.run(obs, data, cat, params, out, sky, ws, stream)
 
     if args.only:
         profile_only(args, rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, n_src)
         return
+
+    tuning = None if args.no_tune else rlf.autotune(obs, data, cat, params, out, sky, ws, TUNE_CACHE, stream)
+    graph = None if args.no_graph else rlf.Graph(obs, data, cat, params, out, sky, ws, stream)
+
+    def step():
+        if graph is not None:
+            graph.launch(stream)
+        else:
+            rlf.run(obs, data, cat, params, out, sky, ws, stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -302,6 +347,14 @@ def main():
         "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2))},
     }
     line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
+    line["launch"] = {"graph": graph is not None, "tuning": None if tuning is None else
+                      {f: int(getattr(params, f)) for f in rlf.TUNE_FIELDS}}
+    if graph is not None:
+        graph.close()
+    if not args.no_batched and world == 1:
+        del ws, data, sky
+        torch.cuda.empty_cache()
+        line["batched_workload"] = batched_line(rlf, torch, dev, args, prec, rank, stream)
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -361,9 +414,11 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     upd_ms = timed(lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream))
     chunk = params.chunk if params.chunk > 0 else n_src
     n_chunks = (n_src + chunk - 1) // chunk
-    # rlf_run: memset + 2 copies + prepare + sky; per chunk: memset + prepare + extract + compact + grid
-    # + estimate + prepare + update  (memsets/copies are not kernels of ours)
-    launches = 2 + n_chunks * 7
+    # kernels of one rlf_run step: prepare + sky model (+ split baselines in split mode); per chunk:
+    # residual (batched chunks only), extraction, partial reduce, compaction, LPT order, persistent
+    # fit, prepare + sky update (memsets and copies are not kernels of ours)
+    per_chunk = 7 + (1 if chunk >= 3 and params.precision != 0 else 0)
+    launches = 2 + (1 if params.precision == 2 else 0) + n_chunks * per_chunk
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
             "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches,
             "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item())}
