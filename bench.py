@@ -358,7 +358,7 @@ def main():
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, obs_np, cat_np)
+        line["cpu_baseline"] = cpu_baseline(W["wl"], obs_np, cat_np)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
