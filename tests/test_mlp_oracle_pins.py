@@ -1,0 +1,92 @@
+"""Pins of the learned-proposal oracle (oracle/mlp.py) on the CPU.
+
+The analytic backward is checked against central finite differences of the loss,
+the loss against its Gaussian definition, Adam against a hand-computed step, the
+simulator against the likelihood's facet model, and the proposal rule against
+its definition on hand-made cases."""
+import math
+
+import numpy as np
+
+import oracle
+from oracle import mlp
+
+
+def _net(rng, n_in=12, n_h=7):
+    W1 = rng.normal(0, 0.3, (n_in, n_h)); b1 = rng.normal(0, 0.1, n_h)
+    W2 = rng.normal(0, 0.3, (n_h, n_h)); b2 = rng.normal(0, 0.1, n_h)
+    W3 = rng.normal(0, 0.3, (n_h, 6)); b3 = rng.normal(0, 0.1, 6)
+    return [W1, b1, W2, b2, W3, b3]
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    P = _net(rng)
+    x = rng.normal(0, 1, (5, 12))
+    y = rng.normal(0, 0.5, (5, 3))
+    o, cache = mlp.forward(x, *P)
+    grads = mlp.backward(cache, P[2], P[4], mlp.nll_grad(o, y))
+    h = 1e-6
+    for pi, g in zip(range(6), grads):
+        flat = P[pi].reshape(-1)
+        for j in rng.choice(flat.size, min(6, flat.size), replace=False):
+            old = flat[j]
+            flat[j] = old + h
+            lp = mlp.nll(mlp.forward(x, *P)[0], y)
+            flat[j] = old - h
+            lm = mlp.nll(mlp.forward(x, *P)[0], y)
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g.reshape(-1)[j]) <= 1e-6 * max(1.0, abs(fd)), (pi, j)
+
+
+def test_nll_is_the_gaussian_negative_log_likelihood():
+    # 1/2 (logvar + r^2/var) = -log N(y; mu, var) - 1/2 log(2 pi)
+    o = np.array([[0.1, -0.2, 0.3, math.log(0.04), math.log(0.09), math.log(0.25)]])
+    y = np.array([[0.15, -0.1, 0.0]])
+    var = np.exp(o[0, 3:])
+    ref = sum(-(-0.5 * math.log(2 * math.pi * v) - 0.5 * (yy - m) ** 2 / v) - 0.5 * math.log(2 * math.pi)
+              for yy, m, v in zip(y[0], o[0, :3], var))
+    assert abs(mlp.nll(o, y) - ref) < 1e-12
+
+
+def test_adam_first_step_is_lr_times_sign():
+    # with bias correction the first step moves every weight by lr * g / (|g| + eps)
+    w = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -0.001, 2.0])
+    w1, m, v = mlp.adam(w, g, np.zeros(3), np.zeros(3), 1, 1e-3)
+    assert np.allclose(w1, w - 1e-3 * g / (np.abs(g) + 1e-8), atol=1e-15)
+
+
+def test_simulated_facet_is_the_likelihood_model():
+    # noise-free simulation equals S s M(k_c) / S from the oracle's Eq. 1 factor
+    N, du = 8, 4000.0
+    counts = np.zeros(N * N); counts[[3, 10, 27, 44]] = [2, 5, 1, 7]
+    sbar = np.where(counts > 0, 0.97, 0.0)
+    x = mlp.simulate(counts, sbar, du, 0.2, -0.3, 1.3, 0.0, np.zeros((2, N * N)), N=N)
+    for c in (3, 10, 27, 44):
+        iu, iv = c % N, c // N
+        M = oracle.shape((iu - N // 2 + 0.5) * du, (iv - N // 2 + 0.5) * du, 1.3 * mlp.ARC, 0.2, -0.3)
+        assert abs(x[c] - 0.97 * M) < 1e-14 and x[N * N + c] == 0.0
+    assert np.count_nonzero(x) == 4
+
+
+def test_proposal_box_and_fallback_rules():
+    p = oracle.default_params()
+    ge, ga = oracle.grid_e(p), oracle.grid_alpha(p)
+    # e1 = 0.17 -> node 12 (0.16), e2 = -0.79 -> node 0, alpha = 1.0" -> node 9 (1.018")
+    origin, wide = mlp.propose(np.array([0.17, -0.79, math.log(1.0)]), np.log([1e-4, 1e-4, 1e-2]), ge, ga)
+    assert origin == (9, 0, 7) and not wide
+    # clamped at the top end of the grid
+    origin, _ = mlp.propose(np.array([0.8, 0.0, math.log(3.5)]), np.zeros(3) - 9, ge, ga)
+    assert origin == (14, 7, 15)
+    # a predicted spread above three node spacings asks for the full grid
+    _, wide = mlp.propose(np.array([0.0, 0.0, 0.0]), np.log([0.25 ** 2, 1e-4, 1e-4]), ge, ga)
+    assert wide
+    ne, na, box = 21, 20, (7, 7, 5)
+    flat = lambda a, b, k: (a * ne + b) * na + k
+    assert mlp.on_inner_boundary(flat(9, 3, 9), (9, 0, 7), box, ne, na)        # lower e1 face, inside the grid
+    assert not mlp.on_inner_boundary(flat(12, 0, 9), (9, 0, 7), box, ne, na)   # e2 face is the grid's edge
+    assert mlp.on_inner_boundary(flat(12, 6, 9), (9, 0, 7), box, ne, na)       # upper e2 face
+    assert mlp.on_inner_boundary(flat(12, 3, 11), (9, 0, 7), box, ne, na)      # upper alpha face
+    assert not mlp.on_inner_boundary(flat(12, 3, 9), (9, 0, 7), box, ne, na)
