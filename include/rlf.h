@@ -230,6 +230,68 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
                    void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Learned proposal of the likelihood sub-grid.  A spec addition; the paper
+ * has no counterpart (its fit searches the likelihood with Nelder-Mead, Sec. 2.4).
+ * A perceptron reads a facet (facet_n must be 64: x = [Re D_c / S, Im D_c / S],
+ * 8192 values, empty cells 0, f16) and predicts (mu, logvar) of (e1, e2,
+ * ln(alpha/arcsec)): h1 = relu(x W1 + b1) [256], h2 = relu(h1 W2 + b2) [256],
+ * o = h2 W3 + b3 [8], o[0:3] = mu, o[3:6] = logvar, o[6:8] = 0.  Trained with the
+ * Gaussian NLL (logvar clamped to [-8, 8]) and Adam (beta 0.9, 0.999, eps 1e-8).
+ *
+ * Weights blob (device, rlf_mlp_weights_size() bytes, caller-owned), with
+ * P = rlf_mlp_n_params() and the parameter order W1 [8192][256], b1 [256],
+ * W2 [256][256], b2 [256], W3 [256][8], b3 [8] (row-major, columns 6 and 7 of W3
+ * zero): f32 params [P] | f32 Adam m [P] | f32 Adam v [P] | f32 gradients [P] |
+ * f16 copies of W1, W2, W3 (used by the tensor-core GEMMs).
+ */
+#define RLF_MLP_IN 8192
+#define RLF_MLP_OUT 8
+size_t rlf_mlp_weights_size(void);
+int64_t rlf_mlp_n_params(void);
+/* Scratch bytes for rlf_mlp_train_step / rlf_mlp_forward with up to max_batch facets. */
+size_t rlf_mlp_workspace_size(int32_t max_batch);
+/* He initialisation from P standard normals (device, e.g. from a seeded RNG); zero biases and moments. */
+rlf_status rlf_mlp_init(void *weights, const float *normals, void *stream);
+/*
+ * Training facets from the likelihood's own facet model (Sec. 2.4): for sample b,
+ * template t = tidx[b] (a facet [4][64*64] as from rlf_extract_facets, of flux
+ * template_flux[t], cell size 1/(K alpha_med(flux)) by Eq. 4), every non-empty cell
+ *   x_c = s_c M(k_c; e1[b], e2[b], alpha_arcsec[b]) + (sigma_jy / flux) z / sqrt(n_c)
+ * with z = normals[b][0 or 1][c] (device [batch][2][4096] standard normals) for the
+ * real and imaginary parts; y[b] = (e1, e2, ln alpha) (device [batch][3] f32).
+ * x_f16: device [batch][8192] f16.
+ */
+rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux, int32_t n_templates,
+                            const int32_t *tidx, const double *e1, const double *e2, const double *alpha_arcsec,
+                            const float *normals, int32_t batch, const rlf_params *p, void *x_f16, float *y,
+                            void *stream);
+/* One Adam step on a batch (x_f16 [batch][8192], y [batch][3]); step >= 1 is the Adam time
+ * step (bias correction); step = 0 computes the gradients into the blob and leaves the
+ * parameters unchanged.  loss (device f32, may be NULL) receives the batch NLL. */
+rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,
+                              int32_t step, float *loss, void *workspace, size_t ws_bytes, void *stream);
+/* out (device [batch][8] f32): the network's outputs for x_f16. */
+rlf_status rlf_mlp_forward(const void *weights, const void *x_f16, int32_t batch, float *out, void *workspace,
+                           size_t ws_bytes, void *stream);
+/* Network inputs (device [count][8192] f16) of facets [count][4][64*64] of sources
+ * [first, first + count).  Workspace: rlf_workspace_size(..., RLF_WS_FIT). */
+rlf_status rlf_mlp_encode(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                          const rlf_params *p, void *x_f16, void *workspace, size_t ws_bytes, void *stream);
+/*
+ * rlf_fit_sources on a narrowed grid: the network proposes each facet's 7 x 7 x 5
+ * box of grid nodes centred on the node nearest mu (clamped inside the grid); the
+ * likelihood and the estimate are computed on the box only (alpha quadrature on the
+ * box's nodes, points outside the box excluded).  A facet is refitted on the full
+ * grid when the predicted spread of e1 or e2 exceeds three node spacings, or when
+ * its box MAP point lies on a face of the box that is not a face of the grid.
+ * n_fallback (device int32, may be NULL) receives the number of refitted facets.
+ * Requires facet_n = 64, a mixed precision mode, n_e >= 7 and n_alpha >= 5.
+ */
+rlf_status rlf_fit_sources_mlp(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                               const rlf_params *p, const void *weights, const rlf_fit_out *out,
+                               int32_t *n_fallback, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * The whole chain as a captured CUDA graph (the batched form: one graph holds the
  * sky model, every extraction, the persistent fit and the update; with chunk =
  * n_src that is one launch per step).  rlf_graph_create records rlf_run's work on

@@ -6,7 +6,10 @@ should be evaluated.  Everything here is the plain definition, in numpy float64:
   encode      x = [Re D_c / S, Im D_c / S] over the N x N window (empty cells 0)
   forward     h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), o = h2 W3 + b3,
               mu = o[0:3] (e1, e2, ln(alpha / arcsec)), logvar = o[3:6]
-  nll         mean over the batch of 1/2 sum_j (logvar_j + (y_j - mu_j)^2 exp(-logvar_j))
+  nll         mean over the batch of 1/2 sum_j (lv_j + (y_j - mu_j)^2 exp(-lv_j)), with
+              lv = logvar clamped to [-8, 8] (zero gradient outside): a predicted
+              spread below e^-4 = 0.018 is finer than the grid needs, and the clamp
+              keeps the f16 gradients of the GPU kernels finite
   backward    the chain rule of the three layers, written out
   adam        Kingma & Ba (2015), bias-corrected moments
   simulate    D_c / S = s_c M(k_c; e, alpha) + (sigma / S) z / sqrt(n_c) per component,
@@ -44,19 +47,24 @@ def forward(x, W1, b1, W2, b2, W3, b3):
     return o, (x, z1, h1, z2, h2)
 
 
+LV_MIN, LV_MAX = -8.0, 8.0
+
+
 def nll(o, y):
-    mu, lv = o[:, :3], o[:, 3:6]
+    mu, lv = o[:, :3], np.clip(o[:, 3:6], LV_MIN, LV_MAX)
     return float(np.mean(0.5 * np.sum(lv + (y - mu) ** 2 * np.exp(-lv), axis=1)))
 
 
 def nll_grad(o, y):
     """d nll / d o."""
     B = o.shape[0]
-    mu, lv = o[:, :3], o[:, 3:6]
+    raw = o[:, 3:6]
+    mu, lv = o[:, :3], np.clip(raw, LV_MIN, LV_MAX)
     r = y - mu
     g = np.zeros_like(o)
     g[:, :3] = -r * np.exp(-lv) / B
-    g[:, 3:6] = 0.5 * (1.0 - r * r * np.exp(-lv)) / B
+    inside = (raw > LV_MIN) & (raw < LV_MAX)
+    g[:, 3:6] = np.where(inside, 0.5 * (1.0 - r * r * np.exp(-lv)) / B, 0.0)
     return g
 
 

@@ -118,6 +118,22 @@ def lib():
             L.rlf_autotune.argtypes = [P(Uvw), _vp, P(Sources), P(Params), P(FitOut), _vp, _vp, sz, _vp,
                                        P(ctypes.c_float)]
             L.rlf_autotune.restype = ctypes.c_int
+            L.rlf_mlp_weights_size.argtypes = []
+            L.rlf_mlp_weights_size.restype = sz
+            L.rlf_mlp_n_params.argtypes = []
+            L.rlf_mlp_n_params.restype = i64
+            L.rlf_mlp_workspace_size.argtypes = [i32]
+            L.rlf_mlp_workspace_size.restype = sz
+            L.rlf_mlp_init.argtypes = [_vp, _vp, _vp]
+            L.rlf_mlp_simulate.argtypes = [_vp, _vp, i32, _vp, _vp, _vp, _vp, _vp, i32, P(Params), _vp, _vp, _vp]
+            L.rlf_mlp_train_step.argtypes = [_vp, _vp, _vp, i32, ctypes.c_float, i32, _vp, _vp, sz, _vp]
+            L.rlf_mlp_forward.argtypes = [_vp, _vp, i32, _vp, _vp, sz, _vp]
+            L.rlf_mlp_encode.argtypes = [_vp, P(Sources), i32, i32, P(Params), _vp, _vp, sz, _vp]
+            L.rlf_fit_sources_mlp.argtypes = [_vp, P(Sources), i32, i32, P(Params), _vp, P(FitOut), _vp, _vp, sz,
+                                              _vp]
+            for f in ("rlf_mlp_init", "rlf_mlp_simulate", "rlf_mlp_train_step", "rlf_mlp_forward",
+                      "rlf_mlp_encode", "rlf_fit_sources_mlp"):
+                getattr(L, f).restype = ctypes.c_int
             L.rlf_sky_model_static.argtypes = [P(Uvw), P(Sources), P(Params), _vp, _vp]
             L.rlf_sky_model_static.restype = ctypes.c_int
             L.rlf_peaks_measure.argtypes = [_vp, sz, _vp, P(Peaks)]
@@ -370,3 +386,87 @@ def peaks_measure(stream=None) -> dict:
     if code != 0:
         raise RuntimeError(f"rlf_peaks_measure failed ({code})")
     return {f: getattr(out, f) for f, _ in Peaks._fields_}
+
+
+# ---- learned proposal ------------------------------------------------------------------
+
+MLP_IN, MLP_HIDDEN, MLP_OUT = 8192, 256, 8
+
+
+def mlp_offsets() -> dict:
+    """Parameter offsets inside the weights blob (see include/rlf.h)."""
+    o = {"W1": 0}
+    o["b1"] = o["W1"] + MLP_IN * MLP_HIDDEN
+    o["W2"] = o["b1"] + MLP_HIDDEN
+    o["b2"] = o["W2"] + MLP_HIDDEN * MLP_HIDDEN
+    o["W3"] = o["b2"] + MLP_HIDDEN
+    o["b3"] = o["W3"] + MLP_HIDDEN * MLP_OUT
+    o["P"] = o["b3"] + MLP_OUT
+    return o
+
+
+class Mlp:
+    """A weights blob on the device with views of its sections."""
+
+    def __init__(self, device="cuda"):
+        import torch
+        n = int(lib().rlf_mlp_weights_size())
+        self.blob = torch.zeros(n, dtype=torch.uint8, device=device)
+        self.P = int(lib().rlf_mlp_n_params())
+        o = mlp_offsets()
+        assert o["P"] == self.P
+        f32 = self.blob[: 4 * self.P * 4].view(torch.float32)
+        self.w, self.m, self.v, self.g = (f32[i * self.P:(i + 1) * self.P] for i in range(4))
+        self.h = self.blob[4 * self.P * 4:].view(torch.float16)
+        self.off = o
+
+    def section(self, vec, name):
+        o = self.off
+        shapes = {"W1": (MLP_IN, MLP_HIDDEN), "b1": (MLP_HIDDEN,), "W2": (MLP_HIDDEN, MLP_HIDDEN),
+                  "b2": (MLP_HIDDEN,), "W3": (MLP_HIDDEN, MLP_OUT), "b3": (MLP_OUT,)}
+        n = int(np.prod(shapes[name]))
+        return vec[o[name]:o[name] + n].view(*shapes[name])
+
+    def half(self, name):
+        sizes = {"W1": MLP_IN * MLP_HIDDEN, "W2": MLP_HIDDEN * MLP_HIDDEN, "W3": MLP_HIDDEN * MLP_OUT}
+        start = {"W1": 0, "W2": sizes["W1"], "W3": sizes["W1"] + sizes["W2"]}[name]
+        shape = {"W1": (MLP_IN, MLP_HIDDEN), "W2": (MLP_HIDDEN, MLP_HIDDEN), "W3": (MLP_HIDDEN, MLP_OUT)}[name]
+        return self.h[start:start + sizes[name]].view(*shape)
+
+    def init(self, normals, stream=None):
+        _check(lib().rlf_mlp_init(_ptr(self.blob), _ptr(normals), _stream(stream)), "rlf_mlp_init")
+
+
+def mlp_workspace(max_batch: int, device="cuda"):
+    import torch
+    return torch.empty(int(lib().rlf_mlp_workspace_size(max_batch)), dtype=torch.uint8, device=device)
+
+
+def mlp_simulate(templates, template_flux, tidx, e1, e2, alpha_arcsec, normals, params: Params, x16, y,
+                 stream=None):
+    _check(lib().rlf_mlp_simulate(_ptr(templates), _ptr(template_flux), int(template_flux.numel()), _ptr(tidx),
+                                  _ptr(e1), _ptr(e2), _ptr(alpha_arcsec), _ptr(normals), int(tidx.numel()),
+                                  ctypes.byref(params), _ptr(x16), _ptr(y), _stream(stream)), "rlf_mlp_simulate")
+
+
+def mlp_train_step(mlp: Mlp, x16, y, lr: float, step: int, loss, workspace, stream=None):
+    _check(lib().rlf_mlp_train_step(_ptr(mlp.blob), _ptr(x16), _ptr(y), int(y.shape[0]), float(lr), int(step),
+                                    _ptr(loss), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "rlf_mlp_train_step")
+
+
+def mlp_forward(mlp: Mlp, x16, out, workspace, stream=None):
+    _check(lib().rlf_mlp_forward(_ptr(mlp.blob), _ptr(x16), int(out.shape[0]), _ptr(out), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)), "rlf_mlp_forward")
+
+
+def mlp_encode(facets, cat: Catalogue, first: int, count: int, params: Params, x16, workspace, stream=None):
+    _check(lib().rlf_mlp_encode(_ptr(facets), ctypes.byref(cat.struct), first, count, ctypes.byref(params),
+                                _ptr(x16), _ptr(workspace), workspace.numel(), _stream(stream)), "rlf_mlp_encode")
+
+
+def fit_sources_mlp(facets, cat: Catalogue, first: int, count: int, params: Params, mlp: Mlp, out: Results,
+                    workspace, n_fallback=None, stream=None):
+    _check(lib().rlf_fit_sources_mlp(_ptr(facets), ctypes.byref(cat.struct), first, count, ctypes.byref(params),
+                                     _ptr(mlp.blob), ctypes.byref(out.struct), _ptr(n_fallback), _ptr(workspace),
+                                     workspace.numel(), _stream(stream)), "rlf_fit_sources_mlp")

@@ -112,6 +112,13 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_order = take(fit ? cap * sizeof(int32_t) : 0);
     const size_t o_count = take(fit ? (cap + 1) * sizeof(int32_t) : 0);
     const size_t o_cc = take(fit ? cap * sizeof(double) : 0);
+    const size_t o_box = take(fit ? cap * 3 * sizeof(int32_t) : 0);
+    const size_t o_wide = take(fit ? cap * sizeof(int32_t) : 0);
+    const size_t o_map = take(fit ? cap * sizeof(int32_t) : 0);
+    const size_t o_refit = take(fit ? (cap + 1) * sizeof(int32_t) : 0);
+    const bool mlp = fit && p.facet_n * p.facet_n * 2 == kMlpIn;
+    const size_t o_mx = take(mlp ? cap * kMlpIn * sizeof(__half) : 0);
+    const size_t o_ms = take(mlp ? mlp_scratch(nullptr, (int32_t)cap).bytes : 0);
     const size_t o_ga = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_gb = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
@@ -131,6 +138,12 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->cells = b + o_cells;
         ws->ncell = reinterpret_cast<int32_t *>(b + o_ncell);
         ws->order = reinterpret_cast<int32_t *>(b + o_order);
+        ws->box = reinterpret_cast<int32_t *>(b + o_box);
+        ws->wide = reinterpret_cast<int32_t *>(b + o_wide);
+        ws->map_index = reinterpret_cast<int32_t *>(b + o_map);
+        ws->refit = reinterpret_cast<int32_t *>(b + o_refit);
+        ws->mlp_x = b + o_mx;
+        ws->mlp_scratch = b + o_ms;
         ws->counters = reinterpret_cast<int32_t *>(b + o_count);
         ws->cc = reinterpret_cast<double *>(b + o_cc);
         ws->ga = reinterpret_cast<double *>(b + o_ga);
@@ -539,6 +552,107 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
         phase_ms[2] = best[2];
     }
     return RLF_OK;
+}
+
+size_t rlf_mlp_weights_size(void) { return mlp_weights_bytes(); }
+
+int64_t rlf_mlp_n_params(void) { return mlp_offsets().P; }
+
+size_t rlf_mlp_workspace_size(int32_t max_batch)
+{
+    if (max_batch <= 0) return 0;
+    return mlp_scratch(nullptr, max_batch).bytes + 256;
+}
+
+static void *align256(void *p) { return reinterpret_cast<void *>((reinterpret_cast<size_t>(p) + 255) / 256 * 256); }
+
+rlf_status rlf_mlp_init(void *weights, const float *normals, void *stream)
+{
+    if (!weights || !normals) return RLF_EINVAL;
+    return cuda_status(mlp_init(mlp_weights(weights), normals, static_cast<cudaStream_t>(stream)));
+}
+
+rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux, int32_t n_templates,
+                            const int32_t *tidx, const double *e1, const double *e2, const double *alpha_arcsec,
+                            const float *normals, int32_t batch, const rlf_params *p, void *x_f16, float *y,
+                            void *stream)
+{
+    if (!templates || !template_flux || !tidx || !e1 || !e2 || !alpha_arcsec || !normals || !x_f16 || !y || !p)
+        return RLF_EINVAL;
+    if (n_templates <= 0 || batch <= 0 || !params_ok(*p)) return RLF_EINVAL;
+    if (p->facet_n * p->facet_n * 2 != kMlpIn) return RLF_EUNSUPPORTED;
+    return cuda_status(mlp_simulate(templates, n_templates, *p, template_flux, tidx, e1, e2, alpha_arcsec, normals, batch,
+                                    p->facet_n, p->sigma_jy, static_cast<__half *>(x_f16), y,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,
+                              int32_t step, float *loss, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!weights || !x_f16 || !y || !workspace || batch <= 0) return RLF_EINVAL;
+    if (ws_bytes < rlf_mlp_workspace_size(batch)) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (loss) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (e == cudaSuccess)
+        e = mlp_train_step(mlp_weights(weights), static_cast<const __half *>(x_f16), y, batch, lr, step, loss,
+                           mlp_scratch(align256(workspace), batch), st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_mlp_forward(const void *weights, const void *x_f16, int32_t batch, float *out, void *workspace,
+                           size_t ws_bytes, void *stream)
+{
+    if (!weights || !x_f16 || !out || !workspace || batch <= 0) return RLF_EINVAL;
+    if (ws_bytes < rlf_mlp_workspace_size(batch)) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const MlpScratch sc = mlp_scratch(align256(workspace), batch);
+    cudaError_t e = mlp_forward(mlp_weights(const_cast<void *>(weights)), static_cast<const __half *>(x_f16), batch,
+                                sc, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, sc.o, (size_t)batch * kMlpOutPad * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_mlp_encode(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                          const rlf_params *p, void *x_f16, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    rlf_status s = check_src(src, first, count);
+    if (s != RLF_OK) return s;
+    if (!facets || !x_f16 || !workspace) return RLF_EINVAL;
+    if (p->facet_n * p->facet_n * 2 != kMlpIn) return RLF_EUNSUPPORTED;
+    Workspace ws;
+    if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
+                                   nullptr, *p, ws.table, ws.status, st);
+    if (e == cudaSuccess) e = mlp_encode(facets, ws.table, count, p->facet_n, static_cast<__half *>(x_f16), st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_fit_sources_mlp(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                               const rlf_params *p, const void *weights, const rlf_fit_out *out,
+                               int32_t *n_fallback, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    rlf_status s = check_src(src, first, count);
+    if (s != RLF_OK) return s;
+    if (!facets || !workspace || !weights || !out || !out->e1 || !out->e2 || !out->sig1 || !out->sig2 ||
+        !out->alpha_arcsec || !out->flux_jy || !out->e1_smooth || !out->e2_smooth || !out->flag)
+        return RLF_EINVAL;
+    if (p->facet_n * p->facet_n * 2 != kMlpIn || p->precision == RLF_PREC_FP64 || p->n_e < kBoxE ||
+        p->n_alpha < kBoxA)
+        return RLF_EUNSUPPORTED;
+    Workspace ws;
+    if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ws.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr, nullptr, *p,
+                           ws.table, ws.status, st);
+    if (e == cudaSuccess) e = launch_fit_mlp(facets, ws.table, count, *p, ws, weights, *out, n_fallback, st);
+    return cuda_status(e);
 }
 
 rlf_status rlf_read_status(void *workspace, int32_t *status_out, void *stream)

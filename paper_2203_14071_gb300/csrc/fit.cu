@@ -125,10 +125,25 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
     __shared__ T sm[5][kCellTile];
     const int pair = tile * kThreads + threadIdx.x;
     const int ne2 = gc.n_e * gc.n_e;
-    const int e_idx = pair / gc.n_ag;
-    const int ag = pair % gc.n_ag;
-    const int i1 = e_idx / gc.n_e, i2 = e_idx % gc.n_e;
-    bool on = e_idx < ne2;
+    int e_idx, ag, i1, i2, k_lo = 0, k_hi = gc.n_alpha;
+    bool on;
+    if (gc.box) {
+        // sub-box mode: pairs run over the box's e points and alpha groups only
+        const int el = pair / gc.n_ag;
+        ag = pair % gc.n_ag;
+        on = el < kBoxE * kBoxE;
+        i1 = gc.box[s * 3 + 0] + el / kBoxE;
+        i2 = gc.box[s * 3 + 1] + el % kBoxE;
+        k_lo = gc.box[s * 3 + 2];
+        k_hi = k_lo + kBoxA;
+        e_idx = on ? i1 * gc.n_e + i2 : ne2;
+    } else {
+        e_idx = pair / gc.n_ag;
+        ag = pair % gc.n_ag;
+        i1 = e_idx / gc.n_e;
+        i2 = e_idx % gc.n_e;
+        on = e_idx < ne2;
+    }
     double e1 = 0.0, e2 = 0.0;
     if (on) {
         e1 = grid_e(gc, i1);
@@ -148,8 +163,8 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
     }
 #pragma unroll
     for (int j = 0; j < AG; ++j) {
-        const int k = ag * AG + j;
-        if (k < gc.n_alpha) {
+        const int k = k_lo + ag * AG + j;
+        if (k < k_hi) {
             const double al = grid_alpha(gc, k) * kArcsec * du;
             calpha[j] = (T)(4.0 * kPi * kPi * al * al);
             nk = j + 1;
@@ -234,7 +249,7 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
         }
     }
     if (e_idx < ne2) {
-        const size_t base = ((size_t)s * ne2 + e_idx) * gc.n_alpha + (size_t)ag * AG;
+        const size_t base = ((size_t)s * ne2 + e_idx) * gc.n_alpha + k_lo + (size_t)ag * AG;
         for (int j = 0; j < nk; ++j) {
             ga[base + j] = on ? da[j] : 0.0;
             gb[base + j] = on ? db[j] : 0.0;
@@ -309,7 +324,7 @@ __device__ void estimate_source(int s, const double *__restrict__ ga, const doub
                                 double *__restrict__ gl, const int32_t *__restrict__ ncell,
                                 const double *__restrict__ ccv, const SrcRow *__restrict__ table,
                                 const GridConst &gc, const rlf_fit_out &out, int32_t out_offset,
-                                int32_t *__restrict__ status)
+                                int32_t *__restrict__ status, int32_t *__restrict__ map_out)
 {
     __shared__ double red[kThreads / 32];
     __shared__ long long redi[kThreads / 32];
@@ -344,7 +359,13 @@ __device__ void estimate_source(int s, const double *__restrict__ ga, const doub
         const int e_idx = (int)(g / na);
         const double e1 = grid_e(gc, e_idx / ne), e2 = grid_e(gc, e_idx % ne);
         double v = -INFINITY;
-        if (nc > 0 && e1 * e1 + e2 * e2 < 1.0) {
+        bool in_box = true;
+        if (gc.box) {
+            const int d1 = e_idx / ne - gc.box[s * 3 + 0], d2 = e_idx % ne - gc.box[s * 3 + 1];
+            const int dk = (int)(g % na) - gc.box[s * 3 + 2];
+            in_box = d1 >= 0 && d1 < kBoxE && d2 >= 0 && d2 < kBoxE && dk >= 0 && dk < kBoxA;
+        }
+        if (in_box && nc > 0 && e1 * e1 + e2 * e2 < 1.0) {
             v = flux_marginal(a[g], b[g], cc, gc.flux_prior);
             if (!isfinite(v)) bad_num = true;
         }
@@ -446,6 +467,7 @@ __device__ void estimate_source(int s, const double *__restrict__ ga, const doub
         out.e1_smooth[o] = Ws > 0 ? s1 / Ws : 0.0;
         out.e2_smooth[o] = Ws > 0 ? s2 / Ws : 0.0;
         out.flag[o] = flag;
+        if (map_out) map_out[s] = best > -INFINITY ? (int32_t)gbest : -1;
     }
 }
 
@@ -473,15 +495,17 @@ template <typename T, int AG>
 __global__ void __launch_bounds__(kThreads, 3)
 fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
                       const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
-                      int32_t count, const int32_t *__restrict__ order, int32_t *__restrict__ counters,
-                      const GridConst gc, double *__restrict__ ga, double *__restrict__ gb,
-                      double *__restrict__ gl, const double *__restrict__ ccv, rlf_fit_out out,
-                      int32_t out_offset, int32_t *__restrict__ status)
+                      int32_t count, const int32_t *__restrict__ count_dev, const int32_t *__restrict__ order,
+                      int32_t *__restrict__ counters, const GridConst gc, double *__restrict__ ga,
+                      double *__restrict__ gb, double *__restrict__ gl, const double *__restrict__ ccv,
+                      rlf_fit_out out, int32_t out_offset, int32_t *__restrict__ status,
+                      int32_t *__restrict__ map_out)
 {
     __shared__ int s_item, s_last;
     int32_t *item_counter = counters;
     int32_t *src_done = counters + 1;
-    const int total = count * tiles_per_src;
+    // the number of facets may be known only on the device (refit list)
+    const int total = (count_dev ? *count_dev : count) * tiles_per_src;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1);
         __syncthreads();
@@ -496,7 +520,7 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
         __syncthreads();
         if (s_last) {
             __threadfence();
-            estimate_source(s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset, status);
+            estimate_source(s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset, status, map_out);
         }
         __syncthreads();
     }
@@ -506,13 +530,34 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
 
 namespace {
 
+// Facets whose sub-box fit must be redone on the full grid: the proposal was too
+// wide, or the MAP point lies on a face of the box that is not a face of the grid.
+__global__ void refit_list_kernel(const int32_t *__restrict__ box, const int32_t *__restrict__ wide,
+                                  const int32_t *__restrict__ map_index, int32_t count, int32_t ne, int32_t na,
+                                  int32_t *__restrict__ refit)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count) return;
+    bool again = wide[s] != 0;
+    const int g = map_index[s];
+    if (!again && g >= 0) {
+        const int i1 = g / (ne * na), i2 = (g / na) % ne, k = g % na;
+        const int o1 = box[s * 3], o2 = box[s * 3 + 1], ok = box[s * 3 + 2];
+        again = (i1 == o1 && o1 > 0) || (i1 == o1 + kBoxE - 1 && o1 + kBoxE < ne) ||
+                (i2 == o2 && o2 > 0) || (i2 == o2 + kBoxE - 1 && o2 + kBoxE < ne) ||
+                (k == ok && ok > 0) || (k == ok + kBoxA - 1 && ok + kBoxA < na);
+    }
+    if (again) refit[1 + atomicAdd(&refit[0], 1)] = s;
+}
+
 template <typename T, int AG>
 cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
-                              GridConst gc, const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
-                              int32_t out_offset, cudaStream_t st)
+                              const int32_t *count_dev, const int32_t *order, GridConst gc, const rlf_params &p,
+                              const Workspace &ws, const rlf_fit_out &out, int32_t out_offset, int32_t *map_out,
+                              cudaStream_t st)
 {
-    gc.n_ag = (gc.n_alpha + AG - 1) / AG;
-    const int pairs = gc.n_e * gc.n_e * gc.n_ag;
+    gc.n_ag = gc.box ? (kBoxA + AG - 1) / AG : (gc.n_alpha + AG - 1) / AG;
+    const int pairs = (gc.box ? kBoxE * kBoxE : gc.n_e * gc.n_e) * gc.n_ag;
     const int tiles = (pairs + kThreads - 1) / kThreads;
     auto kern = fit_persistent_kernel<T, AG>;
     int per_sm = 0;
@@ -527,33 +572,42 @@ cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane,
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > items) grid = items;
     if ((e = cudaMemsetAsync(ws.counters, 0, (size_t)(count + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
-    lpt_order_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.ncell, count, ws.order);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    kern<<<(int)grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, ws.order, ws.counters,
-                                         gc, ws.ga, ws.gb, ws.gl, ws.cc, out, out_offset, ws.status);
+    if (!order) {
+        lpt_order_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.ncell, count, ws.order);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        order = ws.order;
+    }
+    kern<<<(int)grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, count_dev, order,
+                                         ws.counters, gc, ws.ga, ws.gb, ws.gl, ws.cc, out, out_offset, ws.status,
+                                         map_out);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_persistent_ag(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
-                                 const GridConst &gc, const rlf_params &p, const Workspace &ws,
-                                 const rlf_fit_out &out, int32_t out_offset, cudaStream_t st)
+                                 const int32_t *count_dev, const int32_t *order, const GridConst &gc,
+                                 const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
+                                 int32_t out_offset, int32_t *map_out, cudaStream_t st)
 {
     switch (p.tune_fit_ag) {
-    case 2: return launch_persistent<T, 2>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
-    case 8: return launch_persistent<T, 8>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
-    default: return launch_persistent<T, 4>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    case 2:
+        return launch_persistent<T, 2>(cells, table, plane, NN, count, count_dev, order, gc, p, ws, out, out_offset,
+                                       map_out, st);
+    case 8:
+        return launch_persistent<T, 8>(cells, table, plane, NN, count, count_dev, order, gc, p, ws, out, out_offset,
+                                       map_out, st);
+    default:
+        return launch_persistent<T, 4>(cells, table, plane, NN, count, count_dev, order, gc, p, ws, out, out_offset,
+                                       map_out, st);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
-                       const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
-                       int32_t out_offset, cudaStream_t st)
+GridConst grid_const(const rlf_params &p)
 {
-    const int N = p.facet_n, NN = N * N;
     GridConst gc;
+    gc.box = nullptr;
     gc.n_e = p.n_e;
     gc.n_alpha = p.n_alpha;
     gc.n_ag = 0;
@@ -566,21 +620,70 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
     gc.thresh_frac = p.thresh_frac;
     gc.var_sigma_min = p.var_sigma_min;
     gc.var_det_min = p.var_det_min;
+    return gc;
+}
+
+cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
+                       const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
+                       int32_t out_offset, cudaStream_t st)
+{
+    const int N = p.facet_n, NN = N * N;
+    const GridConst gc = grid_const(p);
     const size_t plane = (size_t)count * NN;
+    cudaError_t e;
     if (p.precision != RLF_PREC_FP64) {
         float *cells = static_cast<float *>(ws.cells);
         compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                           ws.ncell, ws.cc);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        return launch_persistent_ag<float>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out,
+                                           out_offset, nullptr, st);
     }
     double *cells = static_cast<double *>(ws.cells);
     compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                        ws.ncell, ws.cc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_persistent<double, 4>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
+                                        nullptr, st);
+}
+
+cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t count, const rlf_params &p,
+                           const Workspace &ws, const void *weights, const rlf_fit_out &out, int32_t *n_fallback,
+                           cudaStream_t st)
+{
+    const int N = p.facet_n, NN = N * N;
+    GridConst gc = grid_const(p);
+    const size_t plane = (size_t)count * NN;
+    float *cells = static_cast<float *>(ws.cells);
+    compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells, ws.ncell,
+                                                      ws.cc);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_persistent<double, 4>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    // the network's proposal of each facet's sub-box
+    const MlpWeights W = mlp_weights(const_cast<void *>(weights));
+    const MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    __half *x = static_cast<__half *>(ws.mlp_x);
+    if (e == cudaSuccess) e = mlp_encode(facets, table, count, N, x, st);
+    if (e == cudaSuccess) e = mlp_forward(W, x, count, sc, st);
+    if (e == cudaSuccess) e = mlp_propose(sc.o, count, gc, ws.box, ws.wide, st);
+    // the likelihood on every facet's sub-box
+    gc.box = ws.box;
+    if (e == cudaSuccess)
+        e = launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, 0,
+                                        ws.map_index, st);
+    // the facets that need the full grid, in one more persistent launch
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.refit, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) {
+        refit_list_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.box, ws.wide, ws.map_index,
+                                                                                 count, p.n_e, p.n_alpha, ws.refit);
+        e = cudaGetLastError();
+    }
+    gc.box = nullptr;
+    if (e == cudaSuccess)
+        e = launch_persistent_ag<float>(cells, table, plane, NN, count, ws.refit, ws.refit + 1, gc, p, ws, out, 0,
+                                        nullptr, st);
+    if (e == cudaSuccess && n_fallback)
+        e = cudaMemcpyAsync(n_fallback, ws.refit, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    return e;
 }
 
 }  // namespace rlf

@@ -1,0 +1,495 @@
+// Learned proposal of the likelihood sub-grid (a spec addition; no
+// counterpart in the paper): a 8192-256-256-6 perceptron reads a facet and
+// predicts the mean and log-variance of (e1, e2, ln alpha); the fit then
+// evaluates only a 7 x 7 x 5 box of the grid around the prediction.
+//
+// Kernels: tensor-core GEMMs (mma.sync m16n8k16, f16 inputs, f32 accumulation)
+// with fused epilogues for the forward and backward passes, the Gaussian NLL and
+// its gradient, bias-gradient column sums, Adam, the facet encoder, the training
+// facet simulator and the proposal rule.  Weights: f32 masters + f16 copies.
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "rlf_internal.cuh"
+
+namespace rlf {
+
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8, GTHREADS = 128;
+
+enum { EPI_F32 = 0, EPI_F32_BIAS = 1, EPI_F16_BIAS_RELU = 2, EPI_F16_MASK = 3 };
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[M x N] = op(A)[M x K] op(B)[K x N]; op = transpose when TA / TB.  Row-major
+// storage: A(m, k) = TA ? A[k * lda + m] : A[m * lda + k];
+//          B(k, n) = TB ? B[n * ldb + k] : B[k * ldb + n].
+// Tiles of 64 x 64 x 32 staged in shared memory as As[m][k] and Bt[n][k]; four
+// warps each own a 32 x 32 block of mma tiles.  Ragged edges are zero-filled.
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(GTHREADS)
+gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __half *__restrict__ B, int ldb,
+            const float *__restrict__ bias, const __half *__restrict__ mask, int ldm, float *__restrict__ C32,
+            __half *__restrict__ C16, int ldc)
+{
+    __shared__ __align__(16) __half As[GBM][GBK + GPAD];
+    __shared__ __align__(16) __half Bt[GBN][GBK + GPAD];
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    const __half zero = __float2half(0.0f);
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        for (int i = threadIdx.x; i < GBM * GBK; i += GTHREADS) {
+            int m, k;
+            if (TA) {
+                m = i % GBM;
+                k = i / GBM;
+            } else {
+                m = i / GBK;
+                k = i % GBK;
+            }
+            const int gm = m0 + m, gk = k0 + k;
+            __half v = zero;
+            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            As[m][k] = v;
+        }
+        for (int i = threadIdx.x; i < GBN * GBK; i += GTHREADS) {
+            int n, k;
+            if (TB) {
+                n = i / GBK;
+                k = i % GBK;
+            } else {
+                n = i % GBN;
+                k = i / GBN;
+            }
+            const int gn = n0 + n, gk = k0 + k;
+            __half v = zero;
+            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+            Bt[n][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int im = 0; im < 2; ++im) {
+                const int r = wm + im * 16 + g;
+                af[im][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
+                af[im][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
+                af[im][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 8 + 2 * t]);
+                af[im][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int in = 0; in < 4; ++in) {
+                const int c = wn + in * 8 + g;
+                bf[in][0] = *reinterpret_cast<const uint32_t *>(&Bt[c][kk + 2 * t]);
+                bf[in][1] = *reinterpret_cast<const uint32_t *>(&Bt[c][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int im = 0; im < 2; ++im)
+#pragma unroll
+                for (int in = 0; in < 4; ++in) mma16816(acc[im][in], af[im], bf[in]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int im = 0; im < 2; ++im)
+#pragma unroll
+        for (int in = 0; in < 4; ++in)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + wm + im * 16 + g + 8 * h;
+                if (r >= M) continue;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = n0 + wn + in * 8 + 2 * t + q;
+                    if (c >= N) continue;
+                    float v = acc[im][in][2 * h + q];
+                    if (EPI == EPI_F32) {
+                        C32[(size_t)r * ldc + c] = v;
+                    } else if (EPI == EPI_F32_BIAS) {
+                        C32[(size_t)r * ldc + c] = v + bias[c];
+                    } else if (EPI == EPI_F16_BIAS_RELU) {
+                        v += bias[c];
+                        C16[(size_t)r * ldc + c] = __float2half(v > 0.0f ? v : 0.0f);
+                    } else {
+                        const bool on = __half2float(mask[(size_t)r * ldm + c]) > 0.0f;
+                        C16[(size_t)r * ldc + c] = __float2half(on ? v : 0.0f);
+                    }
+                }
+            }
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t gemm(int M, int N, int K, const __half *A, int lda, const __half *B, int ldb, const float *bias,
+                 const __half *mask, int ldm, float *C32, __half *C16, int ldc, cudaStream_t st)
+{
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    gemm_kernel<TA, TB, EPI><<<grid, GTHREADS, 0, st>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, C32, C16, ldc);
+    return cudaGetLastError();
+}
+
+// Gaussian NLL of a batch and its gradient d nll / d o (1/B of the batch mean),
+// as f32 and f16 [B][8] (columns 6, 7 zero).  loss (optional) accumulates the mean.
+// The log-variance is clamped to [-8, 8] (zero gradient outside), which keeps the
+// f16 gradients finite; a spread below e^-4 is finer than the grid needs.
+__global__ void nll_kernel(const float *__restrict__ o, const float *__restrict__ y, int B,
+                           float *__restrict__ g32, __half *__restrict__ g16, float *__restrict__ loss)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float l = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float mu = o[b * 8 + j], raw = o[b * 8 + 3 + j];
+        const float lv = fminf(fmaxf(raw, -8.0f), 8.0f);
+        const float r = y[b * 3 + j] - mu;
+        const float iv = expf(-lv);
+        l += 0.5f * (lv + r * r * iv);
+        const float gm = -r * iv / B;
+        const float gv = (raw > -8.0f && raw < 8.0f) ? 0.5f * (1.0f - r * r * iv) / B : 0.0f;
+        g32[b * 8 + j] = gm;
+        g32[b * 8 + 3 + j] = gv;
+        g16[b * 8 + j] = __float2half(gm);
+        g16[b * 8 + 3 + j] = __float2half(gv);
+    }
+    g32[b * 8 + 6] = g32[b * 8 + 7] = 0.0f;
+    g16[b * 8 + 6] = g16[b * 8 + 7] = __float2half(0.0f);
+    if (loss) atomicAdd(loss, l / B);
+}
+
+// out[n] = sum over rows of X[B][N] (f16 or f32), in row order.
+template <typename T>
+__global__ void colsum_kernel(const T *__restrict__ X, int B, int N, float *__restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s += (float)X[(size_t)b * N + n];
+    out[n] = s;
+}
+
+// Adam (Kingma & Ba 2015) over every parameter; refreshes the f16 weight copies.
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, __half *__restrict__ w16, int64_t P, float lr, float bc1,
+                            float bc2, MlpOffsets off)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+        w[i] = wi;
+        int64_t h = -1;
+        if (i < off.b1) h = i;
+        else if (i >= off.W2 && i < off.b2) h = off.W1h_n + (i - off.W2);
+        else if (i >= off.W3 && i < off.b3) h = off.W1h_n + off.W2h_n + (i - off.W3);
+        if (h >= 0) w16[h] = __float2half(wi);
+    }
+}
+
+// He initialisation from caller-supplied standard normals; biases zero.
+__global__ void init_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            __half *__restrict__ w16, const float *__restrict__ z, int64_t P, MlpOffsets off)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        float wi = 0.0f;
+        int64_t h = -1;
+        if (i < off.b1) {
+            wi = z[i] * sqrtf(2.0f / kMlpIn);
+            h = i;
+        } else if (i >= off.W2 && i < off.b2) {
+            wi = z[i] * sqrtf(2.0f / kMlpHidden);
+            h = off.W1h_n + (i - off.W2);
+        } else if (i >= off.W3 && i < off.b3) {
+            const int col = (int)((i - off.W3) % kMlpOutPad);
+            wi = col < kMlpOut ? z[i] * sqrtf(1.0f / kMlpHidden) : 0.0f;
+            h = off.W1h_n + off.W2h_n + (i - off.W3);
+        }
+        w[i] = wi;
+        m[i] = 0.0f;
+        v[i] = 0.0f;
+        if (h >= 0) w16[h] = __float2half(wi);
+    }
+}
+
+// Network input of each facet: [Re D_c / S, Im D_c / S], empty cells 0, f16.
+__global__ void encode_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ table, int NN,
+                              __half *__restrict__ x)
+{
+    const int s = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NN) return;
+    const double *f = facets + (size_t)s * 4 * NN;
+    const double n = f[2 * NN + c];
+    const double S = table[s].flux;
+    float re = 0.0f, im = 0.0f;
+    if (n > 0.0 && S > 0.0) {
+        re = (float)(f[c] / n / S);
+        im = (float)(f[NN + c] / n / S);
+    }
+    x[(size_t)s * 2 * NN + c] = __float2half(re);
+    x[(size_t)s * 2 * NN + NN + c] = __float2half(im);
+}
+
+// Training facets: D_c / S = s_c M(k_c; e, alpha) + (sigma / S) z / sqrt(n_c), from a
+// template facet's counts and spectral sums and its cell size.
+__global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, double add, double esp,
+                                double psf_nat, const double *__restrict__ tflux, const int32_t *__restrict__ tidx,
+                                const double *__restrict__ e1, const double *__restrict__ e2,
+                                const double *__restrict__ alpha_as, const float *__restrict__ z, int N,
+                                double sigma, __half *__restrict__ x, float *__restrict__ y)
+{
+    const int b = blockIdx.y;
+    const int NN = N * N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ti = tidx[b];
+    const bool valid = ti >= 0 && ti < n_tmpl;   // an out-of-range template index gives an all-zero input
+    const double a1 = e1[b], a2 = e2[b], al = alpha_as[b] * kArcsec;
+    if (c == 0) {
+        y[b * 3 + 0] = (float)a1;
+        y[b * 3 + 1] = (float)a2;
+        y[b * 3 + 2] = (float)log(alpha_as[b]);
+    }
+    if (c >= NN) return;
+    const double *f = tmpl + (size_t)(valid ? ti : 0) * 4 * NN;
+    const double n = valid ? f[2 * NN + c] : 0.0;
+    float re = 0.0f, im = 0.0f;
+    if (n > 0.0) {
+        // the template's cell size, 1 / (K alpha_med(S)) with Eq. 4
+        const double du = 1.0 / (psf_nat * exp(add + esp * log(tflux[ti] * 1.0e6)) * kArcsec);
+        const double cu = ((c % N) - N / 2 + 0.5) * du, cv = ((c / N) - N / 2 + 0.5) * du;
+        const double det = 1.0 - a1 * a1 - a2 * a2;
+        const double x1 = ((1.0 + a1) * cu + a2 * cv) / det, x2 = (a2 * cu + (1.0 - a1) * cv) / det;
+        const double q = 1.0 + 4.0 * kPi * kPi * al * al * (x1 * x1 + x2 * x2);
+        const double M = 1.0 / (q * sqrt(q));
+        const double sbar = f[3 * NN + c] / n;
+        const double sr = sigma / tflux[ti] / sqrt(n);
+        re = (float)(sbar * M + sr * z[((size_t)b * 2) * NN + c]);
+        im = (float)(sr * z[((size_t)b * 2 + 1) * NN + c]);
+    }
+    x[(size_t)b * 2 * NN + c] = __float2half(re);
+    x[(size_t)b * 2 * NN + NN + c] = __float2half(im);
+}
+
+// Sub-box of the grid centred on the node nearest the prediction, clamped inside
+// the grid; `wide` when the predicted spread of e1 or e2 exceeds three node spacings.
+__global__ void propose_kernel(const float *__restrict__ o, int count, GridConst gc, int32_t *__restrict__ origin,
+                               int32_t *__restrict__ wide)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count) return;
+    const double de = 2.0 * gc.e_max / (gc.n_e - 1);
+    int idx[2];
+    for (int j = 0; j < 2; ++j) {
+        const double mu = o[s * 8 + j];
+        int best = 0;
+        double bd = 1e300;
+        for (int k = 0; k < gc.n_e; ++k) {
+            const double d = fabs(-gc.e_max + k * de - mu);
+            if (d < bd) {
+                bd = d;
+                best = k;
+            }
+        }
+        idx[j] = best;
+    }
+    const double am = exp((double)o[s * 8 + 2]);
+    int kb = 0;
+    double bd = 1e300;
+    for (int k = 0; k < gc.n_alpha; ++k) {
+        const double tt = gc.n_alpha > 1 ? (double)k / (gc.n_alpha - 1) : 0.0;
+        const double d = fabs(gc.r_min + (gc.r_max - gc.r_min) * tt * tt - am);
+        if (d < bd) {
+            bd = d;
+            kb = k;
+        }
+    }
+    origin[s * 3 + 0] = min(max(idx[0] - kBoxE / 2, 0), gc.n_e - kBoxE);
+    origin[s * 3 + 1] = min(max(idx[1] - kBoxE / 2, 0), gc.n_e - kBoxE);
+    origin[s * 3 + 2] = min(max(kb - kBoxA / 2, 0), gc.n_alpha - kBoxA);
+    const double s1 = exp(0.5 * (double)o[s * 8 + 3]), s2 = exp(0.5 * (double)o[s * 8 + 4]);
+    wide[s] = (s1 > 3.0 * de || s2 > 3.0 * de) ? 1 : 0;
+}
+
+int sm_count_m()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+}  // namespace
+
+MlpOffsets mlp_offsets()
+{
+    MlpOffsets o;
+    o.W1 = 0;
+    o.b1 = o.W1 + (int64_t)kMlpIn * kMlpHidden;
+    o.W2 = o.b1 + kMlpHidden;
+    o.b2 = o.W2 + (int64_t)kMlpHidden * kMlpHidden;
+    o.W3 = o.b2 + kMlpHidden;
+    o.b3 = o.W3 + (int64_t)kMlpHidden * kMlpOutPad;
+    o.P = o.b3 + kMlpOutPad;
+    o.W1h_n = (int64_t)kMlpIn * kMlpHidden;
+    o.W2h_n = (int64_t)kMlpHidden * kMlpHidden;
+    o.W3h_n = (int64_t)kMlpHidden * kMlpOutPad;
+    return o;
+}
+
+MlpWeights mlp_weights(void *blob)
+{
+    const MlpOffsets o = mlp_offsets();
+    MlpWeights w;
+    char *b = static_cast<char *>(blob);
+    w.w = reinterpret_cast<float *>(b);
+    w.m = w.w + o.P;
+    w.v = w.m + o.P;
+    w.g = w.v + o.P;
+    w.h = reinterpret_cast<__half *>(w.g + o.P);
+    return w;
+}
+
+size_t mlp_weights_bytes()
+{
+    const MlpOffsets o = mlp_offsets();
+    return (size_t)o.P * 4 * sizeof(float) + (size_t)(o.W1h_n + o.W2h_n + o.W3h_n) * sizeof(__half);
+}
+
+MlpScratch mlp_scratch(void *base, int32_t max_batch)
+{
+    MlpScratch s;
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t bytes) {
+        char *p = b;
+        b += (bytes + 255) / 256 * 256;
+        return p;
+    };
+    s.h1 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
+    s.h2 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
+    s.o = reinterpret_cast<float *>(take((size_t)max_batch * kMlpOutPad * sizeof(float)));
+    s.g32 = reinterpret_cast<float *>(take((size_t)max_batch * kMlpOutPad * sizeof(float)));
+    s.g16 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpOutPad * sizeof(__half)));
+    s.dz2 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
+    s.dz1 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
+    s.bytes = (size_t)(b - static_cast<char *>(base));
+    return s;
+}
+
+cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const MlpScratch &s, cudaStream_t st)
+{
+    const MlpOffsets o = mlp_offsets();
+    const __half *W1h = W.h, *W2h = W.h + o.W1h_n, *W3h = W.h + o.W1h_n + o.W2h_n;
+    cudaError_t e = gemm<false, false, EPI_F16_BIAS_RELU>(B, kMlpHidden, kMlpIn, x, kMlpIn, W1h, kMlpHidden,
+                                                           W.w + o.b1, nullptr, 0, nullptr, s.h1, kMlpHidden, st);
+    if (e == cudaSuccess)
+        e = gemm<false, false, EPI_F16_BIAS_RELU>(B, kMlpHidden, kMlpHidden, s.h1, kMlpHidden, W2h, kMlpHidden,
+                                                  W.w + o.b2, nullptr, 0, nullptr, s.h2, kMlpHidden, st);
+    if (e == cudaSuccess)
+        e = gemm<false, false, EPI_F32_BIAS>(B, kMlpOutPad, kMlpHidden, s.h2, kMlpHidden, W3h, kMlpOutPad,
+                                             W.w + o.b3, nullptr, 0, s.o, nullptr, kMlpOutPad, st);
+    return e;
+}
+
+cudaError_t mlp_train_step(const MlpWeights &W, const __half *x, const float *y, int32_t B, float lr, int32_t step,
+                           float *loss, const MlpScratch &s, cudaStream_t st)
+{
+    const MlpOffsets o = mlp_offsets();
+    const __half *W2h = W.h + o.W1h_n, *W3h = W.h + o.W1h_n + o.W2h_n;
+    cudaError_t e = mlp_forward(W, x, B, s, st);
+    if (e != cudaSuccess) return e;
+    nll_kernel<<<(B + 127) / 128, 128, 0, st>>>(s.o, y, B, s.g32, s.g16, loss);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // layer 3: dW3 = h2^T g, db3 = sum g, dz2 = (g W3^T) * [h2 > 0]
+    e = gemm<true, false, EPI_F32>(kMlpHidden, kMlpOutPad, B, s.h2, kMlpHidden, s.g16, kMlpOutPad, nullptr, nullptr,
+                                   0, W.g + o.W3, nullptr, kMlpOutPad, st);
+    if (e == cudaSuccess) {
+        colsum_kernel<float><<<1, kMlpOutPad, 0, st>>>(s.g32, B, kMlpOutPad, W.g + o.b3);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = gemm<false, true, EPI_F16_MASK>(B, kMlpHidden, kMlpOutPad, s.g16, kMlpOutPad, W3h, kMlpOutPad, nullptr,
+                                            s.h2, kMlpHidden, nullptr, s.dz2, kMlpHidden, st);
+    // layer 2: dW2 = h1^T dz2, db2 = sum dz2, dz1 = (dz2 W2^T) * [h1 > 0]
+    if (e == cudaSuccess)
+        e = gemm<true, false, EPI_F32>(kMlpHidden, kMlpHidden, B, s.h1, kMlpHidden, s.dz2, kMlpHidden, nullptr,
+                                       nullptr, 0, W.g + o.W2, nullptr, kMlpHidden, st);
+    if (e == cudaSuccess) {
+        colsum_kernel<__half><<<(kMlpHidden + 127) / 128, 128, 0, st>>>(s.dz2, B, kMlpHidden, W.g + o.b2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = gemm<false, true, EPI_F16_MASK>(B, kMlpHidden, kMlpHidden, s.dz2, kMlpHidden, W2h, kMlpHidden, nullptr,
+                                            s.h1, kMlpHidden, nullptr, s.dz1, kMlpHidden, st);
+    // layer 1: dW1 = x^T dz1, db1 = sum dz1
+    if (e == cudaSuccess)
+        e = gemm<true, false, EPI_F32>(kMlpIn, kMlpHidden, B, x, kMlpIn, s.dz1, kMlpHidden, nullptr, nullptr, 0,
+                                       W.g + o.W1, nullptr, kMlpHidden, st);
+    if (e == cudaSuccess) {
+        colsum_kernel<__half><<<(kMlpHidden + 127) / 128, 128, 0, st>>>(s.dz1, B, kMlpHidden, W.g + o.b1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess || step <= 0) return e;
+    const float bc1 = 1.0f - powf(0.9f, (float)step), bc2 = 1.0f - powf(0.999f, (float)step);
+    adam_kernel<<<sm_count_m() * 8, 256, 0, st>>>(W.w, W.g, W.m, W.v, W.h, o.P, lr, bc1, bc2, o);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_init(const MlpWeights &W, const float *z, cudaStream_t st)
+{
+    const MlpOffsets o = mlp_offsets();
+    init_kernel<<<sm_count_m() * 8, 256, 0, st>>>(W.w, W.m, W.v, W.h, z, o.P, o);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_encode(const double *facets, const SrcRow *table, int32_t count, int32_t N, __half *x,
+                       cudaStream_t st)
+{
+    const int NN = N * N;
+    dim3 grid((NN + 255) / 256, count);
+    encode_kernel<<<grid, 256, 0, st>>>(facets, table, NN, x);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_simulate(const double *tmpl, int32_t n_tmpl, const rlf_params &p, const double *tflux,
+                         const int32_t *tidx, const double *e1, const double *e2, const double *alpha_as,
+                         const float *z, int32_t B, int32_t N, double sigma, __half *x, float *y, cudaStream_t st)
+{
+    const int NN = N * N;
+    dim3 grid((NN + 255) / 256, B);
+    simulate_kernel<<<grid, 256, 0, st>>>(tmpl, n_tmpl, p.add, p.esp, p.psf_nat, tflux, tidx, e1, e2, alpha_as, z, N,
+                                          sigma, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_propose(const float *o, int32_t count, const GridConst &gc, int32_t *origin, int32_t *wide,
+                        cudaStream_t st)
+{
+    propose_kernel<<<(count + 127) / 128, 128, 0, st>>>(o, count, gc, origin, wide);
+    return cudaGetLastError();
+}
+
+}  // namespace rlf

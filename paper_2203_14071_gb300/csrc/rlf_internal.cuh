@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rlf.h"
@@ -133,8 +134,12 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo)
     lo = (float)(x - (double)hi);
 }
 
+constexpr int kBoxE = 7, kBoxA = 5;                     // learned-proposal sub-box (e1, e2, alpha nodes)
+constexpr int kMlpIn = 8192, kMlpHidden = 256, kMlpOut = 6, kMlpOutPad = 8;
+
 // Grid constants of the likelihood (Sec. 2.4).
 struct GridConst {
+    const int32_t *box;     // per-facet sub-box origins [count][3] (e1, e2, alpha node), or null: full grid
     int32_t n_e, n_alpha, n_ag, flux_prior;
     double e_max;
     double r_min, r_max;    // arcsec
@@ -152,6 +157,12 @@ struct Workspace {
     int32_t *ncell;         // [cap]
     int32_t *order;         // [cap] facets in largest-first order
     int32_t *counters;      // [cap + 1] work-item counter, per-facet finished tiles
+    int32_t *box;           // [cap][3] learned-proposal sub-box origins
+    int32_t *wide;          // [cap] proposal too wide: full grid
+    int32_t *map_index;     // [cap] flat grid index of each facet's MAP point
+    int32_t *refit;         // [cap + 1] facets to refit on the full grid, count first
+    void *mlp_x;            // [cap][8192] f16 network inputs
+    void *mlp_scratch;      // network activations for cap facets
     double *cc;             // [cap]
     double *ga, *gb, *gl;   // [cap][n_e^2][n_alpha]
     double *e_cur;          // [2][n_src]
@@ -182,5 +193,40 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
                        int32_t out_offset, cudaStream_t st);
+GridConst grid_const(const rlf_params &p);
+// learned-proposal fit: compaction, network, sub-box fit, refit of the facets that need the full grid
+cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t count, const rlf_params &p,
+                           const Workspace &ws, const void *weights, const rlf_fit_out &out, int32_t *n_fallback,
+                           cudaStream_t st);
+
+// ---- learned proposal (mlp.cu) ---------------------------------------------------------
+struct MlpOffsets {
+    int64_t W1, b1, W2, b2, W3, b3, P;   // f32 parameter offsets (W3 padded to 8 columns)
+    int64_t W1h_n, W2h_n, W3h_n;         // f16 copies of the weight matrices, in that order
+};
+struct MlpWeights {
+    float *w, *m, *v, *g;                // parameters, Adam moments, gradients [P]
+    __half *h;                           // f16 W1 | W2 | W3
+};
+struct MlpScratch {
+    __half *h1, *h2, *g16, *dz2, *dz1;
+    float *o, *g32;
+    size_t bytes;
+};
+MlpOffsets mlp_offsets();
+MlpWeights mlp_weights(void *blob);
+size_t mlp_weights_bytes();
+MlpScratch mlp_scratch(void *base, int32_t max_batch);
+cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const MlpScratch &s, cudaStream_t st);
+cudaError_t mlp_train_step(const MlpWeights &W, const __half *x, const float *y, int32_t B, float lr, int32_t step,
+                           float *loss, const MlpScratch &s, cudaStream_t st);
+cudaError_t mlp_init(const MlpWeights &W, const float *z, cudaStream_t st);
+cudaError_t mlp_encode(const double *facets, const SrcRow *table, int32_t count, int32_t N, __half *x,
+                       cudaStream_t st);
+cudaError_t mlp_simulate(const double *tmpl, int32_t n_tmpl, const rlf_params &p, const double *tflux,
+                         const int32_t *tidx, const double *e1, const double *e2, const double *alpha_as,
+                         const float *z, int32_t B, int32_t N, double sigma, __half *x, float *y, cudaStream_t st);
+cudaError_t mlp_propose(const float *o, int32_t count, const GridConst &gc, int32_t *origin, int32_t *wide,
+                        cudaStream_t st);
 
 }  // namespace rlf

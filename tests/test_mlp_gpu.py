@@ -1,0 +1,290 @@
+"""The learned proposal on the GPU against its FP64 oracle (oracle/mlp.py).
+
+Weights are created on the host (seeded numpy) and copied into the blob, so the
+oracle and the kernels start from the same numbers.  The kernels run their GEMMs
+with f16 inputs and f32 accumulation and keep f16 activations, so forward outputs
+and gradients are compared normwise at the f16 level (tolerances in each test).
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp as omlp
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rlf():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2203_14071_gb300 as m
+    from paper_2203_14071_gb300 import build_ext
+    build_ext.build()
+    m.lib()
+    return m
+
+
+def _host_weights(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, math.sqrt(2 / 8192) * scale, (8192, 256))
+    b1 = rng.normal(0, 0.05, 256)
+    W2 = rng.normal(0, math.sqrt(2 / 256) * scale, (256, 256))
+    b2 = rng.normal(0, 0.05, 256)
+    W3 = np.zeros((256, 8))
+    W3[:, :6] = rng.normal(0, math.sqrt(1 / 256), (256, 6))
+    b3 = np.zeros(8)
+    b3[:6] = rng.normal(0, 0.1, 6)
+    return [W1, b1, W2, b2, W3, b3]
+
+
+def _load(rlf, P):
+    """A weights blob holding P (f32 params, f16 copies of the matrices); the f16-rounded
+    matrices are returned for the oracle."""
+    import torch
+    m = rlf.Mlp()
+    names = ["W1", "b1", "W2", "b2", "W3", "b3"]
+    for n, a in zip(names, P):
+        m.section(m.w, n).copy_(torch.from_numpy(a.astype(np.float32)))
+    for n, a in zip(["W1", "W2", "W3"], [P[0], P[2], P[4]]):
+        m.half(n).copy_(torch.from_numpy(a.astype(np.float16)))
+    rounded = [P[0].astype(np.float16).astype(np.float64), P[1].astype(np.float32).astype(np.float64),
+               P[2].astype(np.float16).astype(np.float64), P[3].astype(np.float32).astype(np.float64),
+               P[4].astype(np.float16).astype(np.float64), P[5].astype(np.float32).astype(np.float64)]
+    return m, rounded
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_forward_and_gradients_match_oracle(rlf):
+    import torch
+    P = _host_weights(1)
+    m, R = _load(rlf, P)
+    rng = np.random.default_rng(2)
+    B = 96
+    x = (rng.normal(0.2, 0.5, (B, 8192))).astype(np.float16)
+    y = rng.normal(0, 0.3, (B, 3)).astype(np.float32)
+    x_t, y_t = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = rlf.mlp_workspace(B)
+    out = torch.zeros(B, 8, device="cuda")
+    rlf.mlp_forward(m, x_t, out, ws)
+    loss = torch.zeros(1, device="cuda")
+    rlf.mlp_train_step(m, x_t, y_t, 1e-3, 0, loss, ws)        # step 0: gradients only
+    torch.cuda.synchronize()
+    o_ref, cache = omlp.forward(x.astype(np.float64), *R)
+    assert _nrel(out.cpu().numpy()[:, :6].astype(np.float64), o_ref[:, :6]) < 5e-3
+    assert abs(loss.item() - omlp.nll(o_ref, y.astype(np.float64))) < 5e-3 * max(1.0, abs(omlp.nll(o_ref, y)))
+    grads = omlp.backward(cache, R[2], R[4], omlp.nll_grad(o_ref, y.astype(np.float64)))
+    for name, g_ref in zip(["W1", "b1", "W2", "b2", "W3", "b3"], grads):
+        g = m.section(m.g, name).cpu().numpy().astype(np.float64)
+        if name == "W3" or name == "b3":
+            g, g_ref = g[..., :6], g_ref[..., :6]
+        assert _nrel(g, g_ref) < 2e-2, (name, _nrel(g, g_ref))
+    # unchanged parameters after a gradient-only call
+    assert np.array_equal(m.section(m.w, "b2").cpu().numpy(), P[3].astype(np.float32))
+
+
+def test_adam_step_matches_oracle(rlf):
+    import torch
+    P = _host_weights(3)
+    m, R = _load(rlf, P)
+    rng = np.random.default_rng(4)
+    B, lr = 64, 2e-3
+    x = rng.normal(0.1, 0.4, (B, 8192)).astype(np.float16)
+    y = rng.normal(0, 0.3, (B, 3)).astype(np.float32)
+    ws = rlf.mlp_workspace(B)
+    rlf.mlp_train_step(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), lr, 1, None, ws)
+    torch.cuda.synchronize()
+    o_ref, cache = omlp.forward(x.astype(np.float64), *R)
+    grads = omlp.backward(cache, R[2], R[4], omlp.nll_grad(o_ref, y.astype(np.float64)))
+    for name, w0, g in zip(["W2", "b2", "W3", "b1"], [P[2], P[3], P[4], P[1]], [grads[2], grads[3], grads[4], grads[1]]):
+        w_new, _, _ = omlp.adam(w0, g, np.zeros_like(w0), np.zeros_like(w0), 1, lr)
+        got = m.section(m.w, name).cpu().numpy().astype(np.float64)
+        # the first step is lr * g / (|g| + eps): compare where the gradient is well above its f16 error
+        sure = np.abs(g) > 0.05 * np.abs(g).max()
+        assert np.max(np.abs((got - w0)[sure] - (w_new - w0)[sure])) <= 1e-2 * lr, name
+        assert np.all(np.abs(got - w0) <= lr * (1 + 1e-3) + 1e-7), name
+    # the f16 copy follows the f32 parameters
+    assert np.allclose(m.half("W2").cpu().numpy().astype(np.float64),
+                       m.section(m.w, "W2").cpu().numpy().astype(np.float16).astype(np.float64))
+
+
+def test_init_statistics(rlf):
+    import torch
+    m = rlf.Mlp()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    m.init(torch.randn(m.P, generator=g, device="cuda"))
+    W1 = m.section(m.w, "W1").double()
+    assert abs(W1.std().item() - math.sqrt(2 / 8192)) < 0.01 * math.sqrt(2 / 8192)
+    assert m.section(m.w, "b1").abs().max().item() == 0.0 and m.m.abs().max().item() == 0.0
+    assert m.section(m.w, "W3")[:, 6:].abs().max().item() == 0.0
+
+
+def _oracle_facets(c, idx, facet_n=64):
+    p = c.oracle_params(facet_n=facet_n)
+    al = c.alpha_med_rad()
+    out = []
+    for i in idx:
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p)
+        out.append(oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i],
+                                        c.cat.m[i], c.cat.flux_jy[i], al[i], 0.0, 0.0, du, p))
+    return np.stack(out)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return cases.build(synth.workload("small"), snr10=True)
+
+
+def test_simulate_and_encode_match_oracle(rlf, small):
+    import torch
+    c = small
+    T = _oracle_facets(c, [0, 4, 9])
+    flux = c.cat.flux_jy[[0, 4, 9]]
+    rng = np.random.default_rng(6)
+    B = 6
+    tidx = np.array([0, 1, 2, 2, 1, 0], dtype=np.int32)
+    e1 = rng.uniform(-0.5, 0.5, B)
+    e2 = rng.uniform(-0.5, 0.5, B)
+    al = rng.uniform(0.5, 3.0, B)
+    z = rng.standard_normal((B, 2, 4096)).astype(np.float32)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x16 = torch.empty(B, 8192, dtype=torch.float16, device="cuda")
+    y = torch.empty(B, 3, device="cuda")
+    rlf.mlp_simulate(d(T), d(flux), d(tidx), d(e1), d(e2), d(al), d(z), p, x16, y)
+    po = c.oracle_params()
+    got = x16.cpu().numpy().astype(np.float64)
+    for b in range(B):
+        t = tidx[b]
+        n = T[t][2]
+        sbar = np.where(n > 0, T[t][3] / np.where(n > 0, n, 1), 0)
+        ref = omlp.simulate(n, sbar, oracle.facet_du(flux[t], 0.0, po), e1[b], e2[b], al[b],
+                            c.sigma / flux[t], z[b].astype(np.float64))
+        assert np.all(np.abs(got[b] - ref) <= 1e-3 * np.abs(ref) + 1e-4), b
+        assert np.allclose(y.cpu().numpy()[b], [e1[b], e2[b], math.log(al[b])], atol=1e-6)
+    # encoding of real facets
+    obs, cat = cases.to_device(c)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+    xe = torch.empty(3, 8192, dtype=torch.float16, device="cuda")
+    rlf.mlp_encode(d(T), rlf.Catalogue(cat.l[[0, 4, 9]].contiguous(), cat.m[[0, 4, 9]].contiguous(),
+                                       cat.flux_jy[[0, 4, 9]].contiguous(), cat.e1[:3].contiguous(),
+                                       cat.e2[:3].contiguous()), 0, 3, p, xe, ws)
+    for j in range(3):
+        ref = omlp.encode(T[j], flux[j])
+        assert np.all(np.abs(xe[j].cpu().numpy().astype(np.float64) - ref) <= 1e-3 * np.abs(ref) + 1e-6)
+
+
+def _oracle_narrowed(acc, du, flux, p, o_row):
+    """The oracle's proposal from its own forward pass, box-masked estimate and fallback."""
+    ge, ga = oracle.grid_e(p), oracle.grid_alpha(p)
+    origin, wide = omlp.propose(o_row[:3], o_row[3:6], ge, ga)
+    lg, a, b, nc = oracle.like_grid(acc, du, p)
+    mask = omlp.box_mask(origin, (7, 7, 5), p.n_e, p.n_alpha)
+    lgm = np.where(mask, lg, -np.inf)
+    est, _ = oracle.estimate(lgm, a, b, flux, p, nc)
+    refit = wide or (est[oracle.MAP_INDEX] >= 0 and omlp.on_inner_boundary(int(est[oracle.MAP_INDEX]), origin,
+                                                                            (7, 7, 5), p.n_e, p.n_alpha))
+    if refit:
+        est, _ = oracle.estimate(lg, a, b, flux, p, nc)
+    return est, origin, refit
+
+
+def test_narrowed_fit_matches_oracle(rlf, small):
+    import torch
+    c = small
+    n = c.cat.n_src
+    T = _oracle_facets(c, range(n))
+    P = _host_weights(7, scale=0.3)
+    m, R = _load(rlf, P)
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, precision=rlf.PREC_MIXED_SPLIT)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, n, p, rlf.WS_FIT)
+    out = rlf.Results(n, "cuda")
+    nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rlf.fit_sources_mlp(torch.from_numpy(T).cuda(), cat, 0, n, p, m, out, ws, nfb)
+    got = out.numpy()
+    po = c.oracle_params()
+    X = np.stack([omlp.encode(T[i], c.cat.flux_jy[i]) for i in range(n)]).astype(np.float16).astype(np.float64)
+    O, _ = omlp.forward(X, *R)
+    n_refit = 0
+    for i in range(n):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, po)
+        est, origin, refit = _oracle_narrowed(T[i], du, c.cat.flux_jy[i], po, O[i])
+        n_refit += refit
+        assert cases.est_matches(got, i, est) <= 1e-4, (i, origin, refit)
+    assert int(nfb.item()) == n_refit
+
+
+def test_training_reduces_loss_and_narrowed_fit_gains(rlf):
+    """Train on facets simulated from the mid workload's coverage, then compare the
+    proposal-narrowed fit with the full-grid fit on real facets of that workload."""
+    import torch
+    c = cases.build(synth.workload("mid"), with_data=False)
+    R_, C_ = c.obs.n_rows, c.obs.n_chan
+    n = c.cat.n_src
+    sigma = 1e-3
+    rng = np.random.default_rng(9)
+    skyr = rng.standard_normal((R_, C_, 2), dtype=np.float32) * np.float32(1e-4)
+    data = skyr + synth.noise(R_, C_, sigma, 91)
+    obs, cat = cases.to_device(c, c.cat.e1, c.cat.e2)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=sigma, precision=rlf.PREC_MIXED_SPLIT)
+    wse = rlf.alloc_workspace(R_, C_, n, p, rlf.WS_EXTRACT)
+    fac = torch.empty(rlf.facets_size(n, p) // 8, dtype=torch.float64, device="cuda")
+    rlf.extract_facets(obs, cases.vis_tensor(data), cases.vis_tensor(skyr), cat, 0, n, p, fac, wse)
+    del wse
+    # training set: every source's coverage as a template, random shapes and sizes
+    m = rlf.Mlp()
+    gen = torch.Generator(device="cuda").manual_seed(10)
+    m.init(torch.randn(m.P, generator=gen, device="cuda"))
+    B, steps = 256, 400
+    ws_t = rlf.mlp_workspace(B)
+    x16 = torch.empty(B, 8192, dtype=torch.float16, device="cuda")
+    y = torch.empty(B, 3, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    flux_t = cat.flux_jy
+    losses = []
+    for s in range(1, steps + 1):
+        tidx = torch.randint(0, n, (B,), generator=gen, device="cuda", dtype=torch.int32)
+        e = torch.randn(B, 2, generator=gen, device="cuda", dtype=torch.float64) * 0.3
+        e = e * torch.clamp(0.75 / torch.linalg.norm(e, dim=1, keepdim=True), max=1.0)
+        lna = -0.93 + 0.33 * torch.log(flux_t[tidx.long()] * 1e6) + 0.3136 * torch.randn(
+            B, generator=gen, device="cuda", dtype=torch.float64)
+        al = torch.clamp(torch.exp(lna), 0.3, 3.5)
+        z = torch.randn(B, 2, 4096, generator=gen, device="cuda")
+        rlf.mlp_simulate(fac, flux_t, tidx, e[:, 0].contiguous(), e[:, 1].contiguous(), al, z, p, x16, y)
+        rlf.mlp_train_step(m, x16, y, 1e-3, s, loss, ws_t)
+        if s % 50 == 0:
+            losses.append(loss.item())
+    assert losses[-1] < losses[0] - 1.0, losses
+    # full grid vs proposal-narrowed fit on the real facets (timed, CUDA events)
+    ws = rlf.alloc_workspace(R_, C_, n, p, rlf.WS_FIT)
+    full, narrow = rlf.Results(n, "cuda"), rlf.Results(n, "cuda")
+    nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 3
+    t_full = timed(lambda: rlf.fit_sources(fac, cat, 0, n, p, full, ws))
+    t_mlp = timed(lambda: rlf.fit_sources_mlp(fac, cat, 0, n, p, m, narrow, ws, nfb))
+    F, G = full.numpy(), narrow.numpy()
+    de = np.maximum(np.abs(F["e1"] - G["e1"]), np.abs(F["e2"] - G["e2"]))
+    agree = float(np.mean(de <= 1e-4))
+    print(f"\nfull grid {t_full:.3f} ms, narrowed {t_mlp:.3f} ms ({t_full / t_mlp:.1f}x), "
+          f"fallbacks {int(nfb.item())}/{n}, agreement within 1e-4: {agree:.2%}, losses {losses}")
+    assert t_mlp < t_full
+    assert agree >= 0.9
