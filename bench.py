@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
     ap.add_argument("--no-batched", action="store_true", help="skip the extra 148M-visibility workload line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
     ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update"],
                     help="run only this entry point --steps times after one warm-up (for ncu captures)")
@@ -245,6 +246,70 @@ def batched_line(rlf, torch, dev, args, prec, rank, stream):
             "tuning": {f: int(getattr(p, f)) for f in rlf.TUNE_FIELDS}, "steps": steps}
 
 
+def mlp_line(rlf, torch, dev, W, stream, train_steps=400, batch=256, lr=1e-3, reps=5):
+    """The learned proposal on this workload: train the network on facets simulated from
+    the workload's own coverage (every source's facet as a template, random shapes,
+    scalelengths from the Eq. 4 prior), then fit the real facets with the narrowed
+    grid and with the full grid, timed with CUDA events on the same stream."""
+    obs, cat, p, ws, data, sky = (W[k] for k in ("obs", "cat", "params", "ws", "data", "sky"))
+    n = W["cat_np"].n_src
+    rlf.sky_model(obs, cat, p, sky, ws, stream)
+    fac = torch.empty(rlf.facets_size(n, p) // 8, dtype=torch.float64, device=dev)
+    rlf.extract_facets(obs, data, sky, cat, 0, n, p, fac, ws, stream)
+    m = rlf.Mlp(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4321)
+    m.init(torch.randn(m.P, generator=gen, device=dev), stream)
+    ws_t = rlf.mlp_workspace(batch, dev)
+    x16 = torch.empty(batch, 8192, dtype=torch.float16, device=dev)
+    y = torch.empty(batch, 3, device=dev)
+    loss = torch.zeros(1, device=dev)
+    flux = cat.flux_jy
+
+    def train(s):
+        tidx = torch.randint(0, n, (batch,), generator=gen, device=dev, dtype=torch.int32)
+        e = torch.randn(batch, 2, generator=gen, device=dev, dtype=torch.float64) * 0.3
+        e = e * torch.clamp(0.75 / torch.linalg.norm(e, dim=1, keepdim=True), max=1.0)
+        lna = p.add + p.esp * torch.log(flux[tidx.long()] * 1e6) + p.r_std * torch.randn(
+            batch, generator=gen, device=dev, dtype=torch.float64)
+        al = torch.clamp(torch.exp(lna), p.r_min_arcsec, p.r_max_arcsec)
+        z = torch.randn(batch, 2, 4096, generator=gen, device=dev)
+        rlf.mlp_simulate(fac, flux, tidx, e[:, 0].contiguous(), e[:, 1].contiguous(), al, z, p, x16, y, stream)
+        rlf.mlp_train_step(m, x16, y, lr, s, loss, ws_t, stream)
+
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(1, train_steps + 1):
+        train(s)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = a.elapsed_time(b)
+    final_nll = float(loss.item())
+    full, narrow = rlf.Results(n, dev), rlf.Results(n, dev)
+    nfb = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    t_full = timed(lambda: rlf.fit_sources(fac, cat, 0, n, p, full, ws, stream))
+    t_mlp = timed(lambda: rlf.fit_sources_mlp(fac, cat, 0, n, p, m, narrow, ws, nfb, stream))
+    F, G = full.numpy(), narrow.numpy()
+    de = np.maximum(np.abs(F["e1"] - G["e1"]), np.abs(F["e2"] - G["e2"]))
+    return {"train": {"steps": train_steps, "batch": batch, "lr": lr, "ms": train_ms,
+                      "samples_per_s": train_steps * batch / (train_ms * 1e-3), "final_nll": final_nll},
+            "fit_full_ms": t_full, "fit_mlp_ms": t_mlp, "fit_speedup": t_full / t_mlp,
+            "fallbacks": int(nfb.item()), "n_src": n, "agree_1e-4": float(np.mean(de <= 1e-4)),
+            "max_abs_de": float(de.max()), "box": [7, 7, 5]}
+
 
 def main():
     args = parse()
@@ -351,6 +416,8 @@ def main():
                       {f: int(getattr(params, f)) for f in rlf.TUNE_FIELDS}}
     if graph is not None:
         graph.close()
+    if not args.no_mlp and world == 1:
+        line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream)
     if not args.no_batched and world == 1:
         del ws, data, sky
         torch.cuda.empty_cache()

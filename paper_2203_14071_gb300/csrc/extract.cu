@@ -63,32 +63,27 @@ __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__r
     }
 }
 
-// Flush queue: a lane whose run of equal cells ends appends the run to its
-// warp's queue (ballot + popc, no divergence); when 32 entries are waiting the
-// warp adds them to the shared-memory facet with all lanes active.
-struct RunEntry {
-    int cell, n;
-    float re, im, sp;
-};
-constexpr int kQueue = 64;   // entries per warp
+// Run rings: a lane whose run of equal cells ends appends the run to its own
+// ring of kRing entries in shared memory (slot-major, so a warp's appends are
+// consecutive 16-byte words); no warp vote per visibility.  Once per row the warp
+// checks whether any ring could overflow during the row (at most CG appends) and,
+// if so, every lane adds its own entries to the shared-memory facet.
+constexpr int kRing = 12;    // entries per lane
 
-// Add the first 32 queued runs to the shared-memory facet with the whole warp, move
-// the rest to the front; returns the new queue length.  Kept out of line: it runs
-// once per 32 runs and inlining it into every channel iteration bloats the code.
-__device__ __noinline__ int drain_queue(RunEntry *wq, int qn, int lane, float *sre, float *sim, int *scnt,
-                                        float *ssp)
+// Add lane `tid`'s n_entries ring entries to the facet; entry = {cell | k << 12
+// (cell < 4096, channel k < 128), count, sum Re, sum Im}; the spectral sum of a
+// run is count * (spec_k - spec_off).
+__device__ __noinline__ void drain_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
+                                        int *scnt, float *ssp, const float *dsp_s)
 {
-    __syncwarp();
-    const RunEntry e = wq[lane];
-    atomicAdd(&sre[e.cell], e.re);
-    atomicAdd(&sim[e.cell], e.im);
-    atomicAdd(&scnt[e.cell], e.n);
-    atomicAdd(&ssp[e.cell], e.sp);
-    __syncwarp();
-    const int rest = qn - 32;
-    if (lane < rest) wq[lane] = wq[32 + lane];
-    __syncwarp();
-    return rest;
+    for (int j = 0; j < n_entries; ++j) {
+        const int4 e = ring[j * kThreads + tid];
+        const int cell = e.x & 0xfff;
+        atomicAdd(&sre[cell], __int_as_float(e.z));
+        atomicAdd(&sim[cell], __int_as_float(e.w));
+        atomicAdd(&scnt[cell], e.y);
+        atomicAdd(&ssp[cell], (float)e.y * dsp_s[e.x >> 12]);
+    }
 }
 
 // Cell index of both coordinates, with paired FP32 instructions: floor(t) for
@@ -124,66 +119,50 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
     (void)sky;
-    float *sre = reinterpret_cast<float *>(smraw);
+    int4 *ring = reinterpret_cast<int4 *>(smraw);                       // [kRing][kThreads]
+    float *dsp_s = reinterpret_cast<float *>(ring + kRing * kThreads);  // [RLF_MAX_CHAN]
+    float *sre = dsp_s + RLF_MAX_CHAN;
     float *sim = sre + NN;
     int *scnt = reinterpret_cast<int *>(sim + NN);
     float *ssp = reinterpret_cast<float *>(scnt + NN);
-    RunEntry *queue = reinterpret_cast<RunEntry *>(ssp + NN);
     const int s = blockIdx.x;
     const SrcRow S = table[s];
-    const int lane = threadIdx.x & 31;
-    RunEntry *wq = queue + (threadIdx.x >> 5) * kQueue;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const int tid = threadIdx.x;
 
-    for (int i = threadIdx.x; i < NN; i += kThreads) {
+    for (int i = tid; i < NN; i += kThreads) {
         sre[i] = 0.0f;
         sim[i] = 0.0f;
         scnt[i] = 0;
         ssp[i] = 0.0f;
     }
-    __syncthreads();
-
     const int C = ch.n;
     const int n_groups = (C + CG - 1) / CG;
     const int bpc = kThreads / n_groups;           // baselines per block
-    const int g = threadIdx.x / bpc;
-    const int lane_b = threadIdx.x % bpc;
+    const int g = tid / bpc;
+    const int lane_b = tid % bpc;
     const bool group_on = g < n_groups;
     const int k0 = group_on ? g * CG : 0;
+    for (int k = tid; k < C; k += kThreads) dsp_s[k] = (float)(ch.spec[k] - ch.spec_off);
+    __syncthreads();
     const int half = N / 2;
     const double du = S.du;
     constexpr float kTwoPi = 6.28318530717958647692f;
-    int qn = 0;                                    // warp-uniform queue length
+    int cnt = 0;                                   // entries in this lane's ring
 
-    auto drain32 = [&]() { qn = drain_queue(wq, qn, lane, sre, sim, scnt, ssp); };
-    // every lane of the warp calls push with its own predicate
-    auto push = [&](bool pf, int cell, int n, float re, float im, float sp) {
-        const unsigned m = __ballot_sync(0xffffffffu, pf);
-        if (m == 0u) return;
-        if (pf) {
-            RunEntry e;
-            e.cell = cell;
-            e.n = n;
-            e.re = re;
-            e.im = im;
-            e.sp = sp;
-            wq[qn + __popc(m & lt_mask)] = e;
-        }
-        qn += __popc(m);
-        if (qn >= 32) drain32();
+    auto append = [&](int cell, int k, int n, float re, float im) {
+        ring[cnt * kThreads + tid] = make_int4(cell | (k << 12), n, __float_as_int(re), __float_as_int(im));
+        ++cnt;
     };
 
     if (S.flux > 0.0) {
-        // per-channel constants used for every visibility stay in registers; the
-        // rest is read from the kernel-parameter bank when needed
-        float sdu[CG], f2[CG], fspec[CG], dsp[CG];
+        // per-channel constants used for every visibility stay in registers
+        float sdu[CG], f2[CG], fspec[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
             const int k = min(k0 + c, C - 1);
             sdu[c] = (float)(ch.s[k] / du);
             f2[c] = (float)(ch.s[k] * ch.s[k]);
             fspec[c] = (float)(S.flux * ch.spec[k]);
-            dsp[c] = (float)(ch.spec[k] - ch.spec_off);
         }
         const float q0 = (float)S.q[0], q1 = (float)S.q[1], q2 = (float)S.q[2];
         float lh, ll, mh, ml, nh, nl;
@@ -198,8 +177,8 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
 
         int run_cell[CG], run_n[CG];
         float run_re[CG], run_im[CG];
-        // every lane runs every iteration (the queue's ballots need the whole warp);
-        // lanes without a visibility carry the predicate row_on = false
+        // every lane runs every iteration (the per-row ring check is a warp vote);
+        // lanes without a visibility carry cell = -1, whose runs are never appended
         for (int blk = blockIdx.y; blk < n_blocks; blk += n_parts) {
             const int bl = blk * bpc + lane_b;
             const bool lane_on = group_on && bl < stride;
@@ -220,9 +199,16 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                 nwl = us[5 * n_rows + bl];
             }
             for (int64_t t = 0; t < n_time; ++t) {
+                // a row appends at most CG runs: make room first
+                if (__any_sync(0xffffffffu, cnt > kRing - CG)) {
+                    drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+                    cnt = 0;
+                }
                 const int64_t r = t * stride + bl;
                 const bool row_on = lane_on && r < n_rows;
                 float2 rv[CG];
+#pragma unroll
+                for (int c = 0; c < CG; ++c) rv[c] = make_float2(0.0f, 0.0f);
                 if (vec && row_on) {
                     const float4 *src4 = reinterpret_cast<const float4 *>(data + (r * C + k0));
 #pragma unroll
@@ -231,8 +217,6 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                             const float4 q4 = src4[j];
                             rv[2 * j] = make_float2(q4.x, q4.y);
                             rv[2 * j + 1] = make_float2(q4.z, q4.w);
-                        } else {
-                            rv[2 * j] = rv[2 * j + 1] = make_float2(0.0f, 0.0f);
                         }
                     }
                 }
@@ -308,38 +292,36 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                         iv += half;
                         if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
                     }
-                    const bool change = cell != run_cell[c];
-                    push(change && run_n[c] > 0, run_cell[c], run_n[c], run_re[c], run_im[c],
-                         (float)run_n[c] * dsp[c]);
-                    if (change) {
-                        run_cell[c] = cell;
-                        run_n[c] = 0;
-                        run_re[c] = run_im[c] = 0.0f;
-                    }
-                    if (cell >= 0) {
-                        float rr, ri;
-                        if (vec) {
-                            rr = rv[c].x;
-                            ri = rv[c].y;
-                        } else if (kResid) {
+                    float rr, ri;
+                    if (vec) {
+                        rr = rv[c].x;
+                        ri = rv[c].y;
+                    } else {
+                        rr = ri = 0.0f;
+                        if (cell >= 0) {
                             const float2 dv = data[r * C + k];
                             rr = dv.x;
                             ri = dv.y;
-                        } else {
-                            const float2 dv = data[r * C + k];
-                            const float2 sv = sky[r * C + k];
-                            rr = dv.x - sv.x;
-                            ri = dv.y - sv.y;
+                            if (!kResid) {
+                                const float2 sv = sky[r * C + k];
+                                rr -= sv.x;
+                                ri -= sv.y;
+                            }
                         }
-                        // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn)
-                        float xr = fmaf(rr, cs, ri * sn);
-                        const float xi = fmaf(ri, cs, -rr * sn);
-                        const float rq = rsqrtf(fmaf(q, f2[c], 1.0f));
-                        xr = fmaf(fspec[c], rq * rq * rq, xr);
-                        run_re[c] += xr;
-                        run_im[c] += xi;
-                        run_n[c] += 1;
                     }
+                    // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn), plus the source's model
+                    float xr = fmaf(rr, cs, ri * sn);
+                    const float xi = fmaf(ri, cs, -rr * sn);
+                    const float rq = rsqrtf(fmaf(q, f2[c], 1.0f));
+                    xr = fmaf(fspec[c], rq * rq * rq, xr);
+                    // a run ends when the cell changes; runs of cell -1 are dropped
+                    const bool change = cell != run_cell[c];
+                    if (change && run_cell[c] >= 0) append(run_cell[c], k0 + c, run_n[c], run_re[c], run_im[c]);
+                    const float keep = change ? 0.0f : 1.0f;
+                    run_re[c] = fmaf(run_re[c], keep, xr);
+                    run_im[c] = fmaf(run_im[c], keep, xi);
+                    run_n[c] = change ? 1 : run_n[c] + 1;
+                    run_cell[c] = cell;
                     if (kUniform && c + 1 < CG) {
                         const float cn = cs * cd - sn * sd;
                         sn = fmaf(cs, sd, sn * cd);
@@ -347,24 +329,21 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     }
                 }
             }
+            if (__any_sync(0xffffffffu, cnt > kRing - CG)) {
+                drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+                cnt = 0;
+            }
 #pragma unroll
             for (int c = 0; c < CG; ++c)
-                push(run_n[c] > 0, run_cell[c], run_n[c], run_re[c], run_im[c], (float)run_n[c] * dsp[c]);
+                if (run_cell[c] >= 0) append(run_cell[c], k0 + c, run_n[c], run_re[c], run_im[c]);
         }
     }
-    // the queue's remainder
-    __syncwarp();
-    if (lane < qn) {
-        const RunEntry e = wq[lane];
-        atomicAdd(&sre[e.cell], e.re);
-        atomicAdd(&sim[e.cell], e.im);
-        atomicAdd(&scnt[e.cell], e.n);
-        atomicAdd(&ssp[e.cell], e.sp);
-    }
+    // the rings' remainders
+    drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
     __syncthreads();
     // this CTA's partial facet: plain stores; planes Re, Im, count (int bits), spec - spec_off
     float *o = partial + ((size_t)s * n_parts + blockIdx.y) * 4 * NN;
-    for (int i = threadIdx.x; i < NN; i += kThreads) {
+    for (int i = tid; i < NN; i += kThreads) {
         o[i] = sre[i];
         o[NN + i] = sim[i];
         o[2 * NN + i] = __int_as_float(scnt[i]);
@@ -470,7 +449,8 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
                       const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
                       double *facets, int waves, cudaStream_t st)
 {
-    const size_t smem = 4 * (size_t)N * N * sizeof(float) + (kThreads / 32) * kQueue * sizeof(RunEntry);
+    const size_t smem = (size_t)kRing * kThreads * sizeof(int4) + RLF_MAX_CHAN * sizeof(float) +
+                        4 * (size_t)N * N * sizeof(float);
     const bool resid = sky == nullptr;
     auto kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true> : extract_rl_kernel<CG, true, kSplit, false>)
                            : (resid ? extract_rl_kernel<CG, false, kSplit, true> : extract_rl_kernel<CG, false, kSplit, false>);

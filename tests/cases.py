@@ -46,16 +46,33 @@ def build(wl: synth.Workload, sigma: float | None = None, with_data: bool = True
     sigma = wl.sigma_jy if sigma is None else sigma
     c = Case(wl, obs, cat, sigma)
     if with_data:
-        true = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy,
-                                cat.alpha_arcsec * ARC, cat.e1, cat.e2, nu_ref=wl.nu_ref_hz)
-        d = np.stack([true.real, true.imag], -1)
-        d += synth.noise(obs.n_rows, obs.n_chan, sigma, wl.seed, dtype=np.float64)
-        c.data = d.astype(np.float32)
+        c.data = data_from(true_sky(c), sigma, wl.seed)
         z = np.zeros(cat.n_src)
         s0 = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, c.alpha_med_rad(), z, z,
                               nu_ref=wl.nu_ref_hz)
         c.sky0 = np.stack([s0.real, s0.imag], -1).astype(np.float32)
     return c
+
+
+def true_sky(c: Case) -> np.ndarray:
+    """The oracle's sky model at the catalogue's true shapes and scalelengths, complex128 [R, C]."""
+    return oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                            c.cat.alpha_arcsec * ARC, c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz)
+
+
+def data_from(true: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """Data visibilities: true sky plus seeded Gaussian noise, rounded to complex64 ([R, C, 2] float32)."""
+    d = np.stack([true.real, true.imag], -1)
+    d += synth.noise(true.shape[0], true.shape[1], sigma, seed, dtype=np.float64)
+    return d.astype(np.float32)
+
+
+def fingerprint(data: np.ndarray) -> dict:
+    """A few numbers that identify a data array (sums in float64 and sampled values)."""
+    flat = data.reshape(-1).astype(np.float64)
+    idx = np.linspace(0, flat.size - 1, 16).astype(np.int64)
+    return {"sum": float(flat.sum()), "sum_sq": float(np.dot(flat, flat)), "idx": idx.tolist(),
+            "values": flat[idx].tolist()}
 
 
 def to_device(case: Case, e1=None, e2=None, alpha_arcsec=None, device="cuda"):
