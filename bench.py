@@ -246,11 +246,12 @@ def batched_line(rlf, torch, dev, args, prec, rank, stream):
             "tuning": {f: int(getattr(p, f)) for f in rlf.TUNE_FIELDS}, "steps": steps}
 
 
-def mlp_line(rlf, torch, dev, W, stream, train_steps=400, batch=256, lr=1e-3, reps=5):
+def mlp_line(rlf, torch, dev, W, stream, train_steps=2000, batch=256, lr=1e-3, lr_min=5e-5, chunk=25, reps=5):
     """The learned proposal on this workload: train the network on facets simulated from
     the workload's own coverage (every source's facet as a template, random shapes,
-    scalelengths from the Eq. 4 prior), then fit the real facets with the narrowed
-    grid and with the full grid, timed with CUDA events on the same stream."""
+    scalelengths from the Eq. 4 prior; cosine learning-rate decay), then fit the real
+    facets with the narrowed grid and with the full grid, timed with CUDA events on the
+    same stream.  The random draws of `chunk` steps are made at once."""
     obs, cat, p, ws, data, sky = (W[k] for k in ("obs", "cat", "params", "ws", "data", "sky"))
     n = W["cat_np"].n_src
     rlf.sky_model(obs, cat, p, sky, ws, stream)
@@ -263,49 +264,53 @@ def mlp_line(rlf, torch, dev, W, stream, train_steps=400, batch=256, lr=1e-3, re
     ws_t = rlf.mlp_workspace(batch, dev)
     x16 = torch.empty(batch, 8192, dtype=torch.float16, device=dev)
     y = torch.empty(batch, 3, device=dev)
-    loss = torch.zeros(1, device=dev)
+    losses = torch.zeros(train_steps, device=dev)
     flux = cat.flux_jy
 
-    def train(s):
-        tidx = torch.randint(0, n, (batch,), generator=gen, device=dev, dtype=torch.int32)
-        e = torch.randn(batch, 2, generator=gen, device=dev, dtype=torch.float64) * 0.3
-        e = e * torch.clamp(0.75 / torch.linalg.norm(e, dim=1, keepdim=True), max=1.0)
+    def draws(k):
+        tidx = torch.randint(0, n, (k, batch), generator=gen, device=dev, dtype=torch.int32)
+        e = torch.randn(k, batch, 2, generator=gen, device=dev, dtype=torch.float64) * 0.3
+        e = e * torch.clamp(0.75 / torch.linalg.norm(e, dim=2, keepdim=True), max=1.0)
         lna = p.add + p.esp * torch.log(flux[tidx.long()] * 1e6) + p.r_std * torch.randn(
-            batch, generator=gen, device=dev, dtype=torch.float64)
+            k, batch, generator=gen, device=dev, dtype=torch.float64)
         al = torch.clamp(torch.exp(lna), p.r_min_arcsec, p.r_max_arcsec)
-        z = torch.randn(batch, 2, 4096, generator=gen, device=dev)
-        rlf.mlp_simulate(fac, flux, tidx, e[:, 0].contiguous(), e[:, 1].contiguous(), al, z, p, x16, y, stream)
-        rlf.mlp_train_step(m, x16, y, lr, s, loss, ws_t, stream)
+        z = torch.randn(k, batch, 2, 4096, generator=gen, device=dev)
+        return tidx, e[..., 0].contiguous(), e[..., 1].contiguous(), al, z
 
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for s in range(1, train_steps + 1):
-        train(s)
+    for c0 in range(0, train_steps, chunk):
+        tidx, e1, e2, al, z = draws(min(chunk, train_steps - c0))
+        for j in range(tidx.shape[0]):
+            s = c0 + j + 1
+            lr_s = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * (s - 1) / train_steps))
+            rlf.mlp_simulate(fac, flux, tidx[j], e1[j], e2[j], al[j], z[j], p, x16, y, stream)
+            rlf.mlp_train_step(m, x16, y, lr_s, s, losses[s - 1:s], ws_t, stream)
     b.record(stream)
     torch.cuda.synchronize(dev)
     train_ms = a.elapsed_time(b)
-    final_nll = float(loss.item())
+    tail = losses[-min(100, train_steps):].mean().item()
     full, narrow = rlf.Results(n, dev), rlf.Results(n, dev)
     nfb = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def timed(fn):
         fn()
         torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
             fn()
-        e1.record(stream)
+        e1_.record(stream)
         torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1_) / reps
 
     t_full = timed(lambda: rlf.fit_sources(fac, cat, 0, n, p, full, ws, stream))
     t_mlp = timed(lambda: rlf.fit_sources_mlp(fac, cat, 0, n, p, m, narrow, ws, nfb, stream))
     F, G = full.numpy(), narrow.numpy()
     de = np.maximum(np.abs(F["e1"] - G["e1"]), np.abs(F["e2"] - G["e2"]))
-    return {"train": {"steps": train_steps, "batch": batch, "lr": lr, "ms": train_ms,
-                      "samples_per_s": train_steps * batch / (train_ms * 1e-3), "final_nll": final_nll},
+    return {"train": {"steps": train_steps, "batch": batch, "lr": [lr, lr_min], "ms": train_ms,
+                      "samples_per_s": train_steps * batch / (train_ms * 1e-3), "nll_last_100": tail},
             "fit_full_ms": t_full, "fit_mlp_ms": t_mlp, "fit_speedup": t_full / t_mlp,
             "fallbacks": int(nfb.item()), "n_src": n, "agree_1e-4": float(np.mean(de <= 1e-4)),
             "max_abs_de": float(de.max()), "box": [7, 7, 5]}

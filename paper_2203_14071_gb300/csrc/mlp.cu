@@ -18,6 +18,7 @@ namespace rlf {
 namespace {
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8, GTHREADS = 128;
+constexpr int kL1Slices = 16;   // K slices of the first layer's forward GEMM
 
 enum { EPI_F32 = 0, EPI_F32_BIAS = 1, EPI_F16_BIAS_RELU = 2, EPI_F16_MASK = 3 };
 
@@ -34,15 +35,29 @@ __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const 
 //          B(k, n) = TB ? B[n * ldb + k] : B[k * ldb + n].
 // Tiles of 64 x 64 x 32 staged in shared memory as As[m][k] and Bt[n][k]; four
 // warps each own a 32 x 32 block of mma tiles.  Ragged edges are zero-filled.
+// Staging moves 8 halves per 16-byte load when `vec` (both matrices 16-byte
+// aligned, leading dimensions multiples of 8).  With gridDim.z > 1 the K range is
+// split: slice z sums its share into the f32 partial C32 + z * M * ldc (EPI_F32),
+// and splitk_reduce_kernel adds the slices and applies the epilogue.
+__device__ __forceinline__ uint4 load8h(const __half *p, int avail, bool vec)
+{
+    if (vec && avail >= 8) return *reinterpret_cast<const uint4 *>(p);
+    __align__(16) __half t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = j < avail ? p[j] : __float2half(0.0f);
+    return *reinterpret_cast<const uint4 *>(t);
+}
+
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(GTHREADS)
 gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __half *__restrict__ B, int ldb,
             const float *__restrict__ bias, const __half *__restrict__ mask, int ldm, float *__restrict__ C32,
-            __half *__restrict__ C16, int ldc)
+            __half *__restrict__ C16, int ldc, int k_slice, bool vec)
 {
     __shared__ __align__(16) __half As[GBM][GBK + GPAD];
     __shared__ __align__(16) __half Bt[GBN][GBK + GPAD];
     const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int kb = blockIdx.z * k_slice, ke = min(K, kb + k_slice);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int g = lane >> 2, t = lane & 3;
@@ -53,35 +68,41 @@ gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-    const __half zero = __float2half(0.0f);
-    for (int k0 = 0; k0 < K; k0 += GBK) {
-        for (int i = threadIdx.x; i < GBM * GBK; i += GTHREADS) {
-            int m, k;
-            if (TA) {
-                m = i % GBM;
-                k = i / GBM;
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+        // 64 x 32 halves per operand = 256 groups of 8; two groups per thread
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+            const int i = threadIdx.x + rep * GTHREADS;
+            if (!TA) {
+                const int m = i >> 2, kq = (i & 3) * 8;
+                const int gm = m0 + m, gk = k0 + kq;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gm < M) q = load8h(A + (size_t)gm * lda + gk, min(8, ke - gk), vec);
+                *reinterpret_cast<uint4 *>(&As[m][kq]) = q;
             } else {
-                m = i / GBK;
-                k = i % GBK;
+                const int k = i >> 3, mq = (i & 7) * 8;
+                const int gk = k0 + k, gm = m0 + mq;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gk < ke) q = load8h(A + (size_t)gk * lda + gm, min(8, M - gm), vec);
+                const __half *h = reinterpret_cast<const __half *>(&q);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) As[mq + j][k] = h[j];
             }
-            const int gm = m0 + m, gk = k0 + k;
-            __half v = zero;
-            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[m][k] = v;
-        }
-        for (int i = threadIdx.x; i < GBN * GBK; i += GTHREADS) {
-            int n, k;
             if (TB) {
-                n = i / GBK;
-                k = i % GBK;
+                const int n = i >> 2, kq = (i & 3) * 8;
+                const int gn = n0 + n, gk = k0 + kq;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gn < N) q = load8h(B + (size_t)gn * ldb + gk, min(8, ke - gk), vec);
+                *reinterpret_cast<uint4 *>(&Bt[n][kq]) = q;
             } else {
-                n = i % GBN;
-                k = i / GBN;
+                const int k = i >> 3, nq = (i & 7) * 8;
+                const int gk = k0 + k, gn = n0 + nq;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gk < ke) q = load8h(B + (size_t)gk * ldb + gn, min(8, N - gn), vec);
+                const __half *h = reinterpret_cast<const __half *>(&q);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) Bt[nq + j][k] = h[j];
             }
-            const int gn = n0 + n, gk = k0 + k;
-            __half v = zero;
-            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-            Bt[n][k] = v;
         }
         __syncthreads();
 #pragma unroll
@@ -108,6 +129,7 @@ gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __
         }
         __syncthreads();
     }
+    float *C32z = C32 ? C32 + (size_t)blockIdx.z * M * ldc : nullptr;
 #pragma unroll
     for (int im = 0; im < 2; ++im)
 #pragma unroll
@@ -122,7 +144,7 @@ gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __
                     if (c >= N) continue;
                     float v = acc[im][in][2 * h + q];
                     if (EPI == EPI_F32) {
-                        C32[(size_t)r * ldc + c] = v;
+                        C32z[(size_t)r * ldc + c] = v;
                     } else if (EPI == EPI_F32_BIAS) {
                         C32[(size_t)r * ldc + c] = v + bias[c];
                     } else if (EPI == EPI_F16_BIAS_RELU) {
@@ -136,12 +158,29 @@ gemm_kernel(int M, int N, int K, const __half *__restrict__ A, int lda, const __
             }
 }
 
+// h = relu(sum over slices of part[z][M][N] + bias) as f16, slices added in order.
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, int n_slices, int M, int N,
+                                     const float *__restrict__ bias, __half *__restrict__ h)
+{
+    const int64_t MN = (int64_t)M * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = bias[i % N];
+        for (int z = 0; z < n_slices; ++z) v += part[z * MN + i];
+        h[i] = __float2half(v > 0.0f ? v : 0.0f);
+    }
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const __half *A, int lda, const __half *B, int ldb, const float *bias,
-                 const __half *mask, int ldm, float *C32, __half *C16, int ldc, cudaStream_t st)
+                 const __half *mask, int ldm, float *C32, __half *C16, int ldc, cudaStream_t st, int n_slices = 1)
 {
-    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-    gemm_kernel<TA, TB, EPI><<<grid, GTHREADS, 0, st>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, C32, C16, ldc);
+    const int k_slice = ((K + n_slices - 1) / n_slices + GBK - 1) / GBK * GBK;
+    const bool vec = aligned16(A) && aligned16(B) && lda % 8 == 0 && ldb % 8 == 0;
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, n_slices);
+    gemm_kernel<TA, TB, EPI><<<grid, GTHREADS, 0, st>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, C32, C16, ldc,
+                                                         k_slice, vec);
     return cudaGetLastError();
 }
 
@@ -251,7 +290,8 @@ __global__ void encode_kernel(const double *__restrict__ facets, const SrcRow *_
 }
 
 // Training facets: D_c / S = s_c M(k_c; e, alpha) + (sigma / S) z / sqrt(n_c), from a
-// template facet's counts and spectral sums and its cell size.
+// template facet's counts and spectral sums and its cell size.  The result is f16,
+// so the arithmetic is FP32.
 __global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, double add, double esp,
                                 double psf_nat, const double *__restrict__ tflux, const int32_t *__restrict__ tidx,
                                 const double *__restrict__ e1, const double *__restrict__ e2,
@@ -260,34 +300,41 @@ __global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, dou
 {
     const int b = blockIdx.y;
     const int NN = N * N;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int ti = tidx[b];
     const bool valid = ti >= 0 && ti < n_tmpl;   // an out-of-range template index gives an all-zero input
-    const double a1 = e1[b], a2 = e2[b], al = alpha_as[b] * kArcsec;
-    if (c == 0) {
-        y[b * 3 + 0] = (float)a1;
-        y[b * 3 + 1] = (float)a2;
+    const float a1 = (float)e1[b], a2 = (float)e2[b];
+    const double flux = valid ? tflux[ti] : 1.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        y[b * 3 + 0] = a1;
+        y[b * 3 + 1] = a2;
         y[b * 3 + 2] = (float)log(alpha_as[b]);
     }
-    if (c >= NN) return;
+    // the template's cell size du = 1 / (K alpha_med(S)) with Eq. 4, and the
+    // quadratic form 4 pi^2 alpha^2 |A^-1 k|^2 in cell units (A symmetric)
+    const float du = (float)(1.0 / (psf_nat * exp(add + esp * log(flux * 1.0e6)) * kArcsec));
+    const float al = (float)(alpha_as[b] * kArcsec);
+    const float idet = 1.0f / (1.0f - a1 * a1 - a2 * a2);
+    const float c2 = 4.0f * (float)(kPi * kPi) * al * al * du * du * idet * idet;
+    const float sr0 = (float)(sigma / flux);
     const double *f = tmpl + (size_t)(valid ? ti : 0) * 4 * NN;
-    const double n = valid ? f[2 * NN + c] : 0.0;
-    float re = 0.0f, im = 0.0f;
-    if (n > 0.0) {
-        // the template's cell size, 1 / (K alpha_med(S)) with Eq. 4
-        const double du = 1.0 / (psf_nat * exp(add + esp * log(tflux[ti] * 1.0e6)) * kArcsec);
-        const double cu = ((c % N) - N / 2 + 0.5) * du, cv = ((c / N) - N / 2 + 0.5) * du;
-        const double det = 1.0 - a1 * a1 - a2 * a2;
-        const double x1 = ((1.0 + a1) * cu + a2 * cv) / det, x2 = (a2 * cu + (1.0 - a1) * cv) / det;
-        const double q = 1.0 + 4.0 * kPi * kPi * al * al * (x1 * x1 + x2 * x2);
-        const double M = 1.0 / (q * sqrt(q));
-        const double sbar = f[3 * NN + c] / n;
-        const double sr = sigma / tflux[ti] / sqrt(n);
-        re = (float)(sbar * M + sr * z[((size_t)b * 2) * NN + c]);
-        im = (float)(sr * z[((size_t)b * 2 + 1) * NN + c]);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < NN; c += gridDim.x * blockDim.x) {
+        const double n = valid ? f[2 * NN + c] : 0.0;
+        float re = 0.0f, im = 0.0f;
+        if (n > 0.0) {
+            const float cu = (float)((c % N) - N / 2) + 0.5f, cv = (float)((c / N) - N / 2) + 0.5f;
+            const float x1 = (1.0f + a1) * cu + a2 * cv, x2 = a2 * cu + (1.0f - a1) * cv;
+            const float q = fmaf(c2, x1 * x1 + x2 * x2, 1.0f);
+            const float rq = rsqrtf(q);
+            const float M = rq * rq * rq;
+            const float nf = (float)n;
+            const float sbar = (float)(f[3 * NN + c] / n);
+            const float sr = sr0 * rsqrtf(nf);
+            re = fmaf(sbar, M, sr * z[((size_t)b * 2) * NN + c]);
+            im = sr * z[((size_t)b * 2 + 1) * NN + c];
+        }
+        x[(size_t)b * 2 * NN + c] = __float2half(re);
+        x[(size_t)b * 2 * NN + NN + c] = __float2half(im);
     }
-    x[(size_t)b * 2 * NN + c] = __float2half(re);
-    x[(size_t)b * 2 * NN + NN + c] = __float2half(im);
 }
 
 // Sub-box of the grid centred on the node nearest the prediction, clamped inside
@@ -395,6 +442,7 @@ MlpScratch mlp_scratch(void *base, int32_t max_batch)
     s.g16 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpOutPad * sizeof(__half)));
     s.dz2 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
     s.dz1 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
+    s.part = reinterpret_cast<float *>(take((size_t)kL1Slices * max_batch * kMlpHidden * sizeof(float)));
     s.bytes = (size_t)(b - static_cast<char *>(base));
     return s;
 }
@@ -403,8 +451,15 @@ cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const M
 {
     const MlpOffsets o = mlp_offsets();
     const __half *W1h = W.h, *W2h = W.h + o.W1h_n, *W3h = W.h + o.W1h_n + o.W2h_n;
-    cudaError_t e = gemm<false, false, EPI_F16_BIAS_RELU>(B, kMlpHidden, kMlpIn, x, kMlpIn, W1h, kMlpHidden,
-                                                           W.w + o.b1, nullptr, 0, nullptr, s.h1, kMlpHidden, st);
+    // layer 1 (K = 8192): split over K so that the small batch still fills the GPU
+    cudaError_t e = gemm<false, false, EPI_F32>(B, kMlpHidden, kMlpIn, x, kMlpIn, W1h, kMlpHidden, nullptr, nullptr, 0,
+                                                s.part, nullptr, kMlpHidden, st, kL1Slices);
+    if (e == cudaSuccess) {
+        const int64_t mn = (int64_t)B * kMlpHidden;
+        splitk_reduce_kernel<<<(int)((mn + 255) / 256 < 1024 ? (mn + 255) / 256 : 1024), 256, 0, st>>>(
+            s.part, kL1Slices, B, kMlpHidden, W.w + o.b1, s.h1);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
         e = gemm<false, false, EPI_F16_BIAS_RELU>(B, kMlpHidden, kMlpHidden, s.h1, kMlpHidden, W2h, kMlpHidden,
                                                   W.w + o.b2, nullptr, 0, nullptr, s.h2, kMlpHidden, st);
@@ -479,7 +534,7 @@ cudaError_t mlp_simulate(const double *tmpl, int32_t n_tmpl, const rlf_params &p
                          const float *z, int32_t B, int32_t N, double sigma, __half *x, float *y, cudaStream_t st)
 {
     const int NN = N * N;
-    dim3 grid((NN + 255) / 256, B);
+    dim3 grid(4, B);
     simulate_kernel<<<grid, 256, 0, st>>>(tmpl, n_tmpl, p.add, p.esp, p.psf_nat, tflux, tidx, e1, e2, alpha_as, z, N,
                                           sigma, x, y);
     return cudaGetLastError();

@@ -211,6 +211,7 @@ struct MlpWeights {
 struct MlpScratch {
     __half *h1, *h2, *g16, *dz2, *dz1;
     float *o, *g32;
+    float *part;            // split-K partial sums of the first layer
     size_t bytes;
 };
 MlpOffsets mlp_offsets();

@@ -92,9 +92,11 @@ def test_precision_table(rlf, gold, mid_true, vis_errors, variant):
     sigma = g["sigma_jy"]
     data = cases.data_from(true, sigma, c.wl.seed)
     fp, gfp = cases.fingerprint(data), g["fingerprint"]
+    # sampled values bit for bit; the float64 sums to 1e-9 (numpy's pairwise summation
+    # groups terms differently on different SIMD widths)
     assert fp["values"] == gfp["values"]
-    assert math.isclose(fp["sum"], gfp["sum"], rel_tol=1e-12, abs_tol=1e-12)
-    assert math.isclose(fp["sum_sq"], gfp["sum_sq"], rel_tol=1e-12)
+    assert math.isclose(fp["sum"], gfp["sum"], rel_tol=1e-9, abs_tol=1e-9)
+    assert math.isclose(fp["sum_sq"], gfp["sum_sq"], rel_tol=1e-9)
     est = np.array(g["est"])
     R, C, n = c.obs.n_rows, c.obs.n_chan, c.cat.n_src
     d = cases.vis_tensor(data)
@@ -120,7 +122,7 @@ def test_precision_table(rlf, gold, mid_true, vis_errors, variant):
                           "flag_same": bool(flag_same[i]), "thresh_margin": est[i, oracle.THRESH_MARGIN],
                           "vis_err_rel": vis_errors[name][i]})
         summary[name] = {"max_de": float(de.max()), "median_de": float(np.median(de)),
-                         "n_de_gt_1e-4": int(np.sum(de > 1e-4)), "n_alpha_diff": int(np.sum(da > 1e-9)),
+                         "n_de_gt_1e-4": int(np.sum(de > 1e-4)), "max_abs_dalpha": float(da.max()),
                          "max_rel_dflux": float(ds.max()), "n_flag_diff": int(np.sum(~flag_same)),
                          "max_vis_err_rel": float(vis_errors[name].max()),
                          "n_bad": int(np.sum(res["flag"] & 1))}
