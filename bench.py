@@ -486,18 +486,23 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     upd_ms = timed(lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream))
     chunk = params.chunk if params.chunk > 0 else n_src
     n_chunks = (n_src + chunk - 1) // chunk
-    # kernels of one rlf_run step: prepare + sky model (+ split baselines in split mode); per chunk:
-    # residual (batched chunks only), extraction, partial reduce, compaction, LPT order, persistent
-    # fit, prepare + sky update (memsets and copies are not kernels of ours)
-    per_chunk = 7 + (1 if chunk >= 3 and params.precision != 0 else 0)
-    launches = 2 + (1 if params.precision == 2 else 0) + n_chunks * per_chunk
+    # kernels of one rlf_run step: prepare + sky model; outside FP64 mode the baseline extents,
+    # their order (rows = time x baselines) and the split baselines (split mode); per chunk:
+    # residual (batched chunks only), window reach per source (outside FP64 mode), extraction,
+    # partial reduce, compaction, LPT order, persistent fit, prepare + sky update (memsets and
+    # copies are not kernels of ours)
+    mixed = params.precision != 0
+    is_ordered = obs.n_baselines > 0 and obs.n_rows % obs.n_baselines == 0
+    per_chunk = 7 + (1 if chunk >= 3 and mixed else 0) + (1 if mixed else 0)
+    launches = (2 + (1 if mixed else 0) + (1 if mixed and is_ordered else 0)
+                + (1 if params.precision == 2 else 0) + n_chunks * per_chunk)
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
             "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches,
             "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item())}
 
 
-# Algorithmic operation counts per unit of work: FP32 ops and
-# MUFU ops per unit, plus per (row, source) overheads of the phase argument.
+# Algorithmic operation counts per unit of work: FP32 ops and MUFU ops per unit, plus
+# per (row, source) overheads of the phase argument.
 OPS = {
     "sky_model": {"fp32": 10.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
     "update": {"fp32": 13.0, "mufu": 2.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},

@@ -230,8 +230,8 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
                    void *workspace, size_t ws_bytes, void *stream);
 
 /*
- * Learned proposal of the likelihood sub-grid.  A spec addition; the paper
- * has no counterpart (its fit searches the likelihood with Nelder-Mead, Sec. 2.4).
+ * Learned proposal of the likelihood sub-grid.  An addition to the method: the
+ * paper has no counterpart (its fit searches the likelihood with Nelder-Mead, Sec. 2.4).
  * A perceptron reads a facet (facet_n must be 64: x = [Re D_c / S, Im D_c / S],
  * 8192 values, empty cells 0, f16) and predicts (mu, logvar) of (e1, e2,
  * ln(alpha/arcsec)): h1 = relu(x W1 + b1) [256], h2 = relu(h1 W2 + b2) [256],

@@ -214,6 +214,10 @@ class Observation:
     def n_chan(self):
         return self.struct.n_chan
 
+    @property
+    def n_baselines(self):
+        return self.struct.n_baselines
+
 
 class Catalogue:
     """Device catalogue arrays (float64), sorted by decreasing flux."""

@@ -129,6 +129,10 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_split = take(ext ? 6 * rows * sizeof(float) : 0);
     const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
     const size_t o_part = take(ext ? (size_t)kMaxPartials * 4 * NN * sizeof(float) : 0);
+    const size_t o_ext = take(ext ? rows * sizeof(float) : 0);
+    const size_t o_perm = take(ext ? rows * sizeof(int32_t) : 0);
+    const size_t o_live = take(ext ? (size_t)n_src * sizeof(int32_t) : 0);
+    const size_t o_ocnt = take(ext ? (size_t)kOrderBuckets * kOrderThreads * sizeof(int32_t) : 0);
     const size_t total = off + 256;   // slack for aligning an arbitrary base pointer
     if (ws && base) {
         char *b = reinterpret_cast<char *>(align_up(reinterpret_cast<size_t>(base), 256));
@@ -154,6 +158,10 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
         ws->resid = reinterpret_cast<float *>(b + o_resid);
         ws->partial = reinterpret_cast<float *>(b + o_part);
+        ws->extent = reinterpret_cast<float *>(b + o_ext);
+        ws->perm = reinterpret_cast<int32_t *>(b + o_perm);
+        ws->n_live = reinterpret_cast<int32_t *>(b + o_live);
+        ws->order_counts = reinterpret_cast<int32_t *>(b + o_ocnt);
         ws->bytes = total;
     }
     return total;
@@ -282,9 +290,8 @@ rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const f
     if (e == cudaSuccess)
         e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                            nullptr, *p, ws.table, ws.status, st);
-    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
-    if (e == cudaSuccess)
-        e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws.uvw_split, ws.resid, ws.partial, facets, st);
+    if (e == cudaSuccess) e = launch_extract_prepare(*uvw, *p, ws, st);
+    if (e == cudaSuccess) e = launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, count, *p, ws, facets, st);
     return cuda_status(e);
 }
 
@@ -347,11 +354,10 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
         e = launch_prepare(src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
                            ws.status, st);
     if (e == cudaSuccess) e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
-    if (e == cudaSuccess && p.precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(uvw, ws.uvw_split, st);
+    if (e == cudaSuccess) e = launch_extract_prepare(uvw, p, ws, st);
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
-        e = launch_extract(uvw, ch, vis_data, vis_sky, ws.table + first, cnt, p, ws.uvw_split, ws.resid,
-                           ws.partial, ws.facets, st);
+        e = launch_extract(uvw, ch, vis_data, vis_sky, ws.table + first, cnt, p, ws, ws.facets, st);
         if (e != cudaSuccess) break;
         e = launch_fit(ws.facets, ws.table + first, cnt, p, ws, out, first, st);
         if (e != cudaSuccess) break;
@@ -475,7 +481,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
     // the sky model of the catalogue and the split baselines, inputs of the timed steps
     cudaError_t e = launch_prepare(*src, 0, n, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr, nullptr, q,
                                    ws.table, ws.status, st);
-    if (e == cudaSuccess && q.precision == RLF_PREC_MIXED_SPLIT) e = launch_split_uvw(*uvw, ws.uvw_split, st);
+    if (e == cudaSuccess) e = launch_extract_prepare(*uvw, q, ws, st);
     if (e != cudaSuccess) return RLF_ECUDA;
     float best[3] = {0, 0, 0};
     // 1. sky-model CTAs per SM
@@ -504,8 +510,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
         for (int c : cand) {
             q.tune_extract_waves = c;
             const float t = time_median([&] {
-                return launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws.uvw_split, ws.resid,
-                                      ws.partial, ws.facets, st);
+                return launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws, ws.facets, st);
             }, st, reps);
             if (t < 0) return RLF_ECUDA;
             if (bt == 0 || t < bt) {
@@ -515,8 +520,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
         }
         q.tune_extract_waves = bc;
         best[1] = bt;
-        if (launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws.uvw_split, ws.resid, ws.partial,
-                           ws.facets, st) != cudaSuccess)
+        if (launch_extract(*uvw, ch, vis_data, vis_sky, ws.table, chunk, q, ws, ws.facets, st) != cudaSuccess)
             return RLF_ECUDA;
     }
     // 3. likelihood: scalelength nodes per thread x CTAs per SM

@@ -46,20 +46,111 @@ __global__ void residual_kernel(const float4 *__restrict__ d, const float4 *__re
     }
 }
 
+// u, v, w as float pairs; with `perm`, column j of every time step holds baseline perm[j]
+// (rows are [time][stride] and n is a multiple of stride).
 __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__restrict__ v,
-                                 const double *__restrict__ w, int64_t n, float *__restrict__ out)
+                                 const double *__restrict__ w, int64_t n, int32_t stride,
+                                 const int32_t *__restrict__ perm, float *__restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = perm ? (i / stride) * stride + perm[i % stride] : i;
         float h, l;
-        split_double(u[i], h, l);
+        split_double(u[r], h, l);
         out[i] = h;
         out[n + i] = l;
-        split_double(v[i], h, l);
+        split_double(v[r], h, l);
         out[2 * n + i] = h;
         out[3 * n + i] = l;
-        split_double(w[i], h, l);
+        split_double(w[r], h, l);
         out[4 * n + i] = h;
         out[5 * n + i] = l;
+    }
+}
+
+// Smallest Chebyshev extent max(|u|, |v|) (metres) of each baseline over time, rounded
+// down to FP32: for every row r = b + t * stride, max(|u_r|, |v_r|) >= extent[b].
+__global__ void track_extent_kernel(const double *__restrict__ u, const double *__restrict__ v, int64_t n_rows,
+                                    int32_t stride, float *__restrict__ extent)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < stride; b += gridDim.x * blockDim.x) {
+        double m = 1.0e300;
+        for (int64_t r = b; r < n_rows; r += stride) m = fmin(m, fmax(fabs(u[r]), fabs(v[r])));
+        extent[b] = __double2float_rd(m);
+    }
+}
+
+// Order bucket of an extent: 20 buckets per octave from 0.25 m (any monotone map works;
+// the order only groups baselines of similar extent).
+__device__ __forceinline__ int extent_bucket(float e)
+{
+    if (!(e > 0.25f)) return 0;
+    const int b = (int)floorf((log2f(e) + 2.0f) * 20.0f);
+    return b < kOrderBuckets - 1 ? b : kOrderBuckets - 1;
+}
+
+// Stable counting sort of the n baselines by extent bucket, in one CTA: thread t owns
+// the contiguous index range [t * per, (t + 1) * per); counts[bucket][t] holds its
+// bucket counts, then its output offsets; equal buckets keep index order, so the
+// result is the same on every run.
+__global__ void __launch_bounds__(kOrderThreads)
+order_kernel(const float *__restrict__ extent, int32_t n, int32_t *__restrict__ counts, int32_t *__restrict__ perm)
+{
+    __shared__ int part[kOrderThreads];
+    const int t = threadIdx.x;
+    const int per = (n + kOrderThreads - 1) / kOrderThreads;
+    const int j0 = min(n, t * per), j1 = min(n, j0 + per);
+    for (int b = 0; b < kOrderBuckets; ++b) counts[b * kOrderThreads + t] = 0;
+    for (int j = j0; j < j1; ++j) counts[extent_bucket(extent[j]) * kOrderThreads + t] += 1;
+    __syncthreads();
+    // exclusive scan of counts in (bucket, thread) order: thread t scans entries
+    // [t * kOrderBuckets, (t + 1) * kOrderBuckets) of the flattened array
+    const int e0 = t * kOrderBuckets, e1 = e0 + kOrderBuckets;
+    int local = 0;
+    for (int i = e0; i < e1; ++i) local += counts[i];
+    part[t] = local;
+    __syncthreads();
+    for (int d = 1; d < kOrderThreads; d *= 2) {       // inclusive scan of the thread sums
+        const int add = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    int run = part[t] - local;
+    for (int i = e0; i < e1; ++i) {
+        const int c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    for (int j = j0; j < j1; ++j) {
+        int *slot = &counts[extent_bucket(extent[j]) * kOrderThreads + t];
+        perm[*slot] = j;
+        *slot += 1;
+    }
+}
+
+// Baselines to walk per source: one past the last ordered position whose baseline
+// can reach the facet window.  A baseline cannot when extent * s_min / du >= N / 2
+// (with a 1e-12 margin): then at every row and channel |u| s / du or |v| s / du is at
+// least N / 2, so floor(u s / du) or floor(v s / du) lies outside [-N/2, N/2).
+__global__ void live_count_kernel(const float *__restrict__ extent, const int32_t *__restrict__ perm, int32_t n,
+                                  const SrcRow *__restrict__ table, int32_t N, double s_min,
+                                  int32_t *__restrict__ n_live)
+{
+    __shared__ int best[kThreads / 32];
+    const double lim = 0.5 * N * table[blockIdx.x].du * (1.0 + 1.0e-12);
+    int last = -1;
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+        const int b = perm ? perm[j] : j;
+        if ((double)extent[b] * s_min < lim) last = j;
+    }
+    for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+    if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = -1;
+        for (int w = 0; w < kThreads / 32; ++w) m = max(m, best[w]);
+        n_live[blockIdx.x] = m + 1;
     }
 }
 
@@ -114,7 +205,8 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                   const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
                   int32_t stride, int32_t n_parts, const ChanTable ch,
                   const float2 *__restrict__ data, const float2 *__restrict__ sky,
-                  const SrcRow *__restrict__ table, int32_t N, float *__restrict__ partial)
+                  const SrcRow *__restrict__ table, int32_t N, const int32_t *__restrict__ perm,
+                  const int32_t *__restrict__ n_live, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
@@ -170,7 +262,9 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
         split_double(S.m, mh, ml);
         split_double(S.n1, nh, nl);
         const int64_t n_time = (n_rows + stride - 1) / stride;
-        const int n_blocks = (stride + bpc - 1) / bpc;
+        // the source's baselines, in extent order, that can reach its window
+        const int n_base = n_live[s];
+        const int n_blocks = (n_base + bpc - 1) / bpc;
         // the residual of a row's channel group is read as float4 pairs when the
         // layout allows (even channel count, groups of >= 2 channels)
         const bool vec = kResid && CG >= 2 && (C % 2 == 0);
@@ -180,8 +274,11 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
         // every lane runs every iteration (the per-row ring check is a warp vote);
         // lanes without a visibility carry cell = -1, whose runs are never appended
         for (int blk = blockIdx.y; blk < n_blocks; blk += n_parts) {
-            const int bl = blk * bpc + lane_b;
-            const bool lane_on = group_on && bl < stride;
+            // lane position j in the order; bl the baseline (data rows bl + t * stride);
+            // the split baselines are stored in order, at column j
+            const int j = blk * bpc + lane_b;
+            const bool lane_on = group_on && j < n_base;
+            const int bl = lane_on ? (perm ? perm[j] : j) : 0;
 #pragma unroll
             for (int c = 0; c < CG; ++c) {
                 run_cell[c] = -1;
@@ -191,12 +288,12 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
             // split baselines of the next row are fetched one iteration ahead
             float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
             if (kSplit && lane_on && bl < n_rows) {
-                nuh = us[bl];
-                nul = us[n_rows + bl];
-                nvh = us[2 * n_rows + bl];
-                nvl = us[3 * n_rows + bl];
-                nwh = us[4 * n_rows + bl];
-                nwl = us[5 * n_rows + bl];
+                nuh = us[j];
+                nul = us[n_rows + j];
+                nvh = us[2 * n_rows + j];
+                nvl = us[3 * n_rows + j];
+                nwh = us[4 * n_rows + j];
+                nwl = us[5 * n_rows + j];
             }
             for (int64_t t = 0; t < n_time; ++t) {
                 // a row appends at most CG runs: make room first
@@ -230,13 +327,14 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     wh = nwh;
                     wl = nwl;
                     const int64_t rn = r + stride;
+                    const int64_t cn = (t + 1) * stride + j;
                     if (lane_on && t + 1 < n_time && rn < n_rows) {
-                        nuh = us[rn];
-                        nul = us[n_rows + rn];
-                        nvh = us[2 * n_rows + rn];
-                        nvl = us[3 * n_rows + rn];
-                        nwh = us[4 * n_rows + rn];
-                        nwl = us[5 * n_rows + rn];
+                        nuh = us[cn];
+                        nul = us[n_rows + cn];
+                        nvh = us[2 * n_rows + cn];
+                        nvl = us[3 * n_rows + cn];
+                        nwh = us[4 * n_rows + cn];
+                        nwl = us[5 * n_rows + cn];
                     }
                 } else if (row_on) {
                     const double ud = u[r], vd = v[r], wd = w[r];
@@ -444,10 +542,16 @@ int sm_count_x()
     return n;
 }
 
+// Baseline order of an extraction: perm (null: identity) and per-source counts.
+struct Order {
+    const int32_t *perm;
+    const int32_t *n_live;
+};
+
 template <int CG, bool kSplit>
 cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                      const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
-                      double *facets, int waves, cudaStream_t st)
+                      const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
+                      float *partial, double *facets, int waves, cudaStream_t st)
 {
     const size_t smem = (size_t)kRing * kThreads * sizeof(int4) + RLF_MAX_CHAN * sizeof(float) +
                         4 * (size_t)N * N * sizeof(float);
@@ -478,7 +582,8 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
         dim3 grid(cnt, (unsigned)parts);
         kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
                                            reinterpret_cast<const float2 *>(data),
-                                           reinterpret_cast<const float2 *>(sky), table + first, N, partial);
+                                           reinterpret_cast<const float2 *>(sky), table + first, N, ord.perm,
+                                           ord.n_live + first, partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         dim3 rgrid((NN + kThreads - 1) / kThreads, cnt);
         facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
@@ -490,13 +595,13 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
 
 template <bool kSplit>
 cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                         const SrcRow *table, int32_t count, int32_t N, const float *us, float *partial,
-                         double *facets, int waves, cudaStream_t st)
+                         const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
+                         float *partial, double *facets, int waves, cudaStream_t st)
 {
-    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
-    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
-    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
-    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, partial, facets, waves, st);
+    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
+    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
+    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
+    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
 }
 
 cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
@@ -523,46 +628,81 @@ cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *da
 
 }  // namespace
 
-cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st)
+namespace {
+
+// rows are walked as [time][stride]; stride = baselines per time step when known
+int32_t row_stride(const rlf_uvw &uvw) { return uvw.n_baselines > 0 ? uvw.n_baselines : 1024; }
+
+// the order is used when the rows are exactly [time][baseline]
+bool ordered(const rlf_uvw &uvw) { return uvw.n_baselines > 0 && uvw.n_rows % uvw.n_baselines == 0; }
+
+int64_t grid_for(int64_t n, int64_t cap)
 {
-    const int64_t need = (uvw.n_rows + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)sm_count_x() * 8;
-    split_uvw_kernel<<<(int)(need < cap ? need : cap), kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, out);
-    return cudaGetLastError();
+    const int64_t need = (n + kThreads - 1) / kThreads;
+    return need < 1 ? 1 : (need < cap ? need : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_extract_prepare(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws, cudaStream_t st)
+{
+    if (p.precision == RLF_PREC_FP64) return cudaSuccess;
+    const int32_t stride = row_stride(uvw);
+    const int32_t n_b = (int64_t)stride < uvw.n_rows ? stride : (int32_t)uvw.n_rows;
+    track_extent_kernel<<<(int)grid_for(n_b, (int64_t)sm_count_x() * 8), kThreads, 0, st>>>(uvw.u, uvw.v, uvw.n_rows,
+                                                                                            n_b, ws.extent);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const bool ord = ordered(uvw);
+    if (ord) {
+        order_kernel<<<1, kOrderThreads, 0, st>>>(ws.extent, n_b, ws.order_counts, ws.perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (p.precision == RLF_PREC_MIXED_SPLIT) {
+        split_uvw_kernel<<<(int)grid_for(uvw.n_rows, (int64_t)sm_count_x() * 8), kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, stride, ord ? ws.perm : nullptr, ws.uvw_split);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, float *resid, float *partial,
-                           double *facets, cudaStream_t st)
+                           const rlf_params &p, const Workspace &ws, double *facets, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
     if (p.precision == RLF_PREC_FP64) {
         e = cudaMemsetAsync(facets, 0, (size_t)count * 4 * p.facet_n * p.facet_n * sizeof(double), st);
         if (e != cudaSuccess) return e;
+        return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
     }
     // several sources read every visibility: form D - V_sky once (one streaming pass)
-    if (p.precision != RLF_PREC_FP64 && resid && count >= 3) {
+    if (ws.resid && count >= 3) {
         const int64_t n2 = uvw.n_rows * uvw.n_chan;   // complex values
         if (n2 % 2 == 0) {
             const int64_t n4 = n2 / 2;
-            const int64_t need = (n4 + kThreads - 1) / kThreads;
-            const int64_t cap = (int64_t)sm_count_x() * 16;
-            residual_kernel<<<(int)(need < cap ? need : cap), kThreads, 0, st>>>(
+            residual_kernel<<<(int)grid_for(n4, (int64_t)sm_count_x() * 16), kThreads, 0, st>>>(
                 reinterpret_cast<const float4 *>(data), reinterpret_cast<const float4 *>(sky), n4,
-                reinterpret_cast<float4 *>(resid));
+                reinterpret_cast<float4 *>(ws.resid));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            data = resid;
+            data = ws.resid;
             sky = nullptr;
         }
     }
+    // per source, how far along the baseline order its window can be reached
+    const int32_t stride = row_stride(uvw);
+    const int32_t n_b = (int64_t)stride < uvw.n_rows ? stride : (int32_t)uvw.n_rows;
+    double s_min = ch.s[0];
+    for (int k = 1; k < ch.n; ++k) s_min = ch.s[k] < s_min ? ch.s[k] : s_min;
+    const Order ord{ordered(uvw) ? ws.perm : nullptr, ws.n_live};
+    live_count_kernel<<<count, kThreads, 0, st>>>(ws.extent, ord.perm, n_b, table, p.facet_n, s_min, ws.n_live);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int waves = p.tune_extract_waves > 0 ? p.tune_extract_waves : 2;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, partial, facets, waves, st);
-    if (p.precision == RLF_PREC_MIXED_SPLIT)
-        return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, uvw_split, partial, facets, waves,
-                                  st);
-    return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
+        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, facets,
+                                   waves, st);
+    return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, facets,
+                              waves, st);
 }
 
 }  // namespace rlf

@@ -1,4 +1,4 @@
-// Learned proposal of the likelihood sub-grid (a spec addition; no
+// Learned proposal of the likelihood sub-grid (an addition to the method; no
 // counterpart in the paper): a 8192-256-256-6 perceptron reads a facet and
 // predicts the mean and log-variance of (e1, e2, ln alpha); the fit then
 // evaluates only a 7 x 7 x 5 box of the grid around the prediction.

@@ -15,6 +15,8 @@ constexpr double kC = 299792458.0;                      // speed of light, m/s
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kArcsec = kPi / 648000.0;               // arcsec -> rad
 constexpr int kThreads = 256;                            // threads per CTA of every kernel
+constexpr int kOrderBuckets = 512;                       // extent buckets of the baseline ordering
+constexpr int kOrderThreads = 256;
 constexpr int kSkyTile = 128;                            // sources staged per shared-memory tile
 constexpr int kCellTile = 128;                           // facet cells staged per tile in the fit
 constexpr int kMaxNe = 32;                               // grid nodes per e component (estimator smem)
@@ -170,6 +172,10 @@ struct Workspace {
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
     float *resid;           // [n_rows][n_chan][2]: D - V_sky for batched extraction
     float *partial;         // [kMaxPartials][4][N*N]: per-CTA partial facets of the extraction
+    float *extent;          // [n_rows] per baseline: min over time of max(|u|, |v|), rounded down
+    int32_t *perm;          // [n_rows] baselines in increasing order of extent (first n_baselines used)
+    int32_t *n_live;        // [n_src] per source of an extraction batch: baselines to walk
+    int32_t *order_counts;  // [kOrderBuckets][kOrderThreads] scratch of the ordering
     size_t bytes;
 };
 
@@ -185,11 +191,13 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st,
                        int32_t blocks_per_sm = 0);
-cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
+// Per call, before the extraction batches: each baseline's smallest uv extent over
+// time, the baselines ordered by it, and (split-phase mode) the split baselines in
+// that order.
+cudaError_t launch_extract_prepare(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws, cudaStream_t st);
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
-                           const rlf_params &p, const float *uvw_split, float *resid, float *partial,
-                           double *facets, cudaStream_t st);
+                           const rlf_params &p, const Workspace &ws, double *facets, cudaStream_t st);
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
                        int32_t out_offset, cudaStream_t st);
