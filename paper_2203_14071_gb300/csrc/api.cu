@@ -365,7 +365,17 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
         e = launch_prepare(src, first, cnt, e1c, e2c, out.e1 + first, out.e2 + first, out.flag + first,
                            p.update_mode, e1c, e2c, p, ws.upd, ws.status, st);
         if (e != cudaSuccess) break;
-        e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
+        if (cnt == n) {
+            // one chunk holds every source and the sky model was made from scratch at the
+            // start of this call: the updated model, sum of old terms plus every (new - old),
+            // is the model of the committed shapes, formed directly with one term per source
+            e = launch_prepare(src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
+                               ws.status, st);
+            if (e == cudaSuccess)
+                e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
+        } else {
+            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
+        }
     }
     return e;
 }

@@ -198,6 +198,15 @@ __device__ __forceinline__ void cell_floor2(float uh, float vh, float sdu, int &
     iv = __float_as_int(mv_) - 0x4B400000;
 }
 
+// A 16-byte shared-memory store under a predicate: the append of a finished run
+// costs the same few instructions whether or not the lane appends, with no branch
+// for the warp to diverge on.
+__device__ __forceinline__ void st_shared_v4_if(uint32_t addr, bool p, int a, int b, int c, int d)
+{
+    asm volatile("{ .reg .pred q; setp.ne.b32 q, %0, 0; @q st.shared.v4.b32 [%1], {%2, %3, %4, %5}; }"
+                 :: "r"((int)p), "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
 // kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
 template <int CG, bool kUniform, bool kSplit, bool kResid>
 __global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
@@ -240,6 +249,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     const double du = S.du;
     constexpr float kTwoPi = 6.28318530717958647692f;
     int cnt = 0;                                   // entries in this lane's ring
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
 
     auto append = [&](int cell, int k, int n, float re, float im) {
         ring[cnt * kThreads + tid] = make_int4(cell | (k << 12), n, __float_as_int(re), __float_as_int(im));
@@ -346,7 +356,11 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                 const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
                 float P = 0.0f, E = 0.0f;
                 if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
-                float sn = 0.0f, cs = 1.0f, sd = 0.0f, cd = 1.0f;
+                // uniform channels: the phase of channel c is frac(f0 + c fd) cycles, each
+                // channel's sincos independent of the others (f0 + c fd in FP32 is within
+                // 2^-24 * CG cycles of the exact value)
+                float sn = 0.0f, cs = 1.0f;
+                float f0_keep = 0.0f, fd_keep = 0.0f;
                 if (kUniform) {
                     float f0, fd = 0.0f;
                     if (kSplit) {
@@ -360,12 +374,17 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                             fd = (float)(td - rint(td));
                         }
                     }
-                    __sincosf(f0 * kTwoPi, &sn, &cs);
-                    if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
+                    f0_keep = f0;
+                    fd_keep = fd;
                 }
 #pragma unroll
                 for (int c = 0; c < CG; ++c) {
                     const int k = k0 + c;
+                    if (kUniform) {
+                        float fk = fmaf((float)c, fd_keep, f0_keep);
+                        fk -= rintf(fk);
+                        __sincosf(fk * kTwoPi, &sn, &cs);
+                    }
                     if (!kUniform) {
                         const int kk = min(k, C - 1);
                         float f;
@@ -414,17 +433,19 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     xr = fmaf(fspec[c], rq * rq * rq, xr);
                     // a run ends when the cell changes; runs of cell -1 are dropped
                     const bool change = cell != run_cell[c];
-                    if (change && run_cell[c] >= 0) append(run_cell[c], k0 + c, run_n[c], run_re[c], run_im[c]);
+                    {
+                        const bool app = change && run_cell[c] >= 0;
+                        st_shared_v4_if(ring_s + (uint32_t)(cnt * kThreads + tid) * 16u, app,
+                                        run_cell[c] | ((k0 + c) << 12), run_n[c], __float_as_int(run_re[c]),
+                                        __float_as_int(run_im[c]));
+                        cnt += app ? 1 : 0;
+                    }
                     const float keep = change ? 0.0f : 1.0f;
                     run_re[c] = fmaf(run_re[c], keep, xr);
                     run_im[c] = fmaf(run_im[c], keep, xi);
                     run_n[c] = change ? 1 : run_n[c] + 1;
                     run_cell[c] = cell;
-                    if (kUniform && c + 1 < CG) {
-                        const float cn = cs * cd - sn * sd;
-                        sn = fmaf(cs, sd, sn * cd);
-                        cs = cn;
-                    }
+
                 }
             }
             if (__any_sync(0xffffffffu, cnt > kRing - CG)) {

@@ -225,8 +225,8 @@ def test_run_small_pipeline(rlf, prec, chunk, update_mode):
     torch = _torch()
     c = small_case(True)
     p_or = c.oracle_params(chunk=chunk, update_mode=update_mode)
-    est = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m, c.cat.flux_jy,
-                          None, p_or)
+    est, sky_ref = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m,
+                                   c.cat.flux_jy, None, p_or, want_sky=True)
     obs, cat = cases.to_device(c)
     p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, chunk=chunk,
                            update_mode=update_mode)
@@ -240,6 +240,13 @@ def test_run_small_pipeline(rlf, prec, chunk, update_mode):
     for i in range(c.cat.n_src):
         assert cases.est_matches(got, i, est[i]) <= 1e-4, (i, got["e1"][i], est[i, oracle.E1], got["e2"][i],
                                                            est[i, oracle.E2])
+    # the sky model after the chain's updates (Sec. 3.1).  The two sides' fitted shapes may
+    # differ by up to 1e-4 and one term moves by at most about 1.5 S per unit of e, so the
+    # bound is 2e-5 sum S (FP32 model) + 1.5e-4 sum S; a missed or wrong update moves terms
+    # by ~0.1 S
+    g = sky.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    dv = np.abs(g[..., 0] + 1j * g[..., 1] - sky_ref)
+    assert dv.max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum(), dv.max() / c.cat.flux_jy.sum()
 
 
 def test_invalid_and_empty_sources_are_flagged(rlf):
