@@ -53,8 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
-    ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update"],
-                    help="run only this entry point --steps times after one warm-up (for ncu captures)")
+    ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update", "mlp"],
+                    help="run only this entry point --steps times after one warm-up, or only the "
+                         "learned-proposal comparison (for ncu captures)")
+    ap.add_argument("--mlp-steps", type=int, default=2000, help="training steps of the learned proposal")
     return ap.parse_args()
 
 
@@ -347,6 +349,10 @@ def main():
     n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
     n_vis = R * C
 
+    if args.only == "mlp":
+        print(json.dumps({"only": "mlp", "mlp_proposal": mlp_line(rlf, torch, dev, W, stream,
+                                                                    train_steps=args.mlp_steps)}))
+        return
     if args.only:
         profile_only(args, rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, n_src)
         return
@@ -422,7 +428,7 @@ def main():
     if graph is not None:
         graph.close()
     if not args.no_mlp and world == 1:
-        line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream)
+        line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream, train_steps=args.mlp_steps)
     if not args.no_batched and world == 1:
         del ws, data, sky
         torch.cuda.empty_cache()
@@ -483,6 +489,7 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     ge = -params.e_max + np.arange(params.n_e) * (2.0 * params.e_max / (params.n_e - 1))
     n_valid = int((np.add.outer(ge ** 2, ge ** 2) < 1.0).sum()) * params.n_alpha
     fit_evals = float(n_cells.sum().item()) * n_valid
+    in_window = float(facets.view(n_src, 4, nn)[:, 2, :].sum().item())
     upd_ms = timed(lambda: rlf.sky_update(obs, cat, 0, n_src, out.e1, out.e2, None, params, sky, ws, stream))
     chunk = params.chunk if params.chunk > 0 else n_src
     n_chunks = (n_src + chunk - 1) // chunk
@@ -499,7 +506,8 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
                 + (1 if params.precision == 2 else 0) + n_chunks * per_chunk)
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
             "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches,
-            "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item())}
+            "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item()),
+            "in_window_pairs": in_window}
 
 
 # Algorithmic operation counts per unit of work: FP32 ops and MUFU ops per unit, plus
@@ -510,6 +518,32 @@ OPS = {
     "extract": {"fp32": 16.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gpair/s"},
     "fit": {"fp32": 6.0, "mufu": 1.0, "fp32_rs": 0.0, "mufu_rs": 0.0, "unit": "Geval/s"},
 }
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
+# files hash to the recorded value; otherwise the bench reports null.
+TRAFFIC = {
+    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "79876c13cc0322b7", 981.60e6),
+    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "35ad67cfd86f9797", 349.49e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "1b544397b66df3cc", 17.19e6),
+}
+
+
+def source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2203_14071_gb300", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(name):
+    if name not in TRAFFIC:
+        return None
+    files, digest, nbytes = TRAFFIC[name]
+    return nbytes if source_hash(files) == digest else None
 
 
 def roofline_one(name, t_ms, units, row_src, peaks):
@@ -524,15 +558,20 @@ def roofline_one(name, t_ms, units, row_src, peaks):
     t = t_ms * 1e-3
     return {"kernel": name, "bound": "alu", "limiting_unit": "fp32" if t_fp32 >= t_mufu else "mufu",
             "unit": o["unit"], "achieved": units / t / 1e9, "peak": units / t_min / 1e9, "frac": t_min / t,
-            "units_per_launch": units, "traffic": None,
+            "units_per_launch": units, "traffic": traffic_of(name),
             "peak_basis": "measured FP32 %.3g FMA/s and MUFU %.3g op/s (rlf_peaks_measure)" % (fp32_rate, mufu_rate)}
 
 
 def roofline(comp, peaks, params, n_vis, n_src, R, C):
     ph = comp["phases_ms"]
     out = {}
-    for name in ("sky_model", "update", "extract"):
+    for name in ("sky_model", "update"):
         out[name] = roofline_one(name, ph[name], float(n_vis) * n_src, float(R) * n_src, peaks)
+    # extraction: the algorithmic work is the terms that enter a facet (visibility-source pairs
+    # inside the source's window); pairs outside need no arithmetic, and the (row, source)
+    # phase work is counted in the same proportion
+    frac_in = comp["in_window_pairs"] / (float(n_vis) * n_src)
+    out["extract"] = roofline_one("extract", ph["extract"], comp["in_window_pairs"], float(R) * n_src * frac_in, peaks)
     out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks)
     dom = max(ph, key=ph.get)
     return out[dom], out

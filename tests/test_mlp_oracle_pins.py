@@ -90,3 +90,22 @@ def test_proposal_box_and_fallback_rules():
     assert mlp.on_inner_boundary(flat(12, 6, 9), (9, 0, 7), box, ne, na)       # upper e2 face
     assert mlp.on_inner_boundary(flat(12, 3, 11), (9, 0, 7), box, ne, na)      # upper alpha face
     assert not mlp.on_inner_boundary(flat(12, 3, 9), (9, 0, 7), box, ne, na)
+
+
+def test_simulated_noise_has_the_cell_variance():
+    # the noise of a cell mean of n_c visibilities with per-component sigma, over S:
+    # variance sigma^2 / (S^2 n_c) on Re and Im, zero mean (Sec. 2.4 weights w_c = n_c / sigma^2)
+    N, du, sig_rel = 4, 4000.0, 0.5
+    counts = np.array([1, 4, 9, 16] + [0] * (N * N - 4), dtype=float)
+    sbar = np.where(counts > 0, 1.0, 0.0)
+    rng = np.random.default_rng(3)
+    draws = np.stack([mlp.simulate(counts, sbar, du, 0.0, 0.0, 1.0, sig_rel, rng.standard_normal((2, N * N)), N=N)
+                      for _ in range(20000)])
+    M = np.array([oracle.shape((c % N - N // 2 + 0.5) * du, (c // N - N // 2 + 0.5) * du, mlp.ARC, 0.0, 0.0)
+                  for c in range(4)])
+    for c in range(4):
+        want = sig_rel ** 2 / counts[c]
+        for part, mean in ((draws[:, c], M[c]), (draws[:, N * N + c], 0.0)):
+            assert abs(part.mean() - mean) < 5 * math.sqrt(want / 20000)
+            assert abs(part.var() / want - 1.0) < 0.05
+    assert np.all(draws[:, 4:N * N] == 0.0)
