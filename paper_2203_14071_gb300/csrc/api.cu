@@ -119,8 +119,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const bool mlp = fit && p.facet_n * p.facet_n * 2 == kMlpIn;
     const size_t o_mx = take(mlp ? cap * kMlpIn * sizeof(__half) : 0);
     const size_t o_ms = take(mlp ? mlp_scratch(nullptr, (int32_t)cap).bytes : 0);
-    const size_t o_ga = take(fit ? cap * ng * sizeof(double) : 0);
-    const size_t o_gb = take(fit ? cap * ng * sizeof(double) : 0);
+    const size_t o_ga = take(fit ? kMaxFitParts * cap * ng * sizeof(double) : 0);
+    const size_t o_gb = take(fit ? kMaxFitParts * cap * ng * sizeof(double) : 0);
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
@@ -152,6 +152,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->cc = reinterpret_cast<double *>(b + o_cc);
         ws->ga = reinterpret_cast<double *>(b + o_ga);
         ws->gb = reinterpret_cast<double *>(b + o_gb);
+        ws->part_stride = cap * ng;
         ws->gl = reinterpret_cast<double *>(b + o_gl);
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
         ws->facets = reinterpret_cast<double *>(b + o_fac);

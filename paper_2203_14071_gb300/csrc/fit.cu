@@ -116,11 +116,13 @@ __device__ __forceinline__ double grid_alpha(const GridConst &g, int k)
 }
 
 // One work item of the likelihood grid: facet s, threads over (e point, alpha group)
-// pairs tile * kThreads .. tile * kThreads + kThreads - 1.  Writes a, b in FP64.
+// pairs tile * kThreads .. tile * kThreads + kThreads - 1, over part `part` of
+// `n_parts` equal ranges of the facet's cells.  Writes the part's a, b sums in FP64
+// to ga, gb (the caller offsets them to the part's slice).
 template <typename T, int AG>
-__device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const int32_t *__restrict__ ncell,
-                          const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst &gc,
-                          double *__restrict__ ga, double *__restrict__ gb)
+__device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__restrict__ cells,
+                          const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table, size_t plane,
+                          int32_t NN, const GridConst &gc, double *__restrict__ ga, double *__restrict__ gb)
 {
     __shared__ T sm[5][kCellTile];
     const int pair = tile * kThreads + threadIdx.x;
@@ -172,13 +174,27 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
             calpha[j] = T(0);
         }
     }
+    // FP64 path: FP64 accumulators; FP32 path: the 128-cell tile sums are added to
+    // float pairs (hi + lo, exact two-sum), about 48 significant bits, at FP32 speed
     double da[AG], db[AG];
+    float ah[AG], al[AG], bh[AG], bl[AG];
 #pragma unroll
-    for (int j = 0; j < AG; ++j) da[j] = db[j] = 0.0;
+    for (int j = 0; j < AG; ++j) {
+        da[j] = db[j] = 0.0;
+        ah[j] = al[j] = bh[j] = bl[j] = 0.0f;
+    }
+    auto ff_add = [](float &hi, float &lo, float x) {
+        float sum, err;
+        two_sum(hi, x, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, err);
+    };
 
-    const int nc = ncell[s];
+    const int nc_all = ncell[s];
+    const int c_begin = (int)((int64_t)nc_all * part / n_parts);
+    const int nc = (int)((int64_t)nc_all * (part + 1) / n_parts);
     const T *cu = cells + (size_t)s * NN;
-    for (int c0 = 0; c0 < nc; c0 += kCellTile) {
+    for (int c0 = c_begin; c0 < nc; c0 += kCellTile) {
         const int nt = min(kCellTile, nc - c0);
         __syncthreads();
         for (int j = threadIdx.x; j < nt; j += kThreads) {
@@ -214,10 +230,10 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
                 float a0, a1, b0, b1;
                 up2(pa2[j], a0, a1);
                 up2(pb2[j], b0, b1);
-                da[2 * j] += (double)a0;
-                da[2 * j + 1] += (double)a1;
-                db[2 * j] += (double)b0;
-                db[2 * j + 1] += (double)b1;
+                ff_add(ah[2 * j], al[2 * j], a0);
+                ff_add(ah[2 * j + 1], al[2 * j + 1], a1);
+                ff_add(bh[2 * j], bl[2 * j], b0);
+                ff_add(bh[2 * j + 1], bl[2 * j + 1], b1);
             }
         } else {
             T pa[AG], pb[AG];
@@ -243,9 +259,21 @@ __device__ void grid_tile(int s, int tile, const T *__restrict__ cells, const in
             }
 #pragma unroll
             for (int j = 0; j < AG; ++j) {
-                da[j] += (double)pa[j];
-                db[j] += (double)pb[j];
+                if constexpr (std::is_same<T, float>::value) {
+                    ff_add(ah[j], al[j], pa[j]);
+                    ff_add(bh[j], bl[j], pb[j]);
+                } else {
+                    da[j] += (double)pa[j];
+                    db[j] += (double)pb[j];
+                }
             }
+        }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+        for (int j = 0; j < AG; ++j) {
+            da[j] = (double)ah[j] + (double)al[j];
+            db[j] = (double)bh[j] + (double)bl[j];
         }
     }
     if (e_idx < ne2) {
@@ -319,8 +347,23 @@ __device__ double flux_marginal(double a, double b, double cc, int flux_prior)
     return -0.5 * cc + b * b / (2.0 * a) + 0.5 * log(kPi / (2.0 * a)) + log(erfc(x));
 }
 
-// Estimate of facet s from its complete a, b grid (block-wide, FP64).
-__device__ void estimate_source(int s, const double *__restrict__ ga, const double *__restrict__ gb,
+// The same with the logarithms and error functions, whose values are O(1), in FP32:
+// absolute error ~1e-6 in ln L (far below the FP32 model's ~1e-7 b^2/a); the terms
+// that cancel at high SNR, -C/2 + b^2/(2a), stay FP64.  Used by the mixed modes,
+// where the FP64 transcendentals of 8820 grid points in one CTA dominated the
+// estimate's time.
+__device__ double flux_marginal_mixed(double a, double b, double cc, int flux_prior)
+{
+    const float lg = 0.5f * logf((float)(kPi / (2.0 * a)));
+    if (flux_prior == 1) return -0.5 * cc + b * b / (2.0 * a) + (double)(lg + 0.5f * 1.38629436111989061883f);
+    const float x = (float)(-b) * rsqrtf((float)(2.0 * a));
+    if (x > 0.0f) return -0.5 * cc + (double)(lg + logf(erfcxf(x)));
+    return -0.5 * cc + b * b / (2.0 * a) + (double)(lg + logf(erfcf(x)));
+}
+
+// Estimate of facet s from its complete a, b grid (block-wide, FP64; with `mixed`
+// the logarithms, error functions and exponentials in FP32).
+__device__ void estimate_source(bool mixed, int s, const double *__restrict__ ga, const double *__restrict__ gb,
                                 double *__restrict__ gl, const int32_t *__restrict__ ncell,
                                 const double *__restrict__ ccv, const SrcRow *__restrict__ table,
                                 const GridConst &gc, const rlf_fit_out &out, int32_t out_offset,
@@ -366,7 +409,7 @@ __device__ void estimate_source(int s, const double *__restrict__ ga, const doub
             in_box = d1 >= 0 && d1 < kBoxE && d2 >= 0 && d2 < kBoxE && dk >= 0 && dk < kBoxA;
         }
         if (in_box && nc > 0 && e1 * e1 + e2 * e2 < 1.0) {
-            v = flux_marginal(a[g], b[g], cc, gc.flux_prior);
+            v = mixed ? flux_marginal_mixed(a[g], b[g], cc, gc.flux_prior) : flux_marginal(a[g], b[g], cc, gc.flux_prior);
             if (!isfinite(v)) bad_num = true;
         }
         lg[g] = v;
@@ -382,7 +425,7 @@ __device__ void estimate_source(int s, const double *__restrict__ ga, const doub
         for (int k = 0; k < na; ++k) {
             const double v = lg[(size_t)e * na + k];
             if (v == -INFINITY) continue;
-            const double t = qp[k] * exp(v - lmax);
+            const double t = qp[k] * (mixed ? (double)expf((float)(v - lmax)) : exp(v - lmax));
             sL += t;
             sA += t * alph[k];
         }
@@ -488,39 +531,66 @@ __global__ void lpt_order_kernel(const int32_t *__restrict__ ncell, int32_t coun
 }
 
 // Persistent likelihood fit: every CTA takes work items (facet in LPT order,
-// tile of grid pairs) from an atomic counter until none is left; the CTA that
-// completes a facet's last tile (per-facet atomic counter after a fence) runs
-// that facet's estimate.  Nothing waits on another CTA.
+// tile of grid pairs, part of the facet's cells) from an atomic counter until none
+// is left; the CTA that completes a facet's last item (per-facet atomic counter
+// after a fence) adds the parts' sums in part order and runs that facet's
+// estimate.  Nothing waits on another CTA.  When the launch has fewer (facet, tile)
+// items than CTAs (few facets, or the 7 x 7 x 5 sub-box), each facet's cells are
+// split into up to kMaxFitParts parts so that every CTA has work; the number of
+// facets may be known only on the device (refit list), so the split is chosen here.
 template <typename T, int AG>
 __global__ void __launch_bounds__(kThreads, 3)
 fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
                       const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
                       int32_t count, const int32_t *__restrict__ count_dev, const int32_t *__restrict__ order,
                       int32_t *__restrict__ counters, const GridConst gc, double *__restrict__ ga,
-                      double *__restrict__ gb, double *__restrict__ gl, const double *__restrict__ ccv,
-                      rlf_fit_out out, int32_t out_offset, int32_t *__restrict__ status,
-                      int32_t *__restrict__ map_out)
+                      double *__restrict__ gb, size_t part_stride, double *__restrict__ gl,
+                      const double *__restrict__ ccv, rlf_fit_out out, int32_t out_offset,
+                      int32_t *__restrict__ status, int32_t *__restrict__ map_out)
 {
     __shared__ int s_item, s_last;
     int32_t *item_counter = counters;
     int32_t *src_done = counters + 1;
-    // the number of facets may be known only on the device (refit list)
-    const int total = (count_dev ? *count_dev : count) * tiles_per_src;
+    const int n_src = count_dev ? *count_dev : count;
+    const int64_t pairs_items = (int64_t)n_src * tiles_per_src;
+    int n_parts = pairs_items > 0 ? (int)((gridDim.x + pairs_items - 1) / pairs_items) : 1;
+    n_parts = n_parts < 1 ? 1 : (n_parts > kMaxFitParts ? kMaxFitParts : n_parts);
+    const int per_src = tiles_per_src * n_parts;
+    const int total = n_src * per_src;
+    const size_t ng = (size_t)gc.n_e * gc.n_e * gc.n_alpha;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= total) break;
-        const int s = order[item / tiles_per_src];
-        const int tile = item % tiles_per_src;
-        grid_tile<T, AG>(s, tile, cells, ncell, table, plane, NN, gc, ga, gb);
+        const int s = order[item / per_src];
+        const int rem = item % per_src;
+        const int tile = rem / n_parts, part = rem % n_parts;
+        grid_tile<T, AG>(s, tile, part, n_parts, cells, ncell, table, plane, NN, gc, ga + part * part_stride,
+                         gb + part * part_stride);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&src_done[s], 1) == tiles_per_src - 1;
+        if (threadIdx.x == 0) s_last = atomicAdd(&src_done[s], 1) == per_src - 1;
         __syncthreads();
         if (s_last) {
             __threadfence();
-            estimate_source(s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset, status, map_out);
+            if (n_parts > 1) {
+                // parts 1.. into part 0, in part order (entries a part did not write are
+                // outside the sub-box and never read)
+                double *a0 = ga + (size_t)s * ng, *b0 = gb + (size_t)s * ng;
+                for (size_t g = threadIdx.x; g < ng; g += kThreads) {
+                    double a = a0[g], b = b0[g];
+                    for (int q = 1; q < n_parts; ++q) {
+                        a += a0[q * part_stride + g];
+                        b += b0[q * part_stride + g];
+                    }
+                    a0[g] = a;
+                    b0[g] = b;
+                }
+                __syncthreads();
+            }
+            estimate_source(std::is_same<T, float>::value, s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset,
+                            status, map_out);
         }
         __syncthreads();
     }
@@ -568,9 +638,8 @@ cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t items = (int64_t)count * tiles;
-    int64_t grid = (int64_t)sms * per_sm;
-    if (grid > items) grid = items;
+    // one full wave: with fewer (facet, tile) items than CTAs the kernel splits cells
+    const int64_t grid = (int64_t)sms * per_sm;
     if ((e = cudaMemsetAsync(ws.counters, 0, (size_t)(count + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
     if (!order) {
         lpt_order_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.ncell, count, ws.order);
@@ -578,8 +647,8 @@ cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane,
         order = ws.order;
     }
     kern<<<(int)grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, count_dev, order,
-                                         ws.counters, gc, ws.ga, ws.gb, ws.gl, ws.cc, out, out_offset, ws.status,
-                                         map_out);
+                                         ws.counters, gc, ws.ga, ws.gb, ws.part_stride, ws.gl, ws.cc, out,
+                                         out_offset, ws.status, map_out);
     return cudaGetLastError();
 }
 
@@ -666,9 +735,10 @@ cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t co
     if (e == cudaSuccess) e = mlp_forward(W, x, count, sc, st);
     if (e == cudaSuccess) e = mlp_propose(sc.o, count, gc, ws.box, ws.wide, st);
     // the likelihood on every facet's sub-box
+    // one scalelength node per thread: 7 x 7 x 5 = 245 of the CTA's 256 threads busy
     gc.box = ws.box;
     if (e == cudaSuccess)
-        e = launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, 0,
+        e = launch_persistent<float, 1>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, 0,
                                         ws.map_index, st);
     // the facets that need the full grid, in one more persistent launch
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.refit, 0, sizeof(int32_t), st);

@@ -15,6 +15,7 @@ constexpr double kC = 299792458.0;                      // speed of light, m/s
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kArcsec = kPi / 648000.0;               // arcsec -> rad
 constexpr int kThreads = 256;                            // threads per CTA of every kernel
+constexpr int kMaxFitParts = 4;                          // cell parts per facet in a persistent fit
 constexpr int kOrderBuckets = 512;                       // extent buckets of the baseline ordering
 constexpr int kOrderThreads = 256;
 constexpr int kSkyTile = 128;                            // sources staged per shared-memory tile
@@ -166,7 +167,9 @@ struct Workspace {
     void *mlp_x;            // [cap][8192] f16 network inputs
     void *mlp_scratch;      // network activations for cap facets
     double *cc;             // [cap]
-    double *ga, *gb, *gl;   // [cap][n_e^2][n_alpha]
+    double *ga, *gb;        // [kMaxFitParts][cap][n_e^2][n_alpha] per-part likelihood sums
+    size_t part_stride;     // cap * n_e^2 * n_alpha
+    double *gl;             // [cap][n_e^2][n_alpha]
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
