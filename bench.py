@@ -124,6 +124,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (every rank gets it); the job's clock is the slowest replica."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n_src: int, world: int, ms: float) -> float:
+    """Fits per second of the whole job: every replica fits n_src sources per step."""
+    return n_src * world / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------------------------
 # CPU arm: the FP64 oracle on a bounded sample
 
@@ -392,10 +408,7 @@ def main():
     # per-kernel timing of the dominant phases (same stream, CUDA events), and e2e
     comp = component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, args, n_src)
     clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     e2e = None if args.no_e2e else e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, args)
     res = out.numpy()
@@ -404,7 +417,7 @@ def main():
             dist.destroy_process_group()
         return
     peaks = rlf.peaks_measure(stream)
-    value = n_src * world / (ms * 1e-3)
+    value = whole_job_value(n_src, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
