@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="sources per extract/fit/update step (0: all)")
     ap.add_argument("--precision", default="split", choices=["split", "mixed", "fp64"])
     ap.add_argument("--update-mode", type=int, default=1)
+    ap.add_argument("--profile", default="exponential", choices=["exponential", "gaussian"],
+                    help="source brightness profile (data and fit)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time rlf_run calls instead of the captured graph")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
@@ -228,7 +230,8 @@ def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
     cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
     truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
     params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=args.chunk,
-                                precision=prec, update_mode=args.update_mode)
+                                precision=prec, update_mode=args.update_mode,
+                                profile=rlf.PROFILE_GAUSSIAN if args.profile == "gaussian" else 0)
     ws = rlf.alloc_workspace(R, C, n, params, rlf.WS_RUN, device=dev)
     data = torch.empty(R * C * 2, dtype=torch.float32, device=dev)
     rlf.sky_model(obs, truth, params, data, ws, stream)
@@ -426,7 +429,8 @@ def main():
                    "n_time": obs_np.n_time, "n_chan": C, "n_vis": n_vis, "n_src": n_src,
                    "facet_n": params.facet_n, "grid": [params.n_e, params.n_e, params.n_alpha],
                    "chunk": args.chunk if args.chunk > 0 else n_src, "precision": args.precision,
-                   "update_mode": args.update_mode, "l2": "inputs larger than L2 (no flush)"},
+                   "update_mode": args.update_mode, "profile": args.profile,
+                   "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
         "phases_ms": comp["phases_ms"],
         "mean_cells_per_facet": comp["mean_cells_per_facet"],

@@ -62,6 +62,14 @@ enum {
                               at its FP32 rate instead of its much lower FP64 rate */
 };
 
+/* source brightness profile (Sec. 2.2 and its footnote); alpha keeps its meaning (grid,
+   Eq. 4 prior, facet cell size) under both */
+enum {
+    RLF_PROFILE_EXPONENTIAL = 0, /* I(r) ~ exp(-r / alpha): (1 + 4 pi^2 alpha^2 |A^-T k|^2)^{-3/2} */
+    RLF_PROFILE_GAUSSIAN = 1     /* I(r) ~ exp(-r^2 / (2 sigma^2)) of the same FWHM, sigma = alpha
+                                    sqrt(ln 2 / 2): exp(-2 pi^2 sigma^2 |A^-T k|^2) */
+};
+
 /* bits of the per-source fit flag */
 enum {
     RLF_FLAG_BAD = 1,      /* Sec. 4.1 cut: sigma(e_i) or sqrt(det cov) not above its minimum */
@@ -134,7 +142,8 @@ typedef struct {
     int32_t tune_fit_blocks;    /* CTAs per SM of the persistent fit (default: all that fit) */
     int32_t tune_extract_waves; /* CTA waves per extraction batch (default 2) */
     int32_t tune_sky_blocks;    /* CTAs per SM of the sky-model kernels (default 8) */
-    int32_t reserved;
+    int32_t profile;         /* source brightness profile: RLF_PROFILE_EXPONENTIAL (Eq. 1, the
+                                default) or RLF_PROFILE_GAUSSIAN (footnote to Sec. 2.2) */
 } rlf_params;
 
 /* Per-source results, each a device array of `count` entries. */

@@ -60,14 +60,14 @@ class Params(ctypes.Structure):
                 ("thresh_frac", ctypes.c_double), ("var_sigma_min", ctypes.c_double),
                 ("var_det_min", ctypes.c_double), ("facet_n", ctypes.c_int32), ("n_e", ctypes.c_int32),
                 ("n_alpha", ctypes.c_int32), ("flux_prior", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("update_mode", ctypes.c_int32)]
+                ("update_mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def default_params(**kw) -> Params:
     p = Params(add=-0.93, esp=0.33, psf_nat=38.0, beta=-0.7, nu_ref_hz=1.0e9, sigma_jy=1e-6,
                e_max=0.8, r_min_arcsec=0.3, r_max_arcsec=3.5, r_std=0.3136,
                thresh_frac=0.05, var_sigma_min=5e-3, var_det_min=5e-5,
-               facet_n=64, n_e=21, n_alpha=20, flux_prior=0, chunk=0, update_mode=0)
+               facet_n=64, n_e=21, n_alpha=20, flux_prior=0, chunk=0, update_mode=0, profile=0, pad=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -85,15 +85,15 @@ def lib():
             L.rlfo_alpha_med.restype = d
             L.rlfo_alpha_med.argtypes = [d, d, d]
             L.rlfo_shape.restype = d
-            L.rlfo_shape.argtypes = [d, d, d, d, d]
+            L.rlfo_shape.argtypes = [d, d, d, d, d, ctypes.c_int]
             L.rlfo_model_vis.restype = None
-            L.rlfo_model_vis.argtypes = [d] * 12 + [vp, vp]
+            L.rlfo_model_vis.argtypes = [d] * 12 + [ctypes.c_int, vp, vp]
             L.rlfo_sky_model.restype = None
             L.rlfo_sky_model.argtypes = [i64, i32, vp, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
-                                         d, d, vp, vp, ctypes.c_int]
+                                         d, d, ctypes.c_int, vp, vp, ctypes.c_int]
             L.rlfo_extract_facet.restype = None
-            L.rlfo_extract_facet.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp] + [d] * 9 + \
-                                            [i32, vp, vp]
+            L.rlfo_extract_facet.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp] + [d] * 8 + \
+                                            [ctypes.c_int, d, i32, vp, vp]
             L.rlfo_flux_marginal.restype = d
             L.rlfo_flux_marginal.argtypes = [d, d, d, ctypes.c_int]
             L.rlfo_grid_e.restype = d
@@ -136,20 +136,21 @@ def alpha_med(flux_jy: float, add: float = -0.93, esp: float = 0.33) -> float:
     return lib().rlfo_alpha_med(flux_jy, add, esp)
 
 
-def shape(ku, kv, alpha_rad, e1, e2) -> float:
-    return lib().rlfo_shape(ku, kv, alpha_rad, e1, e2)
+def shape(ku, kv, alpha_rad, e1, e2, profile: int = 0) -> float:
+    """Eq. 1 brightness factor; profile 0 exponential, 1 Gaussian of equal FWHM."""
+    return lib().rlfo_shape(ku, kv, alpha_rad, e1, e2, profile)
 
 
-def model_vis(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.0e9) -> complex:
+def model_vis(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.0e9, profile: int = 0) -> complex:
     """Eq. 1 for one source at one baseline (metres) and frequency (Hz)."""
     re, im = ctypes.c_double(), ctypes.c_double()
-    lib().rlfo_model_vis(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta, nu_ref,
+    lib().rlfo_model_vis(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta, nu_ref, profile,
                          ctypes.byref(re), ctypes.byref(im))
     return complex(re.value, im.value)
 
 
 def sky_model(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.0e9,
-              rows=None, with_abs=False, n_threads=0):
+              rows=None, with_abs=False, n_threads=0, profile: int = 0):
     """Sky model (Sec. 2.2) as complex128 [n_out, n_chan]; optionally also sum |term|."""
     u, v, w, freq = _f64(u), _f64(v), _f64(w), _f64(freq)
     l, m, flux, alpha_rad, e1, e2 = map(_f64, (l, m, flux, alpha_rad, e1, e2))
@@ -160,7 +161,7 @@ def sky_model(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.
     ab = np.zeros((n_out, n_chan), dtype=np.float64) if with_abs else None
     lib().rlfo_sky_model(n_rows, n_chan, _p(u), _p(v), _p(w), _p(freq), _p(rows_a), n_out,
                          l.shape[0], _p(l), _p(m), _p(flux), _p(alpha_rad), _p(e1), _p(e2),
-                         beta, nu_ref, _p(out), _p(ab), n_threads)
+                         beta, nu_ref, profile, _p(out), _p(ab), n_threads)
     vis = out[..., 0] + 1j * out[..., 1]
     return (vis, ab) if with_abs else vis
 
@@ -187,7 +188,7 @@ def extract_facet(u, v, w, freq, data, sky, l, m, flux, alpha_sky_rad, e1_cur, e
     ab = np.zeros(N * N, dtype=np.float64) if with_abs else None
     lib().rlfo_extract_facet(u.shape[0], freq.shape[0], _p(u), _p(v), _p(w), _p(freq), _p(data),
                              _p(sky_f), _p(sky_d), l, m, flux, alpha_sky_rad, e1_cur, e2_cur,
-                             params.beta, params.nu_ref_hz, du, N, _p(acc), _p(ab))
+                             params.beta, params.nu_ref_hz, params.profile, du, N, _p(acc), _p(ab))
     return (acc, ab) if with_abs else acc
 
 

@@ -89,23 +89,26 @@ def adam(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def shape_factor(cu, cv, du, e1, e2, alpha_rad):
-    """Eq. 1 brightness factor at cell centres (cu, cv in units of du)."""
+def shape_factor(cu, cv, du, e1, e2, alpha_rad, profile=0):
+    """Eq. 1 brightness factor at cell centres (cu, cv in units of du); profile 1 is the
+    Gaussian of the same FWHM, sigma = alpha sqrt(ln 2 / 2) (footnote to Sec. 2.2)."""
     A = np.array([[1 - e1, -e2], [-e2, 1 + e1]])
     T = np.linalg.inv(A).T
     ku, kv = cu * du, cv * du
     x = T[0, 0] * ku + T[0, 1] * kv
     y = T[1, 0] * ku + T[1, 1] * kv
+    if profile == 1:
+        return np.exp(-2.0 * math.pi ** 2 * alpha_rad ** 2 * math.log(2.0) / 2.0 * (x * x + y * y))
     return (1.0 + 4.0 * math.pi ** 2 * alpha_rad ** 2 * (x * x + y * y)) ** -1.5
 
 
-def simulate(counts, sbar, du, e1, e2, alpha_arcsec, sigma_rel, z, N: int = 64) -> np.ndarray:
+def simulate(counts, sbar, du, e1, e2, alpha_arcsec, sigma_rel, z, N: int = 64, profile: int = 0) -> np.ndarray:
     """One simulated network input: counts, sbar over the N*N cells (iv*N + iu), z [2, N*N] normals."""
     iu = np.arange(N * N) % N
     iv = np.arange(N * N) // N
     cu = iu - N // 2 + 0.5
     cv = iv - N // 2 + 0.5
-    M = shape_factor(cu, cv, du, e1, e2, alpha_arcsec * ARC)
+    M = shape_factor(cu, cv, du, e1, e2, alpha_arcsec * ARC, profile)
     x = np.zeros(2 * N * N)
     on = counts > 0
     sq = np.sqrt(np.where(on, counts, 1.0))

@@ -44,6 +44,7 @@ typedef struct {
     double thresh_frac, var_sigma_min, var_det_min;
     int32_t facet_n, n_e, n_alpha, flux_prior; /* flux_prior 0: S in [0, inf); 1: real line */
     int32_t chunk, update_mode;                /* update_mode 0: good fits only; 1: all */
+    int32_t profile, pad;                      /* 0: exponential (Eq. 1); 1: Gaussian of equal FWHM */
 } rlfo_params;
 
 int rlfo_nest(void) { return RLFO_NEST; }
@@ -68,10 +69,20 @@ static double sheared_k2(double ku, double kv, double e1, double e2)
     return x * x + y * y;
 }
 
-/* the Eq. 1 brightness factor (1 + 4 pi^2 alpha^2 |A^{-T} k|^2)^{-3/2}; k in wavelengths */
-double rlfo_shape(double ku, double kv, double alpha_rad, double e1, double e2)
+/*
+ * The Eq. 1 brightness factor; k in wavelengths.
+ *   profile 0, exponential disc: (1 + 4 pi^2 alpha^2 |A^{-T} k|^2)^{-3/2}
+ *   profile 1, Gaussian: exp(-2 pi^2 sigma^2 |A^{-T} k|^2), the transform of
+ *     exp(-r^2 / (2 sigma^2)), with sigma = alpha sqrt(ln 2 / 2) so that its FWHM,
+ *     2 sigma sqrt(2 ln 2), equals the exponential's 2 alpha ln 2 (footnote to Sec. 2.2)
+ */
+double rlfo_shape(double ku, double kv, double alpha_rad, double e1, double e2, int profile)
 {
     double k2 = sheared_k2(ku, kv, e1, e2);
+    if (profile == 1) {
+        double sigma2 = alpha_rad * alpha_rad * log(2.0) / 2.0;
+        return exp(-2.0 * RLFO_PI * RLFO_PI * sigma2 * k2);
+    }
     return pow(1.0 + 4.0 * RLFO_PI * RLFO_PI * alpha_rad * alpha_rad * k2, -1.5);
 }
 
@@ -85,11 +96,11 @@ static double n_minus_1(double l, double m)
 /* Eq. 1: visibility of one source at baseline (u, v, w) metres and frequency freq. */
 void rlfo_model_vis(double u, double v, double w, double freq, double l, double m,
                     double flux_jy, double alpha_rad, double e1, double e2,
-                    double beta, double nu_ref, double *re, double *im)
+                    double beta, double nu_ref, int profile, double *re, double *im)
 {
     double s = freq / RLFO_C;
     double ku = u * s, kv = v * s, kw = w * s;
-    double amp = pow(freq / nu_ref, beta) * flux_jy * rlfo_shape(ku, kv, alpha_rad, e1, e2);
+    double amp = pow(freq / nu_ref, beta) * flux_jy * rlfo_shape(ku, kv, alpha_rad, e1, e2, profile);
     double ph = 2.0 * RLFO_PI * (ku * l + kv * m + kw * n_minus_1(l, m));
     *re = amp * cos(ph);
     *im = amp * sin(ph);
@@ -105,7 +116,7 @@ void rlfo_sky_model(int64_t n_rows, int32_t n_chan, const double *u, const doubl
                     const double *w, const double *freq, const int64_t *rows, int64_t n_out,
                     int32_t n_src, const double *l, const double *m, const double *flux,
                     const double *alpha_rad, const double *e1, const double *e2,
-                    double beta, double nu_ref, double *out, double *abs_out, int n_threads)
+                    double beta, double nu_ref, int profile, double *out, double *abs_out, int n_threads)
 {
     if (!rows) n_out = n_rows;
 #ifdef _OPENMP
@@ -119,7 +130,7 @@ void rlfo_sky_model(int64_t n_rows, int32_t n_chan, const double *u, const doubl
             for (int32_t j = 0; j < n_src; ++j) {
                 double re, im;
                 rlfo_model_vis(u[r], v[r], w[r], freq[c], l[j], m[j], flux[j], alpha_rad[j],
-                               e1[j], e2[j], beta, nu_ref, &re, &im);
+                               e1[j], e2[j], beta, nu_ref, profile, &re, &im);
                 sr += re;
                 si += im;
                 sa += sqrt(re * re + im * im);
@@ -147,7 +158,7 @@ void rlfo_extract_facet(int64_t n_rows, int32_t n_chan, const double *u, const d
                         const double *w, const double *freq, const float *data,
                         const float *sky_f, const double *sky_d,
                         double l, double m, double flux, double alpha_sky_rad,
-                        double e1_cur, double e2_cur, double beta, double nu_ref,
+                        double e1_cur, double e2_cur, double beta, double nu_ref, int profile,
                         double du, int32_t facet_n, double *acc, double *abs_acc)
 {
     const int64_t nc = (int64_t)facet_n * facet_n;
@@ -167,7 +178,7 @@ void rlfo_extract_facet(int64_t n_rows, int32_t n_chan, const double *u, const d
             double ski = sky_f ? (double)sky_f[idx + 1] : sky_d[idx + 1];
             double mr, mi;
             rlfo_model_vis(u[r], v[r], w[r], freq[c], l, m, flux, alpha_sky_rad, e1_cur, e2_cur,
-                           beta, nu_ref, &mr, &mi);
+                           beta, nu_ref, profile, &mr, &mi);
             double rr = (double)data[idx] - skr + mr;
             double ri = (double)data[idx + 1] - ski + mi;
             double ph = -2.0 * RLFO_PI * (ku * l + kv * m + kw * n1);
@@ -271,7 +282,7 @@ int rlfo_like_grid(const double *acc, double du, const rlfo_params *p,
                 double al = rlfo_grid_alpha(p, k) * RLFO_ARCSEC;
                 double a = 0.0, b = 0.0;
                 for (int c = 0; c < ncell; ++c) {
-                    double M = rlfo_shape(cu[c], cv[c], al, e1, e2);
+                    double M = rlfo_shape(cu[c], cv[c], al, e1, e2, p->profile);
                     a += cw[c] * cs[c] * cs[c] * M * M;
                     b += cw[c] * cs[c] * M * cd[c];
                 }
@@ -446,7 +457,7 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
         alpha_sky[j] = a * RLFO_ARCSEC;
     }
     rlfo_sky_model(n_rows, n_chan, u, v, w, freq, NULL, 0, n_src, l, m, flux, alpha_sky, e1c, e2c,
-                   p->beta, p->nu_ref_hz, sky, NULL, n_threads);
+                   p->beta, p->nu_ref_hz, p->profile, sky, NULL, n_threads);
     int chunk = p->chunk > 0 ? p->chunk : n_src;
     for (int first = 0; first < n_src; first += chunk) {
         int cnt = (first + chunk <= n_src) ? chunk : n_src - first;
@@ -460,8 +471,8 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
             double *lg = malloc(sizeof(double) * ng * 3);
             double du = rlfo_facet_du(flux[i], alpha_cat_arcsec ? alpha_cat_arcsec[i] : 0.0, p);
             rlfo_extract_facet(n_rows, n_chan, u, v, w, freq, data, NULL, sky, l[i], m[i], flux[i],
-                               alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, du, p->facet_n,
-                               acc, NULL);
+                               alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, du,
+                               p->facet_n, acc, NULL);
             rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, est + (int64_t)i * RLFO_NEST);
             free(acc);
             free(lg);
@@ -478,9 +489,9 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
                     if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
                     double nr, ni, orr, oi;
                     rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
-                                   e[RLFO_E1], e[RLFO_E2], p->beta, p->nu_ref_hz, &nr, &ni);
+                                   e[RLFO_E1], e[RLFO_E2], p->beta, p->nu_ref_hz, p->profile, &nr, &ni);
                     rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
-                                   e1c[i], e2c[i], p->beta, p->nu_ref_hz, &orr, &oi);
+                                   e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, &orr, &oi);
                     sky[(r * n_chan + c) * 2 + 0] += nr - orr;
                     sky[(r * n_chan + c) * 2 + 1] += ni - oi;
                 }

@@ -30,6 +30,7 @@ bool params_ok(const rlf_params &p)
         return false;
     if (p.flux_prior != 0 && p.flux_prior != 1) return false;
     if (p.update_mode != 0 && p.update_mode != 1) return false;
+    if (p.profile != RLF_PROFILE_EXPONENTIAL && p.profile != RLF_PROFILE_GAUSSIAN) return false;
     if (p.tune_fit_ag != 0 && p.tune_fit_ag != 2 && p.tune_fit_ag != 4 && p.tune_fit_ag != 8) return false;
     if (p.tune_fit_blocks < 0 || p.tune_extract_waves < 0 || p.tune_sky_blocks < 0) return false;
     return true;
@@ -74,6 +75,8 @@ ChanTable make_chan_table(const rlf_uvw &uvw, const rlf_params &p)
     ch.ds = ch.n > 1 ? (ch.s[ch.n - 1] - ch.s[0]) / (ch.n - 1) : 0.0;
     ch.ds_hi = (float)ch.ds;
     ch.ds_lo = (float)(ch.ds - (double)ch.ds_hi);
+    ch.profile = p.profile;
+    ch.pad = 0;
     ch.uniform = 1;
     for (int k = 0; k < ch.n; ++k)
         if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;

@@ -208,7 +208,8 @@ __device__ __forceinline__ void st_shared_v4_if(uint32_t addr, bool p, int a, in
 }
 
 // kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
-template <int CG, bool kUniform, bool kSplit, bool kResid>
+// kGauss: the Gaussian source profile instead of the exponential one.
+template <int CG, bool kUniform, bool kSplit, bool kResid, bool kGauss>
 __global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
 extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                   const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
@@ -429,8 +430,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn), plus the source's model
                     float xr = fmaf(rr, cs, ri * sn);
                     const float xi = fmaf(ri, cs, -rr * sn);
-                    const float rq = rsqrtf(fmaf(q, f2[c], 1.0f));
-                    xr = fmaf(fspec[c], rq * rq * rq, xr);
+                    xr = fmaf(fspec[c], brightness<kGauss>(q, f2[c]), xr);
                     // a run ends when the cell changes; runs of cell -1 are dropped
                     const bool change = cell != run_cell[c];
                     {
@@ -530,8 +530,8 @@ extract_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
             sincospi(2.0 * (t - rint(t)), &sn, &cs);
             double xr = rr * cs + ri * sn;
             const double xi = ri * cs - rr * sn;
-            const double x = 1.0 + (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * ch.s[k] * ch.s[k];
-            xr += S.flux * ch.spec[k] / (x * sqrt(x));
+            const double qs = (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * ch.s[k] * ch.s[k];
+            xr += S.flux * ch.spec[k] * brightness64(qs, ch.profile);
             const int cell = iv * N + iu;
             atomicAdd(&acc[cell], xr);
             atomicAdd(&acc[NN + cell], xi);
@@ -577,8 +577,13 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
     const size_t smem = (size_t)kRing * kThreads * sizeof(int4) + RLF_MAX_CHAN * sizeof(float) +
                         4 * (size_t)N * N * sizeof(float);
     const bool resid = sky == nullptr;
-    auto kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true> : extract_rl_kernel<CG, true, kSplit, false>)
-                           : (resid ? extract_rl_kernel<CG, false, kSplit, true> : extract_rl_kernel<CG, false, kSplit, false>);
+    decltype(&extract_rl_kernel<CG, true, kSplit, true, false>) kern;
+    if (ch.profile == RLF_PROFILE_GAUSSIAN)
+        kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true, true> : extract_rl_kernel<CG, true, kSplit, false, true>)
+                          : (resid ? extract_rl_kernel<CG, false, kSplit, true, true> : extract_rl_kernel<CG, false, kSplit, false, true>);
+    else
+        kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true, false> : extract_rl_kernel<CG, true, kSplit, false, false>)
+                          : (resid ? extract_rl_kernel<CG, false, kSplit, true, false> : extract_rl_kernel<CG, false, kSplit, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

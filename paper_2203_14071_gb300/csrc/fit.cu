@@ -119,7 +119,7 @@ __device__ __forceinline__ double grid_alpha(const GridConst &g, int k)
 // pairs tile * kThreads .. tile * kThreads + kThreads - 1, over part `part` of
 // `n_parts` equal ranges of the facet's cells.  Writes the part's a, b sums in FP64
 // to ga, gb (the caller offsets them to the part's slice).
-template <typename T, int AG>
+template <typename T, int AG, bool kGauss>
 __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__restrict__ cells,
                           const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table, size_t plane,
                           int32_t NN, const GridConst &gc, double *__restrict__ ga, double *__restrict__ gb)
@@ -205,11 +205,13 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
         if (!on) continue;
         if constexpr (std::is_same<T, float>::value && AG % 2 == 0) {
             // two scalelength nodes per paired FP32 instruction
+            // Gaussian profile: c2 carries -alpha-coefficient / 4 and M = 2^(c2 Q)
             f32x2 c2[AG / 2], pa2[AG / 2], pb2[AG / 2];
             const f32x2 one2 = pk2(1.0f, 1.0f), zero2 = pk2(0.0f, 0.0f);
+            const float cs = kGauss ? -0.25f : 1.0f;
 #pragma unroll
             for (int j = 0; j < AG / 2; ++j) {
-                c2[j] = pk2(calpha[2 * j], calpha[2 * j + 1]);
+                c2[j] = pk2(cs * calpha[2 * j], cs * calpha[2 * j + 1]);
                 pa2[j] = pb2[j] = zero2;
             }
             for (int c = 0; c < nt; ++c) {
@@ -218,9 +220,15 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
 #pragma unroll
                 for (int j = 0; j < AG / 2; ++j) {
                     float x0, x1;
-                    up2(fma2(c2[j], Q2, one2), x0, x1);
-                    const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
-                    const f32x2 M2 = mul2(mul2(r2, r2), r2);
+                    f32x2 M2;
+                    if (kGauss) {
+                        up2(mul2(c2[j], Q2), x0, x1);
+                        M2 = pk2(ex2_approx(x0), ex2_approx(x1));
+                    } else {
+                        up2(fma2(c2[j], Q2, one2), x0, x1);
+                        const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
+                        M2 = mul2(mul2(r2, r2), r2);
+                    }
                     pa2[j] = fma2(mul2(A2, M2), M2, pa2[j]);
                     pb2[j] = fma2(B2, M2, pb2[j]);
                 }
@@ -244,13 +252,11 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
                 const T A = sm[3][c], B = sm[4][c];
 #pragma unroll
                 for (int j = 0; j < AG; ++j) {
-                    const T x = calpha[j] * Q + T(1);
                     T M;
                     if constexpr (std::is_same<T, float>::value) {
-                        const T r = rsqrtf(x);
-                        M = r * r * r;
+                        M = brightness<kGauss>(calpha[j], Q);
                     } else {
-                        M = T(1) / (x * sqrt(x));
+                        M = brightness64(calpha[j] * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
                     }
                     const T AM = A * M;
                     pa[j] += AM * M;
@@ -538,7 +544,7 @@ __global__ void lpt_order_kernel(const int32_t *__restrict__ ncell, int32_t coun
 // items than CTAs (few facets, or the 7 x 7 x 5 sub-box), each facet's cells are
 // split into up to kMaxFitParts parts so that every CTA has work; the number of
 // facets may be known only on the device (refit list), so the split is chosen here.
-template <typename T, int AG>
+template <typename T, int AG, bool kGauss>
 __global__ void __launch_bounds__(kThreads, 3)
 fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
                       const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
@@ -566,7 +572,7 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
         const int s = order[item / per_src];
         const int rem = item % per_src;
         const int tile = rem / n_parts, part = rem % n_parts;
-        grid_tile<T, AG>(s, tile, part, n_parts, cells, ncell, table, plane, NN, gc, ga + part * part_stride,
+        grid_tile<T, AG, kGauss>(s, tile, part, n_parts, cells, ncell, table, plane, NN, gc, ga + part * part_stride,
                          gb + part * part_stride);
         __threadfence();
         __syncthreads();
@@ -629,7 +635,8 @@ cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane,
     gc.n_ag = gc.box ? (kBoxA + AG - 1) / AG : (gc.n_alpha + AG - 1) / AG;
     const int pairs = (gc.box ? kBoxE * kBoxE : gc.n_e * gc.n_e) * gc.n_ag;
     const int tiles = (pairs + kThreads - 1) / kThreads;
-    auto kern = fit_persistent_kernel<T, AG>;
+    auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? fit_persistent_kernel<T, AG, true>
+                                                   : fit_persistent_kernel<T, AG, false>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     if (e != cudaSuccess) return e;
@@ -681,6 +688,8 @@ GridConst grid_const(const rlf_params &p)
     gc.n_alpha = p.n_alpha;
     gc.n_ag = 0;
     gc.flux_prior = p.flux_prior;
+    gc.profile = p.profile;
+    gc.pad = 0;
     gc.e_max = p.e_max;
     gc.r_min = p.r_min_arcsec;
     gc.r_max = p.r_max_arcsec;

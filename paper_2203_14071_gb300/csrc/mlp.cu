@@ -292,7 +292,7 @@ __global__ void encode_kernel(const double *__restrict__ facets, const SrcRow *_
 // Training facets: D_c / S = s_c M(k_c; e, alpha) + (sigma / S) z / sqrt(n_c), from a
 // template facet's counts and spectral sums and its cell size.  The result is f16,
 // so the arithmetic is FP32.
-__global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, double add, double esp,
+__global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, int profile, double add, double esp,
                                 double psf_nat, const double *__restrict__ tflux, const int32_t *__restrict__ tidx,
                                 const double *__restrict__ e1, const double *__restrict__ e2,
                                 const double *__restrict__ alpha_as, const float *__restrict__ z, int N,
@@ -323,9 +323,8 @@ __global__ void simulate_kernel(const double *__restrict__ tmpl, int n_tmpl, dou
         if (n > 0.0) {
             const float cu = (float)((c % N) - N / 2) + 0.5f, cv = (float)((c / N) - N / 2) + 0.5f;
             const float x1 = (1.0f + a1) * cu + a2 * cv, x2 = a2 * cu + (1.0f - a1) * cv;
-            const float q = fmaf(c2, x1 * x1 + x2 * x2, 1.0f);
-            const float rq = rsqrtf(q);
-            const float M = rq * rq * rq;
+            const float M = profile == RLF_PROFILE_GAUSSIAN ? brightness<true>(c2, x1 * x1 + x2 * x2)
+                                                            : brightness<false>(c2, x1 * x1 + x2 * x2);
             const float nf = (float)n;
             const float sbar = (float)(f[3 * NN + c] / n);
             const float sr = sr0 * rsqrtf(nf);
@@ -535,7 +534,7 @@ cudaError_t mlp_simulate(const double *tmpl, int32_t n_tmpl, const rlf_params &p
 {
     const int NN = N * N;
     dim3 grid(4, B);
-    simulate_kernel<<<grid, 256, 0, st>>>(tmpl, n_tmpl, p.add, p.esp, p.psf_nat, tflux, tidx, e1, e2, alpha_as, z, N,
+    simulate_kernel<<<grid, 256, 0, st>>>(tmpl, n_tmpl, p.profile, p.add, p.esp, p.psf_nat, tflux, tidx, e1, e2, alpha_as, z, N,
                                           sigma, x, y);
     return cudaGetLastError();
 }

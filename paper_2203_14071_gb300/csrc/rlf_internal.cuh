@@ -40,6 +40,8 @@ struct SrcRow {
 struct ChanTable {
     int32_t n;              // channels
     int32_t uniform;        // s[k] = s0 + k ds to 1e-12 relative
+    int32_t profile;        // RLF_PROFILE_EXPONENTIAL or RLF_PROFILE_GAUSSIAN
+    int32_t pad;
     double s0, ds;          // nu / c of channel 0 and its step, 1/m
     double spec_off;        // mean spectral factor: FP32 sums accumulate spec - spec_off
     double s[RLF_MAX_CHAN];     // nu_k / c (host division, the value the cell index uses)
@@ -94,6 +96,34 @@ __device__ __forceinline__ float frac_cycles(float P, float E, float sh, float s
     return f - rintf(f);
 }
 
+// ---- the source profile's brightness factor (Eq. 1) -------------------------------------
+// From qs = 4 pi^2 alpha^2 |A^{-T} k|^2 (the source's quadratic form times s^2):
+//   exponential disc (1 + qs)^{-3/2};
+//   Gaussian exp(-2 pi^2 sigma^2 |A^{-T} k|^2) with sigma^2 = alpha^2 ln 2 / 2 (the FWHM of
+//   the exponential of scalelength alpha), i.e. 2^{-qs/4}.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// q = the quadratic form in metres^2, f2 = s^2 (one FMA or two multiplies, one MUFU)
+template <bool kGauss>
+__device__ __forceinline__ float brightness(float q, float f2)
+{
+    if (kGauss) return ex2_approx(-0.25f * q * f2);
+    const float r = rsqrtf(fmaf(q, f2, 1.0f));
+    return r * r * r;
+}
+
+__device__ __forceinline__ double brightness64(double qs, int profile)
+{
+    if (profile == RLF_PROFILE_GAUSSIAN) return exp2(-0.25 * qs);
+    const double x = 1.0 + qs;
+    return 1.0 / (x * sqrt(x));
+}
+
 // ---- paired FP32 arithmetic (Blackwell f32x2 instructions) ----------------------------
 // Two floats in one 64-bit register pair; one instruction issues both lanes.
 typedef unsigned long long f32x2;
@@ -144,6 +174,7 @@ constexpr int kMlpIn = 8192, kMlpHidden = 256, kMlpOut = 6, kMlpOutPad = 8;
 struct GridConst {
     const int32_t *box;     // per-facet sub-box origins [count][3] (e1, e2, alpha node), or null: full grid
     int32_t n_e, n_alpha, n_ag, flux_prior;
+    int32_t profile, pad;
     double e_max;
     double r_min, r_max;    // arcsec
     double r_std;

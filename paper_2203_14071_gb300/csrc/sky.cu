@@ -95,7 +95,7 @@ struct SkySrc {
 
 // Mixed precision sky model / update.  CG channels per thread.  kSplit selects
 // the float-pair phase argument instead of the FP64 one.
-template <int CG, bool kUpdate, bool kUniform, bool kSplit>
+template <int CG, bool kUpdate, bool kUniform, bool kSplit, bool kGauss>
 __global__ void __launch_bounds__(kThreads)
 sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                  const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
@@ -210,14 +210,8 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                         }
                         __sincosf(f * kTwoPi, &sn, &cs);
                     }
-                    const float x = fmaf(q, f2[c], 1.0f);
-                    const float rr = rsqrtf(x);
-                    float M = rr * rr * rr;
-                    if (kUpdate) {
-                        const float xn = fmaf(qn, f2[c], 1.0f);
-                        const float rn = rsqrtf(xn);
-                        M = rn * rn * rn - M;
-                    }
+                    float M = brightness<kGauss>(q, f2[c]);
+                    if (kUpdate) M = brightness<kGauss>(qn, f2[c]) - M;
                     const float a = S.flux * M;
                     are[c] = fmaf(a, cs, are[c]);
                     aim[c] = fmaf(a, sn, aim[c]);
@@ -280,12 +274,9 @@ sky_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
                 double sn, cs;
                 sincospi(2.0 * (t - rint(t)), &sn, &cs);
                 const double q = (S.q[0] * ud * ud + S.q[1] * ud * vd + S.q[2] * vd * vd) * f2;
-                const double x = 1.0 + q;
-                double M = 1.0 / (x * sqrt(x));
-                if (kUpdate) {
-                    const double xn = 1.0 + (S.qn[0] * ud * ud + S.qn[1] * ud * vd + S.qn[2] * vd * vd) * f2;
-                    M = 1.0 / (xn * sqrt(xn)) - M;
-                }
+                double M = brightness64(q, ch.profile);
+                if (kUpdate)
+                    M = brightness64((S.qn[0] * ud * ud + S.qn[1] * ud * vd + S.qn[2] * vd * vd) * f2, ch.profile) - M;
                 are += S.flux * M * cs;
                 aim += S.flux * M * sn;
             }
@@ -324,12 +315,20 @@ void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, 
     const int64_t blocks_needed = (uvw.n_rows + lanes - 1) / lanes;
     const int64_t cap = (int64_t)sm_count() * blocks_per_sm;
     const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
-    if (ch.uniform)
-        sky_mixed_kernel<CG, kUpdate, true, kSplit><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
+    float2 *out = reinterpret_cast<float2 *>(vis);
+    const bool gauss = ch.profile == RLF_PROFILE_GAUSSIAN;
+    if (ch.uniform && !gauss)
+        sky_mixed_kernel<CG, kUpdate, true, kSplit, false><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+    else if (ch.uniform)
+        sky_mixed_kernel<CG, kUpdate, true, kSplit, true><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+    else if (!gauss)
+        sky_mixed_kernel<CG, kUpdate, false, kSplit, false><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
     else
-        sky_mixed_kernel<CG, kUpdate, false, kSplit><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, reinterpret_cast<float2 *>(vis));
+        sky_mixed_kernel<CG, kUpdate, false, kSplit, true><<<grid, kThreads, 0, st>>>(
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
 }
 
 template <bool kUpdate, bool kSplit>

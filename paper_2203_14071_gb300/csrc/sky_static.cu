@@ -80,6 +80,8 @@ rlf::ChanTable channel_table(const rlf_uvw &uvw, const rlf_params &p)
     ch.ds = ch.n > 1 ? (ch.s[ch.n - 1] - ch.s[0]) / (ch.n - 1) : 0.0;
     ch.ds_hi = (float)ch.ds;
     ch.ds_lo = (float)(ch.ds - (double)ch.ds_hi);
+    ch.profile = p.profile;
+    ch.pad = 0;
     ch.uniform = 1;
     for (int k = 0; k < ch.n; ++k)
         if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;

@@ -22,10 +22,12 @@ class Case:
     sigma: float
     data: np.ndarray | None = None      # [R, C, 2] float32
     sky0: np.ndarray | None = None      # [R, C, 2] float32 (circular sky model)
+    profile: int = 0                    # 0 exponential (Eq. 1), 1 Gaussian of equal FWHM
 
     def oracle_params(self, **kw):
         kw.setdefault("nu_ref_hz", self.wl.nu_ref_hz)
         kw.setdefault("sigma_jy", self.sigma)
+        kw.setdefault("profile", self.profile)
         return oracle.default_params(**kw)
 
     def alpha_med_rad(self):
@@ -38,18 +40,18 @@ def snr10_sigma(obs: synth.Observation, cat: synth.Catalogue) -> float:
 
 
 def build(wl: synth.Workload, sigma: float | None = None, with_data: bool = True, snr10: bool = False,
-          n_src: int | None = None) -> Case:
+          n_src: int | None = None, profile: int = 0) -> Case:
     obs = synth.make_observation(wl)
     cat = synth.make_catalogue(wl, n_src)
     if snr10:
         sigma = snr10_sigma(obs, cat)
     sigma = wl.sigma_jy if sigma is None else sigma
-    c = Case(wl, obs, cat, sigma)
+    c = Case(wl, obs, cat, sigma, profile=profile)
     if with_data:
         c.data = data_from(true_sky(c), sigma, wl.seed)
         z = np.zeros(cat.n_src)
         s0 = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, c.alpha_med_rad(), z, z,
-                              nu_ref=wl.nu_ref_hz)
+                              nu_ref=wl.nu_ref_hz, profile=profile)
         c.sky0 = np.stack([s0.real, s0.imag], -1).astype(np.float32)
     return c
 
@@ -57,7 +59,7 @@ def build(wl: synth.Workload, sigma: float | None = None, with_data: bool = True
 def true_sky(c: Case) -> np.ndarray:
     """The oracle's sky model at the catalogue's true shapes and scalelengths, complex128 [R, C]."""
     return oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
-                            c.cat.alpha_arcsec * ARC, c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz)
+                            c.cat.alpha_arcsec * ARC, c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz, profile=c.profile)
 
 
 def data_from(true: np.ndarray, sigma: float, seed: int) -> np.ndarray:

@@ -69,6 +69,12 @@ def test_simulated_facet_is_the_likelihood_model():
         M = oracle.shape((iu - N // 2 + 0.5) * du, (iv - N // 2 + 0.5) * du, 1.3 * mlp.ARC, 0.2, -0.3)
         assert abs(x[c] - 0.97 * M) < 1e-14 and x[N * N + c] == 0.0
     assert np.count_nonzero(x) == 4
+    # the Gaussian profile's facet model
+    x = mlp.simulate(counts, sbar, du, 0.2, -0.3, 1.3, 0.0, np.zeros((2, N * N)), N=N, profile=1)
+    for c in (3, 10, 27, 44):
+        iu, iv = c % N, c // N
+        M = oracle.shape((iu - N // 2 + 0.5) * du, (iv - N // 2 + 0.5) * du, 1.3 * mlp.ARC, 0.2, -0.3, 1)
+        assert abs(x[c] - 0.97 * M) < 1e-14
 
 
 def test_proposal_box_and_fallback_rules():

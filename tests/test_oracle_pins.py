@@ -394,20 +394,55 @@ def test_bad_fit_flag_on_narrow_posterior():
     assert abs(est[oracle.E1] - 0.16) < 1e-12 and est[oracle.SIG1] == 0.0
 
 
-def test_pipeline_recovers_isolated_shapes_small_noise():
-    # end-to-end on a tiny case: a single source, data simulated with Eq. 1 at the
-    # true shape, moderate noise; the estimate lies near the truth
+@pytest.mark.parametrize("profile", [0, 1])
+def test_pipeline_recovers_isolated_shapes_small_noise(profile):
+    # end-to-end on a tiny case: a single source, data simulated with Eq. 1 (or its Gaussian
+    # variant) at the true shape, moderate noise; the estimate lies near the truth
     wl = synth.tiny(seed=21, n_src=1, n_ant=24, n_time=24, n_chan=2, r_max_m=1500.0)
     obs, cat = synth.make_observation(wl), synth.make_catalogue(wl)
-    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=2e-5, update_mode=1)
+    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=2e-5, update_mode=1, profile=profile)
     al = np.array([oracle.alpha_med(s) for s in cat.flux_jy]) * ARC
     d = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al, cat.e1, cat.e2,
-                         nu_ref=wl.nu_ref_hz)
+                         nu_ref=wl.nu_ref_hz, profile=profile)
     d2 = np.stack([d.real, d.imag], -1).astype(np.float32)
     est, sky = oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, d2, cat.l, cat.m, cat.flux_jy, None, p,
                                want_sky=True)
     assert abs(est[0, oracle.E1] - cat.e1[0]) < 0.1 and abs(est[0, oracle.E2] - cat.e2[0]) < 0.1
     # after the update the sky model holds the measured shape
     upd = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al,
-                           est[:, oracle.E1], est[:, oracle.E2], nu_ref=wl.nu_ref_hz)
+                           est[:, oracle.E1], est[:, oracle.E2], nu_ref=wl.nu_ref_hz, profile=profile)
     assert np.max(np.abs(sky - upd)) < 1e-15
+
+
+def _sigma_of_equal_fwhm(alpha):
+    # the exponential profile's half-maximum radius, then the Gaussian width with the same one
+    # (footnote to Sec. 2.2: FWHM = 2 alpha ln 2 and 2 sigma sqrt(2 ln 2)), both solved numerically
+    from scipy.optimize import brentq
+    r_half = brentq(lambda r: math.exp(-r / alpha) - 0.5, 0.0, 10 * alpha, xtol=1e-15)
+    return brentq(lambda sg: math.exp(-r_half ** 2 / (2 * sg * sg)) - 0.5, 1e-3 * alpha, 10 * alpha, xtol=1e-15)
+
+
+def test_gaussian_profile_is_hankel_transform_of_equal_fwhm_gaussian():
+    # circular Gaussian I(r) = exp(-r^2 / (2 sigma^2)) / (2 pi sigma^2): F(k) = 2 pi int r I J0(2 pi k r) dr
+    alpha = 1.0
+    sg = _sigma_of_equal_fwhm(alpha)
+    for k in (0.02, 0.1, 0.35, 0.7):
+        f = lambda r: r * math.exp(-r * r / (2 * sg * sg)) / (sg * sg) * special.j0(2 * math.pi * k * r)
+        val, err = integrate.quad(f, 0, 40 * sg, limit=2000, epsabs=1e-14, epsrel=1e-12)
+        assert abs(val - oracle.shape(k, 0.0, alpha, 0.0, 0.0, 1)) < 1e-9
+    # the two profiles differ away from k = 0 and agree at it
+    assert oracle.shape(0.0, 0.0, alpha, 0.3, 0.1, 1) == 1.0
+    assert abs(oracle.shape(0.3, 0.0, alpha, 0.0, 0.0, 1) - oracle.shape(0.3, 0.0, alpha, 0.0, 0.0, 0)) > 0.01
+
+
+def test_gaussian_sheared_image_fourier_transform(pixel_grid):
+    X, Y, h = pixel_grid
+    sg = _sigma_of_equal_fwhm(1.0)
+    for e1, e2 in ((0.3, -0.2), (-0.45, 0.1), (0.0, 0.55)):
+        A = np.array([[1 - e1, -e2], [-e2, 1 + e1]])
+        ax = A[0, 0] * X + A[0, 1] * Y
+        ay = A[1, 0] * X + A[1, 1] * Y
+        f = abs(np.linalg.det(A)) / (2 * np.pi * sg * sg) * np.exp(-(ax * ax + ay * ay) / (2 * sg * sg))
+        for ku, kv in ((0.05, 0.0), (0.0, 0.12), (0.1, 0.07), (0.25, -0.15)):
+            F = (f * np.cos(2 * np.pi * (ku * X + kv * Y))).sum() * h * h
+            assert abs(F - oracle.shape(ku, kv, 1.0, e1, e2, 1)) < 1e-9, (e1, e2, ku, kv)

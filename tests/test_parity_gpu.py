@@ -249,6 +249,48 @@ def test_run_small_pipeline(rlf, prec, chunk, update_mode):
     assert dv.max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum(), dv.max() / c.cat.flux_jy.sum()
 
 
+@pytest.mark.parametrize("prec", ["split", "mixed", "fp64"])
+def test_gaussian_profile_sky_model_and_chain(rlf, prec):
+    # the Gaussian source profile (footnote to Sec. 2.2) through the sky model and the whole
+    # chain: data from the oracle's Gaussian sky model, every step on the GPU with profile 1
+    torch = _torch()
+    c = cases.build(synth.workload("small"), snr10=True, profile=1)
+    obs, cat = cases.to_device(c, c.cat.e1, c.cat.e2, c.cat.alpha_arcsec)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma,
+                           profile=rlf.PROFILE_GAUSSIAN)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_SKY)
+    vis = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.sky_model(obs, cat, p, vis, ws)
+    got = vis.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    ref, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                               c.cat.alpha_arcsec * cases.ARC, c.cat.e1, c.cat.e2, nu_ref=c.wl.nu_ref_hz,
+                               with_abs=True, profile=1)
+    _check_vis(got, ref, ab, 1e-10 if prec == "fp64" else 1e-5)
+    # the whole chain from a circular catalogue
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, update_mode=1,
+                           profile=rlf.PROFILE_GAUSSIAN)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.run(obs, cases.vis_tensor(c.data), cat, p, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    est, sky_ref = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m,
+                                   c.cat.flux_jy, None, c.oracle_params(chunk=0, update_mode=1), want_sky=True)
+    res = out.numpy()
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(res, i, est[i]) <= 1e-4, (i, res["e1"][i], est[i, oracle.E1])
+    g = sky.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    assert np.abs(g[..., 0] + 1j * g[..., 1] - sky_ref).max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum()
+    # the profile changes the answer: the exponential model fits these data differently
+    p0 = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, update_mode=1)
+    out0 = rlf.Results(cat.n_src, "cuda")
+    rlf.run(obs, cases.vis_tensor(c.data), cat, p0, out0, sky, ws)
+    r0 = out0.numpy()
+    assert np.max(np.abs(r0["alpha_arcsec"] - res["alpha_arcsec"])) > 0.05
+
+
 def test_invalid_and_empty_sources_are_flagged(rlf):
     torch = _torch()
     wl = synth.tiny(seed=61, n_ant=12, n_time=9, n_chan=2, n_src=4, r_max_m=3000.0)
