@@ -512,15 +512,17 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     n_chunks = (n_src + chunk - 1) // chunk
     # kernels of one rlf_run step: prepare + sky model; outside FP64 mode the baseline extents,
     # their order (rows = time x baselines) and the split baselines (split mode); per chunk:
-    # residual (batched chunks only), window reach per source (outside FP64 mode), extraction,
+    # residual (batched chunks only; several chunks in mixed modes keep the residual resident:
+    # one difference before the chunks and one after), window reach per source (outside FP64 mode), extraction,
     # partial reduce, compaction, LPT order, persistent fit, prepare + sky update (one chunk:
     # prepare of the committed shapes + their sky model instead; memsets and copies are not
     # kernels of ours)
     mixed = params.precision != 0
     is_ordered = obs.n_baselines > 0 and obs.n_rows % obs.n_baselines == 0
-    per_chunk = 7 + (1 if chunk >= 3 and mixed else 0) + (1 if mixed else 0) + (1 if n_chunks == 1 else 0)
+    track = n_chunks > 1 and mixed and (obs.n_rows * obs.n_chan) % 2 == 0
+    per_chunk = 7 + (1 if chunk >= 3 and mixed and not track else 0) + (1 if mixed else 0) + (1 if n_chunks == 1 else 0)
     launches = (2 + (1 if mixed else 0) + (1 if mixed and is_ordered else 0)
-                + (1 if params.precision == 2 else 0) + n_chunks * per_chunk)
+                + (1 if params.precision == 2 else 0) + (2 if track else 0) + n_chunks * per_chunk)
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
             "sky_gvis_s": obs.n_rows * obs.n_chan / (sky_ms * 1e-3) / 1e9, "launches_per_step": launches,
             "fit_evals": fit_evals, "mean_cells_per_facet": float(n_cells.mean().item()),

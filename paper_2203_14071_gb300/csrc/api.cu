@@ -122,8 +122,10 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const bool mlp = fit && p.facet_n * p.facet_n * 2 == kMlpIn;
     const size_t o_mx = take(mlp ? cap * kMlpIn * sizeof(__half) : 0);
     const size_t o_ms = take(mlp ? mlp_scratch(nullptr, (int32_t)cap).bytes : 0);
-    const size_t o_ga = take(fit ? kMaxFitParts * cap * ng * sizeof(double) : 0);
-    const size_t o_gb = take(fit ? kMaxFitParts * cap * ng * sizeof(double) : 0);
+    // a few facets at a time split their cells further (the serial order fits one facet per chunk)
+    const size_t fit_parts = cap <= 16 ? 16 : kMaxFitParts;
+    const size_t o_ga = take(fit ? fit_parts * cap * ng * sizeof(double) : 0);
+    const size_t o_gb = take(fit ? fit_parts * cap * ng * sizeof(double) : 0);
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
@@ -156,6 +158,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->ga = reinterpret_cast<double *>(b + o_ga);
         ws->gb = reinterpret_cast<double *>(b + o_gb);
         ws->part_stride = cap * ng;
+        ws->fit_parts = (int32_t)fit_parts;
         ws->gl = reinterpret_cast<double *>(b + o_gl);
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
         ws->facets = reinterpret_cast<double *>(b + o_fac);
@@ -359,9 +362,16 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
                            ws.status, st);
     if (e == cudaSuccess) e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
     if (e == cudaSuccess) e = launch_extract_prepare(uvw, p, ws, st);
+    // several chunks (mixed modes): keep the residual R = D - V resident instead of V, so
+    // that each chunk's extraction reads one array; the updates subtract their terms
+    // from R and the sky model is restored at the end as V = D - R
+    const int64_t n_vis = uvw.n_rows * uvw.n_chan;
+    const bool track_resid = chunk < n && p.precision != RLF_PREC_FP64 && ws.resid && n_vis % 2 == 0;
+    if (e == cudaSuccess && track_resid) e = launch_difference(vis_data, vis_sky, n_vis, ws.resid, st);
     for (int32_t first = 0; first < n && e == cudaSuccess; first += chunk) {
         const int32_t cnt = first + chunk <= n ? chunk : n - first;
-        e = launch_extract(uvw, ch, vis_data, vis_sky, ws.table + first, cnt, p, ws, ws.facets, st);
+        e = track_resid ? launch_extract(uvw, ch, ws.resid, nullptr, ws.table + first, cnt, p, ws, ws.facets, st)
+                        : launch_extract(uvw, ch, vis_data, vis_sky, ws.table + first, cnt, p, ws, ws.facets, st);
         if (e != cudaSuccess) break;
         e = launch_fit(ws.facets, ws.table + first, cnt, p, ws, out, first, st);
         if (e != cudaSuccess) break;
@@ -377,10 +387,13 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
                                ws.status, st);
             if (e == cudaSuccess)
                 e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
+        } else if (track_resid) {
+            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f);
         } else {
             e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
         }
     }
+    if (e == cudaSuccess && track_resid) e = launch_difference(vis_data, ws.resid, n_vis, vis_sky, st);
     return e;
 }
 

@@ -216,7 +216,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                   int32_t stride, int32_t n_parts, const ChanTable ch,
                   const float2 *__restrict__ data, const float2 *__restrict__ sky,
                   const SrcRow *__restrict__ table, int32_t N, const int32_t *__restrict__ perm,
-                  const int32_t *__restrict__ n_live, float *__restrict__ partial)
+                  const int32_t *__restrict__ n_live, int32_t n_tslices, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
@@ -284,7 +284,11 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
         float run_re[CG], run_im[CG];
         // every lane runs every iteration (the per-row ring check is a warp vote);
         // lanes without a visibility carry cell = -1, whose runs are never appended
-        for (int blk = blockIdx.y; blk < n_blocks; blk += n_parts) {
+        // work units: (block of baselines, slice of the time series); a few sources at a
+        // time also split each baseline's time series so that the grid fills the GPU
+        for (int wk = blockIdx.y; wk < n_blocks * n_tslices; wk += n_parts) {
+            const int blk = wk % n_blocks, ts = wk / n_blocks;
+            const int64_t t_begin = n_time * ts / n_tslices, t_end = n_time * (ts + 1) / n_tslices;
             // lane position j in the order; bl the baseline (data rows bl + t * stride);
             // the split baselines are stored in order, at column j
             const int j = blk * bpc + lane_b;
@@ -298,15 +302,16 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
             }
             // split baselines of the next row are fetched one iteration ahead
             float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
-            if (kSplit && lane_on && bl < n_rows) {
-                nuh = us[j];
-                nul = us[n_rows + j];
-                nvh = us[2 * n_rows + j];
-                nvl = us[3 * n_rows + j];
-                nwh = us[4 * n_rows + j];
-                nwl = us[5 * n_rows + j];
+            if (kSplit && lane_on && t_begin < t_end && t_begin * stride + bl < n_rows) {
+                const int64_t c0 = t_begin * stride + j;
+                nuh = us[c0];
+                nul = us[n_rows + c0];
+                nvh = us[2 * n_rows + c0];
+                nvl = us[3 * n_rows + c0];
+                nwh = us[4 * n_rows + c0];
+                nwl = us[5 * n_rows + c0];
             }
-            for (int64_t t = 0; t < n_time; ++t) {
+            for (int64_t t = t_begin; t < t_end; ++t) {
                 // a row appends at most CG runs: make room first
                 if (__any_sync(0xffffffffu, cnt > kRing - CG)) {
                     drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
@@ -339,7 +344,7 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     wl = nwl;
                     const int64_t rn = r + stride;
                     const int64_t cn = (t + 1) * stride + j;
-                    if (lane_on && t + 1 < n_time && rn < n_rows) {
+                    if (lane_on && t + 1 < t_end && rn < n_rows) {
                         nuh = us[cn];
                         nul = us[n_rows + cn];
                         nvh = us[2 * n_rows + cn];
@@ -470,27 +475,49 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     }
 }
 
-// Sum of the parts of every cell in FP64, in part order.
+// Sum of the parts of every cell in FP64: a CTA takes 32 cells of one facet and
+// eight groups of threads sum every eighth part each; the groups' sums are then
+// added in group order (the result does not depend on timing).
+constexpr int kReduceCells = 32, kReduceGroups = kThreads / kReduceCells;
+
 __global__ void facet_reduce_kernel(const float *__restrict__ partial, int32_t n_parts, int32_t NN,
                                     double spec_off, double *__restrict__ facets)
 {
+    __shared__ double sre[kReduceGroups][kReduceCells], sim[kReduceGroups][kReduceCells],
+        ssp[kReduceGroups][kReduceCells];
+    __shared__ long long scnt[kReduceGroups][kReduceCells];
     const int s = blockIdx.y;
-    const int cell = blockIdx.x * kThreads + threadIdx.x;
-    if (cell >= NN) return;
+    const int lc = threadIdx.x % kReduceCells, grp = threadIdx.x / kReduceCells;
+    const int cell = blockIdx.x * kReduceCells + lc;
     double re = 0.0, im = 0.0, sp = 0.0;
     long long n = 0;
-    for (int p = 0; p < n_parts; ++p) {
-        const float *q = partial + ((size_t)s * n_parts + p) * 4 * NN;
-        re += (double)q[cell];
-        im += (double)q[NN + cell];
-        n += __float_as_int(q[2 * NN + cell]);
-        sp += (double)q[3 * NN + cell];
+    if (cell < NN) {
+        for (int p = grp; p < n_parts; p += kReduceGroups) {
+            const float *q = partial + ((size_t)s * n_parts + p) * 4 * NN;
+            re += (double)q[cell];
+            im += (double)q[NN + cell];
+            n += __float_as_int(q[2 * NN + cell]);
+            sp += (double)q[3 * NN + cell];
+        }
     }
-    double *f = facets + (size_t)s * 4 * NN;
-    f[cell] = re;
-    f[NN + cell] = im;
-    f[2 * NN + cell] = (double)n;
-    f[3 * NN + cell] = sp + (double)n * spec_off;
+    sre[grp][lc] = re;
+    sim[grp][lc] = im;
+    ssp[grp][lc] = sp;
+    scnt[grp][lc] = n;
+    __syncthreads();
+    if (grp == 0 && cell < NN) {
+        for (int g = 1; g < kReduceGroups; ++g) {
+            re += sre[g][lc];
+            im += sim[g][lc];
+            sp += ssp[g][lc];
+            n += scnt[g][lc];
+        }
+        double *f = facets + (size_t)s * 4 * NN;
+        f[cell] = re;
+        f[NN + cell] = im;
+        f[2 * NN + cell] = (double)n;
+        f[3 * NN + cell] = sp + (double)n * spec_off;
+    }
 }
 
 // FP64 extraction: every operation in double precision, one visibility at a time.
@@ -595,23 +622,32 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
     const int n_groups = (ch.n + CG - 1) / CG;
     const int bpc = kThreads / n_groups;
     const int64_t n_blocks = (stride + bpc - 1) / bpc;
+    const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
     const int NN = N * N;
     const int64_t slots = (int64_t)sm_count_x() * per_sm;
     // sources are handled in batches whose partial facets fit the workspace
     for (int32_t first = 0; first < count; first += kMaxPartials) {
         const int32_t cnt = count - first < kMaxPartials ? count - first : kMaxPartials;
-        // parts per source: about `waves` waves of CTAs, at most one part per baseline block
+        // parts per source: about `waves` waves of CTAs; beyond one part per baseline block
+        // (few sources) the time series are split too, into slices of at least 16 steps
         int64_t parts = ((int64_t)waves * slots + cnt - 1) / cnt;
-        if (parts > n_blocks) parts = n_blocks;
+        int64_t slices = 1;
+        if (parts > n_blocks) {
+            slices = (parts + n_blocks - 1) / n_blocks;
+            const int64_t max_slices = n_time / 16 > 1 ? n_time / 16 : 1;
+            if (slices > max_slices) slices = max_slices;
+            if (slices > 32) slices = 32;
+        }
+        if (parts > n_blocks * slices) parts = n_blocks * slices;
         if (parts > kMaxPartials / cnt) parts = kMaxPartials / cnt;
         if (parts < 1) parts = 1;
         dim3 grid(cnt, (unsigned)parts);
         kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
                                            reinterpret_cast<const float2 *>(data),
                                            reinterpret_cast<const float2 *>(sky), table + first, N, ord.perm,
-                                           ord.n_live + first, partial);
+                                           ord.n_live + first, (int32_t)slices, partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        dim3 rgrid((NN + kThreads - 1) / kThreads, cnt);
+        dim3 rgrid((NN + kReduceCells - 1) / kReduceCells, cnt);
         facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
                                                         facets + (size_t)first * 4 * NN);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -670,6 +706,15 @@ int64_t grid_for(int64_t n, int64_t cap)
 
 }  // namespace
 
+cudaError_t launch_difference(const float *a, const float *b, int64_t n_complex, float *out, cudaStream_t st)
+{
+    if (n_complex % 2 != 0) return cudaErrorInvalidValue;
+    const int64_t n4 = n_complex / 2;
+    residual_kernel<<<(int)grid_for(n4, (int64_t)sm_count_x() * 16), kThreads, 0, st>>>(
+        reinterpret_cast<const float4 *>(a), reinterpret_cast<const float4 *>(b), n4, reinterpret_cast<float4 *>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_extract_prepare(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws, cudaStream_t st)
 {
     if (p.precision == RLF_PREC_FP64) return cudaSuccess;
@@ -703,7 +748,7 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
         return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
     }
     // several sources read every visibility: form D - V_sky once (one streaming pass)
-    if (ws.resid && count >= 3) {
+    if (sky && ws.resid && count >= 3) {
         const int64_t n2 = uvw.n_rows * uvw.n_chan;   // complex values
         if (n2 % 2 == 0) {
             const int64_t n4 = n2 / 2;

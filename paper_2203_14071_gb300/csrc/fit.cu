@@ -542,7 +542,8 @@ __global__ void lpt_order_kernel(const int32_t *__restrict__ ncell, int32_t coun
 // after a fence) adds the parts' sums in part order and runs that facet's
 // estimate.  Nothing waits on another CTA.  When the launch has fewer (facet, tile)
 // items than CTAs (few facets, or the 7 x 7 x 5 sub-box), each facet's cells are
-// split into up to kMaxFitParts parts so that every CTA has work; the number of
+// split into up to max_parts parts (kMaxFitParts, or more for a small workspace)
+// so that every CTA has work; the number of
 // facets may be known only on the device (refit list), so the split is chosen here.
 template <typename T, int AG, bool kGauss>
 __global__ void __launch_bounds__(kThreads, 3)
@@ -550,7 +551,7 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
                       const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
                       int32_t count, const int32_t *__restrict__ count_dev, const int32_t *__restrict__ order,
                       int32_t *__restrict__ counters, const GridConst gc, double *__restrict__ ga,
-                      double *__restrict__ gb, size_t part_stride, double *__restrict__ gl,
+                      double *__restrict__ gb, size_t part_stride, int32_t max_parts, double *__restrict__ gl,
                       const double *__restrict__ ccv, rlf_fit_out out, int32_t out_offset,
                       int32_t *__restrict__ status, int32_t *__restrict__ map_out)
 {
@@ -560,7 +561,7 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
     const int n_src = count_dev ? *count_dev : count;
     const int64_t pairs_items = (int64_t)n_src * tiles_per_src;
     int n_parts = pairs_items > 0 ? (int)((gridDim.x + pairs_items - 1) / pairs_items) : 1;
-    n_parts = n_parts < 1 ? 1 : (n_parts > kMaxFitParts ? kMaxFitParts : n_parts);
+    n_parts = n_parts < 1 ? 1 : (n_parts > max_parts ? max_parts : n_parts);
     const int per_src = tiles_per_src * n_parts;
     const int total = n_src * per_src;
     const size_t ng = (size_t)gc.n_e * gc.n_e * gc.n_alpha;
@@ -654,7 +655,7 @@ cudaError_t launch_persistent(const T *cells, const SrcRow *table, size_t plane,
         order = ws.order;
     }
     kern<<<(int)grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, count_dev, order,
-                                         ws.counters, gc, ws.ga, ws.gb, ws.part_stride, ws.gl, ws.cc, out,
+                                         ws.counters, gc, ws.ga, ws.gb, ws.part_stride, ws.fit_parts, ws.gl, ws.cc, out,
                                          out_offset, ws.status, map_out);
     return cudaGetLastError();
 }

@@ -198,8 +198,9 @@ struct Workspace {
     void *mlp_x;            // [cap][8192] f16 network inputs
     void *mlp_scratch;      // network activations for cap facets
     double *cc;             // [cap]
-    double *ga, *gb;        // [kMaxFitParts][cap][n_e^2][n_alpha] per-part likelihood sums
+    double *ga, *gb;        // [fit_parts][cap][n_e^2][n_alpha] per-part likelihood sums
     size_t part_stride;     // cap * n_e^2 * n_alpha
+    int32_t fit_parts;      // cell parts per facet the grids hold (kMaxFitParts; 16 when cap <= 16)
     double *gl;             // [cap][n_e^2][n_alpha]
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
@@ -224,7 +225,9 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st);
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st,
-                       int32_t blocks_per_sm = 0);
+                       int32_t blocks_per_sm = 0, float sign = 1.0f);
+// out = a - b over n4 float4 (the residual D - V, or the sky model D - R)
+cudaError_t launch_difference(const float *a, const float *b, int64_t n_complex, float *out, cudaStream_t st);
 // Per call, before the extraction batches: each baseline's smallest uv extent over
 // time, the baselines ordered by it, and (split-phase mode) the split baselines in
 // that order.

@@ -99,7 +99,7 @@ template <int CG, bool kUpdate, bool kUniform, bool kSplit, bool kGauss>
 __global__ void __launch_bounds__(kThreads)
 sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                  const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
-                 const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis)
+                 const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis, float sign)
 {
     __shared__ SkySrc sm[kSkyTile];
     const int C = ch.n;
@@ -224,17 +224,37 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
             }
         }
         if (act) {
+            // channel pairs as one 16-byte access when the layout allows (even channel
+            // count: a pair starts on an even complex index); the update adds sign * terms
+            if (CG >= 2 && C % 2 == 0) {
 #pragma unroll
-            for (int c = 0; c < CG; ++c) {
-                const int k = k0 + c;
-                if (k < C) {
-                    float2 o = make_float2(are[c] * spec[c], aim[c] * spec[c]);
-                    if (kUpdate) {
-                        const float2 p = vis[r * C + k];
-                        o.x += p.x;
-                        o.y += p.y;
+                for (int c = 0; c < CG; c += 2) {
+                    const int k = k0 + c;
+                    if (k < C) {
+                        float4 o = make_float4(are[c] * spec[c], aim[c] * spec[c], are[c + 1] * spec[c + 1],
+                                               aim[c + 1] * spec[c + 1]);
+                        float4 *dst = reinterpret_cast<float4 *>(vis + (r * C + k));
+                        if (kUpdate) {
+                            const float4 p = *dst;
+                            o = make_float4(fmaf(sign, o.x, p.x), fmaf(sign, o.y, p.y), fmaf(sign, o.z, p.z),
+                                            fmaf(sign, o.w, p.w));
+                        }
+                        *dst = o;
                     }
-                    vis[r * C + k] = o;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    const int k = k0 + c;
+                    if (k < C) {
+                        float2 o = make_float2(are[c] * spec[c], aim[c] * spec[c]);
+                        if (kUpdate) {
+                            const float2 p = vis[r * C + k];
+                            o.x = fmaf(sign, o.x, p.x);
+                            o.y = fmaf(sign, o.y, p.y);
+                        }
+                        vis[r * C + k] = o;
+                    }
                 }
             }
         }
@@ -246,7 +266,7 @@ template <bool kUpdate>
 __global__ void __launch_bounds__(kThreads)
 sky_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
                 const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
-                const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis)
+                const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis, double sign)
 {
     __shared__ SrcRow sm[kSkyTile / 2];
     constexpr int kTile = kSkyTile / 2;
@@ -286,8 +306,8 @@ sky_fp64_kernel(const double *__restrict__ u, const double *__restrict__ v,
             float2 out = make_float2((float)(are * sp), (float)(aim * sp));
             if (kUpdate) {
                 const float2 p = vis[o];
-                out.x = (float)((double)p.x + are * sp);
-                out.y = (float)((double)p.y + aim * sp);
+                out.x = (float)((double)p.x + sign * are * sp);
+                out.y = (float)((double)p.y + sign * aim * sp);
             }
             vis[o] = out;
         }
@@ -308,7 +328,7 @@ int sm_count()
 
 template <int CG, bool kUpdate, bool kSplit>
 void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                  float *vis, int blocks_per_sm, cudaStream_t st)
+                  float *vis, int blocks_per_sm, float sign, cudaStream_t st)
 {
     const int n_groups = (ch.n + CG - 1) / CG;
     const int lanes = kThreads / n_groups;
@@ -319,26 +339,26 @@ void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, 
     const bool gauss = ch.profile == RLF_PROFILE_GAUSSIAN;
     if (ch.uniform && !gauss)
         sky_mixed_kernel<CG, kUpdate, true, kSplit, false><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
     else if (ch.uniform)
         sky_mixed_kernel<CG, kUpdate, true, kSplit, true><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
     else if (!gauss)
         sky_mixed_kernel<CG, kUpdate, false, kSplit, false><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
     else
         sky_mixed_kernel<CG, kUpdate, false, kSplit, true><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out);
+            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
 }
 
 template <bool kUpdate, bool kSplit>
 void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table,
-                     int32_t n_src, float *vis, int bps, cudaStream_t st)
+                     int32_t n_src, float *vis, int bps, float sign, cudaStream_t st)
 {
-    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
-    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
-    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
-    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, st);
+    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
+    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
+    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
+    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
 }
 
 }  // namespace
@@ -357,15 +377,16 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
 }
 
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                       bool update, int32_t precision, float *vis, cudaStream_t st, int32_t blocks_per_sm)
+                       bool update, int32_t precision, float *vis, cudaStream_t st, int32_t blocks_per_sm,
+                       float sign)
 {
     const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
     if (precision == RLF_PREC_MIXED) {
-        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, bps, st);
-        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, bps, st);
+        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, bps, sign, st);
+        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, bps, 1.0f, st);
     } else if (precision == RLF_PREC_MIXED_SPLIT) {
-        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, bps, st);
-        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, bps, st);
+        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, bps, sign, st);
+        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, bps, 1.0f, st);
     } else {
         const int64_t n_out = uvw.n_rows * ch.n;
         const int64_t need = (n_out + kThreads - 1) / kThreads;
@@ -373,10 +394,10 @@ cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *ta
         const int grid = (int)(need < cap ? need : cap);
         if (update)
             sky_fp64_kernel<true><<<grid, kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table,
-                                                             n_src, reinterpret_cast<float2 *>(vis));
+                                                             n_src, reinterpret_cast<float2 *>(vis), (double)sign);
         else
             sky_fp64_kernel<false><<<grid, kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table,
-                                                              n_src, reinterpret_cast<float2 *>(vis));
+                                                              n_src, reinterpret_cast<float2 *>(vis), 1.0);
     }
     return cudaGetLastError();
 }
