@@ -32,8 +32,9 @@ _LIB_PATH = os.path.join(_BUILD, "librlf_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NEST = 13
-E1, E2, SIG1, SIG2, ALPHA, FLUX, FLAG, E1_SMOOTH, E2_SMOOTH, LOGL_MAX, THRESH_MARGIN, MAP_INDEX, NC = range(NEST)
+NEST = 16
+(E1, E2, SIG1, SIG2, ALPHA, FLUX, FLAG, E1_SMOOTH, E2_SMOOTH, LOGL_MAX, THRESH_MARGIN, MAP_INDEX, NC,
+ LEVELS, STEP, NKEPT) = range(NEST)
 C_LIGHT = 299792458.0
 ARCSEC = np.pi / 648000.0
 
@@ -60,14 +61,16 @@ class Params(ctypes.Structure):
                 ("thresh_frac", ctypes.c_double), ("var_sigma_min", ctypes.c_double),
                 ("var_det_min", ctypes.c_double), ("facet_n", ctypes.c_int32), ("n_e", ctypes.c_int32),
                 ("n_alpha", ctypes.c_int32), ("flux_prior", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("update_mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("update_mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("e_res", ctypes.c_double), ("np_max", ctypes.c_int32), ("estimator", ctypes.c_int32)]
 
 
 def default_params(**kw) -> Params:
     p = Params(add=-0.93, esp=0.33, psf_nat=38.0, beta=-0.7, nu_ref_hz=1.0e9, sigma_jy=1e-6,
                e_max=0.8, r_min_arcsec=0.3, r_max_arcsec=3.5, r_std=0.3136,
                thresh_frac=0.05, var_sigma_min=5e-3, var_det_min=5e-5,
-               facet_n=64, n_e=21, n_alpha=20, flux_prior=0, chunk=0, update_mode=0, profile=0, pad=0)
+               facet_n=64, n_e=21, n_alpha=20, flux_prior=0, chunk=0, update_mode=0, profile=0, pad=0,
+               e_res=0.003, np_max=30, estimator=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -100,6 +103,8 @@ def lib():
             L.rlfo_grid_e.argtypes = [vp, ctypes.c_int]
             L.rlfo_grid_alpha.restype = d
             L.rlfo_grid_alpha.argtypes = [vp, ctypes.c_int]
+            L.rlfo_fit_facet_adaptive.restype = None
+            L.rlfo_fit_facet_adaptive.argtypes = [vp, d, d, vp, vp]
             L.rlfo_fit_facet.restype = None
             L.rlfo_fit_facet.argtypes = [vp, d, d, vp, vp, vp, vp, vp]
             L.rlfo_like_grid.restype = ctypes.c_int
@@ -198,6 +203,15 @@ class Fit:
     a: np.ndarray
     b: np.ndarray
     est: np.ndarray       # [NEST]
+
+
+def fit_facet_adaptive(acc, du, flux_cat, params: Params) -> np.ndarray:
+    """Estimate of one facet by adaptive sampling around the maximum (Sec. 2.4):
+    the fixed grid, then halved lattices around the kept samples until np_max of
+    them or a step of e_res.  Returns est [NEST] (LEVELS, STEP, NKEPT filled)."""
+    est = np.zeros(NEST)
+    lib().rlfo_fit_facet_adaptive(_p(_f64(acc)), du, flux_cat, ctypes.byref(params), _p(est))
+    return est
 
 
 def fit_facet(acc, du, flux_cat, params: Params) -> Fit:

@@ -35,7 +35,7 @@
 enum {
     RLFO_E1 = 0, RLFO_E2, RLFO_SIG1, RLFO_SIG2, RLFO_ALPHA, RLFO_FLUX, RLFO_FLAG,
     RLFO_E1_SMOOTH, RLFO_E2_SMOOTH, RLFO_LOGL_MAX, RLFO_THRESH_MARGIN, RLFO_MAP_INDEX,
-    RLFO_NC, RLFO_NEST
+    RLFO_NC, RLFO_LEVELS, RLFO_STEP, RLFO_NKEPT, RLFO_NEST
 };
 
 typedef struct {
@@ -45,6 +45,9 @@ typedef struct {
     int32_t facet_n, n_e, n_alpha, flux_prior; /* flux_prior 0: S in [0, inf); 1: real line */
     int32_t chunk, update_mode;                /* update_mode 0: good fits only; 1: all */
     int32_t profile, pad;                      /* 0: exponential (Eq. 1); 1: Gaussian of equal FWHM */
+    double e_res;                              /* adaptive sampling: finest step in e (E_RES) */
+    int32_t np_max;                            /* adaptive sampling: samples above threshold wanted (NP_MAX) */
+    int32_t estimator;                         /* 0: the fixed grid; 1: adaptive sampling around the maximum */
 } rlfo_params;
 
 int rlfo_nest(void) { return RLFO_NEST; }
@@ -412,7 +415,249 @@ void rlfo_estimate(const double *loglike, const double *a_out, const double *b_o
     est[RLFO_THRESH_MARGIN] = margin;
     est[RLFO_MAP_INDEX] = (double)gmap;
     est[RLFO_NC] = (double)ncell;
+    est[RLFO_LEVELS] = 0.0;
+    est[RLFO_STEP] = 2.0 * p->e_max / (ne - 1);
+    est[RLFO_NKEPT] = 0.0;
+    for (int e = 0; e < ne * ne; ++e)
+        if (Le[e] > 0.0 && Le[e] >= p->thresh_frac * Lmax) est[RLFO_NKEPT] += 1.0;
     free(qp); free(Le); free(Ae);
+}
+
+/*
+ * Adaptive sampling of the alpha-marginal likelihood L(e) around its maximum
+ * (Sec. 2.4), read as successive lattices: level 0 is the fixed grid (step h0 =
+ * 2 e_max / (n_e - 1)); while fewer than np_max samples lie at or above
+ * thresh_frac of the level's maximum and the step is above e_res, the step is
+ * halved and L(e) is sampled at every multiple of the new step in the box spanned
+ * by the kept samples, widened by the previous step (points with |e| >= 1
+ * skipped; at most 17 per component, centred on the level's MAP sample).  The
+ * estimate is the last level's: the same threshold moments, MAP flux and bad-fit
+ * cut as the grid estimate, over its samples.  est[RLFO_LEVELS] = refinements
+ * made, est[RLFO_STEP] = last step, est[RLFO_NKEPT] = samples kept.
+ */
+typedef struct {
+    int ncell;
+    double cc;
+    double *cu, *cv, *cw, *cs, *cd;
+} rlfo_cells;
+
+static void cells_of_facet(const double *acc, double du, const rlfo_params *p, rlfo_cells *C)
+{
+    const int N = p->facet_n;
+    const int64_t nc = (int64_t)N * N;
+    const double sig2 = p->sigma_jy * p->sigma_jy;
+    C->cu = malloc(sizeof(double) * nc);
+    C->cv = malloc(sizeof(double) * nc);
+    C->cw = malloc(sizeof(double) * nc);
+    C->cs = malloc(sizeof(double) * nc);
+    C->cd = malloc(sizeof(double) * nc);
+    C->ncell = 0;
+    C->cc = 0.0;
+    for (int iv = 0; iv < N; ++iv)
+        for (int iu = 0; iu < N; ++iu) {
+            int64_t cell = (int64_t)iv * N + iu;
+            double n = acc[2 * nc + cell];
+            if (n <= 0.0) continue;
+            double dr = acc[cell] / n, di = acc[nc + cell] / n;
+            int c = C->ncell++;
+            C->cu[c] = (iu - N / 2 + 0.5) * du;
+            C->cv[c] = (iv - N / 2 + 0.5) * du;
+            C->cw[c] = n / sig2;
+            C->cs[c] = acc[3 * nc + cell] / n;
+            C->cd[c] = dr;
+            C->cc += C->cw[c] * (dr * dr + di * di);
+        }
+}
+
+static void free_cells(rlfo_cells *C)
+{
+    free(C->cu); free(C->cv); free(C->cw); free(C->cs); free(C->cd);
+}
+
+/* loglike, a, b of every (sample, alpha node) pair: [np][n_alpha] */
+static void sample_likelihood(const rlfo_cells *C, const double *e1s, const double *e2s, int np,
+                              const rlfo_params *p, double *loglike, double *a_out, double *b_out)
+{
+    const int na = p->n_alpha;
+    for (int i = 0; i < np; ++i)
+        for (int k = 0; k < na; ++k) {
+            int64_t g = (int64_t)i * na + k;
+            if (!(e1s[i] * e1s[i] + e2s[i] * e2s[i] < 1.0) || C->ncell == 0) {
+                loglike[g] = -INFINITY;
+                a_out[g] = b_out[g] = 0.0;
+                continue;
+            }
+            double al = rlfo_grid_alpha(p, k) * RLFO_ARCSEC;
+            double a = 0.0, b = 0.0;
+            for (int c = 0; c < C->ncell; ++c) {
+                double M = rlfo_shape(C->cu[c], C->cv[c], al, e1s[i], e2s[i], p->profile);
+                a += C->cw[c] * C->cs[c] * C->cs[c] * M * M;
+                b += C->cw[c] * C->cs[c] * M * C->cd[c];
+            }
+            a_out[g] = a;
+            b_out[g] = b;
+            loglike[g] = rlfo_flux_marginal(a, b, C->cc, p->flux_prior);
+        }
+}
+
+/*
+ * The estimate of Sec. 2.4 over an explicit list of e samples (the grid estimate
+ * restated for any sample set): alpha marginal, threshold moments, MAP sample
+ * (logL + ln p(alpha), ties to the lowest (sample, alpha) index), bad-fit cut.
+ * Also returns the number of kept samples, the box they span and the MAP sample.
+ */
+static void estimate_samples(const double *e1s, const double *e2s, int np, const double *loglike,
+                             const double *a_out, const double *b_out, double flux_cat, int ncell,
+                             const rlfo_params *p, double *est, int *n_kept, double box[4], int *map_sample)
+{
+    const int na = p->n_alpha;
+    double lmax = -INFINITY;
+    for (int64_t g = 0; g < (int64_t)np * na; ++g)
+        if (loglike[g] > lmax) lmax = loglike[g];
+    double mu = p->add + p->esp * log(flux_cat * 1.0e6);
+    double *Le = malloc(sizeof(double) * np), *Ae = malloc(sizeof(double) * np);
+    double Lmax = 0.0;
+    for (int i = 0; i < np; ++i) {
+        double sL = 0.0, sA = 0.0;
+        for (int k = 0; k < na; ++k) {
+            double lg = loglike[(int64_t)i * na + k];
+            if (lg == -INFINITY) continue;
+            double t = rlfo_alpha_weight(p, flux_cat, k) * exp(lg - lmax);
+            sL += t;
+            sA += t * rlfo_grid_alpha(p, k);
+        }
+        Le[i] = sL;
+        Ae[i] = sA;
+        if (sL > Lmax) Lmax = sL;
+    }
+    double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0, margin = INFINITY;
+    int kept = 0;
+    box[0] = box[2] = INFINITY;
+    box[1] = box[3] = -INFINITY;
+    for (int i = 0; i < np; ++i) {
+        if (!(Le[i] > 0.0)) continue;
+        Ws += Le[i];
+        s1 += Le[i] * e1s[i];
+        s2 += Le[i] * e2s[i];
+        double dm = fabs(log(Le[i] / Lmax) - log(p->thresh_frac));
+        if (dm < margin) margin = dm;
+        if (Le[i] >= p->thresh_frac * Lmax) {
+            ++kept;
+            W += Le[i];
+            m1 += Le[i] * e1s[i];
+            m2 += Le[i] * e2s[i];
+            WA += Ae[i];
+            if (e1s[i] < box[0]) box[0] = e1s[i];
+            if (e1s[i] > box[1]) box[1] = e1s[i];
+            if (e2s[i] < box[2]) box[2] = e2s[i];
+            if (e2s[i] > box[3]) box[3] = e2s[i];
+        }
+    }
+    double e1m = 0, e2m = 0, c11 = 0, c22 = 0, c12 = 0, am = 0;
+    if (W > 0) {
+        e1m = m1 / W;
+        e2m = m2 / W;
+        am = WA / W;
+        for (int i = 0; i < np; ++i) {
+            if (!(Le[i] > 0.0) || Le[i] < p->thresh_frac * Lmax) continue;
+            double d1 = e1s[i] - e1m, d2 = e2s[i] - e2m;
+            c11 += Le[i] * d1 * d1;
+            c22 += Le[i] * d2 * d2;
+            c12 += Le[i] * d1 * d2;
+        }
+        c11 /= W;
+        c22 /= W;
+        c12 /= W;
+    }
+    int64_t gmap = -1;
+    double best = -INFINITY;
+    for (int64_t g = 0; g < (int64_t)np * na; ++g) {
+        if (loglike[g] == -INFINITY) continue;
+        double ak = rlfo_grid_alpha(p, (int)(g % na));
+        double z = (log(ak) - mu) / p->r_std;
+        double lp = loglike[g] - 0.5 * z * z - log(ak);
+        if (lp > best) {
+            best = lp;
+            gmap = g;
+        }
+    }
+    double s1d = sqrt(c11), s2d = sqrt(c22);
+    double det = c11 * c22 - c12 * c12;
+    double sdet = det > 0 ? sqrt(det) : 0.0;
+    int bad = (W <= 0) || (s1d <= p->var_sigma_min) || (s2d <= p->var_sigma_min) || (sdet <= p->var_det_min);
+    est[RLFO_E1] = e1m;
+    est[RLFO_E2] = e2m;
+    est[RLFO_SIG1] = s1d;
+    est[RLFO_SIG2] = s2d;
+    est[RLFO_ALPHA] = am;
+    est[RLFO_FLUX] = (gmap >= 0 && a_out[gmap] > 0) ? b_out[gmap] / a_out[gmap] : 0.0;
+    est[RLFO_FLAG] = bad ? 1.0 : 0.0;
+    est[RLFO_E1_SMOOTH] = Ws > 0 ? s1 / Ws : 0.0;
+    est[RLFO_E2_SMOOTH] = Ws > 0 ? s2 / Ws : 0.0;
+    est[RLFO_LOGL_MAX] = lmax;
+    est[RLFO_THRESH_MARGIN] = margin;
+    est[RLFO_MAP_INDEX] = (double)gmap;
+    est[RLFO_NC] = (double)ncell;
+    *n_kept = kept;
+    *map_sample = gmap >= 0 ? (int)(gmap / na) : -1;
+    free(Le);
+    free(Ae);
+}
+
+void rlfo_fit_facet_adaptive(const double *acc, double du, double flux_cat, const rlfo_params *p, double *est)
+{
+    const int ne = p->n_e, na = p->n_alpha;
+    const int kMaxSide = 17;
+    rlfo_cells C;
+    cells_of_facet(acc, du, p, &C);
+    /* level 0: the fixed grid, samples in grid order (e1 outer, e2 inner) */
+    int np = ne * ne;
+    int cap = kMaxSide * kMaxSide > np ? kMaxSide * kMaxSide : np;
+    double *e1s = malloc(sizeof(double) * cap), *e2s = malloc(sizeof(double) * cap);
+    double *lg = malloc(sizeof(double) * cap * na), *ga = malloc(sizeof(double) * cap * na);
+    double *gb = malloc(sizeof(double) * cap * na);
+    for (int i1 = 0; i1 < ne; ++i1)
+        for (int i2 = 0; i2 < ne; ++i2) {
+            e1s[i1 * ne + i2] = rlfo_grid_e(p, i1);
+            e2s[i1 * ne + i2] = rlfo_grid_e(p, i2);
+        }
+    double h = 2.0 * p->e_max / (ne - 1);
+    int level = 0, kept = 0, map_i = -1;
+    double box[4];
+    for (;;) {
+        sample_likelihood(&C, e1s, e2s, np, p, lg, ga, gb);
+        estimate_samples(e1s, e2s, np, lg, ga, gb, flux_cat, C.ncell, p, est, &kept, box, &map_i);
+        if (p->estimator != 1 || kept >= p->np_max || h <= p->e_res || map_i < 0) break;
+        /* the next lattice: multiples of h/2 in the kept box widened by h */
+        double hn = 0.5 * h;
+        int lo[2], hi[2];
+        double cen[2] = {e1s[map_i], e2s[map_i]};
+        for (int d = 0; d < 2; ++d) {
+            lo[d] = (int)ceil((box[2 * d] - h) / hn - 1e-9);
+            hi[d] = (int)floor((box[2 * d + 1] + h) / hn + 1e-9);
+            if (hi[d] - lo[d] + 1 > kMaxSide) {
+                int c = (int)llround(cen[d] / hn);
+                lo[d] = c - kMaxSide / 2;
+                hi[d] = c + kMaxSide / 2;
+            }
+        }
+        np = 0;
+        for (int i1 = lo[0]; i1 <= hi[0]; ++i1)
+            for (int i2 = lo[1]; i2 <= hi[1]; ++i2) {
+                double a1 = i1 * hn, a2 = i2 * hn;
+                if (!(a1 * a1 + a2 * a2 < 1.0)) continue;
+                e1s[np] = a1;
+                e2s[np] = a2;
+                ++np;
+            }
+        h = hn;
+        ++level;
+    }
+    est[RLFO_LEVELS] = level;
+    est[RLFO_STEP] = h;
+    est[RLFO_NKEPT] = kept;
+    free(e1s); free(e2s); free(lg); free(ga); free(gb);
+    free_cells(&C);
 }
 
 /* likelihood grid followed by the estimate */
@@ -473,7 +718,10 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
             rlfo_extract_facet(n_rows, n_chan, u, v, w, freq, data, NULL, sky, l[i], m[i], flux[i],
                                alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, du,
                                p->facet_n, acc, NULL);
-            rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, est + (int64_t)i * RLFO_NEST);
+            if (p->estimator == 1)
+                rlfo_fit_facet_adaptive(acc, du, flux[i], p, est + (int64_t)i * RLFO_NEST);
+            else
+                rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, est + (int64_t)i * RLFO_NEST);
             free(acc);
             free(lg);
         }

@@ -446,3 +446,70 @@ def test_gaussian_sheared_image_fourier_transform(pixel_grid):
         for ku, kv in ((0.05, 0.0), (0.0, 0.12), (0.1, 0.07), (0.25, -0.15)):
             F = (f * np.cos(2 * np.pi * (ku * X + kv * Y))).sum() * h * h
             assert abs(F - oracle.shape(ku, kv, 1.0, e1, e2, 1)) < 1e-9, (e1, e2, ku, kv)
+
+
+# ---- adaptive sampling around the maximum (Sec. 2.4) ----------------------------------
+
+def test_adaptive_sampling_stops_at_the_grid_when_it_has_enough_samples():
+    # np_max = 0: the fixed grid already holds enough samples above the threshold, so the
+    # adaptive estimate is the grid estimate itself
+    wl = synth.tiny(seed=31, n_src=1, n_ant=24, n_time=24, n_chan=2, r_max_m=1500.0)
+    obs, cat = synth.make_observation(wl), synth.make_catalogue(wl)
+    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=3e-5)
+    al = oracle.alpha_med(cat.flux_jy[0]) * ARC
+    d = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, np.array([al]), cat.e1,
+                         cat.e2, nu_ref=wl.nu_ref_hz)
+    d2 = (np.stack([d.real, d.imag], -1) + synth.noise(obs.n_rows, obs.n_chan, 3e-5, 5)).astype(np.float32)
+    du = oracle.facet_du(cat.flux_jy[0], 0.0, p)
+    acc = oracle.extract_facet(obs.u, obs.v, obs.w, obs.freq_hz, d2, np.zeros_like(d2), cat.l[0], cat.m[0],
+                               cat.flux_jy[0], al, 0.0, 0.0, du, p)
+    grid = oracle.fit_facet(acc, du, cat.flux_jy[0], p).est
+    p.estimator, p.np_max = 1, 0
+    ad = oracle.fit_facet_adaptive(acc, du, cat.flux_jy[0], p)
+    assert ad[oracle.LEVELS] == 0 and ad[oracle.STEP] == pytest.approx(0.08)
+    for f in range(oracle.NC + 1):
+        assert ad[f] == grid[f], f
+
+
+def test_adaptive_sampling_resolves_an_off_grid_source():
+    # a noise-free source sampled at cell centres whose shape lies between grid nodes: the
+    # fixed grid can only return nodes, the adaptive lattices close in on the true shape
+    N, nu = 16, 1.0e9
+    p = oracle.default_params(facet_n=N, nu_ref_hz=nu, sigma_jy=1e-7)
+    ga = oracle.grid_alpha(p)
+    flux = 1.2e-4
+    du = oracle.facet_du(flux, 0.0, p)
+    rng = np.random.default_rng(19)
+    iuv = sorted({(int(a), int(b)) for a, b in rng.integers(1, N - 1, size=(90, 2))})
+    u, v, w = _cell_centre_observation(N, du, nu, iuv)
+    l, m = 1.1e-3, 0.4e-3
+    e1, e2, al = 0.123, -0.057, ga[6] * ARC
+    data = np.array([[oracle.model_vis(u[r], v[r], w[r], nu, l, m, flux, al, e1, e2, -0.7, nu)] for r in range(len(u))])
+    d2 = np.stack([data.real, data.imag], -1)
+    # the sky model holds the source at its current shape, so the facet holds its model alone
+    acc = oracle.extract_facet(u, v, w, np.array([nu]), d2.astype(np.float32), d2, l, m, flux, al,
+                               e1, e2, du, p)
+    grid = oracle.fit_facet(acc, du, flux, p).est
+    assert max(abs(grid[oracle.E1] - e1), abs(grid[oracle.E2] - e2)) > 0.01
+    p.estimator = 1
+    ad = oracle.fit_facet_adaptive(acc, du, flux, p)
+    assert ad[oracle.LEVELS] >= 1
+    assert ad[oracle.STEP] == pytest.approx(0.08 / 2 ** ad[oracle.LEVELS])
+    assert ad[oracle.NKEPT] >= p.np_max or ad[oracle.STEP] <= p.e_res          # the stopping rule
+    assert abs(ad[oracle.E1] - e1) < p.e_res and abs(ad[oracle.E2] - e2) < p.e_res
+    assert abs(ad[oracle.FLUX] / flux - 1) < 1e-2
+
+
+def test_adaptive_sampling_of_a_resolved_posterior_stops_early():
+    # a broad posterior (low SNR) keeps more than np_max grid samples above the threshold:
+    # no refinement
+    wl = synth.tiny(seed=33, n_src=1, n_ant=24, n_time=24, n_chan=2, r_max_m=1500.0)
+    obs, cat = synth.make_observation(wl), synth.make_catalogue(wl)
+    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=5e-4, estimator=1)
+    al = oracle.alpha_med(cat.flux_jy[0]) * ARC
+    d2 = synth.noise(obs.n_rows, obs.n_chan, 5e-4, 8).astype(np.float32)
+    du = oracle.facet_du(cat.flux_jy[0], 0.0, p)
+    acc = oracle.extract_facet(obs.u, obs.v, obs.w, obs.freq_hz, d2, np.zeros_like(d2), cat.l[0], cat.m[0],
+                               cat.flux_jy[0], al, 0.0, 0.0, du, p)
+    ad = oracle.fit_facet_adaptive(acc, du, cat.flux_jy[0], p)
+    assert ad[oracle.LEVELS] == 0 and ad[oracle.NKEPT] >= p.np_max
