@@ -62,6 +62,16 @@ enum {
                               at its FP32 rate instead of its much lower FP64 rate */
 };
 
+/* estimator of the ellipticity from the likelihood (Sec. 2.4) */
+enum {
+    RLF_ESTIMATOR_GRID = 0,      /* threshold moments over the fixed (e1, e2) grid */
+    RLF_ESTIMATOR_ADAPTIVE = 1   /* then, while fewer than np_max samples are kept, halved lattices
+                                    around the kept samples down to a step of e_res; the
+                                    estimate is the last lattice's.  The number of halvings is
+                                    returned in bits 8-11 of the fit flag. */
+};
+#define RLF_FLAG_LEVELS_SHIFT 8
+
 /* source brightness profile (Sec. 2.2 and its footnote); alpha keeps its meaning (grid,
    Eq. 4 prior, facet cell size) under both */
 enum {
@@ -144,6 +154,12 @@ typedef struct {
     int32_t tune_sky_blocks;    /* CTAs per SM of the sky-model kernels (default 8) */
     int32_t profile;         /* source brightness profile: RLF_PROFILE_EXPONENTIAL (Eq. 1, the
                                 default) or RLF_PROFILE_GAUSSIAN (footnote to Sec. 2.2) */
+    double e_res;            /* adaptive sampling: finest step in e, E_RES (0.003, Sec. 2.4) */
+    int32_t np_max;          /* adaptive sampling: kept samples that end it, NP_MAX (30, Sec. 2.4) */
+    int32_t estimator;       /* RLF_ESTIMATOR_GRID (default) or RLF_ESTIMATOR_ADAPTIVE */
+    int32_t refit_bad;       /* rlf_run: 1 = fit the bad fits again after every other source,
+                                against the final sky model (Sec. 2.4) */
+    int32_t reserved;
 } rlf_params;
 
 /* Per-source results, each a device array of `count` entries. */

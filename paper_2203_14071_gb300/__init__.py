@@ -27,6 +27,8 @@ HEADER = os.path.join(INCLUDE, "rlf.h")
 RLF_OK, RLF_EINVAL, RLF_ECUDA, RLF_ENOSPACE, RLF_ETIMEOUT, RLF_ENUMERIC, RLF_EUNSUPPORTED = range(7)
 PREC_FP64, PREC_MIXED, PREC_MIXED_SPLIT = 0, 1, 2
 PROFILE_EXPONENTIAL, PROFILE_GAUSSIAN = 0, 1
+ESTIMATOR_GRID, ESTIMATOR_ADAPTIVE = 0, 1
+FLAG_LEVELS_SHIFT = 8
 FLAG_BAD, FLAG_INVALID, FLAG_EMPTY = 1, 2, 4
 DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
 WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
@@ -63,7 +65,8 @@ class Params(ctypes.Structure):
                 ("update_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tune_fit_ag", ctypes.c_int32), ("tune_fit_blocks", ctypes.c_int32),
                 ("tune_extract_waves", ctypes.c_int32), ("tune_sky_blocks", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("e_res", ctypes.c_double), ("np_max", ctypes.c_int32),
+                ("estimator", ctypes.c_int32), ("refit_bad", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Peaks(ctypes.Structure):

@@ -31,6 +31,10 @@ bool params_ok(const rlf_params &p)
     if (p.flux_prior != 0 && p.flux_prior != 1) return false;
     if (p.update_mode != 0 && p.update_mode != 1) return false;
     if (p.profile != RLF_PROFILE_EXPONENTIAL && p.profile != RLF_PROFILE_GAUSSIAN) return false;
+    if (p.estimator != RLF_ESTIMATOR_GRID && p.estimator != RLF_ESTIMATOR_ADAPTIVE) return false;
+    if (p.estimator == RLF_ESTIMATOR_ADAPTIVE && !(p.np_max >= 1 && p.e_res > 0 && std::isfinite(p.e_res)))
+        return false;
+    if (p.refit_bad != 0 && p.refit_bad != 1) return false;
     if (p.tune_fit_ag != 0 && p.tune_fit_ag != 2 && p.tune_fit_ag != 4 && p.tune_fit_ag != 8) return false;
     if (p.tune_fit_blocks < 0 || p.tune_extract_waves < 0 || p.tune_sky_blocks < 0) return false;
     return true;
@@ -127,6 +131,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_ga = take(fit ? fit_parts * cap * ng * sizeof(double) : 0);
     const size_t o_gb = take(fit ? fit_parts * cap * ng * sizeof(double) : 0);
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
+    const bool adapt = fit && p.estimator == RLF_ESTIMATOR_ADAPTIVE;
+    const size_t o_ad = take(adapt ? cap * 289 * (size_t)p.n_alpha * 3 * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
     const bool ext = which == RLF_WS_EXTRACT || run;
@@ -160,6 +166,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->part_stride = cap * ng;
         ws->fit_parts = (int32_t)fit_parts;
         ws->gl = reinterpret_cast<double *>(b + o_gl);
+        ws->adapt = reinterpret_cast<double *>(b + o_ad);
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
         ws->facets = reinterpret_cast<double *>(b + o_fac);
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
@@ -204,6 +211,9 @@ void rlf_params_default(rlf_params *p)
     p->chunk = 0;
     p->update_mode = 0;
     p->precision = RLF_PREC_MIXED;
+    p->e_res = 0.003;
+    p->np_max = 30;
+    p->estimator = RLF_ESTIMATOR_GRID;
 }
 
 size_t rlf_workspace_size(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params *p,

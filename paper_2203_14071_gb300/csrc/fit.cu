@@ -603,6 +603,289 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
     }
 }
 
+// ---- adaptive sampling around the maximum (Sec. 2.4) ---------------------------------
+// After the grid fit: one CTA per facet.  Level 0 is the grid (its log-likelihood
+// grid gl and sums ga, gb); while fewer than np_max samples of the alpha marginal
+// L(e) lie at or above thresh_frac of its maximum and the step exceeds e_res, the
+// step is halved and every multiple of it in the box of the kept samples, widened by
+// the previous step, is sampled (|e| < 1, at most 17 per component around the MAP
+// sample).  The estimate is the last level's, by the rules of the grid estimate.
+constexpr int kAdaptSide = 17, kAdaptMax = kAdaptSide * kAdaptSide;
+
+struct AdaptResult {
+    double e1m, e2m, sd1, sd2, am, flux, e1s, e2s;
+    int bad, kept, map_i;
+    double box[4];
+};
+
+// block-wide estimate over np samples (e of sample i: grid node i / n_e, i % n_e when
+// e1s is null); lg, a, b are [np][n_alpha]
+__device__ void estimate_over_samples(bool mixed, int np, const double *e1s, const double *e2s,
+                                      const double *__restrict__ lg, const double *__restrict__ a,
+                                      const double *__restrict__ b, const GridConst &gc, const double *qp,
+                                      const double *alph, const double *lnp, double *Ls, double *As,
+                                      AdaptResult &res)
+{
+    __shared__ double red[kThreads / 32];
+    __shared__ long long redi[kThreads / 32];
+    const int na = gc.n_alpha, ne = gc.n_e;
+    const long long npa = (long long)np * na;
+    auto e1_of = [&](int i) { return e1s ? e1s[i] : grid_e(gc, i / ne); };
+    auto e2_of = [&](int i) { return e2s ? e2s[i] : grid_e(gc, i % ne); };
+    double lmax = -INFINITY;
+    for (long long g = threadIdx.x; g < npa; g += kThreads) lmax = fmax(lmax, lg[g]);
+    lmax = block_max(lmax, red);
+    __syncthreads();
+    double Lm = 0.0;
+    for (int i = threadIdx.x; i < np; i += kThreads) {
+        double sL = 0.0, sA = 0.0;
+        for (int k = 0; k < na; ++k) {
+            const double v = lg[(size_t)i * na + k];
+            if (v == -INFINITY) continue;
+            const double t = qp[k] * (mixed ? (double)expf((float)(v - lmax)) : exp(v - lmax));
+            sL += t;
+            sA += t * alph[k];
+        }
+        Ls[i] = sL;
+        As[i] = sA;
+        Lm = fmax(Lm, sL);
+    }
+    const double Lmax = block_max(Lm, red);
+    __syncthreads();
+    double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0, kept = 0;
+    double lo1 = INFINITY, hi1 = -INFINITY, lo2 = INFINITY, hi2 = -INFINITY;
+    for (int i = threadIdx.x; i < np; i += kThreads) {
+        const double L = Ls[i];
+        if (!(L > 0.0)) continue;
+        const double e1 = e1_of(i), e2 = e2_of(i);
+        Ws += L;
+        s1 += L * e1;
+        s2 += L * e2;
+        if (L >= gc.thresh_frac * Lmax) {
+            kept += 1.0;
+            W += L;
+            m1 += L * e1;
+            m2 += L * e2;
+            WA += As[i];
+            lo1 = fmin(lo1, e1);
+            hi1 = fmax(hi1, e1);
+            lo2 = fmin(lo2, e2);
+            hi2 = fmax(hi2, e2);
+        }
+    }
+    W = block_sum(W, red);
+    m1 = block_sum(m1, red);
+    m2 = block_sum(m2, red);
+    WA = block_sum(WA, red);
+    Ws = block_sum(Ws, red);
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    kept = block_sum(kept, red);
+    lo1 = -block_max(-lo1, red);
+    hi1 = block_max(hi1, red);
+    lo2 = -block_max(-lo2, red);
+    hi2 = block_max(hi2, red);
+    const double e1m = W > 0 ? m1 / W : 0.0, e2m = W > 0 ? m2 / W : 0.0;
+    double c11 = 0, c22 = 0, c12 = 0;
+    for (int i = threadIdx.x; i < np; i += kThreads) {
+        const double L = Ls[i];
+        if (!(L > 0.0) || L < gc.thresh_frac * Lmax) continue;
+        const double d1 = e1_of(i) - e1m, d2 = e2_of(i) - e2m;
+        c11 += L * d1 * d1;
+        c22 += L * d2 * d2;
+        c12 += L * d1 * d2;
+    }
+    c11 = block_sum(c11, red);
+    c22 = block_sum(c22, red);
+    c12 = block_sum(c12, red);
+    double best = -INFINITY;
+    long long gbest = 0x7fffffffffffffffLL;
+    for (long long g = threadIdx.x; g < npa; g += kThreads) {
+        const double v = lg[g];
+        if (v == -INFINITY) continue;
+        const double lp = v + lnp[g % na];
+        if (lp > best || (lp == best && g < gbest)) {
+            best = lp;
+            gbest = g;
+        }
+    }
+    block_argmax(best, gbest, red, redi);
+    if (threadIdx.x == 0) {
+        if (W > 0) {
+            c11 /= W;
+            c22 /= W;
+            c12 /= W;
+        }
+        const double det = c11 * c22 - c12 * c12;
+        res.e1m = e1m;
+        res.e2m = e2m;
+        res.sd1 = sqrt(c11);
+        res.sd2 = sqrt(c22);
+        const double sdet = det > 0 ? sqrt(det) : 0.0;
+        res.bad = !(W > 0) || res.sd1 <= gc.var_sigma_min || res.sd2 <= gc.var_sigma_min || sdet <= gc.var_det_min;
+        res.am = W > 0 ? WA / W : 0.0;
+        res.flux = (best > -INFINITY && a[gbest] > 0) ? b[gbest] / a[gbest] : 0.0;
+        res.e1s = Ws > 0 ? s1 / Ws : 0.0;
+        res.e2s = Ws > 0 ? s2 / Ws : 0.0;
+        res.kept = (int)kept;
+        res.map_i = best > -INFINITY ? (int)(gbest / na) : -1;
+        res.box[0] = lo1;
+        res.box[1] = hi1;
+        res.box[2] = lo2;
+        res.box[3] = hi2;
+    }
+    __syncthreads();
+}
+
+template <typename T, bool kGauss>
+__global__ void __launch_bounds__(kThreads)
+adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table,
+                size_t plane, int32_t NN, const GridConst gc, const double *__restrict__ ga,
+                const double *__restrict__ gb, const double *__restrict__ gl, const double *__restrict__ ccv,
+                double *__restrict__ scratch, rlf_fit_out out, int32_t out_offset)
+{
+    constexpr bool mixed = std::is_same<T, float>::value;
+    __shared__ T sm[5][kCellTile];
+    __shared__ double qp[64], alph[64], lnp[64];
+    __shared__ double Ls[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
+    __shared__ double As[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
+    __shared__ double e1s[kAdaptMax], e2s[kAdaptMax];
+    __shared__ AdaptResult res;
+    __shared__ int s_np;
+    const int s = blockIdx.x;
+    const int ne = gc.n_e, na = gc.n_alpha;
+    const size_t ng = (size_t)ne * ne * na;
+    const SrcRow S = table[s];
+    const int nc = ncell[s];
+    const double cc = ccv[s];
+    if (threadIdx.x < na) {
+        const int k = threadIdx.x;
+        const double ak = grid_alpha(gc, k);
+        double q;
+        if (na == 1) q = 1.0;
+        else if (k == 0) q = 0.5 * (grid_alpha(gc, 1) - ak);
+        else if (k == na - 1) q = 0.5 * (ak - grid_alpha(gc, na - 2));
+        else q = 0.5 * (grid_alpha(gc, k + 1) - grid_alpha(gc, k - 1));
+        const double z = (log(ak) - S.mu) / gc.r_std;
+        qp[k] = q * exp(-0.5 * z * z) / (ak * gc.r_std * sqrt(2.0 * kPi));
+        alph[k] = ak;
+        lnp[k] = -0.5 * z * z - log(ak);
+    }
+    __syncthreads();
+    // level 0: the grid
+    estimate_over_samples(mixed, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
+                          lnp, Ls, As, res);
+    double h = 2.0 * gc.e_max / (ne - 1);
+    int level = 0;
+    double *slg = scratch + (size_t)s * kAdaptMax * na * 3;
+    double *sa = slg + (size_t)kAdaptMax * na, *sb = sa + (size_t)kAdaptMax * na;
+    while (res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0) {
+        // the next lattice (thread 0), then every (sample, alpha) pair over the cells
+        const double hn = 0.5 * h;
+        if (threadIdx.x == 0) {
+            const double cen[2] = {level == 0 ? grid_e(gc, res.map_i / ne) : e1s[res.map_i],
+                                   level == 0 ? grid_e(gc, res.map_i % ne) : e2s[res.map_i]};
+            int lo[2], hi[2];
+            for (int d = 0; d < 2; ++d) {
+                lo[d] = (int)ceil((res.box[2 * d] - h) / hn - 1e-9);
+                hi[d] = (int)floor((res.box[2 * d + 1] + h) / hn + 1e-9);
+                if (hi[d] - lo[d] + 1 > kAdaptSide) {
+                    const int c = (int)llround(cen[d] / hn);
+                    lo[d] = c - kAdaptSide / 2;
+                    hi[d] = c + kAdaptSide / 2;
+                }
+            }
+            int np = 0;
+            for (int i1 = lo[0]; i1 <= hi[0]; ++i1)
+                for (int i2 = lo[1]; i2 <= hi[1]; ++i2) {
+                    const double a1 = i1 * hn, a2 = i2 * hn;
+                    if (!(a1 * a1 + a2 * a2 < 1.0)) continue;
+                    e1s[np] = a1;
+                    e2s[np] = a2;
+                    ++np;
+                }
+            s_np = np;
+        }
+        __syncthreads();
+        const int np = s_np;
+        const T *cu = cells + (size_t)s * NN;
+        for (int base = 0; base < np * na; base += kThreads) {
+            const int pr = base + threadIdx.x;
+            const bool on = pr < np * na;
+            const int i = on ? pr / na : 0, k = on ? pr % na : 0;
+            const double e1 = e1s[i], e2 = e2s[i];
+            const double det = 1.0 - e1 * e1 - e2 * e2;
+            const double id2 = 1.0 / (det * det);
+            const T p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+            const T p12 = (T)(4.0 * e2 * id2);
+            const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+            const double alr = alph[k] * kArcsec * S.du;
+            const T ca = (T)(4.0 * kPi * kPi * alr * alr);
+            float ah = 0.0f, al = 0.0f, bh = 0.0f, bl = 0.0f;
+            double da = 0.0, db = 0.0;
+            for (int c0 = 0; c0 < nc; c0 += kCellTile) {
+                const int nt = min(kCellTile, nc - c0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < nt; j += kThreads) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
+                }
+                __syncthreads();
+                if (!on) continue;
+                T pa = T(0), pb = T(0);
+                for (int c = 0; c < nt; ++c) {
+                    const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                    T M;
+                    if constexpr (mixed) M = brightness<kGauss>(ca, Q);
+                    else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
+                    pa += sm[3][c] * M * M;
+                    pb += sm[4][c] * M;
+                }
+                if constexpr (mixed) {
+                    float sum, err;
+                    two_sum(ah, pa, sum, err);
+                    ah = sum;
+                    al = __fadd_rn(al, err);
+                    two_sum(bh, pb, sum, err);
+                    bh = sum;
+                    bl = __fadd_rn(bl, err);
+                } else {
+                    da += (double)pa;
+                    db += (double)pb;
+                }
+            }
+            if (on) {
+                if constexpr (mixed) {
+                    da = (double)ah + (double)al;
+                    db = (double)bh + (double)bl;
+                }
+                sa[pr] = da;
+                sb[pr] = db;
+                slg[pr] = mixed ? flux_marginal_mixed(da, db, cc, gc.flux_prior) : flux_marginal(da, db, cc, gc.flux_prior);
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+        estimate_over_samples(mixed, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
+        h = hn;
+        ++level;
+    }
+    if (level > 0 && threadIdx.x == 0) {
+        int flag = res.bad ? RLF_FLAG_BAD : 0;
+        if (S.invalid) flag |= RLF_FLAG_INVALID;
+        const int o = out_offset + s;
+        out.e1[o] = res.e1m;
+        out.e2[o] = res.e2m;
+        out.sig1[o] = res.sd1;
+        out.sig2[o] = res.sd2;
+        out.alpha_arcsec[o] = res.am;
+        out.flux_jy[o] = res.flux;
+        out.e1_smooth[o] = res.e1s;
+        out.e2_smooth[o] = res.e2s;
+        out.flag[o] = flag | (level << RLF_FLAG_LEVELS_SHIFT);
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -679,6 +962,20 @@ cudaError_t launch_persistent_ag(const T *cells, const SrcRow *table, size_t pla
     }
 }
 
+template <typename T>
+cudaError_t launch_adaptive(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                            const GridConst &gc, const Workspace &ws, const rlf_fit_out &out, int32_t out_offset,
+                            cudaStream_t st)
+{
+    if (gc.profile == RLF_PROFILE_GAUSSIAN)
+        adaptive_kernel<T, true><<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb,
+                                                             ws.gl, ws.cc, ws.adapt, out, out_offset);
+    else
+        adaptive_kernel<T, false><<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb,
+                                                              ws.gl, ws.cc, ws.adapt, out, out_offset);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 GridConst grid_const(const rlf_params &p)
@@ -691,6 +988,9 @@ GridConst grid_const(const rlf_params &p)
     gc.flux_prior = p.flux_prior;
     gc.profile = p.profile;
     gc.pad = 0;
+    gc.estimator = p.estimator;
+    gc.np_max = p.np_max;
+    gc.e_res = p.e_res;
     gc.e_max = p.e_max;
     gc.r_min = p.r_min_arcsec;
     gc.r_max = p.r_max_arcsec;
@@ -715,15 +1015,21 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
         compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                           ws.ncell, ws.cc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        return launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out,
-                                           out_offset, nullptr, st);
+        e = launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out,
+                                        out_offset, nullptr, st);
+        if (e == cudaSuccess && p.estimator == RLF_ESTIMATOR_ADAPTIVE)
+            e = launch_adaptive<float>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+        return e;
     }
     double *cells = static_cast<double *>(ws.cells);
     compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
                                                        ws.ncell, ws.cc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_persistent<double, 4>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
-                                        nullptr, st);
+    e = launch_persistent<double, 4>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
+                                     nullptr, st);
+    if (e == cudaSuccess && p.estimator == RLF_ESTIMATOR_ADAPTIVE)
+        e = launch_adaptive<double>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+    return e;
 }
 
 cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t count, const rlf_params &p,

@@ -175,6 +175,8 @@ struct GridConst {
     const int32_t *box;     // per-facet sub-box origins [count][3] (e1, e2, alpha node), or null: full grid
     int32_t n_e, n_alpha, n_ag, flux_prior;
     int32_t profile, pad;
+    int32_t estimator, np_max;
+    double e_res;
     double e_max;
     double r_min, r_max;    // arcsec
     double r_std;
@@ -202,6 +204,7 @@ struct Workspace {
     size_t part_stride;     // cap * n_e^2 * n_alpha
     int32_t fit_parts;      // cell parts per facet the grids hold (kMaxFitParts; 16 when cap <= 16)
     double *gl;             // [cap][n_e^2][n_alpha]
+    double *adapt;          // adaptive sampling: [cap][289][n_alpha][3] log-likelihood, a, b
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)

@@ -39,7 +39,7 @@ def test_struct_sizes_match_header():
     # pointers and 64-bit fields must land where the C compiler puts them
     assert ctypes.sizeof(rlf.Uvw) == 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(rlf.Sources) == 4 + 4 + 6 * 8
-    assert ctypes.sizeof(rlf.Params) == 13 * 8 + 12 * 4
+    assert ctypes.sizeof(rlf.Params) == 14 * 8 + 16 * 4
     assert ctypes.sizeof(rlf.FitOut) == 9 * 8
 
 

@@ -291,6 +291,40 @@ def test_gaussian_profile_sky_model_and_chain(rlf, prec):
     assert np.max(np.abs(r0["alpha_arcsec"] - res["alpha_arcsec"])) > 0.05
 
 
+@pytest.mark.parametrize("prec", ["split", "mixed", "fp64"])
+def test_adaptive_estimator_matches_oracle(rlf, prec):
+    # adaptive sampling around the maximum (Sec. 2.4) on facets whose posteriors are
+    # narrower than the grid: the brightest source at SNR ~100; the oracle's facets in,
+    # the number of halvings and the estimates compared with the oracle's
+    torch = _torch()
+    c0 = cases.build(synth.workload("small"), with_data=False)
+    snr_max = c0.cat.flux_jy.max() * math.sqrt(c0.obs.n_rows * c0.obs.n_chan) / c0.cat.flux_jy.min()
+    c = cases.build(synth.workload("small"), sigma=cases.snr10_sigma(c0.obs, c0.cat) * snr_max / 100.0)
+    po = c.oracle_params(estimator=1)
+    al = c.alpha_med_rad()
+    facets, ests = [], []
+    for i in range(c.cat.n_src):
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, po)
+        acc = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i], c.cat.m[i],
+                                   c.cat.flux_jy[i], al[i], 0.0, 0.0, du, po)
+        facets.append(acc)
+        ests.append(oracle.fit_facet_adaptive(acc, du, c.cat.flux_jy[i], po))
+    levels = np.array([int(e[oracle.LEVELS]) for e in ests])
+    assert levels.max() >= 2 and levels.min() == 0        # both kinds of posterior are present
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, precision=PRECS[prec],
+                           estimator=rlf.ESTIMATOR_ADAPTIVE)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+    out = rlf.Results(cat.n_src, "cuda")
+    rlf.fit_sources(torch.from_numpy(np.stack(facets)).cuda(), cat, 0, cat.n_src, p, out, ws)
+    got = out.numpy()
+    for i, est in enumerate(ests):
+        assert (int(got["flag"][i]) >> rlf.FLAG_LEVELS_SHIFT) & 15 == levels[i], i
+        assert cases.est_matches(got, i, est) <= 1e-4, (i, levels[i], got["e1"][i], est[oracle.E1])
+        assert abs(got["sig1"][i] - est[oracle.SIG1]) <= 1e-4 + 1e-3 * est[oracle.SIG1]
+        assert (int(got["flag"][i]) & rlf.FLAG_BAD != 0) == (est[oracle.FLAG] != 0)
+
+
 def test_invalid_and_empty_sources_are_flagged(rlf):
     torch = _torch()
     wl = synth.tiny(seed=61, n_ant=12, n_time=9, n_chan=2, n_src=4, r_max_m=3000.0)
