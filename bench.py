@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--update-mode", type=int, default=1)
     ap.add_argument("--profile", default="exponential", choices=["exponential", "gaussian"],
                     help="source brightness profile (data and fit)")
+    ap.add_argument("--estimator", default="grid", choices=["grid", "adaptive"],
+                    help="ellipticity estimator: the fixed grid, or adaptive sampling around the maximum")
+    ap.add_argument("--sigma-scale", type=float, default=1.0, help="noise per visibility x this")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time rlf_run calls instead of the captured graph")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
@@ -229,15 +232,18 @@ def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
     zeros = torch.zeros(n, dtype=torch.float64, device=dev)
     cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
     truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
-    params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=args.chunk,
+    sigma = wl.sigma_jy * getattr(args, "sigma_scale", 1.0)
+    params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=sigma, chunk=args.chunk,
                                 precision=prec, update_mode=args.update_mode,
-                                profile=rlf.PROFILE_GAUSSIAN if args.profile == "gaussian" else 0)
+                                profile=rlf.PROFILE_GAUSSIAN if args.profile == "gaussian" else 0,
+                                estimator=rlf.ESTIMATOR_ADAPTIVE if getattr(args, "estimator", "grid") == "adaptive"
+                                else rlf.ESTIMATOR_GRID)
     ws = rlf.alloc_workspace(R, C, n, params, rlf.WS_RUN, device=dev)
     data = torch.empty(R * C * 2, dtype=torch.float32, device=dev)
     rlf.sky_model(obs, truth, params, data, ws, stream)
     gen = torch.Generator(device=dev)
     gen.manual_seed(1234 + rank)
-    data += torch.randn(R * C * 2, generator=gen, device=dev, dtype=torch.float32) * wl.sigma_jy
+    data += torch.randn(R * C * 2, generator=gen, device=dev, dtype=torch.float32) * sigma
     sky = torch.empty_like(data)
     out = rlf.Results(n, dev)
     return {"wl": wl, "obs_np": obs_np, "cat_np": cat_np, "obs": obs, "cat": cat, "truth": truth,
@@ -429,7 +435,8 @@ def main():
                    "n_time": obs_np.n_time, "n_chan": C, "n_vis": n_vis, "n_src": n_src,
                    "facet_n": params.facet_n, "grid": [params.n_e, params.n_e, params.n_alpha],
                    "chunk": args.chunk if args.chunk > 0 else n_src, "precision": args.precision,
-                   "update_mode": args.update_mode, "profile": args.profile,
+                   "update_mode": args.update_mode, "profile": args.profile, "estimator": args.estimator,
+                   "sigma_jy": params.sigma_jy,
                    "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
         "phases_ms": comp["phases_ms"],
@@ -437,7 +444,8 @@ def main():
         "gpu_launches": comp["launches_per_step"] * args.steps,
         "clocks": clocks.summary(),
         "measured_unit_peaks": peaks,
-        "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2))},
+        "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2)),
+                 "refinements": np.bincount((res["flag"] >> 8) & 15, minlength=6).tolist()},
     }
     line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
     line["launch"] = {"graph": graph is not None, "tuning": None if tuning is None else
