@@ -35,7 +35,7 @@
 enum {
     RLFO_E1 = 0, RLFO_E2, RLFO_SIG1, RLFO_SIG2, RLFO_ALPHA, RLFO_FLUX, RLFO_FLAG,
     RLFO_E1_SMOOTH, RLFO_E2_SMOOTH, RLFO_LOGL_MAX, RLFO_THRESH_MARGIN, RLFO_MAP_INDEX,
-    RLFO_NC, RLFO_LEVELS, RLFO_STEP, RLFO_NKEPT, RLFO_NEST
+    RLFO_NC, RLFO_LEVELS, RLFO_STEP, RLFO_NKEPT, RLFO_REFIT, RLFO_NEST
 };
 
 typedef struct {
@@ -48,6 +48,7 @@ typedef struct {
     double e_res;                              /* adaptive sampling: finest step in e (E_RES) */
     int32_t np_max;                            /* adaptive sampling: samples above threshold wanted (NP_MAX) */
     int32_t estimator;                         /* 0: the fixed grid; 1: adaptive sampling around the maximum */
+    int32_t refit_bad, pad2;                   /* 1: fit the bad fits again after the whole catalogue */
 } rlfo_params;
 
 int rlfo_nest(void) { return RLFO_NEST; }
@@ -675,6 +676,64 @@ double rlfo_facet_du(double flux_jy, double alpha_cat_arcsec, const rlfo_params 
     return 1.0 / (p->psf_nat * a * RLFO_ARCSEC);
 }
 
+/* One chunk of the chain: extract the listed sources' facets from the current sky
+   model, fit them, and replace their shapes in the sky model (good fits, or all
+   with update_mode 1). */
+static void chunk_step(int64_t n_rows, int32_t n_chan, const double *u, const double *v, const double *w,
+                       const double *freq, const float *data, const double *l, const double *m,
+                       const double *flux, const double *alpha_cat_arcsec, const rlfo_params *p, double *est,
+                       double *sky, const double *alpha_sky, double *e1c, double *e2c, const int *list, int cnt,
+                       int n_threads)
+{
+    const int64_t nc = (int64_t)p->facet_n * p->facet_n;
+    const int ng = p->n_e * p->n_e * p->n_alpha;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int t = 0; t < cnt; ++t) {
+        int i = list[t];
+        double *acc = malloc(sizeof(double) * 4 * nc);
+        double *lg = malloc(sizeof(double) * ng * 3);
+        double du = rlfo_facet_du(flux[i], alpha_cat_arcsec ? alpha_cat_arcsec[i] : 0.0, p);
+        rlfo_extract_facet(n_rows, n_chan, u, v, w, freq, data, NULL, sky, l[i], m[i], flux[i],
+                           alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, du,
+                           p->facet_n, acc, NULL);
+        double *e = est + (int64_t)i * RLFO_NEST;
+        if (p->estimator == 1)
+            rlfo_fit_facet_adaptive(acc, du, flux[i], p, e);
+        else
+            rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, e);
+        free(acc);
+        free(lg);
+    }
+    /* sky update: V += model_i(e_new) - model_i(e_cur) for the chunk */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t r = 0; r < n_rows; ++r)
+        for (int32_t c = 0; c < n_chan; ++c)
+            for (int t = 0; t < cnt; ++t) {
+                int i = list[t];
+                const double *e = est + (int64_t)i * RLFO_NEST;
+                if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
+                double nr, ni, orr, oi;
+                rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
+                               e[RLFO_E1], e[RLFO_E2], p->beta, p->nu_ref_hz, p->profile, &nr, &ni);
+                rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
+                               e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, &orr, &oi);
+                sky[(r * n_chan + c) * 2 + 0] += nr - orr;
+                sky[(r * n_chan + c) * 2 + 1] += ni - oi;
+            }
+    for (int t = 0; t < cnt; ++t) {
+        int i = list[t];
+        const double *e = est + (int64_t)i * RLFO_NEST;
+        if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
+        e1c[i] = e[RLFO_E1];
+        e2c[i] = e[RLFO_E2];
+    }
+}
+
 /*
  * Whole chain (Sec. 2): circular sky model, then for each chunk of sources in
  * catalogue order: extract every facet of the chunk from the current sky model,
@@ -690,8 +749,6 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
                   double *sky_out, int n_threads)
 {
     const int64_t nv = n_rows * n_chan;
-    const int64_t nc = (int64_t)p->facet_n * p->facet_n;
-    const int ng = p->n_e * p->n_e * p->n_alpha;
     double *sky = malloc(sizeof(double) * nv * 2);
     double *alpha_sky = malloc(sizeof(double) * n_src);
     double *e1c = calloc(n_src, sizeof(double)), *e2c = calloc(n_src, sizeof(double));
@@ -704,53 +761,28 @@ int rlfo_pipeline(int64_t n_rows, int32_t n_chan, const double *u, const double 
     rlfo_sky_model(n_rows, n_chan, u, v, w, freq, NULL, 0, n_src, l, m, flux, alpha_sky, e1c, e2c,
                    p->beta, p->nu_ref_hz, p->profile, sky, NULL, n_threads);
     int chunk = p->chunk > 0 ? p->chunk : n_src;
+    int *idx = malloc(sizeof(int) * n_src);
+    if (!idx) return 1;
+    for (int i = 0; i < n_src; ++i) idx[i] = i;
     for (int first = 0; first < n_src; first += chunk) {
         int cnt = (first + chunk <= n_src) ? chunk : n_src - first;
-#ifdef _OPENMP
-        if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
-#endif
-        for (int t = 0; t < cnt; ++t) {
-            int i = first + t;
-            double *acc = malloc(sizeof(double) * 4 * nc);
-            double *lg = malloc(sizeof(double) * ng * 3);
-            double du = rlfo_facet_du(flux[i], alpha_cat_arcsec ? alpha_cat_arcsec[i] : 0.0, p);
-            rlfo_extract_facet(n_rows, n_chan, u, v, w, freq, data, NULL, sky, l[i], m[i], flux[i],
-                               alpha_sky[i], e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, du,
-                               p->facet_n, acc, NULL);
-            if (p->estimator == 1)
-                rlfo_fit_facet_adaptive(acc, du, flux[i], p, est + (int64_t)i * RLFO_NEST);
-            else
-                rlfo_fit_facet(acc, du, flux[i], p, lg, lg + ng, lg + 2 * ng, est + (int64_t)i * RLFO_NEST);
-            free(acc);
-            free(lg);
-        }
-        /* sky update: V += model_i(e_new) - model_i(e_cur) for the chunk */
-#ifdef _OPENMP
-#pragma omp parallel for schedule(static)
-#endif
-        for (int64_t r = 0; r < n_rows; ++r)
-            for (int32_t c = 0; c < n_chan; ++c)
-                for (int t = 0; t < cnt; ++t) {
-                    int i = first + t;
-                    const double *e = est + (int64_t)i * RLFO_NEST;
-                    if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
-                    double nr, ni, orr, oi;
-                    rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
-                                   e[RLFO_E1], e[RLFO_E2], p->beta, p->nu_ref_hz, p->profile, &nr, &ni);
-                    rlfo_model_vis(u[r], v[r], w[r], freq[c], l[i], m[i], flux[i], alpha_sky[i],
-                                   e1c[i], e2c[i], p->beta, p->nu_ref_hz, p->profile, &orr, &oi);
-                    sky[(r * n_chan + c) * 2 + 0] += nr - orr;
-                    sky[(r * n_chan + c) * 2 + 1] += ni - oi;
-                }
-        for (int t = 0; t < cnt; ++t) {
-            int i = first + t;
-            const double *e = est + (int64_t)i * RLFO_NEST;
-            if (p->update_mode == 0 && e[RLFO_FLAG] != 0.0) continue;
-            e1c[i] = e[RLFO_E1];
-            e2c[i] = e[RLFO_E2];
+        chunk_step(n_rows, n_chan, u, v, w, freq, data, l, m, flux, alpha_cat_arcsec, p, est, sky, alpha_sky,
+                   e1c, e2c, idx + first, cnt, n_threads);
+    }
+    /* the bad fits once more, against the sky model of every other measured shape
+       (Sec. 2.4), in catalogue order and chunks of the same size */
+    if (p->refit_bad) {
+        int nb = 0;
+        for (int i = 0; i < n_src; ++i)
+            if (est[(int64_t)i * RLFO_NEST + RLFO_FLAG] != 0.0) idx[nb++] = i;
+        for (int first = 0; first < nb; first += chunk) {
+            int cnt = (first + chunk <= nb) ? chunk : nb - first;
+            chunk_step(n_rows, n_chan, u, v, w, freq, data, l, m, flux, alpha_cat_arcsec, p, est, sky, alpha_sky,
+                       e1c, e2c, idx + first, cnt, n_threads);
+            for (int t = 0; t < cnt; ++t) est[(int64_t)idx[first + t] * RLFO_NEST + RLFO_REFIT] = 1.0;
         }
     }
+    free(idx);
     if (sky_out) memcpy(sky_out, sky, sizeof(double) * nv * 2);
     free(sky);
     free(alpha_sky);

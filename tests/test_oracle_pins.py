@@ -513,3 +513,48 @@ def test_adaptive_sampling_of_a_resolved_posterior_stops_early():
                                cat.flux_jy[0], al, 0.0, 0.0, du, p)
     ad = oracle.fit_facet_adaptive(acc, du, cat.flux_jy[0], p)
     assert ad[oracle.LEVELS] == 0 and ad[oracle.NKEPT] >= p.np_max
+
+
+# ---- refit of the bad fits after the whole catalogue (Sec. 2.4) --------------------------
+
+def _refit_case(sigma):
+    wl = synth.tiny(seed=41, n_src=3, n_ant=24, n_time=24, n_chan=2, r_max_m=1500.0)
+    obs, cat = synth.make_observation(wl), synth.make_catalogue(wl)
+    al = np.array([oracle.alpha_med(s) for s in cat.flux_jy]) * ARC
+    d = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al, cat.e1, cat.e2,
+                         nu_ref=wl.nu_ref_hz)
+    d2 = (np.stack([d.real, d.imag], -1) + synth.noise(obs.n_rows, obs.n_chan, sigma, 7)).astype(np.float32)
+    return wl, obs, cat, al, d2
+
+
+def test_refit_changes_nothing_without_bad_fits():
+    wl, obs, cat, al, d2 = _refit_case(3e-4)
+    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=3e-4, update_mode=1)
+    est0 = oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, d2, cat.l, cat.m, cat.flux_jy, None, p)
+    assert np.all(est0[:, oracle.FLAG] == 0)
+    p.refit_bad = 1
+    est1 = oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, d2, cat.l, cat.m, cat.flux_jy, None, p)
+    assert np.array_equal(est0, est1) and np.all(est1[:, oracle.REFIT] == 0)
+
+
+def test_refit_fits_bad_sources_against_the_final_sky_model():
+    # every fit is bad (the posteriors collapse onto grid nodes): each source is fitted once
+    # more against the sky model that holds every main-pass shape; rebuilt here from the
+    # oracle's sky model, extraction and fit
+    wl, obs, cat, al, d2 = _refit_case(1e-7)
+    p = oracle.default_params(facet_n=32, nu_ref_hz=wl.nu_ref_hz, sigma_jy=1e-7, update_mode=1)
+    main = oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, d2, cat.l, cat.m, cat.flux_jy, None, p)
+    assert np.all(main[:, oracle.FLAG] != 0)
+    p.refit_bad = 1
+    est = oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, d2, cat.l, cat.m, cat.flux_jy, None, p)
+    assert np.all(est[:, oracle.REFIT] == 1)
+    sky = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al, main[:, oracle.E1],
+                           main[:, oracle.E2], nu_ref=wl.nu_ref_hz)
+    s2 = np.stack([sky.real, sky.imag], -1)
+    for i in range(cat.n_src):
+        du = oracle.facet_du(cat.flux_jy[i], 0.0, p)
+        acc = oracle.extract_facet(obs.u, obs.v, obs.w, obs.freq_hz, d2, s2, cat.l[i], cat.m[i], cat.flux_jy[i],
+                                   al[i], main[i, oracle.E1], main[i, oracle.E2], du, p)
+        ref = oracle.fit_facet(acc, du, cat.flux_jy[i], p).est
+        for f in (oracle.E1, oracle.E2, oracle.SIG1, oracle.SIG2, oracle.FLUX, oracle.FLAG):
+            assert abs(est[i, f] - ref[f]) <= 1e-12 * max(1.0, abs(ref[f])), (i, f)
