@@ -84,7 +84,8 @@ enum {
 enum {
     RLF_FLAG_BAD = 1,      /* Sec. 4.1 cut: sigma(e_i) or sqrt(det cov) not above its minimum */
     RLF_FLAG_INVALID = 2,  /* the source's input values are out of range */
-    RLF_FLAG_EMPTY = 4     /* the facet holds no visibility */
+    RLF_FLAG_EMPTY = 4,    /* the facet holds no visibility */
+    RLF_FLAG_REFIT = 8     /* rlf_run with refit_bad: fitted again after the whole catalogue */
 };
 
 /* bits of the device status word */
@@ -249,6 +250,11 @@ rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t
  * chunk = n_src extracts every facet from the initial model (Sec. 3.1).
  * vis_sky (device, [n_rows][n_chan][2]) ends holding the final sky model; out
  * holds n_src results.  The workspace must be rlf_workspace_size(..., RLF_WS_RUN).
+ * With p->refit_bad = 1 the fits flagged bad are then fitted once more, in source
+ * order and chunks of the same size, against the sky model that holds every other
+ * measured shape (Sec. 2.4); their results replace the first ones and carry
+ * RLF_FLAG_REFIT.  Their number sizes those launches, so rlf_run then synchronises
+ * `stream` once.
  */
 rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,
                    const rlf_params *p, const rlf_fit_out *out, float *vis_sky,
@@ -326,6 +332,7 @@ rlf_status rlf_fit_sources_mlp(const double *facets, const rlf_sources *src, int
  * rlf_graph_launch enqueues one replay on `stream`.  The graph object is host
  * memory owned by the library; free it with rlf_graph_destroy.  Sec. 2 and Sec. 3.1
  * define the chain; the graph is an execution form, not a change of the method.
+ * p->refit_bad = 1 is not capturable (RLF_EUNSUPPORTED).
  */
 typedef struct rlf_graph_s rlf_graph;
 rlf_status rlf_graph_create(const rlf_uvw *uvw, const float *vis_data, const rlf_sources *src,

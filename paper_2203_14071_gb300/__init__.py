@@ -29,7 +29,7 @@ PREC_FP64, PREC_MIXED, PREC_MIXED_SPLIT = 0, 1, 2
 PROFILE_EXPONENTIAL, PROFILE_GAUSSIAN = 0, 1
 ESTIMATOR_GRID, ESTIMATOR_ADAPTIVE = 0, 1
 FLAG_LEVELS_SHIFT = 8
-FLAG_BAD, FLAG_INVALID, FLAG_EMPTY = 1, 2, 4
+FLAG_BAD, FLAG_INVALID, FLAG_EMPTY, FLAG_REFIT = 1, 2, 4, 8
 DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
 WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
 MAX_CHAN, MAX_FACET_N, STATIC_MAX_SRC = 128, 64, 4096

@@ -134,6 +134,9 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const bool adapt = fit && p.estimator == RLF_ESTIMATOR_ADAPTIVE;
     const size_t o_ad = take(adapt ? cap * 289 * (size_t)p.n_alpha * 3 * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
+    const size_t o_bad = take(run ? ((size_t)n_src + 1) * sizeof(int32_t) : 0);
+    const size_t o_ftmp = take(run ? 8 * cap * sizeof(double) : 0);
+    const size_t o_gtmp = take(run ? cap * sizeof(int32_t) : 0);
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
     const bool ext = which == RLF_WS_EXTRACT || run;
     const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
@@ -168,6 +171,9 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->gl = reinterpret_cast<double *>(b + o_gl);
         ws->adapt = reinterpret_cast<double *>(b + o_ad);
         ws->e_cur = reinterpret_cast<double *>(b + o_ecur);
+        ws->bad_list = reinterpret_cast<int32_t *>(b + o_bad);
+        ws->fit_tmp = reinterpret_cast<double *>(b + o_ftmp);
+        ws->flag_tmp = reinterpret_cast<int32_t *>(b + o_gtmp);
         ws->facets = reinterpret_cast<double *>(b + o_fac);
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
         ws->resid = reinterpret_cast<float *>(b + o_resid);
@@ -403,6 +409,41 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
             e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
         }
     }
+    // the bad fits once more, against the sky model of every other measured shape (Sec. 2.4),
+    // in source order and chunks of the same size; their number sizes the launches, so the
+    // stream is synchronised once here (not capturable)
+    if (e == cudaSuccess && p.refit_bad) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return e;
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+        e = launch_bad_list(out.flag, n, ws.bad_list, st);
+        int32_t nb = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, ws.bad_list, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        const size_t cap = (size_t)chunk;
+        const rlf_fit_out tmp{ws.fit_tmp, ws.fit_tmp + cap, ws.fit_tmp + 2 * cap, ws.fit_tmp + 3 * cap,
+                              ws.fit_tmp + 4 * cap, ws.fit_tmp + 5 * cap, ws.fit_tmp + 6 * cap, ws.fit_tmp + 7 * cap,
+                              ws.flag_tmp};
+        for (int32_t first = 0; first < nb && e == cudaSuccess; first += chunk) {
+            const int32_t cnt = first + chunk <= nb ? chunk : nb - first;
+            const int32_t *list = ws.bad_list + 1 + first;
+            e = launch_prepare(src, 0, cnt, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
+                               ws.status, st, list);
+            if (e != cudaSuccess) break;
+            e = track_resid ? launch_extract(uvw, ch, ws.resid, nullptr, ws.table, cnt, p, ws, ws.facets, st)
+                            : launch_extract(uvw, ch, vis_data, vis_sky, ws.table, cnt, p, ws, ws.facets, st);
+            if (e != cudaSuccess) break;
+            e = launch_fit(ws.facets, ws.table, cnt, p, ws, tmp, 0, st);
+            if (e != cudaSuccess) break;
+            e = launch_scatter(ws.fit_tmp, ws.flag_tmp, cap, list, cnt, out, st);
+            if (e != cudaSuccess) break;
+            e = launch_prepare(src, 0, cnt, e1c, e2c, tmp.e1, tmp.e2, tmp.flag, p.update_mode, e1c, e2c, p, ws.upd,
+                               ws.status, st, list);
+            if (e != cudaSuccess) break;
+            e = track_resid ? launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f)
+                            : launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
+        }
+    }
     if (e == cudaSuccess && track_resid) e = launch_difference(vis_data, ws.resid, n_vis, vis_sky, st);
     return e;
 }
@@ -464,6 +505,8 @@ rlf_status rlf_graph_create(const rlf_uvw *uvw, const float *vis_data, const rlf
     Workspace ws;
     const rlf_status s = check_run(uvw, vis_data, src, p, out, vis_sky, workspace, ws_bytes, &ws);
     if (s != RLF_OK) return s;
+    // the refit pass sizes its launches from the number of bad fits, read on the host
+    if (p->refit_bad) return RLF_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RLF_ECUDA;

@@ -978,6 +978,65 @@ cudaError_t launch_adaptive(const T *cells, const SrcRow *table, size_t plane, i
 
 }  // namespace
 
+namespace {
+
+// The bad fits in source order, in one CTA: list[0] = their number, list[1..] = indices.
+__global__ void bad_list_kernel(const int32_t *__restrict__ flag, int32_t n, int32_t *__restrict__ list)
+{
+    __shared__ int wsum[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const bool on = i < n && (flag[i] & RLF_FLAG_BAD);
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        int off = 0;
+        for (int j = 0; j < w; ++j) off += wsum[j];
+        if (on) list[1 + base + off + __popc(m & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base += off + __popc(m);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) list[0] = base;
+}
+
+// Results of a refit chunk (rows t) back to their sources list[t], marked as refitted.
+__global__ void scatter_kernel(const double *__restrict__ tmp, const int32_t *__restrict__ ftmp, size_t cap,
+                               const int32_t *__restrict__ list, int32_t cnt, rlf_fit_out out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int i = list[t];
+    out.e1[i] = tmp[t];
+    out.e2[i] = tmp[cap + t];
+    out.sig1[i] = tmp[2 * cap + t];
+    out.sig2[i] = tmp[3 * cap + t];
+    out.alpha_arcsec[i] = tmp[4 * cap + t];
+    out.flux_jy[i] = tmp[5 * cap + t];
+    out.e1_smooth[i] = tmp[6 * cap + t];
+    out.e2_smooth[i] = tmp[7 * cap + t];
+    out.flag[i] = ftmp[t] | RLF_FLAG_REFIT;
+}
+
+}  // namespace
+
+cudaError_t launch_bad_list(const int32_t *flag, int32_t n, int32_t *list, cudaStream_t st)
+{
+    bad_list_kernel<<<1, 1024, 0, st>>>(flag, n, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const double *tmp, const int32_t *ftmp, size_t cap, const int32_t *list, int32_t cnt,
+                           const rlf_fit_out &out, cudaStream_t st)
+{
+    scatter_kernel<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, st>>>(tmp, ftmp, cap, list, cnt, out);
+    return cudaGetLastError();
+}
+
 GridConst grid_const(const rlf_params &p)
 {
     GridConst gc;

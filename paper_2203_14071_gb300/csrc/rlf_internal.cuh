@@ -205,6 +205,9 @@ struct Workspace {
     int32_t fit_parts;      // cell parts per facet the grids hold (kMaxFitParts; 16 when cap <= 16)
     double *gl;             // [cap][n_e^2][n_alpha]
     double *adapt;          // adaptive sampling: [cap][289][n_alpha][3] log-likelihood, a, b
+    int32_t *bad_list;      // refit pass: [n_src + 1] count, then the bad fits in source order
+    double *fit_tmp;        // refit pass: [8][cap] results of a refit chunk (FP64 fields)
+    int32_t *flag_tmp;      // refit pass: [cap] flags of a refit chunk
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
@@ -225,7 +228,8 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            const double *e1, const double *e2, const double *e1n,
                            const double *e2n, const int32_t *flag, int32_t update_mode,
                            double *e1_commit, double *e2_commit,
-                           const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st);
+                           const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st,
+                           const int32_t *list = nullptr);
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st,
                        int32_t blocks_per_sm = 0, float sign = 1.0f);
@@ -238,6 +242,10 @@ cudaError_t launch_extract_prepare(const rlf_uvw &uvw, const rlf_params &p, cons
 cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float *data,
                            const float *sky, const SrcRow *table, int32_t count,
                            const rlf_params &p, const Workspace &ws, double *facets, cudaStream_t st);
+// refit pass: the bad fits in source order (list[0] = count), results scattered back
+cudaError_t launch_bad_list(const int32_t *flag, int32_t n, int32_t *list, cudaStream_t st);
+cudaError_t launch_scatter(const double *tmp, const int32_t *ftmp, size_t cap, const int32_t *list, int32_t cnt,
+                           const rlf_fit_out &out, cudaStream_t st);
 cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
                        const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
                        int32_t out_offset, cudaStream_t st);

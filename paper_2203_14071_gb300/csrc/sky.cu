@@ -38,11 +38,13 @@ __global__ void prepare_kernel(rlf_sources src, int32_t first, int32_t count,
                                const double *__restrict__ e1n, const double *__restrict__ e2n,
                                const int32_t *__restrict__ flag, double *__restrict__ e1c,
                                double *__restrict__ e2c, PrepConst pc,
-                               SrcRow *__restrict__ out, int32_t *__restrict__ status)
+                               SrcRow *__restrict__ out, int32_t *__restrict__ status,
+                               const int32_t *__restrict__ list)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
-    const int i = first + t;
+    // row t is source first + t, or source list[t] when a list is given
+    const int i = list ? list[t] : first + t;
     const double l = src.l[i], m = src.m[i], S = src.flux_jy[i];
     const double acat = src.alpha_arcsec ? src.alpha_arcsec[i] : 0.0;
     const double a1 = e1[i], a2 = e2[i];
@@ -367,12 +369,13 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            const double *e1, const double *e2, const double *e1n,
                            const double *e2n, const int32_t *flag, int32_t update_mode,
                            double *e1_commit, double *e2_commit,
-                           const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st)
+                           const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st,
+                           const int32_t *list)
 {
     PrepConst pc{p.add, p.esp, p.psf_nat, e1n != nullptr, update_mode};
     const int grid = (count + kThreads - 1) / kThreads;
     prepare_kernel<<<grid, kThreads, 0, st>>>(src, first, count, e1, e2, e1n, e2n, flag, e1_commit,
-                                              e2_commit, pc, out, status);
+                                              e2_commit, pc, out, status, list);
     return cudaGetLastError();
 }
 

@@ -325,6 +325,35 @@ def test_adaptive_estimator_matches_oracle(rlf, prec):
         assert (int(got["flag"][i]) & rlf.FLAG_BAD != 0) == (est[oracle.FLAG] != 0)
 
 
+@pytest.mark.parametrize("chunk,update_mode", [(0, 1), (3, 0)])
+def test_refit_pass_matches_oracle(rlf, chunk, update_mode):
+    # sigma = 1 uJy: every first-pass posterior collapses onto one grid node (bad), so every
+    # source is fitted again after the whole catalogue (Sec. 2.4)
+    torch = _torch()
+    c = small_case(False)
+    est, sky_ref = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m,
+                                   c.cat.flux_jy, None, c.oracle_params(chunk=chunk, update_mode=update_mode,
+                                                                        refit_bad=1), want_sky=True)
+    assert np.all(est[:, oracle.REFIT] == 1)
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(precision=PRECS["split"], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, chunk=chunk,
+                           update_mode=update_mode, refit_bad=1)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    data = cases.vis_tensor(c.data)
+    rlf.run(obs, data, cat, p, out, sky, ws)
+    got = out.numpy()
+    assert np.all(got["flag"] & rlf.FLAG_REFIT)
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(got, i, est[i]) <= 1e-4, (i, got["e1"][i], est[i, oracle.E1])
+    g = sky.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    assert np.abs(g[..., 0] + 1j * g[..., 1] - sky_ref).max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum()
+    # the refit pass reads a count on the host: not capturable
+    with pytest.raises(RuntimeError):
+        rlf.Graph(obs, data, cat, p, out, sky, ws, torch.cuda.Stream())
+
+
 def test_invalid_and_empty_sources_are_flagged(rlf):
     torch = _torch()
     wl = synth.tiny(seed=61, n_ant=12, n_time=9, n_chan=2, n_src=4, r_max_m=3000.0)
