@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--estimator", default="grid", choices=["grid", "adaptive"],
                     help="ellipticity estimator: the fixed grid, or adaptive sampling around the maximum")
     ap.add_argument("--sigma-scale", type=float, default=1.0, help="noise per visibility x this")
+    ap.add_argument("--refit-bad", action="store_true",
+                    help="fit the bad fits again after the whole catalogue (times rlf_run calls: not capturable)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time rlf_run calls instead of the captured graph")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
@@ -237,7 +239,7 @@ def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
                                 precision=prec, update_mode=args.update_mode,
                                 profile=rlf.PROFILE_GAUSSIAN if args.profile == "gaussian" else 0,
                                 estimator=rlf.ESTIMATOR_ADAPTIVE if getattr(args, "estimator", "grid") == "adaptive"
-                                else rlf.ESTIMATOR_GRID)
+                                else rlf.ESTIMATOR_GRID, refit_bad=1 if getattr(args, "refit_bad", False) else 0)
     ws = rlf.alloc_workspace(R, C, n, params, rlf.WS_RUN, device=dev)
     data = torch.empty(R * C * 2, dtype=torch.float32, device=dev)
     rlf.sky_model(obs, truth, params, data, ws, stream)
@@ -383,7 +385,7 @@ def main():
         return
 
     tuning = None if args.no_tune else rlf.autotune(obs, data, cat, params, out, sky, ws, TUNE_CACHE, stream)
-    graph = None if args.no_graph else rlf.Graph(obs, data, cat, params, out, sky, ws, stream)
+    graph = None if (args.no_graph or args.refit_bad) else rlf.Graph(obs, data, cat, params, out, sky, ws, stream)
 
     def step():
         if graph is not None:
@@ -413,6 +415,7 @@ def main():
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
+    res = out.numpy()          # the chain's results (the entry-point timings below reuse `out`)
 
     # per-kernel timing of the dominant phases (same stream, CUDA events), and e2e
     comp = component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, args, n_src)
@@ -420,7 +423,6 @@ def main():
     ms = max_over_ranks(ms, world, dev)
 
     e2e = None if args.no_e2e else e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, args)
-    res = out.numpy()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -436,16 +438,17 @@ def main():
                    "facet_n": params.facet_n, "grid": [params.n_e, params.n_e, params.n_alpha],
                    "chunk": args.chunk if args.chunk > 0 else n_src, "precision": args.precision,
                    "update_mode": args.update_mode, "profile": args.profile, "estimator": args.estimator,
-                   "sigma_jy": params.sigma_jy,
+                   "sigma_jy": params.sigma_jy, "refit_bad": bool(args.refit_bad),
                    "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
         "phases_ms": comp["phases_ms"],
         "mean_cells_per_facet": comp["mean_cells_per_facet"],
-        "gpu_launches": comp["launches_per_step"] * args.steps,
+        "gpu_launches": (comp["launches_per_step"] + refit_launches(params, res, n_src)) * args.steps,
         "clocks": clocks.summary(),
         "measured_unit_peaks": peaks,
         "fits": {"n_bad": int(np.sum(res["flag"] & 1)), "n_invalid": int(np.sum(res["flag"] & 2)),
-                 "refinements": np.bincount((res["flag"] >> 8) & 15, minlength=6).tolist()},
+                 "refinements": np.bincount((res["flag"] >> 8) & 15, minlength=6).tolist(),
+                 "n_refit": int(np.sum((res["flag"] & 8) != 0))},
     }
     line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
     line["launch"] = {"graph": graph is not None, "tuning": None if tuning is None else
@@ -528,7 +531,8 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
     mixed = params.precision != 0
     is_ordered = obs.n_baselines > 0 and obs.n_rows % obs.n_baselines == 0
     track = n_chunks > 1 and mixed and (obs.n_rows * obs.n_chan) % 2 == 0
-    per_chunk = 7 + (1 if chunk >= 3 and mixed and not track else 0) + (1 if mixed else 0) + (1 if n_chunks == 1 else 0)
+    per_chunk = (7 + (1 if chunk >= 3 and mixed and not track else 0) + (1 if mixed else 0) + (1 if n_chunks == 1 else 0)
+                 + (1 if params.estimator == 1 else 0))
     launches = (2 + (1 if mixed else 0) + (1 if mixed and is_ordered else 0)
                 + (1 if params.precision == 2 else 0) + (2 if track else 0) + n_chunks * per_chunk)
     return {"phases_ms": {"sky_model": sky_ms, "extract": ext_ms, "fit": fit_ms, "update": upd_ms},
@@ -571,6 +575,25 @@ def traffic_of(name):
         return None
     files, digest, nbytes = TRAFFIC[name]
     return nbytes if source_hash(files) == digest else None
+
+
+def refit_launches(params, res, n_src):
+    """Kernels of the refit pass: the bad list, then per chunk of refitted sources: prepare,
+    residual (three or more sources, when the sky model is not resident as a residual),
+    window reach, extraction, partial reduce, compaction, LPT order, persistent fit
+    (+ adaptive sampling), scatter, prepare + sky update."""
+    if not params.refit_bad:
+        return 0
+    nb = int(np.sum((res["flag"] & 8) != 0))
+    if nb == 0:
+        return 1
+    chunk = params.chunk if params.chunk > 0 else n_src
+    per = 11 + (1 if params.estimator == 1 else 0)
+    launches = 1
+    for first in range(0, nb, chunk):
+        cnt = min(chunk, nb - first)
+        launches += per + (1 if cnt >= 3 and chunk >= n_src else 0)
+    return launches
 
 
 def roofline_one(name, t_ms, units, row_src, peaks):
