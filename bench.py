@@ -555,9 +555,9 @@ OPS = {
 # the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
 # files hash to the recorded value; otherwise the bench reports null.
 TRAFFIC = {
-    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "79876c13cc0322b7", 981.60e6),
-    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "35ad67cfd86f9797", 349.49e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "1b544397b66df3cc", 17.19e6),
+    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "48f9918d62c68e27", 1015.36e6),
+    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "255373d125bff890", 353.96e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "42a6075882c64c39", 17.24e6),
 }
 
 
