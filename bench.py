@@ -441,6 +441,7 @@ def main():
                    "sigma_jy": params.sigma_jy, "refit_bad": bool(args.refit_bad),
                    "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
+        "fit_only_fits_per_s": n_src / (comp["phases_ms"]["fit"] * 1e-3),
         "phases_ms": comp["phases_ms"],
         "mean_cells_per_facet": comp["mean_cells_per_facet"],
         "gpu_launches": (comp["launches_per_step"] + refit_launches(params, res, n_src)) * args.steps,
