@@ -63,7 +63,8 @@ class Params(ctypes.Structure):
                 ("n_alpha", ctypes.c_int32), ("flux_prior", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("update_mode", ctypes.c_int32), ("profile", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("e_res", ctypes.c_double), ("np_max", ctypes.c_int32), ("estimator", ctypes.c_int32),
-                ("refit_bad", ctypes.c_int32), ("pad2", ctypes.c_int32)]
+                ("refit_bad", ctypes.c_int32), ("pad2", ctypes.c_int32), ("pos_step_arcsec", ctypes.c_double),
+                ("n_pos", ctypes.c_int32), ("pad3", ctypes.c_int32)]
 
 
 def default_params(**kw) -> Params:
@@ -71,7 +72,7 @@ def default_params(**kw) -> Params:
                e_max=0.8, r_min_arcsec=0.3, r_max_arcsec=3.5, r_std=0.3136,
                thresh_frac=0.05, var_sigma_min=5e-3, var_det_min=5e-5,
                facet_n=64, n_e=21, n_alpha=20, flux_prior=0, chunk=0, update_mode=0, profile=0, pad=0,
-               e_res=0.003, np_max=30, estimator=0, refit_bad=0, pad2=0)
+               e_res=0.003, np_max=30, estimator=0, refit_bad=0, pad2=0, pos_step_arcsec=0.1, n_pos=1, pad3=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

@@ -49,6 +49,8 @@ typedef struct {
     int32_t np_max;                            /* adaptive sampling: samples above threshold wanted (NP_MAX) */
     int32_t estimator;                         /* 0: the fixed grid; 1: adaptive sampling around the maximum */
     int32_t refit_bad, pad2;                   /* 1: fit the bad fits again after the whole catalogue */
+    double pos_step_arcsec;                    /* position marginal: offset step */
+    int32_t n_pos, pad3;                       /* position marginal: offsets per axis (1: position exact) */
 } rlfo_params;
 
 int rlfo_nest(void) { return RLFO_NEST; }
@@ -238,6 +240,108 @@ double rlfo_grid_alpha(const rlfo_params *p, int k)
     return p->r_min_arcsec + (p->r_max_arcsec - p->r_min_arcsec) * t * t;
 }
 
+typedef struct {
+    int ncell;
+    double cc;
+    double *cu, *cv, *cw, *cs, *cd, *ci;
+} rlfo_cells;
+
+static void cells_of_facet(const double *acc, double du, const rlfo_params *p, rlfo_cells *C)
+{
+    const int N = p->facet_n;
+    const int64_t nc = (int64_t)N * N;
+    const double sig2 = p->sigma_jy * p->sigma_jy;
+    C->cu = malloc(sizeof(double) * nc);
+    C->cv = malloc(sizeof(double) * nc);
+    C->cw = malloc(sizeof(double) * nc);
+    C->cs = malloc(sizeof(double) * nc);
+    C->cd = malloc(sizeof(double) * nc);
+    C->ci = malloc(sizeof(double) * nc);
+    C->ncell = 0;
+    C->cc = 0.0;
+    for (int iv = 0; iv < N; ++iv)
+        for (int iu = 0; iu < N; ++iu) {
+            int64_t cell = (int64_t)iv * N + iu;
+            double n = acc[2 * nc + cell];
+            if (n <= 0.0) continue;
+            double dr = acc[cell] / n, di = acc[nc + cell] / n;
+            int c = C->ncell++;
+            C->cu[c] = (iu - N / 2 + 0.5) * du;
+            C->cv[c] = (iv - N / 2 + 0.5) * du;
+            C->cw[c] = n / sig2;
+            C->cs[c] = acc[3 * nc + cell] / n;
+            C->cd[c] = dr;
+            C->ci[c] = di;
+            C->cc += C->cw[c] * (dr * dr + di * di);
+        }
+}
+
+static void free_cells(rlfo_cells *C)
+{
+    free(C->cu); free(C->cv); free(C->cw); free(C->cs); free(C->cd); free(C->ci);
+}
+
+
+/*
+ * Flux-marginalised log-likelihood of one (e, alpha) point over a facet's cells
+ * (Sec. 2.4): a = sum w s^2 M^2, b = sum w s M Re D.  With n_pos > 1 the source
+ * position is marginalised too, with a uniform prior over an n_pos x n_pos grid of
+ * offsets x0 (step pos_step_arcsec, centred on the catalogue position; n_pos odd,
+ * at most 7, else NaN): an offset
+ * source's facet model carries exp(+2 pi i k.x0), so a and C are unchanged and
+ * b(x0) = sum w s M Re(D exp(-2 pi i k.x0)); the marginal is the mean of
+ * exp(logL(x0)) over the offsets, and *b_out is b at the best offset.
+ */
+static double like_point(const rlfo_cells *C, double e1, double e2, double al, const rlfo_params *p,
+                         double *a_out, double *b_out)
+{
+    double a = 0.0;
+    if (p->n_pos <= 1) {
+        double b = 0.0;
+        for (int c = 0; c < C->ncell; ++c) {
+            double M = rlfo_shape(C->cu[c], C->cv[c], al, e1, e2, p->profile);
+            a += C->cw[c] * C->cs[c] * C->cs[c] * M * M;
+            b += C->cw[c] * C->cs[c] * M * C->cd[c];
+        }
+        *a_out = a;
+        *b_out = b;
+        return rlfo_flux_marginal(a, b, C->cc, p->flux_prior);
+    }
+    const int np = p->n_pos, nj = np * np;
+    if (np > 7 || np % 2 == 0) {   /* odd grids up to 7 x 7 only */
+        *a_out = *b_out = NAN;
+        return NAN;
+    }
+    const double step = p->pos_step_arcsec * RLFO_ARCSEC;
+    double bj[64];
+    for (int j = 0; j < nj; ++j) bj[j] = 0.0;
+    for (int c = 0; c < C->ncell; ++c) {
+        double M = rlfo_shape(C->cu[c], C->cv[c], al, e1, e2, p->profile);
+        a += C->cw[c] * C->cs[c] * C->cs[c] * M * M;
+        double wsm = C->cw[c] * C->cs[c] * M;
+        for (int j = 0; j < nj; ++j) {
+            double dl = (j / np - (np - 1) / 2) * step, dm = (j % np - (np - 1) / 2) * step;
+            double th = 2.0 * RLFO_PI * (C->cu[c] * dl + C->cv[c] * dm);
+            bj[j] += wsm * (C->cd[c] * cos(th) + C->ci[c] * sin(th));
+        }
+    }
+    double lmax = -INFINITY;
+    int jbest = 0;
+    double lj[64];
+    for (int j = 0; j < nj; ++j) {
+        lj[j] = rlfo_flux_marginal(a, bj[j], C->cc, p->flux_prior);
+        if (lj[j] > lmax) {
+            lmax = lj[j];
+            jbest = j;
+        }
+    }
+    double s = 0.0;
+    for (int j = 0; j < nj; ++j) s += exp(lj[j] - lmax);
+    *a_out = a;
+    *b_out = bj[jbest];
+    return lmax + log(s / nj);
+}
+
 /*
  * Likelihood grid of one facet (Sec. 2.4) on e1, e2 in {-e_max .. e_max} (n_e
  * nodes, |e| < 1 only) x alpha nodes.  loglike/a_out/b_out are
@@ -248,54 +352,27 @@ double rlfo_grid_alpha(const rlfo_params *p, int k)
 int rlfo_like_grid(const double *acc, double du, const rlfo_params *p,
                    double *loglike, double *a_out, double *b_out)
 {
-    const int N = p->facet_n, ne = p->n_e, na = p->n_alpha;
-    const int64_t nc = (int64_t)N * N;
-    const double sig2 = p->sigma_jy * p->sigma_jy;
+    const int ne = p->n_e, na = p->n_alpha;
     /* cell averages and weights: D_c = mean x, s_c = mean spectral factor, w_c = n_c / sigma^2 */
-    int ncell = 0;
-    double cc = 0.0;
-    double *cu = malloc(sizeof(double) * nc), *cv = malloc(sizeof(double) * nc);
-    double *cw = malloc(sizeof(double) * nc), *cs = malloc(sizeof(double) * nc);
-    double *cd = malloc(sizeof(double) * nc);
-    for (int iv = 0; iv < N; ++iv)
-        for (int iu = 0; iu < N; ++iu) {
-            int64_t cell = (int64_t)iv * N + iu;
-            double n = acc[2 * nc + cell];
-            if (n <= 0.0) continue;
-            double dr = acc[0 * nc + cell] / n, di = acc[1 * nc + cell] / n;
-            cu[ncell] = (iu - N / 2 + 0.5) * du;
-            cv[ncell] = (iv - N / 2 + 0.5) * du;
-            cw[ncell] = n / sig2;
-            cs[ncell] = acc[3 * nc + cell] / n;
-            cd[ncell] = dr;
-            cc += cw[ncell] * (dr * dr + di * di);
-            ++ncell;
-        }
+    rlfo_cells C;
+    cells_of_facet(acc, du, p, &C);
     for (int i1 = 0; i1 < ne; ++i1)
         for (int i2 = 0; i2 < ne; ++i2) {
             double e1 = rlfo_grid_e(p, i1), e2 = rlfo_grid_e(p, i2);
             int valid = (e1 * e1 + e2 * e2 < 1.0);
             for (int k = 0; k < na; ++k) {
                 int64_t g = ((int64_t)i1 * ne + i2) * na + k;
-                if (!valid || ncell == 0) {
+                if (!valid || C.ncell == 0) {
                     loglike[g] = -INFINITY;
                     a_out[g] = 0.0;
                     b_out[g] = 0.0;
                     continue;
                 }
-                double al = rlfo_grid_alpha(p, k) * RLFO_ARCSEC;
-                double a = 0.0, b = 0.0;
-                for (int c = 0; c < ncell; ++c) {
-                    double M = rlfo_shape(cu[c], cv[c], al, e1, e2, p->profile);
-                    a += cw[c] * cs[c] * cs[c] * M * M;
-                    b += cw[c] * cs[c] * M * cd[c];
-                }
-                a_out[g] = a;
-                b_out[g] = b;
-                loglike[g] = rlfo_flux_marginal(a, b, cc, p->flux_prior);
+                loglike[g] = like_point(&C, e1, e2, rlfo_grid_alpha(p, k) * RLFO_ARCSEC, p, &a_out[g], &b_out[g]);
             }
         }
-    free(cu); free(cv); free(cw); free(cs); free(cd);
+    int ncell = C.ncell;
+    free_cells(&C);
     return ncell;
 }
 
@@ -436,45 +513,6 @@ void rlfo_estimate(const double *loglike, const double *a_out, const double *b_o
  * cut as the grid estimate, over its samples.  est[RLFO_LEVELS] = refinements
  * made, est[RLFO_STEP] = last step, est[RLFO_NKEPT] = samples kept.
  */
-typedef struct {
-    int ncell;
-    double cc;
-    double *cu, *cv, *cw, *cs, *cd;
-} rlfo_cells;
-
-static void cells_of_facet(const double *acc, double du, const rlfo_params *p, rlfo_cells *C)
-{
-    const int N = p->facet_n;
-    const int64_t nc = (int64_t)N * N;
-    const double sig2 = p->sigma_jy * p->sigma_jy;
-    C->cu = malloc(sizeof(double) * nc);
-    C->cv = malloc(sizeof(double) * nc);
-    C->cw = malloc(sizeof(double) * nc);
-    C->cs = malloc(sizeof(double) * nc);
-    C->cd = malloc(sizeof(double) * nc);
-    C->ncell = 0;
-    C->cc = 0.0;
-    for (int iv = 0; iv < N; ++iv)
-        for (int iu = 0; iu < N; ++iu) {
-            int64_t cell = (int64_t)iv * N + iu;
-            double n = acc[2 * nc + cell];
-            if (n <= 0.0) continue;
-            double dr = acc[cell] / n, di = acc[nc + cell] / n;
-            int c = C->ncell++;
-            C->cu[c] = (iu - N / 2 + 0.5) * du;
-            C->cv[c] = (iv - N / 2 + 0.5) * du;
-            C->cw[c] = n / sig2;
-            C->cs[c] = acc[3 * nc + cell] / n;
-            C->cd[c] = dr;
-            C->cc += C->cw[c] * (dr * dr + di * di);
-        }
-}
-
-static void free_cells(rlfo_cells *C)
-{
-    free(C->cu); free(C->cv); free(C->cw); free(C->cs); free(C->cd);
-}
-
 /* loglike, a, b of every (sample, alpha node) pair: [np][n_alpha] */
 static void sample_likelihood(const rlfo_cells *C, const double *e1s, const double *e2s, int np,
                               const rlfo_params *p, double *loglike, double *a_out, double *b_out)
@@ -488,16 +526,8 @@ static void sample_likelihood(const rlfo_cells *C, const double *e1s, const doub
                 a_out[g] = b_out[g] = 0.0;
                 continue;
             }
-            double al = rlfo_grid_alpha(p, k) * RLFO_ARCSEC;
-            double a = 0.0, b = 0.0;
-            for (int c = 0; c < C->ncell; ++c) {
-                double M = rlfo_shape(C->cu[c], C->cv[c], al, e1s[i], e2s[i], p->profile);
-                a += C->cw[c] * C->cs[c] * C->cs[c] * M * M;
-                b += C->cw[c] * C->cs[c] * M * C->cd[c];
-            }
-            a_out[g] = a;
-            b_out[g] = b;
-            loglike[g] = rlfo_flux_marginal(a, b, C->cc, p->flux_prior);
+            loglike[g] = like_point(C, e1s[i], e2s[i], rlfo_grid_alpha(p, k) * RLFO_ARCSEC, p, &a_out[g],
+                                    &b_out[g]);
         }
 }
 
