@@ -101,6 +101,8 @@ enum { RLF_WS_SKY = 0, RLF_WS_EXTRACT = 1, RLF_WS_FIT = 2, RLF_WS_RUN = 3 };
 /* Largest channel count and facet side handled by one call. */
 #define RLF_MAX_CHAN 128
 #define RLF_MAX_FACET_N 64
+/* Largest position-offset grid side (rlf_params.n_pos). */
+#define RLF_MAX_POS 5
 
 /* Observation: baselines in metres (Sec. 2.2: (u, v, w) with w towards the phase centre). */
 typedef struct {
@@ -160,7 +162,11 @@ typedef struct {
     int32_t estimator;       /* RLF_ESTIMATOR_GRID (default) or RLF_ESTIMATOR_ADAPTIVE */
     int32_t refit_bad;       /* rlf_run: 1 = fit the bad fits again after every other source,
                                 against the final sky model (Sec. 2.4) */
-    int32_t reserved;
+    int32_t n_pos;           /* position marginal (Sec. 2.4): offsets per axis, 1 (0 reads as 1:
+                                the catalogue position is exact, the default), 3 or RLF_MAX_POS;
+                                uniform prior over the n_pos x n_pos grid of offsets centred on the
+                                catalogue position.  Not with rlf_fit_mlp (RLF_EUNSUPPORTED). */
+    double pos_step_arcsec;  /* position marginal: offset step, > 0 (default 0.1") */
 } rlf_params;
 
 /* Per-source results, each a device array of `count` entries. */
@@ -237,6 +243,12 @@ rlf_status rlf_extract_facets(const rlf_uvw *uvw, const float *vis_data, const f
  * trapezoid weights and a log-normal prior (mean ln alpha from Eq. 4, width
  * R_STD); the e points at or above thresh_frac of the maximum give the mean and
  * spread; the Sec. 4.1 cut sets RLF_FLAG_BAD.  Results go to *out.
+ * With p->n_pos > 1 the position is marginalised too (Sec. 2.4), with a uniform
+ * prior over the offsets x_j = (i - h, k - h) pos_step_arcsec, h = (n_pos - 1)/2:
+ * a source offset by x_j carries exp(2 pi i k.x_j) in its facet model, so a and C
+ * are unchanged, b_j = sum w_c s_c M_c Re(D_c exp(-2 pi i k_c.x_j)), and logL is
+ * the log of the mean over j of exp(logL(b_j)); flux_jy is b/a at the best offset
+ * of the MAP point.
  */
 rlf_status rlf_fit_sources(const double *facets, const rlf_sources *src, int32_t first,
                            int32_t count, const rlf_params *p, const rlf_fit_out *out,

@@ -244,6 +244,7 @@ typedef struct {
     int ncell;
     double cc;
     double *cu, *cv, *cw, *cs, *cd, *ci;
+    double *cr;   /* position marginal: [n_pos^2][ncell] Re(D_c exp(-2 pi i k_c.x_j)), else NULL */
 } rlfo_cells;
 
 static void cells_of_facet(const double *acc, double du, const rlfo_params *p, rlfo_cells *C)
@@ -274,11 +275,26 @@ static void cells_of_facet(const double *acc, double du, const rlfo_params *p, r
             C->ci[c] = di;
             C->cc += C->cw[c] * (dr * dr + di * di);
         }
+    /* the data of every cell seen from each position offset x_j (Sec. 2.4): an offset
+       source's model carries exp(+2 pi i k.x_j), so its b uses Re(D exp(-2 pi i k.x_j)) */
+    C->cr = NULL;
+    if (p->n_pos > 1 && p->n_pos <= 7 && p->n_pos % 2 == 1) {
+        const int np = p->n_pos, nj = np * np;
+        const double step = p->pos_step_arcsec * RLFO_ARCSEC;
+        C->cr = malloc(sizeof(double) * nj * (C->ncell > 0 ? C->ncell : 1));
+        for (int j = 0; j < nj; ++j) {
+            double dl = (j / np - (np - 1) / 2) * step, dm = (j % np - (np - 1) / 2) * step;
+            for (int c = 0; c < C->ncell; ++c) {
+                double th = 2.0 * RLFO_PI * (C->cu[c] * dl + C->cv[c] * dm);
+                C->cr[(int64_t)j * C->ncell + c] = C->cd[c] * cos(th) + C->ci[c] * sin(th);
+            }
+        }
+    }
 }
 
 static void free_cells(rlfo_cells *C)
 {
-    free(C->cu); free(C->cv); free(C->cw); free(C->cs); free(C->cd); free(C->ci);
+    free(C->cu); free(C->cv); free(C->cw); free(C->cs); free(C->cd); free(C->ci); free(C->cr);
 }
 
 
@@ -312,18 +328,13 @@ static double like_point(const rlfo_cells *C, double e1, double e2, double al, c
         *a_out = *b_out = NAN;
         return NAN;
     }
-    const double step = p->pos_step_arcsec * RLFO_ARCSEC;
     double bj[64];
     for (int j = 0; j < nj; ++j) bj[j] = 0.0;
     for (int c = 0; c < C->ncell; ++c) {
         double M = rlfo_shape(C->cu[c], C->cv[c], al, e1, e2, p->profile);
         a += C->cw[c] * C->cs[c] * C->cs[c] * M * M;
         double wsm = C->cw[c] * C->cs[c] * M;
-        for (int j = 0; j < nj; ++j) {
-            double dl = (j / np - (np - 1) / 2) * step, dm = (j % np - (np - 1) / 2) * step;
-            double th = 2.0 * RLFO_PI * (C->cu[c] * dl + C->cv[c] * dm);
-            bj[j] += wsm * (C->cd[c] * cos(th) + C->ci[c] * sin(th));
-        }
+        for (int j = 0; j < nj; ++j) bj[j] += wsm * C->cr[(int64_t)j * C->ncell + c];
     }
     double lmax = -INFINITY;
     int jbest = 0;

@@ -32,7 +32,7 @@ FLAG_LEVELS_SHIFT = 8
 FLAG_BAD, FLAG_INVALID, FLAG_EMPTY, FLAG_REFIT = 1, 2, 4, 8
 DEV_INVALID_SOURCE, DEV_NONFINITE, DEV_TIMEOUT = 1, 2, 4
 WS_SKY, WS_EXTRACT, WS_FIT, WS_RUN = range(4)
-MAX_CHAN, MAX_FACET_N, STATIC_MAX_SRC = 128, 64, 4096
+MAX_CHAN, MAX_FACET_N, STATIC_MAX_SRC, MAX_POS = 128, 64, 4096, 5
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -66,7 +66,8 @@ class Params(ctypes.Structure):
                 ("tune_fit_ag", ctypes.c_int32), ("tune_fit_blocks", ctypes.c_int32),
                 ("tune_extract_waves", ctypes.c_int32), ("tune_sky_blocks", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("e_res", ctypes.c_double), ("np_max", ctypes.c_int32),
-                ("estimator", ctypes.c_int32), ("refit_bad", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("estimator", ctypes.c_int32), ("refit_bad", ctypes.c_int32), ("n_pos", ctypes.c_int32),
+                ("pos_step_arcsec", ctypes.c_double)]
 
 
 class Peaks(ctypes.Structure):

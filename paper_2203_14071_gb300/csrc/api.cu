@@ -35,6 +35,8 @@ bool params_ok(const rlf_params &p)
     if (p.estimator == RLF_ESTIMATOR_ADAPTIVE && !(p.np_max >= 1 && p.e_res > 0 && std::isfinite(p.e_res)))
         return false;
     if (p.refit_bad != 0 && p.refit_bad != 1) return false;
+    if (!(p.n_pos >= 0 && p.n_pos <= RLF_MAX_POS && (p.n_pos <= 1 || p.n_pos % 2 == 1))) return false;
+    if (p.n_pos > 1 && !(p.pos_step_arcsec > 0 && std::isfinite(p.pos_step_arcsec))) return false;
     if (p.tune_fit_ag != 0 && p.tune_fit_ag != 2 && p.tune_fit_ag != 4 && p.tune_fit_ag != 8) return false;
     if (p.tune_fit_blocks < 0 || p.tune_extract_waves < 0 || p.tune_sky_blocks < 0) return false;
     return true;
@@ -114,7 +116,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_status = take(64 * sizeof(int32_t));
     const size_t o_table = take((size_t)n_src * sizeof(SrcRow));
     const size_t o_upd = take((which == RLF_WS_SKY || run) ? (size_t)n_src * sizeof(SrcRow) : 0);
-    const size_t o_cells = take(fit ? 5 * cap * NN * sizeof(double) : 0);
+    const size_t o_cells = take(fit ? (4 + (size_t)n_offsets(p)) * cap * NN * sizeof(double) : 0);
     const size_t o_ncell = take(fit ? cap * sizeof(int32_t) : 0);
     const size_t o_order = take(fit ? cap * sizeof(int32_t) : 0);
     const size_t o_count = take(fit ? (cap + 1) * sizeof(int32_t) : 0);
@@ -220,6 +222,8 @@ void rlf_params_default(rlf_params *p)
     p->e_res = 0.003;
     p->np_max = 30;
     p->estimator = RLF_ESTIMATOR_GRID;
+    p->n_pos = 1;
+    p->pos_step_arcsec = 0.1;
 }
 
 size_t rlf_workspace_size(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params *p,
@@ -726,7 +730,7 @@ rlf_status rlf_fit_sources_mlp(const double *facets, const rlf_sources *src, int
         !out->alpha_arcsec || !out->flux_jy || !out->e1_smooth || !out->e2_smooth || !out->flag)
         return RLF_EINVAL;
     if (p->facet_n * p->facet_n * 2 != kMlpIn || p->precision == RLF_PREC_FP64 || p->n_e < kBoxE ||
-        p->n_alpha < kBoxA)
+        p->n_alpha < kBoxA || n_offsets(*p) > 1)
         return RLF_EUNSUPPORTED;
     Workspace ws;
     if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;

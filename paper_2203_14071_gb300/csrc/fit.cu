@@ -32,8 +32,8 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ table, int32_t N,
-               double inv_sigma2, size_t plane, T *__restrict__ cells, int32_t *__restrict__ ncell,
-               double *__restrict__ cc_out)
+               double inv_sigma2, int32_t n_pos, double pos_step, size_t plane, T *__restrict__ cells,
+               int32_t *__restrict__ ncell, double *__restrict__ cc_out)
 {
     __shared__ int32_t warp_tot[kThreads / 32];
     __shared__ double warp_cc[kThreads / 32];
@@ -69,7 +69,8 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
     for (int i = 0; i < wid; ++i) base += warp_tot[i];
     int pos = base + incl - mine;
     const double du = table[s].du;
-    (void)du;
+    const int nj = n_pos > 1 ? n_pos * n_pos : 1;
+    const int h = (n_pos - 1) / 2;
     T *uu = cells + (size_t)s * NN;
     T *uv = uu + plane;
     T *vv = uv + plane;
@@ -88,7 +89,26 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
             uv[pos] = (T)(cu * cv);
             vv[pos] = (T)(cv * cv);
             A[pos] = (T)(wc * sbar * sbar);
-            B[pos] = (T)(wc * sbar * dr);
+            if (nj == 1) {
+                B[pos] = (T)(wc * sbar * dr);
+            } else {
+                // B of offset x_j = (dl, dm): w s Re(D exp(-2 pi i k.x_j)), k = du (cu, cv)
+                const double di = f[NN + c] / n;
+                for (int j = 0; j < nj; ++j) {
+                    const double dl = (j / n_pos - h) * pos_step, dm = (j % n_pos - h) * pos_step;
+                    const double th = 2.0 * du * (cu * dl + cv * dm);   // phase / pi
+                    double sn, cs;
+                    if constexpr (std::is_same<T, float>::value) {
+                        float sf, cf;
+                        sincospif((float)th, &sf, &cf);
+                        sn = sf;
+                        cs = cf;
+                    } else {
+                        sincospi(th, &sn, &cs);
+                    }
+                    B[(size_t)j * plane + pos] = (T)(wc * sbar * (dr * cs + di * sn));
+                }
+            }
             ++pos;
         }
     }
@@ -367,9 +387,163 @@ __device__ double flux_marginal_mixed(double a, double b, double cc, int flux_pr
     return -0.5 * cc + b * b / (2.0 * a) + (double)(lg + logf(erfcf(x)));
 }
 
+// Position marginal (Sec. 2.4): ln of the mean over the NJ offsets of exp(logL(a, b_j)),
+// and the b of the best offset (the first of equal ones).  `mixed`: the exponentials
+// and the final logarithm, whose arguments are O(1), in FP32.
+template <int NJ>
+__device__ double position_marginal(bool mixed, double a, const double *b, double cc, int flux_prior,
+                                    double &b_best)
+{
+    double m = -INFINITY, sum = 0.0;
+    b_best = b[0];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const double v = mixed ? flux_marginal_mixed(a, b[j], cc, flux_prior) : flux_marginal(a, b[j], cc, flux_prior);
+        if (v > m) {
+            const double r = m == -INFINITY ? 0.0 : (mixed ? (double)expf((float)(m - v)) : exp(m - v));
+            sum = sum * r + 1.0;
+            m = v;
+            b_best = b[j];
+        } else {
+            sum += mixed ? (double)expf((float)(v - m)) : exp(v - m);
+        }
+    }
+    return m + (mixed ? (double)logf((float)(sum / NJ)) : log(sum / NJ));
+}
+
+// One work item of the likelihood grid with the position marginal: facet s, one
+// (e point, alpha node) per thread for pairs tile * kThreads .. + kThreads - 1, every
+// cell, every offset.  Per cell: the brightness M once, a += A M^2 and, for the NJ
+// offsets, b_j += B_j M, two offsets per paired FP32 instruction (FP32 tile sums added
+// to float pairs, as in grid_tile).  The thread then writes a, the best offset's b and
+// the marginal logL of its point (ga, gb, gl).
+template <typename T, int NJ, bool kGauss>
+__device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, const int32_t *__restrict__ ncell,
+                              const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst &gc,
+                              const double *__restrict__ ccv, double *__restrict__ ga, double *__restrict__ gb,
+                              double *__restrict__ gl)
+{
+    constexpr bool f32 = std::is_same<T, float>::value;
+    constexpr int NB = (NJ + 3) / 4 * 4;            // offsets padded to whole 16-byte rows (FP32)
+    constexpr int NP = (NJ + 1) / 2;                // offset pairs
+    constexpr int kT = f32 ? kCellTile : kCellTile / 2;
+    __shared__ __align__(16) T sg[kT][4];           // uu, uv, vv, A of each staged cell
+    __shared__ __align__(16) T sb[kT][NB];          // B_j of each staged cell
+    const int pair = tile * kThreads + threadIdx.x;
+    const int ne2 = gc.n_e * gc.n_e, na = gc.n_alpha;
+    const int e_idx = pair / na, k = pair % na;
+    const int i1 = e_idx / gc.n_e, i2 = e_idx % gc.n_e;
+    bool on = e_idx < ne2;
+    double e1 = 0.0, e2 = 0.0;
+    if (on) {
+        e1 = grid_e(gc, i1);
+        e2 = grid_e(gc, i2);
+        on = e1 * e1 + e2 * e2 < 1.0;
+    }
+    const double du = table[s].du;
+    T p11 = 0, p12 = 0, p22 = 0, ca = 0;
+    if (on) {
+        const double det = 1.0 - e1 * e1 - e2 * e2;
+        const double id2 = 1.0 / (det * det);
+        p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+        p12 = (T)(4.0 * e2 * id2);
+        p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+        const double al = grid_alpha(gc, k) * kArcsec * du;
+        ca = (T)(4.0 * kPi * kPi * al * al);
+    }
+    double da = 0.0, db[NJ];
+    float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        db[j] = 0.0;
+        bh[j] = bl[j] = 0.0f;
+    }
+    auto ff_add = [](float &hi, float &lo, float x) {
+        float sum, err;
+        two_sum(hi, x, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, err);
+    };
+    const int nc = ncell[s];
+    const T *cu = cells + (size_t)s * NN;
+    for (int c0 = 0; c0 < nc; c0 += kT) {
+        const int nt = min(kT, nc - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * nt; i += kThreads) sg[i % nt][i / nt] = cu[(i / nt) * plane + c0 + i % nt];
+        for (int i = threadIdx.x; i < NB * nt; i += kThreads) {
+            const int j = i / nt, c = i % nt;
+            sb[c][j] = j < NJ ? cu[(4 + j) * plane + c0 + c] : T(0);
+        }
+        __syncthreads();
+        if (!on) continue;
+        if constexpr (f32) {
+            float pa = 0.0f;
+            f32x2 pb2[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) pb2[q] = pk2(0.0f, 0.0f);
+            for (int c = 0; c < nt; ++c) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(&sg[c][0]);
+                const float Q = p11 * g4.x + p12 * g4.y + p22 * g4.z;
+                const float M = brightness<kGauss>(ca, Q);
+                pa = fmaf(g4.w * M, M, pa);
+                const f32x2 M2 = pk2(M, M);
+                const ulonglong2 *row = reinterpret_cast<const ulonglong2 *>(&sb[c][0]);
+#pragma unroll
+                for (int q = 0; q < NB / 4; ++q) {
+                    const ulonglong2 v = row[q];
+                    pb2[2 * q] = fma2(v.x, M2, pb2[2 * q]);
+                    if (2 * q + 1 < NP) pb2[2 * q + 1] = fma2(v.y, M2, pb2[2 * q + 1]);
+                }
+            }
+            ff_add(ah, al, pa);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float b0, b1;
+                up2(pb2[q], b0, b1);
+                ff_add(bh[2 * q], bl[2 * q], b0);
+                if (2 * q + 1 < NJ) ff_add(bh[2 * q + 1], bl[2 * q + 1], b1);
+            }
+        } else {
+            T pa = T(0), pb[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) pb[j] = T(0);
+            for (int c = 0; c < nt; ++c) {
+                const T Q = p11 * sg[c][0] + p12 * sg[c][1] + p22 * sg[c][2];
+                const T M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
+                const T AM = sg[c][3] * M;
+                pa += AM * M;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) pb[j] += sb[c][j] * M;
+            }
+            da += (double)pa;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
+        }
+    }
+    if (e_idx >= ne2) return;
+    if constexpr (f32) {
+        da = (double)ah + (double)al;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) db[j] = (double)bh[j] + (double)bl[j];
+    }
+    const size_t g = ((size_t)s * ne2 + e_idx) * na + k;
+    if (on && nc > 0) {
+        double bb;
+        gl[g] = position_marginal<NJ>(f32, da, db, ccv[s], gc.flux_prior, bb);
+        ga[g] = da;
+        gb[g] = bb;
+    } else {
+        gl[g] = -INFINITY;
+        ga[g] = 0.0;
+        gb[g] = 0.0;
+    }
+}
+
 // Estimate of facet s from its complete a, b grid (block-wide, FP64; with `mixed`
-// the logarithms, error functions and exponentials in FP32).
-__device__ void estimate_source(bool mixed, int s, const double *__restrict__ ga, const double *__restrict__ gb,
+// the logarithms, error functions and exponentials in FP32).  logl_ready: gl already
+// holds logL of every valid point (the position marginal's grid writes it).
+__device__ void estimate_source(bool mixed, bool logl_ready, int s, const double *__restrict__ ga,
+                                const double *__restrict__ gb,
                                 double *__restrict__ gl, const int32_t *__restrict__ ncell,
                                 const double *__restrict__ ccv, const SrcRow *__restrict__ table,
                                 const GridConst &gc, const rlf_fit_out &out, int32_t out_offset,
@@ -415,7 +589,8 @@ __device__ void estimate_source(bool mixed, int s, const double *__restrict__ ga
             in_box = d1 >= 0 && d1 < kBoxE && d2 >= 0 && d2 < kBoxE && dk >= 0 && dk < kBoxA;
         }
         if (in_box && nc > 0 && e1 * e1 + e2 * e2 < 1.0) {
-            v = mixed ? flux_marginal_mixed(a[g], b[g], cc, gc.flux_prior) : flux_marginal(a[g], b[g], cc, gc.flux_prior);
+            if (logl_ready) v = lg[g];
+            else v = mixed ? flux_marginal_mixed(a[g], b[g], cc, gc.flux_prior) : flux_marginal(a[g], b[g], cc, gc.flux_prior);
             if (!isfinite(v)) bad_num = true;
         }
         lg[g] = v;
@@ -596,8 +771,42 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
                 }
                 __syncthreads();
             }
-            estimate_source(std::is_same<T, float>::value, s, ga, gb, gl, ncell, ccv, table, gc, out, out_offset,
-                            status, map_out);
+            estimate_source(std::is_same<T, float>::value, false, s, ga, gb, gl, ncell, ccv, table, gc, out,
+                            out_offset, status, map_out);
+        }
+        __syncthreads();
+    }
+}
+
+// The persistent fit with the position marginal: work item = (facet in LPT order, tile
+// of (e point, alpha node) pairs) over every cell; the CTA completing a facet's last
+// tile runs its estimate on the marginal logL the tiles wrote.
+template <typename T, int NJ, bool kGauss>
+__global__ void __launch_bounds__(kThreads, 2)
+fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell,
+                          const SrcRow *__restrict__ table, size_t plane, int32_t NN, int32_t tiles_per_src,
+                          int32_t count, const int32_t *__restrict__ order, int32_t *__restrict__ counters,
+                          const GridConst gc, double *__restrict__ ga, double *__restrict__ gb,
+                          double *__restrict__ gl, const double *__restrict__ ccv, rlf_fit_out out,
+                          int32_t out_offset, int32_t *__restrict__ status)
+{
+    __shared__ int s_item, s_last;
+    const int total = count * tiles_per_src;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counters, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int s = order[item / tiles_per_src];
+        grid_tile_pos<T, NJ, kGauss>(s, item % tiles_per_src, cells, ncell, table, plane, NN, gc, ccv, ga, gb, gl);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&counters[1 + s], 1) == tiles_per_src - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            estimate_source(std::is_same<T, float>::value, true, s, ga, gb, gl, ncell, ccv, table, gc, out,
+                            out_offset, status, nullptr);
         }
         __syncthreads();
     }
@@ -737,7 +946,7 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
     __syncthreads();
 }
 
-template <typename T, bool kGauss>
+template <typename T, bool kGauss, int NJ>
 __global__ void __launch_bounds__(kThreads)
 adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table,
                 size_t plane, int32_t NN, const GridConst gc, const double *__restrict__ ga,
@@ -745,7 +954,9 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                 double *__restrict__ scratch, rlf_fit_out out, int32_t out_offset)
 {
     constexpr bool mixed = std::is_same<T, float>::value;
-    __shared__ T sm[5][kCellTile];
+    // cells per staged tile: uu, uv, vv, A and NJ B planes (B per position offset)
+    constexpr int kTA = (NJ > 1 && !mixed) ? kCellTile / 2 : kCellTile;
+    __shared__ T sm[4 + NJ][kTA];
     __shared__ double qp[64], alph[64], lnp[64];
     __shared__ double Ls[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
     __shared__ double As[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
@@ -821,47 +1032,67 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
             const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
             const double alr = alph[k] * kArcsec * S.du;
             const T ca = (T)(4.0 * kPi * kPi * alr * alr);
-            float ah = 0.0f, al = 0.0f, bh = 0.0f, bl = 0.0f;
-            double da = 0.0, db = 0.0;
-            for (int c0 = 0; c0 < nc; c0 += kCellTile) {
-                const int nt = min(kCellTile, nc - c0);
+            float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
+            double da = 0.0, db[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                bh[j] = bl[j] = 0.0f;
+                db[j] = 0.0;
+            }
+            for (int c0 = 0; c0 < nc; c0 += kTA) {
+                const int nt = min(kTA, nc - c0);
                 __syncthreads();
                 for (int j = threadIdx.x; j < nt; j += kThreads) {
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
+                    for (int q = 0; q < 4 + NJ; ++q) sm[q][j] = cu[q * plane + c0 + j];
                 }
                 __syncthreads();
                 if (!on) continue;
-                T pa = T(0), pb = T(0);
+                T pa = T(0), pb[NJ];
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) pb[j] = T(0);
                 for (int c = 0; c < nt; ++c) {
                     const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
                     T M;
                     if constexpr (mixed) M = brightness<kGauss>(ca, Q);
                     else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
                     pa += sm[3][c] * M * M;
-                    pb += sm[4][c] * M;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) pb[j] += sm[4 + j][c] * M;
                 }
                 if constexpr (mixed) {
                     float sum, err;
                     two_sum(ah, pa, sum, err);
                     ah = sum;
                     al = __fadd_rn(al, err);
-                    two_sum(bh, pb, sum, err);
-                    bh = sum;
-                    bl = __fadd_rn(bl, err);
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        two_sum(bh[j], pb[j], sum, err);
+                        bh[j] = sum;
+                        bl[j] = __fadd_rn(bl[j], err);
+                    }
                 } else {
                     da += (double)pa;
-                    db += (double)pb;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
                 }
             }
             if (on) {
                 if constexpr (mixed) {
                     da = (double)ah + (double)al;
-                    db = (double)bh + (double)bl;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) db[j] = (double)bh[j] + (double)bl[j];
                 }
                 sa[pr] = da;
-                sb[pr] = db;
-                slg[pr] = mixed ? flux_marginal_mixed(da, db, cc, gc.flux_prior) : flux_marginal(da, db, cc, gc.flux_prior);
+                if constexpr (NJ == 1) {
+                    sb[pr] = db[0];
+                    slg[pr] = mixed ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
+                                    : flux_marginal(da, db[0], cc, gc.flux_prior);
+                } else {
+                    double bb;
+                    slg[pr] = position_marginal<NJ>(mixed, da, db, cc, gc.flux_prior, bb);
+                    sb[pr] = bb;
+                }
             }
         }
         __threadfence_block();
@@ -962,18 +1193,76 @@ cudaError_t launch_persistent_ag(const T *cells, const SrcRow *table, size_t pla
     }
 }
 
+template <typename T, int NJ>
+cudaError_t launch_adaptive_nj(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                               const GridConst &gc, const Workspace &ws, const rlf_fit_out &out, int32_t out_offset,
+                               cudaStream_t st)
+{
+    auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? adaptive_kernel<T, true, NJ> : adaptive_kernel<T, false, NJ>;
+    kern<<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc, ws.adapt, out,
+                                     out_offset);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_adaptive(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
                             const GridConst &gc, const Workspace &ws, const rlf_fit_out &out, int32_t out_offset,
                             cudaStream_t st)
 {
-    if (gc.profile == RLF_PROFILE_GAUSSIAN)
-        adaptive_kernel<T, true><<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb,
-                                                             ws.gl, ws.cc, ws.adapt, out, out_offset);
-    else
-        adaptive_kernel<T, false><<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb,
-                                                              ws.gl, ws.cc, ws.adapt, out, out_offset);
+    switch (gc.n_pos) {
+    case 3: return launch_adaptive_nj<T, 9>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+    case 5: return launch_adaptive_nj<T, 25>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+    default: return launch_adaptive_nj<T, 1>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+    }
+}
+
+template <typename T, int NJ>
+cudaError_t launch_persistent_pos(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                                  const GridConst &gc, const rlf_params &p, const Workspace &ws,
+                                  const rlf_fit_out &out, int32_t out_offset, cudaStream_t st)
+{
+    const int pairs = gc.n_e * gc.n_e * gc.n_alpha;
+    const int tiles = (pairs + kThreads - 1) / kThreads;
+    auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? fit_persistent_pos_kernel<T, NJ, true>
+                                                   : fit_persistent_pos_kernel<T, NJ, false>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (p.tune_fit_blocks > 0 && p.tune_fit_blocks < per_sm) per_sm = p.tune_fit_blocks;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (int64_t)count * tiles, wave = (int64_t)sms * per_sm;
+    const int grid = (int)(items < wave ? items : wave);
+    if ((e = cudaMemsetAsync(ws.counters, 0, (size_t)(count + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
+    lpt_order_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, st>>>(ws.ncell, count, ws.order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kern<<<grid, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, tiles, count, ws.order, ws.counters, gc, ws.ga,
+                                    ws.gb, ws.gl, ws.cc, out, out_offset, ws.status);
     return cudaGetLastError();
+}
+
+// the grid fit (and adaptive refinement) of `count` compacted facets
+template <typename T>
+cudaError_t launch_grid_fit(const T *cells, const SrcRow *table, size_t plane, int32_t NN, int32_t count,
+                            const GridConst &gc, const rlf_params &p, const Workspace &ws, const rlf_fit_out &out,
+                            int32_t out_offset, cudaStream_t st)
+{
+    cudaError_t e;
+    if (gc.n_pos == 3)
+        e = launch_persistent_pos<T, 9>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    else if (gc.n_pos == 5)
+        e = launch_persistent_pos<T, 25>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
+    else if constexpr (std::is_same<T, float>::value)
+        e = launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
+                                        nullptr, st);
+    else
+        e = launch_persistent<double, 4>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
+                                         nullptr, st);
+    if (e == cudaSuccess && p.estimator == RLF_ESTIMATOR_ADAPTIVE)
+        e = launch_adaptive<T>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
+    return e;
 }
 
 }  // namespace
@@ -1046,7 +1335,8 @@ GridConst grid_const(const rlf_params &p)
     gc.n_ag = 0;
     gc.flux_prior = p.flux_prior;
     gc.profile = p.profile;
-    gc.pad = 0;
+    gc.n_pos = p.n_pos > 1 ? p.n_pos : 1;
+    gc.pos_step = p.pos_step_arcsec * kArcsec;
     gc.estimator = p.estimator;
     gc.np_max = p.np_max;
     gc.e_res = p.e_res;
@@ -1071,24 +1361,16 @@ cudaError_t launch_fit(const double *facets, const SrcRow *table, int32_t count,
     cudaError_t e;
     if (p.precision != RLF_PREC_FP64) {
         float *cells = static_cast<float *>(ws.cells);
-        compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
-                                                          ws.ncell, ws.cc);
+        compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, gc.n_pos, gc.pos_step,
+                                                          plane, cells, ws.ncell, ws.cc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = launch_persistent_ag<float>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out,
-                                        out_offset, nullptr, st);
-        if (e == cudaSuccess && p.estimator == RLF_ESTIMATOR_ADAPTIVE)
-            e = launch_adaptive<float>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
-        return e;
+        return launch_grid_fit<float>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
     }
     double *cells = static_cast<double *>(ws.cells);
-    compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells,
-                                                       ws.ncell, ws.cc);
+    compact_kernel<double><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, gc.n_pos, gc.pos_step, plane,
+                                                       cells, ws.ncell, ws.cc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_persistent<double, 4>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, out_offset,
-                                     nullptr, st);
-    if (e == cudaSuccess && p.estimator == RLF_ESTIMATOR_ADAPTIVE)
-        e = launch_adaptive<double>(cells, table, plane, NN, count, gc, ws, out, out_offset, st);
-    return e;
+    return launch_grid_fit<double>(cells, table, plane, NN, count, gc, p, ws, out, out_offset, st);
 }
 
 cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t count, const rlf_params &p,
@@ -1099,8 +1381,8 @@ cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t co
     GridConst gc = grid_const(p);
     const size_t plane = (size_t)count * NN;
     float *cells = static_cast<float *>(ws.cells);
-    compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, plane, cells, ws.ncell,
-                                                      ws.cc);
+    compact_kernel<float><<<count, kThreads, 0, st>>>(facets, table, N, gc.inv_sigma2, 1, 0.0, plane, cells,
+                                                      ws.ncell, ws.cc);
     cudaError_t e = cudaGetLastError();
     // the network's proposal of each facet's sub-box
     const MlpWeights W = mlp_weights(const_cast<void *>(weights));

@@ -170,11 +170,19 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo)
 constexpr int kBoxE = 7, kBoxA = 5;                     // learned-proposal sub-box (e1, e2, alpha nodes)
 constexpr int kMlpIn = 8192, kMlpHidden = 256, kMlpOut = 6, kMlpOutPad = 8;
 
+// Position offsets of the likelihood's position marginal (Sec. 2.4): n_pos^2, 1 when
+// the position is exact.
+inline int n_offsets(const rlf_params &p)
+{
+    return p.n_pos > 1 ? p.n_pos * p.n_pos : 1;
+}
+
 // Grid constants of the likelihood (Sec. 2.4).
 struct GridConst {
     const int32_t *box;     // per-facet sub-box origins [count][3] (e1, e2, alpha node), or null: full grid
     int32_t n_e, n_alpha, n_ag, flux_prior;
-    int32_t profile, pad;
+    int32_t profile, n_pos; // n_pos: position offsets per axis (1: position exact)
+    double pos_step;        // position offset step, radians
     int32_t estimator, np_max;
     double e_res;
     double e_max;
@@ -189,7 +197,7 @@ struct Workspace {
     int32_t *status;        // [64] device status words
     SrcRow *table;          // [n_src]
     SrcRow *upd;            // [n_src] update table
-    void *cells;            // [5][cap][N*N] T
+    void *cells;            // [4 + n_pos^2][cap][N*N] T: uu, uv, vv, A, then B per position offset
     int32_t *ncell;         // [cap]
     int32_t *order;         // [cap] facets in largest-first order
     int32_t *counters;      // [cap + 1] work-item counter, per-facet finished tiles

@@ -39,7 +39,7 @@ def test_struct_sizes_match_header():
     # pointers and 64-bit fields must land where the C compiler puts them
     assert ctypes.sizeof(rlf.Uvw) == 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(rlf.Sources) == 4 + 4 + 6 * 8
-    assert ctypes.sizeof(rlf.Params) == 14 * 8 + 16 * 4
+    assert ctypes.sizeof(rlf.Params) == 15 * 8 + 16 * 4
     assert ctypes.sizeof(rlf.FitOut) == 9 * 8
 
 
@@ -64,6 +64,11 @@ def test_sizes(L):
     assert rlf.workspace_size(1000, 8, 200, p1, rlf.WS_RUN) < run
     bad = rlf.params_default(facet_n=63)
     assert rlf.workspace_size(1000, 8, 200, bad, rlf.WS_RUN) == 0
+    # the position marginal keeps one B plane per offset: 4 + n_pos^2 cell planes
+    pos = rlf.params_default(n_pos=5)
+    grow = rlf.workspace_size(1000, 8, 200, pos, rlf.WS_FIT) - fit
+    assert grow == 24 * 200 * 64 * 64 * 8
+    assert rlf.params_default().n_pos == 1 and rlf.params_default().pos_step_arcsec == 0.1
     assert rlf.workspace_size(1000, 8, 0, p, rlf.WS_RUN) == 0
 
 
@@ -104,7 +109,9 @@ def test_host_argument_checks(L):
     assert f(ctypes.byref(uvw2), ctypes.byref(src), ctypes.byref(p), 0x3000, ws, 1 << 40, None) == rlf.RLF_EUNSUPPORTED
     # parameters out of range
     for bad in (dict(facet_n=65), dict(facet_n=7), dict(n_e=1), dict(n_e=33), dict(sigma_jy=0.0),
-                dict(precision=4), dict(r_min_arcsec=2.0, r_max_arcsec=1.0), dict(thresh_frac=0.0)):
+                dict(precision=4), dict(r_min_arcsec=2.0, r_max_arcsec=1.0), dict(thresh_frac=0.0),
+                dict(n_pos=2), dict(n_pos=7), dict(n_pos=-1), dict(n_pos=3, pos_step_arcsec=0.0),
+                dict(n_pos=5, pos_step_arcsec=float("nan"))):
         pb = rlf.params_default(**bad)
         assert f(ctypes.byref(uvw), ctypes.byref(src), ctypes.byref(pb), 0x3000, ws, 1 << 40, None) == rlf.RLF_EINVAL
     # source range checks
