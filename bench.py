@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--estimator", default="grid", choices=["grid", "adaptive"],
                     help="ellipticity estimator: the fixed grid, or adaptive sampling around the maximum")
     ap.add_argument("--sigma-scale", type=float, default=1.0, help="noise per visibility x this")
+    ap.add_argument("--n-pos", type=int, default=1, choices=[1, 3, 5],
+                    help="position marginal: offsets per axis (1: catalogue positions exact)")
+    ap.add_argument("--pos-step", type=float, default=0.1, help="position marginal: offset step, arcsec")
+    ap.add_argument("--pos-error", type=float, default=0.0,
+                    help="catalogue positions off the true ones by a seeded uniform offset of up to this, arcsec")
     ap.add_argument("--refit-bad", action="store_true",
                     help="fit the bad fits again after the whole catalogue (times rlf_run calls: not capturable)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -191,7 +196,8 @@ def run_reference(args, rank, world):
     wl = synth.workload(args.workload)
     obs = synth.make_observation(wl)
     cat = synth.make_catalogue(wl)
-    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy)
+    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, n_pos=args.n_pos,
+                                   pos_step_arcsec=args.pos_step)
     oracle.build()
     for _ in range(args.warmup):
         oracle_sample_step(wl, obs, cat, params)
@@ -209,7 +215,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": sec_per_source * cat.n_src * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "n_vis": obs.n_rows * obs.n_chan, "n_src": cat.n_src},
+            "config": {"workload": args.workload, "n_vis": obs.n_rows * obs.n_chan, "n_src": cat.n_src,
+                       "n_pos": args.n_pos},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "fits/s", "cores": 1, "sample": sample,
                              "wall_s": wall},
             "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -232,14 +239,20 @@ def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
     t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
     obs = rlf.Observation(t64(obs_np.u), t64(obs_np.v), t64(obs_np.w), obs_np.freq_hz, obs_np.n_bl)
     zeros = torch.zeros(n, dtype=torch.float64, device=dev)
-    cat = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), t64(cat_np.flux_jy), zeros.clone(), zeros.clone())
-    truth = rlf.Catalogue(cat.l, cat.m, cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2), t64(cat_np.alpha_arcsec))
+    # the catalogue the chain is given; its positions may be off the true ones (position marginal)
+    pos_err = getattr(args, "pos_error", 0.0) * math.pi / 648000.0
+    off = np.random.default_rng(4321).uniform(-1.0, 1.0, size=(2, n)) * pos_err
+    cat = rlf.Catalogue(t64(cat_np.l + off[0]), t64(cat_np.m + off[1]), t64(cat_np.flux_jy), zeros.clone(),
+                        zeros.clone())
+    truth = rlf.Catalogue(t64(cat_np.l), t64(cat_np.m), cat.flux_jy, t64(cat_np.e1), t64(cat_np.e2),
+                          t64(cat_np.alpha_arcsec))
     sigma = wl.sigma_jy * getattr(args, "sigma_scale", 1.0)
     params = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=sigma, chunk=args.chunk,
                                 precision=prec, update_mode=args.update_mode,
                                 profile=rlf.PROFILE_GAUSSIAN if args.profile == "gaussian" else 0,
                                 estimator=rlf.ESTIMATOR_ADAPTIVE if getattr(args, "estimator", "grid") == "adaptive"
-                                else rlf.ESTIMATOR_GRID, refit_bad=1 if getattr(args, "refit_bad", False) else 0)
+                                else rlf.ESTIMATOR_GRID, refit_bad=1 if getattr(args, "refit_bad", False) else 0,
+                                n_pos=getattr(args, "n_pos", 1), pos_step_arcsec=getattr(args, "pos_step", 0.1))
     ws = rlf.alloc_workspace(R, C, n, params, rlf.WS_RUN, device=dev)
     data = torch.empty(R * C * 2, dtype=torch.float32, device=dev)
     rlf.sky_model(obs, truth, params, data, ws, stream)
@@ -439,6 +452,7 @@ def main():
                    "chunk": args.chunk if args.chunk > 0 else n_src, "precision": args.precision,
                    "update_mode": args.update_mode, "profile": args.profile, "estimator": args.estimator,
                    "sigma_jy": params.sigma_jy, "refit_bad": bool(args.refit_bad),
+                   "n_pos": args.n_pos, "pos_step_arcsec": args.pos_step, "pos_error_arcsec": args.pos_error,
                    "l2": "inputs larger than L2 (no flush)"},
         "sky_model_gvis_s": comp["sky_gvis_s"],
         "fit_only_fits_per_s": n_src / (comp["phases_ms"]["fit"] * 1e-3),
@@ -456,7 +470,7 @@ def main():
                       {f: int(getattr(params, f)) for f in rlf.TUNE_FIELDS}}
     if graph is not None:
         graph.close()
-    if not args.no_mlp and world == 1:
+    if not args.no_mlp and world == 1 and args.n_pos == 1:
         line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream, train_steps=args.mlp_steps)
     if not args.no_batched and world == 1:
         del ws, data, sky
@@ -465,7 +479,7 @@ def main():
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(W["wl"], obs_np, cat_np)
+        line["cpu_baseline"] = cpu_baseline(W["wl"], obs_np, cat_np, args.n_pos, args.pos_step)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -597,10 +611,12 @@ def refit_launches(params, res, n_src):
     return launches
 
 
-def roofline_one(name, t_ms, units, row_src, peaks):
+def roofline_one(name, t_ms, units, row_src, peaks, fp32=None):
     """ALU roofline: the shortest time the FP32 and MUFU budgets allow for the
     algorithmic op counts, against the measured unit rates."""
-    o = OPS[name]
+    o = dict(OPS[name])
+    if fp32 is not None:
+        o["fp32"] = fp32
     fp32_rate = max(peaks["fp32_fma_per_s"], peaks.get("fp32x2_fma_per_s", 0.0))
     mufu_rate = min(peaks["mufu_rsqrt_per_s"], peaks["mufu_sin_per_s"])
     t_fp32 = (o["fp32"] * units + o["fp32_rs"] * row_src) / fp32_rate
@@ -623,7 +639,9 @@ def roofline(comp, peaks, params, n_vis, n_src, R, C):
     # phase work is counted in the same proportion
     frac_in = comp["in_window_pairs"] / (float(n_vis) * n_src)
     out["extract"] = roofline_one("extract", ph["extract"], comp["in_window_pairs"], float(R) * n_src * frac_in, peaks)
-    out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks)
+    # the fit's FP32 ops per evaluation: the brightness (3), a (2) and one b per position offset
+    nj = params.n_pos * params.n_pos if params.n_pos > 1 else 1
+    out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks, fp32=5.0 + nj)
     dom = max(ph, key=ph.get)
     return out[dom], out
 
@@ -662,9 +680,10 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
             "d2h_bytes_per_step": 2 * n * 8}
 
 
-def cpu_baseline(wl, obs_np, cat_np):
+def cpu_baseline(wl, obs_np, cat_np, n_pos=1, pos_step=0.1):
     import oracle
-    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy)
+    params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, n_pos=n_pos,
+                                   pos_step_arcsec=pos_step)
     oracle.build()
     t0 = time.perf_counter()
     sec = oracle_sample_step(wl, obs_np, cat_np, params, rows_stride=1)

@@ -116,7 +116,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_status = take(64 * sizeof(int32_t));
     const size_t o_table = take((size_t)n_src * sizeof(SrcRow));
     const size_t o_upd = take((which == RLF_WS_SKY || run) ? (size_t)n_src * sizeof(SrcRow) : 0);
-    const size_t o_cells = take(fit ? (4 + (size_t)n_offsets(p)) * cap * NN * sizeof(double) : 0);
+    const size_t o_cells = take(fit ? (4 + (size_t)b_stride(n_offsets(p))) * cap * NN * sizeof(double) : 0);
     const size_t o_ncell = take(fit ? cap * sizeof(int32_t) : 0);
     const size_t o_order = take(fit ? cap * sizeof(int32_t) : 0);
     const size_t o_count = take(fit ? (cap + 1) * sizeof(int32_t) : 0);

@@ -92,8 +92,12 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
             if (nj == 1) {
                 B[pos] = (T)(wc * sbar * dr);
             } else {
-                // B of offset x_j = (dl, dm): w s Re(D exp(-2 pi i k.x_j)), k = du (cu, cv)
+                // B of offset x_j = (dl, dm): w s Re(D exp(-2 pi i k.x_j)), k = du (cu, cv); the
+                // cell's values side by side (zero padding)
                 const double di = f[NN + c] / n;
+                const int nb = b_stride(nj);
+                T *row = cells + 4 * plane + ((size_t)s * NN + pos) * nb;
+                for (int j = nj; j < nb; ++j) row[j] = T(0);
                 for (int j = 0; j < nj; ++j) {
                     const double dl = (j / n_pos - h) * pos_step, dm = (j % n_pos - h) * pos_step;
                     const double th = 2.0 * du * (cu * dl + cv * dm);   // phase / pi
@@ -106,7 +110,7 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
                     } else {
                         sincospi(th, &sn, &cs);
                     }
-                    B[(size_t)j * plane + pos] = (T)(wc * sbar * (dr * cs + di * sn));
+                    row[j] = (T)(wc * sbar * (dr * cs + di * sn));
                 }
             }
             ++pos;
@@ -387,28 +391,72 @@ __device__ double flux_marginal_mixed(double a, double b, double cc, int flux_pr
     return -0.5 * cc + b * b / (2.0 * a) + (double)(lg + logf(erfcf(x)));
 }
 
-// Position marginal (Sec. 2.4): ln of the mean over the NJ offsets of exp(logL(a, b_j)),
-// and the b of the best offset (the first of equal ones).  `mixed`: the exponentials
-// and the final logarithm, whose arguments are O(1), in FP32.
+// Position marginal (Sec. 2.4), FP64: ln of the mean over the NJ offsets of
+// exp(logL(a, b_j)), and the b of the best offset (the first of equal ones).
 template <int NJ>
-__device__ double position_marginal(bool mixed, double a, const double *b, double cc, int flux_prior,
-                                    double &b_best)
+__device__ double position_marginal(double a, const double *b, double cc, int flux_prior, double &b_best)
 {
     double m = -INFINITY, sum = 0.0;
     b_best = b[0];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-        const double v = mixed ? flux_marginal_mixed(a, b[j], cc, flux_prior) : flux_marginal(a, b[j], cc, flux_prior);
+        const double v = flux_marginal(a, b[j], cc, flux_prior);
         if (v > m) {
-            const double r = m == -INFINITY ? 0.0 : (mixed ? (double)expf((float)(m - v)) : exp(m - v));
-            sum = sum * r + 1.0;
+            sum = sum * (m == -INFINITY ? 0.0 : exp(m - v)) + 1.0;
             m = v;
             b_best = b[j];
         } else {
-            sum += mixed ? (double)expf((float)(v - m)) : exp(v - m);
+            sum += exp(v - m);
         }
     }
-    return m + (mixed ? (double)logf((float)(sum / NJ)) : log(sum / NJ));
+    return m + log(sum / NJ);
+}
+
+// The same from float-pair sums b_j = bh_j + bl_j, with no FP64 per offset.  logL
+// grows with b (flux prior S >= 0; with the real-line prior, with |b|), so the best
+// offset is the largest b, and logL_j - logL_best = F(b_j) - F(b_best) with
+// F(b) = b^2/(2a) + ln erfc(-b/sqrt(2a)) (= ln erfcx(-b/sqrt(2a)) for b < 0): the b^2
+// part is (b_j - b_m)(b_j + b_m)/(2a), both factors formed from the pairs in FP32, so
+// it keeps FP32 relative accuracy however large b^2/(2a) is.  One FP64 logL, at the
+// best offset.
+template <int NJ>
+__device__ double position_marginal_ff(double a, const float *bh, const float *bl, double cc, int flux_prior,
+                                       double &b_best)
+{
+    float mh = bh[0], ml = bl[0];
+#pragma unroll
+    for (int j = 1; j < NJ; ++j) {
+        const float d = (bh[j] - mh) + (bl[j] - ml);
+        const float s = (bh[j] + mh) + (bl[j] + ml);
+        if (flux_prior == 1 ? d * s > 0.0f : d > 0.0f) {
+            mh = bh[j];
+            ml = bl[j];
+        }
+    }
+    b_best = (double)mh + (double)ml;
+    const float ia = 0.5f / (float)a, r2a = rsqrtf((float)(2.0 * a));
+    const float bm = mh + ml;
+    float lm = 0.0f;
+    if (flux_prior != 1) {
+        const float xm = -bm * r2a;
+        lm = xm > 0.0f ? logf(erfcxf(xm)) : logf(erfcf(xm));
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const float d = (bh[j] - mh) + (bl[j] - ml);
+        const float s = (bh[j] + mh) + (bl[j] + ml);
+        float G;
+        if (flux_prior == 1) {
+            G = d * s * ia;
+        } else {
+            const float bj = bh[j] + bl[j], xj = -bj * r2a;
+            const float q = bj >= 0.0f ? d * s * ia : (bm >= 0.0f ? -bm * bm * ia : 0.0f);
+            G = q + (xj > 0.0f ? logf(erfcxf(xj)) : logf(erfcf(xj))) - lm;
+        }
+        sum += expf(G);
+    }
+    return flux_marginal_mixed(a, b_best, cc, flux_prior) + (double)logf(sum / NJ);
 }
 
 // One work item of the likelihood grid with the position marginal: facet s, one
@@ -424,7 +472,7 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
                               double *__restrict__ gl)
 {
     constexpr bool f32 = std::is_same<T, float>::value;
-    constexpr int NB = (NJ + 3) / 4 * 4;            // offsets padded to whole 16-byte rows (FP32)
+    constexpr int NB = (NJ + 3) / 4 * 4;            // B values per cell (b_stride)
     constexpr int NP = (NJ + 1) / 2;                // offset pairs
     constexpr int kT = f32 ? kCellTile : kCellTile / 2;
     __shared__ __align__(16) T sg[kT][4];           // uu, uv, vv, A of each staged cell
@@ -470,9 +518,14 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
         const int nt = min(kT, nc - c0);
         __syncthreads();
         for (int i = threadIdx.x; i < 4 * nt; i += kThreads) sg[i % nt][i / nt] = cu[(i / nt) * plane + c0 + i % nt];
-        for (int i = threadIdx.x; i < NB * nt; i += kThreads) {
-            const int j = i / nt, c = i % nt;
-            sb[c][j] = j < NJ ? cu[(4 + j) * plane + c0 + c] : T(0);
+        // the cells' B rows: one contiguous run (16-byte vectors in FP32)
+        const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
+        if constexpr (f32) {
+            const float4 *src = reinterpret_cast<const float4 *>(brow);
+            float4 *dst = reinterpret_cast<float4 *>(&sb[0][0]);
+            for (int i = threadIdx.x; i < nt * NB / 4; i += kThreads) dst[i] = src[i];
+        } else {
+            for (int i = threadIdx.x; i < nt * NB; i += kThreads) (&sb[0][0])[i] = brow[i];
         }
         __syncthreads();
         if (!on) continue;
@@ -481,6 +534,7 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
             f32x2 pb2[NP];
 #pragma unroll
             for (int q = 0; q < NP; ++q) pb2[q] = pk2(0.0f, 0.0f);
+#pragma unroll 2
             for (int c = 0; c < nt; ++c) {
                 const float4 g4 = *reinterpret_cast<const float4 *>(&sg[c][0]);
                 const float Q = p11 * g4.x + p12 * g4.y + p22 * g4.z;
@@ -521,15 +575,15 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
         }
     }
     if (e_idx >= ne2) return;
-    if constexpr (f32) {
-        da = (double)ah + (double)al;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) db[j] = (double)bh[j] + (double)bl[j];
-    }
     const size_t g = ((size_t)s * ne2 + e_idx) * na + k;
     if (on && nc > 0) {
         double bb;
-        gl[g] = position_marginal<NJ>(f32, da, db, ccv[s], gc.flux_prior, bb);
+        if constexpr (f32) {
+            da = (double)ah + (double)al;
+            gl[g] = position_marginal_ff<NJ>(da, bh, bl, ccv[s], gc.flux_prior, bb);
+        } else {
+            gl[g] = position_marginal<NJ>(da, db, ccv[s], gc.flux_prior, bb);
+        }
         ga[g] = da;
         gb[g] = bb;
     } else {
@@ -956,7 +1010,9 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
     constexpr bool mixed = std::is_same<T, float>::value;
     // cells per staged tile: uu, uv, vv, A and NJ B planes (B per position offset)
     constexpr int kTA = (NJ > 1 && !mixed) ? kCellTile / 2 : kCellTile;
-    __shared__ T sm[4 + NJ][kTA];
+    constexpr int NB = NJ > 1 ? (NJ + 3) / 4 * 4 : 1;   // B values per cell (b_stride)
+    __shared__ T sm[NJ > 1 ? 4 : 5][kTA];
+    __shared__ __align__(16) T sbr[NJ > 1 ? kTA : 1][NB];
     __shared__ double qp[64], alph[64], lnp[64];
     __shared__ double Ls[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
     __shared__ double As[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
@@ -1044,7 +1100,11 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                 __syncthreads();
                 for (int j = threadIdx.x; j < nt; j += kThreads) {
 #pragma unroll
-                    for (int q = 0; q < 4 + NJ; ++q) sm[q][j] = cu[q * plane + c0 + j];
+                    for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
+                }
+                if constexpr (NJ > 1) {
+                    const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
+                    for (int i = threadIdx.x; i < nt * NB; i += kThreads) (&sbr[0][0])[i] = brow[i];
                 }
                 __syncthreads();
                 if (!on) continue;
@@ -1057,8 +1117,12 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                     if constexpr (mixed) M = brightness<kGauss>(ca, Q);
                     else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
                     pa += sm[3][c] * M * M;
+                    if constexpr (NJ == 1) {
+                        pb[0] += sm[4][c] * M;
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) pb[j] += sm[4 + j][c] * M;
+                        for (int j = 0; j < NJ; ++j) pb[j] += sbr[c][j] * M;
+                    }
                 }
                 if constexpr (mixed) {
                     float sum, err;
@@ -1090,7 +1154,8 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                                     : flux_marginal(da, db[0], cc, gc.flux_prior);
                 } else {
                     double bb;
-                    slg[pr] = position_marginal<NJ>(mixed, da, db, cc, gc.flux_prior, bb);
+                    if constexpr (mixed) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
+                    else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
                     sb[pr] = bb;
                 }
             }

@@ -177,6 +177,13 @@ inline int n_offsets(const rlf_params &p)
     return p.n_pos > 1 ? p.n_pos * p.n_pos : 1;
 }
 
+// Values per cell of the compacted B block: one plane when the position is exact, else
+// the offsets' B of each cell side by side, padded to whole 16-byte FP32 vectors.
+__host__ __device__ inline int b_stride(int n_offsets)
+{
+    return n_offsets > 1 ? (n_offsets + 3) / 4 * 4 : 1;
+}
+
 // Grid constants of the likelihood (Sec. 2.4).
 struct GridConst {
     const int32_t *box;     // per-facet sub-box origins [count][3] (e1, e2, alpha node), or null: full grid
@@ -197,7 +204,7 @@ struct Workspace {
     int32_t *status;        // [64] device status words
     SrcRow *table;          // [n_src]
     SrcRow *upd;            // [n_src] update table
-    void *cells;            // [4 + n_pos^2][cap][N*N] T: uu, uv, vv, A, then B per position offset
+    void *cells;            // T: planes uu, uv, vv, A [4][cap][N*N], then B [cap][N*N][b_stride]
     int32_t *ncell;         // [cap]
     int32_t *order;         // [cap] facets in largest-first order
     int32_t *counters;      // [cap + 1] work-item counter, per-facet finished tiles

@@ -64,10 +64,11 @@ def test_sizes(L):
     assert rlf.workspace_size(1000, 8, 200, p1, rlf.WS_RUN) < run
     bad = rlf.params_default(facet_n=63)
     assert rlf.workspace_size(1000, 8, 200, bad, rlf.WS_RUN) == 0
-    # the position marginal keeps one B plane per offset: 4 + n_pos^2 cell planes
+    # the position marginal keeps one B per offset and cell, padded to a multiple of four:
+    # 28 values per cell for 25 offsets instead of one
     pos = rlf.params_default(n_pos=5)
     grow = rlf.workspace_size(1000, 8, 200, pos, rlf.WS_FIT) - fit
-    assert grow == 24 * 200 * 64 * 64 * 8
+    assert grow == 27 * 200 * 64 * 64 * 8
     assert rlf.params_default().n_pos == 1 and rlf.params_default().pos_step_arcsec == 0.1
     assert rlf.workspace_size(1000, 8, 0, p, rlf.WS_RUN) == 0
 
