@@ -570,9 +570,9 @@ OPS = {
 # the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
 # files hash to the recorded value; otherwise the bench reports null.
 TRAFFIC = {
-    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "8f49e42324b62981", 1018.79e6),
-    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "9a3d8b15b9db61e2", 353.39e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "31523c5da7433a80", 17.16e6),
+    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "38616469eab718e1", 1079.57e6),
+    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "a3f20da1d2685124", 353.39e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "c839c0eecbdaa8db", 17.16e6),
 }
 
 

@@ -142,7 +142,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
     const bool ext = which == RLF_WS_EXTRACT || run;
     const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
-    const size_t o_split = take(ext ? 6 * rows * sizeof(float) : 0);
+    const size_t o_split = take(ext ? 8 * rows * sizeof(float) : 0);
     const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
     const size_t o_part = take(ext ? (size_t)kMaxPartials * 4 * NN * sizeof(float) : 0);
     const size_t o_ext = take(ext ? rows * sizeof(float) : 0);

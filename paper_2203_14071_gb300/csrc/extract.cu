@@ -46,24 +46,22 @@ __global__ void residual_kernel(const float4 *__restrict__ d, const float4 *__re
     }
 }
 
-// u, v, w as float pairs; with `perm`, column j of every time step holds baseline perm[j]
-// (rows are [time][stride] and n is a multiple of stride).
+// u, v, w as float pairs, one 32-byte record per row (two vector loads in the
+// extraction); with `perm`, column j of every time step holds baseline perm[j] (rows
+// are [time][stride] and n is a multiple of stride).
 __global__ void split_uvw_kernel(const double *__restrict__ u, const double *__restrict__ v,
                                  const double *__restrict__ w, int64_t n, int32_t stride,
                                  const int32_t *__restrict__ perm, float *__restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = perm ? (i / stride) * stride + perm[i % stride] : i;
-        float h, l;
-        split_double(u[r], h, l);
-        out[i] = h;
-        out[n + i] = l;
-        split_double(v[r], h, l);
-        out[2 * n + i] = h;
-        out[3 * n + i] = l;
-        split_double(w[r], h, l);
-        out[4 * n + i] = h;
-        out[5 * n + i] = l;
+        float uh, ul, vh, vl, wh, wl;
+        split_double(u[r], uh, ul);
+        split_double(v[r], vh, vl);
+        split_double(w[r], wh, wl);
+        float4 *o = reinterpret_cast<float4 *>(out) + 2 * i;
+        o[0] = make_float4(uh, ul, vh, vl);
+        o[1] = make_float4(wh, wl, 0.0f, 0.0f);
     }
 }
 
@@ -304,12 +302,14 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
             float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
             if (kSplit && lane_on && t_begin < t_end && t_begin * stride + bl < n_rows) {
                 const int64_t c0 = t_begin * stride + j;
-                nuh = us[c0];
-                nul = us[n_rows + c0];
-                nvh = us[2 * n_rows + c0];
-                nvl = us[3 * n_rows + c0];
-                nwh = us[4 * n_rows + c0];
-                nwl = us[5 * n_rows + c0];
+                const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * c0];
+                const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
+                nuh = a4.x;
+                nul = a4.y;
+                nvh = a4.z;
+                nvl = a4.w;
+                nwh = b2.x;
+                nwl = b2.y;
             }
             for (int64_t t = t_begin; t < t_end; ++t) {
                 // a row appends at most CG runs: make room first
@@ -345,12 +345,14 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     const int64_t rn = r + stride;
                     const int64_t cn = (t + 1) * stride + j;
                     if (lane_on && t + 1 < t_end && rn < n_rows) {
-                        nuh = us[cn];
-                        nul = us[n_rows + cn];
-                        nvh = us[2 * n_rows + cn];
-                        nvl = us[3 * n_rows + cn];
-                        nwh = us[4 * n_rows + cn];
-                        nwl = us[5 * n_rows + cn];
+                        const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * cn];
+                        const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * cn + 2];
+                        nuh = a4.x;
+                        nul = a4.y;
+                        nvh = a4.z;
+                        nvl = a4.w;
+                        nwh = b2.x;
+                        nwl = b2.y;
                     }
                 } else if (row_on) {
                     const double ud = u[r], vd = v[r], wd = w[r];

@@ -225,7 +225,7 @@ struct Workspace {
     int32_t *flag_tmp;      // refit pass: [cap] flags of a refit chunk
     double *e_cur;          // [2][n_src]
     double *facets;         // [chunk][4][N*N]
-    float *uvw_split;       // [6][n_rows]: u, v, w as float pairs (split-phase mode)
+    float *uvw_split;       // [n_rows][8]: uh, ul, vh, vl, wh, wl, 0, 0 (u, v, w as float pairs; split mode)
     float *resid;           // [n_rows][n_chan][2]: D - V_sky for batched extraction
     float *partial;         // [kMaxPartials][4][N*N]: per-CTA partial facets of the extraction
     float *extent;          // [n_rows] per baseline: min over time of max(|u|, |v|), rounded down

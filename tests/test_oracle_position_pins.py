@@ -38,13 +38,16 @@ def _complex_facet(N=8):
     return acc, cells
 
 
-@pytest.mark.parametrize("n_pos,step", [(3, 0.7), (5, 0.45)])
-def test_position_marginal_brute_force(n_pos, step):
-    # mean over offsets of int_0^inf exp(-chi2(S, x0)/2) dS, with chi2 the sum of complex
-    # residuals |D_c - S s_c M_c exp(2 pi i k_c.x0)|^2 w_c, done by quadrature
+@pytest.mark.parametrize("n_pos,step,flux_prior,profile", [(3, 0.7, 0, 0), (5, 0.45, 0, 0), (3, 0.7, 1, 0),
+                                                             (3, 0.7, 0, 1)])
+def test_position_marginal_brute_force(n_pos, step, flux_prior, profile):
+    # mean over offsets of int exp(-chi2(S, x0)/2) dS (S >= 0, or the real line with
+    # flux_prior 1), with chi2 the sum of complex residuals |D_c - S s_c M_c
+    # exp(2 pi i k_c.x0)|^2 w_c, done by quadrature; both source profiles
     N = 8
     p = oracle.default_params(facet_n=N, n_e=3, e_max=0.4, n_alpha=2, r_min_arcsec=0.5, r_max_arcsec=2.0,
-                              sigma_jy=4e-5, n_pos=n_pos, pos_step_arcsec=step)
+                              sigma_jy=4e-5, n_pos=n_pos, pos_step_arcsec=step, flux_prior=flux_prior,
+                              profile=profile)
     du = 3.0e4
     acc, cells = _complex_facet(N)
     lg, a, b, nc = oracle.like_grid(acc, du, p)
@@ -57,7 +60,7 @@ def test_position_marginal_brute_force(n_pos, step):
                 for iu, iv, sre, sim, n, ss in cells:
                     ku, kv = (iu - N // 2 + 0.5) * du, (iv - N // 2 + 0.5) * du
                     terms.append((n / p.sigma_jy ** 2, (sre + 1j * sim) / n, ss / n,
-                                  oracle.shape(ku, kv, al, e1, e2), ku, kv))
+                                  oracle.shape(ku, kv, al, e1, e2, profile=profile), ku, kv))
                 vals, peaks = [], []
                 for dl, dm in _offsets(n_pos, step):
                     ph = [np.exp(2j * math.pi * (ku * dl + kv * dm)) for *_, ku, kv in terms]
@@ -66,9 +69,10 @@ def test_position_marginal_brute_force(n_pos, step):
                         return sum(w * abs(d - S * s * M * z) ** 2 for (w, d, s, M, _, _), z in zip(terms, ph))
                     aa = sum(w * s * s * M * M for w, d, s, M, _, _ in terms)
                     bb = sum(w * s * M * (d * np.conj(z)).real for (w, d, s, M, _, _), z in zip(terms, ph))
-                    s0 = max(bb / aa, 0.0)
+                    s0 = bb / aa if flux_prior == 1 else max(bb / aa, 0.0)
                     c0 = chi2(s0)
-                    val, _ = integrate.quad(lambda S: math.exp(-0.5 * (chi2(S) - c0)), 0, s0 + 60 / math.sqrt(aa),
+                    lo = s0 - 60 / math.sqrt(aa) if flux_prior == 1 else 0.0
+                    val, _ = integrate.quad(lambda S: math.exp(-0.5 * (chi2(S) - c0)), lo, s0 + 60 / math.sqrt(aa),
                                             points=[s0], epsabs=0, epsrel=1e-11, limit=400)
                     vals.append(math.log(val) - 0.5 * c0)
                     peaks.append(bb)

@@ -100,6 +100,28 @@ def test_position_fit_from_oracle_facets(rlf, displaced, prec, n_pos):
 
 
 @pytest.mark.parametrize("prec", ["split", "fp64"])
+@pytest.mark.parametrize("profile,flux_prior", [(1, 0), (0, 1)])
+def test_position_fit_gaussian_profile_and_real_line_prior(rlf, displaced, prec, profile, flux_prior):
+    # the Gaussian profile's brightness and the real-line flux prior through the
+    # position-marginal grid (the best offset is then the largest |b|)
+    import torch
+    c, l_cat, m_cat, sky0 = displaced
+    po = c.oracle_params(n_pos=3, pos_step_arcsec=STEP, profile=profile, flux_prior=flux_prior)
+    facets = _oracle_facets(c, l_cat, m_cat, sky0, po)
+    ests = [oracle.fit_facet(acc, du, c.cat.flux_jy[i], po).est for i, (acc, du) in enumerate(facets)]
+    obs, cat = _catalogue(rlf, c, l_cat, m_cat)
+    p = rlf.params_default(precision=PRECS[prec], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, n_pos=3,
+                           pos_step_arcsec=STEP, profile=profile, flux_prior=flux_prior)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
+    out = rlf.Results(cat.n_src, "cuda")
+    fac = torch.from_numpy(np.ascontiguousarray(np.stack([f for f, _ in facets]))).cuda()
+    rlf.fit_sources(fac, cat, 0, cat.n_src, p, out, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    _compare(rlf, out.numpy(), ests)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp64"])
 def test_position_adaptive_from_oracle_facets(rlf, displaced, prec):
     # adaptive sampling around the maximum with the position marginal at every sample: a
     # brighter copy of the data (noise scaled down) so that posteriors are narrow enough
