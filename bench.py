@@ -623,10 +623,26 @@ def roofline_one(name, t_ms, units, row_src, peaks, fp32=None):
     t_mufu = (o["mufu"] * units + o["mufu_rs"] * row_src) / mufu_rate
     t_min = max(t_fp32, t_mufu)
     t = t_ms * 1e-3
-    return {"kernel": name, "bound": "alu", "limiting_unit": "fp32" if t_fp32 >= t_mufu else "mufu",
+    traffic = traffic_of(name)
+    line = {"kernel": name, "bound": "alu", "limiting_unit": "fp32" if t_fp32 >= t_mufu else "mufu",
             "unit": o["unit"], "achieved": units / t / 1e9, "peak": units / t_min / 1e9, "frac": t_min / t,
-            "units_per_launch": units, "traffic": traffic_of(name),
+            "units_per_launch": units, "traffic": traffic,
             "peak_basis": "measured FP32 %.3g FMA/s and MUFU %.3g op/s (rlf_peaks_measure)" % (fp32_rate, mufu_rate)}
+    # the memory side beside it: the captured DRAM bytes per launch over this launch's time,
+    # against the measured copy bandwidth
+    hbm = hbm_peak_gbs()
+    if traffic is not None and hbm:
+        line["dram_gb_s"] = traffic / t / 1e9
+        line["hbm_frac_of_measured"] = traffic / t / 1e9 / hbm
+    return line
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def roofline(comp, peaks, params, n_vis, n_src, R, C):

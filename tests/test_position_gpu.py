@@ -181,3 +181,46 @@ def test_position_marginal_rejected_by_the_learned_proposal(rlf, displaced):
     with pytest.raises(rlf.RlfError) as e:
         rlf.fit_sources_mlp(fac, cat, 0, cat.n_src, p, rlf.Mlp(), out, ws)
     assert e.value.code == rlf.RLF_EUNSUPPORTED
+
+
+def test_position_graph_replay_and_refit(rlf, displaced):
+    # the chain with the position marginal captured as a CUDA graph replays the run's
+    # results; and the refit of bad fits (Sec. 2.4) with the marginal matches the oracle
+    import torch
+    c, l_cat, m_cat, _ = displaced
+    obs, cat = _catalogue(rlf, c, l_cat, m_cat)
+    data = cases.vis_tensor(c.data)
+    p = rlf.params_default(precision=PRECS["split"], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, update_mode=1,
+                           n_pos=3, pos_step_arcsec=STEP)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        rlf.run(obs, data, cat, p, out, sky, ws, stream)
+        stream.synchronize()
+        ref = out.numpy()
+        g = rlf.Graph(obs, data, cat, p, out, sky, ws, stream)
+        out.e1.zero_()
+        out.e2.zero_()
+        g.launch(stream)
+        stream.synchronize()
+        got = out.numpy()
+        g.close()
+    for f in ("e1", "e2", "sig1", "sig2", "flux_jy"):
+        assert np.allclose(got[f], ref[f], rtol=1e-5, atol=1e-5), f
+    # refit pass: sigma = 1 uJy collapses every first-pass posterior onto one node (bad)
+    sigma = c.wl.sigma_jy
+    dat1 = cases.data_from(cases.true_sky(c), sigma, c.wl.seed)
+    po = c.oracle_params(chunk=0, update_mode=1, refit_bad=1, n_pos=3, pos_step_arcsec=STEP, sigma_jy=sigma)
+    est = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, dat1, l_cat, m_cat, c.cat.flux_jy, None, po)
+    assert np.all(est[:, oracle.REFIT] == 1)
+    p1 = rlf.params_default(precision=PRECS["split"], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=sigma, update_mode=1,
+                            refit_bad=1, n_pos=3, pos_step_arcsec=STEP)
+    rlf.run(obs, cases.vis_tensor(dat1), cat, p1, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    got = out.numpy()
+    assert np.all(got["flag"] & rlf.FLAG_REFIT)
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(got, i, est[i]) <= 1e-4, (i, got["e1"][i], est[i, oracle.E1])
