@@ -333,12 +333,17 @@ TUNE_FIELDS = ("tune_sky_blocks", "tune_extract_waves", "tune_fit_ag", "tune_fit
 
 
 def tuning_key(obs: Observation, n_src: int, params: Params) -> str:
-    """Cache key: workload shape, grid, precision, chunk and the GPU's SM count."""
+    """Cache key: workload shape, grid, precision, chunk, profile, position offsets, the
+    GPU's SM count and the tuner's candidate sets (TUNER_VERSION)."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    return "rows%d_chan%d_bl%d_src%d_N%d_e%d_a%d_prec%d_chunk%d_sm%d" % (
-        obs.n_rows, obs.n_chan, obs.struct.n_baselines, n_src, params.facet_n, params.n_e, params.n_alpha,
-        params.precision, params.chunk, sms)
+    return "v%d_rows%d_chan%d_bl%d_src%d_N%d_e%d_a%d_prec%d_chunk%d_prof%d_pos%d_sm%d" % (
+        TUNER_VERSION, obs.n_rows, obs.n_chan, obs.struct.n_baselines, n_src, params.facet_n, params.n_e,
+        params.n_alpha, params.precision, params.chunk, params.profile, params.n_pos, sms)
+
+
+# bumped whenever rlf_autotune's candidate sets change, so that cached choices are redone
+TUNER_VERSION = 2
 
 
 def autotune(obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results, vis_sky, workspace,

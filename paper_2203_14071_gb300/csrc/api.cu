@@ -1,6 +1,7 @@
 // C ABI entry points (include/rlf.h): argument checks, the channel table,
 // workspace carve-up and the whole-chain driver.  Host code only; the work is
 // in sky.cu, extract.cu and fit.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -144,7 +145,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
     const size_t o_split = take(ext ? 8 * rows * sizeof(float) : 0);
     const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
-    const size_t o_part = take(ext ? (size_t)kMaxPartials * 4 * NN * sizeof(float) : 0);
+    const size_t n_partials = std::min((size_t)kMaxPartials, (size_t)kPartialsPerSource * (size_t)(n_src > 0 ? n_src : 1));
+    const size_t o_part = take(ext ? n_partials * 4 * NN * sizeof(float) : 0);
     const size_t o_ext = take(ext ? rows * sizeof(float) : 0);
     const size_t o_perm = take(ext ? rows * sizeof(int32_t) : 0);
     const size_t o_live = take(ext ? (size_t)n_src * sizeof(int32_t) : 0);
@@ -180,6 +182,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
         ws->uvw_split = reinterpret_cast<float *>(b + o_split);
         ws->resid = reinterpret_cast<float *>(b + o_resid);
         ws->partial = reinterpret_cast<float *>(b + o_part);
+        ws->n_partials = (int32_t)n_partials;
         ws->extent = reinterpret_cast<float *>(b + o_ext);
         ws->perm = reinterpret_cast<int32_t *>(b + o_perm);
         ws->n_live = reinterpret_cast<int32_t *>(b + o_live);
@@ -588,7 +591,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
     }
     // 2. extraction waves (first chunk of sources)
     {
-        const int cand[] = {1, 2, 3, 4};
+        const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
         float bt = 0;
         int bc = 2;
         for (int c : cand) {

@@ -601,7 +601,7 @@ struct Order {
 template <int CG, bool kSplit>
 cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
                       const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
-                      float *partial, double *facets, int waves, cudaStream_t st)
+                      float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
 {
     const size_t smem = (size_t)kRing * kThreads * sizeof(int4) + RLF_MAX_CHAN * sizeof(float) +
                         4 * (size_t)N * N * sizeof(float);
@@ -628,8 +628,8 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
     const int NN = N * N;
     const int64_t slots = (int64_t)sm_count_x() * per_sm;
     // sources are handled in batches whose partial facets fit the workspace
-    for (int32_t first = 0; first < count; first += kMaxPartials) {
-        const int32_t cnt = count - first < kMaxPartials ? count - first : kMaxPartials;
+    for (int32_t first = 0; first < count; first += max_partials) {
+        const int32_t cnt = count - first < max_partials ? count - first : max_partials;
         // parts per source: about `waves` waves of CTAs; beyond one part per baseline block
         // (few sources) the time series are split too, into slices of at least 16 steps
         int64_t parts = ((int64_t)waves * slots + cnt - 1) / cnt;
@@ -641,7 +641,7 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
             if (slices > 32) slices = 32;
         }
         if (parts > n_blocks * slices) parts = n_blocks * slices;
-        if (parts > kMaxPartials / cnt) parts = kMaxPartials / cnt;
+        if (parts > max_partials / cnt) parts = max_partials / cnt;
         if (parts < 1) parts = 1;
         dim3 grid(cnt, (unsigned)parts);
         kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
@@ -660,12 +660,12 @@ cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data
 template <bool kSplit>
 cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
                          const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
-                         float *partial, double *facets, int waves, cudaStream_t st)
+                         float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
 {
-    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
-    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
-    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
-    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, facets, waves, st);
+    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
+    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
+    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
+    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
 }
 
 cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
@@ -772,9 +772,9 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int waves = p.tune_extract_waves > 0 ? p.tune_extract_waves : 2;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, facets,
+        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, ws.n_partials, facets,
                                    waves, st);
-    return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, facets,
+    return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, ws.n_partials, facets,
                               waves, st);
 }
 

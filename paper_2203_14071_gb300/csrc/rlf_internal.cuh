@@ -21,7 +21,8 @@ constexpr int kOrderThreads = 256;
 constexpr int kSkyTile = 128;                            // sources staged per shared-memory tile
 constexpr int kCellTile = 128;                           // facet cells staged per tile in the fit
 constexpr int kMaxNe = 32;                               // grid nodes per e component (estimator smem)
-constexpr int kMaxPartials = 2048;                       // (source, part) partial facets per extraction batch
+constexpr int kMaxPartials = 8192;                       // (source, part) partial facets per extraction batch
+constexpr int kPartialsPerSource = 64;                  // workspace partials per source below kMaxPartials
 
 // Per-source constants derived on the device from the catalogue (Sec. 2.2, 2.3).
 struct SrcRow {
@@ -227,7 +228,8 @@ struct Workspace {
     double *facets;         // [chunk][4][N*N]
     float *uvw_split;       // [n_rows][8]: uh, ul, vh, vl, wh, wl, 0, 0 (u, v, w as float pairs; split mode)
     float *resid;           // [n_rows][n_chan][2]: D - V_sky for batched extraction
-    float *partial;         // [kMaxPartials][4][N*N]: per-CTA partial facets of the extraction
+    float *partial;         // [n_partials][4][N*N]: per-CTA partial facets of the extraction
+    int32_t n_partials;     // min(kMaxPartials, 64 n_src)
     float *extent;          // [n_rows] per baseline: min over time of max(|u|, |v|), rounded down
     int32_t *perm;          // [n_rows] baselines in increasing order of extent (first n_baselines used)
     int32_t *n_live;        // [n_src] per source of an extraction batch: baselines to walk
