@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
+    ap.add_argument("--extract-waves", type=int, default=0,
+                    help="CTA waves of the extraction (0: the autotuner's choice, or the library default "
+                         "with --no-tune or --only)")
     ap.add_argument("--only", default="", choices=["", "sky_model", "extract", "fit", "update", "mlp"],
                     help="run only this entry point --steps times after one warm-up, or only the "
                          "learned-proposal comparison (for ncu captures)")
@@ -398,6 +401,8 @@ def main():
         return
 
     tuning = None if args.no_tune else rlf.autotune(obs, data, cat, params, out, sky, ws, TUNE_CACHE, stream)
+    if args.extract_waves > 0:
+        params.tune_extract_waves = args.extract_waves
     graph = None if (args.no_graph or args.refit_bad) else rlf.Graph(obs, data, cat, params, out, sky, ws, stream)
 
     def step():
@@ -487,6 +492,8 @@ def main():
 
 def profile_only(args, rlf, torch, obs, data, cat, params, ws, sky, out, stream, dev, n_src):
     """One entry point alone (after the chain ran once), for profiler captures."""
+    if args.extract_waves > 0:
+        params.tune_extract_waves = args.extract_waves
     facets = torch.empty(rlf.facets_size(n_src, params) // 8, dtype=torch.float64, device=dev)
     ws_fit = rlf.alloc_workspace(obs.n_rows, obs.n_chan, n_src, params, rlf.WS_FIT, device=dev)
     rlf.run(obs, data, cat, params, out, sky, ws, stream)
@@ -570,9 +577,9 @@ OPS = {
 # the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
 # files hash to the recorded value; otherwise the bench reports null.
 TRAFFIC = {
-    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "38616469eab718e1", 1079.57e6),
-    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "a3f20da1d2685124", 353.39e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "c839c0eecbdaa8db", 17.16e6),
+    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "7393f27be8ba8832", 1019.73e6),
+    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "da0e5b3577e5ccc1", 356.49e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "3b044cfaa06f9dad", 16.92e6),
 }
 
 
