@@ -12,8 +12,11 @@ ctypes.  Functions and the passages they follow:
     alpha_med        Eq. 4 (Sec. 2.2)
     sky_model        sum of Eq. 1 over the catalogue (Sec. 2.2)
     extract_facet    Sec. 2.3 (residual, phase shift, facet of K * alpha)
-    fit_facet        Sec. 2.4 (chi^2, flux and scalelength marginals, estimate)
-    pipeline         Sec. 2 and Sec. 3.1 (chunked sky-model update)
+    fit_facet        Sec. 2.4 (chi^2, flux, scalelength and position marginals,
+                     estimate)
+    fit_facet_adaptive  Sec. 2.4 (adaptive sampling around the maximum)
+    pipeline         Sec. 2 and Sec. 3.1 (chunked sky-model update), Sec. 2.4
+                     (refit of bad fits)
 """
 from __future__ import annotations
 

@@ -14,9 +14,12 @@
  *                       (Sec. 2.3), facet size K * alpha (Sec. 2.3, Sec. 4.1)
  *   rlfo_fit_facet      chi^2 likelihood, analytic flux marginal, numeric
  *                       scalelength marginal, 5% threshold moments and the
- *                       bad-fit cut (Sec. 2.4, Sec. 4.1)
+ *                       bad-fit cut (Sec. 2.4, Sec. 4.1); with n_pos > 1 the
+ *                       position marginal over a grid of offsets (Sec. 2.4)
+ *   rlfo_fit_facet_adaptive  the estimate on halved lattices around the kept
+ *                       samples (adaptive sampling, Sec. 2.4)
  *   rlfo_pipeline       the whole chain with the sky-model update in chunks
- *                       (Sec. 2.2, Sec. 3.1)
+ *                       (Sec. 2.2, Sec. 3.1), and the refit of bad fits (Sec. 2.4)
  * Readings where the paper is silent are stated beside the code that takes them.
  */
 #include <math.h>
