@@ -143,7 +143,8 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_fac = take(run ? cap * 4 * NN * sizeof(double) : 0);
     const bool ext = which == RLF_WS_EXTRACT || run;
     const size_t rows = (size_t)(n_rows > 0 ? n_rows : 0), chans = (size_t)(n_chan > 0 ? n_chan : 0);
-    const size_t o_split = take(ext ? 8 * rows * sizeof(float) : 0);
+    // split baselines: the extraction's (in baseline order) and the sky calls' (row order)
+    const size_t o_split = take((ext || which == RLF_WS_SKY) ? 8 * rows * sizeof(float) : 0);
     const size_t o_resid = take(ext ? rows * chans * 2 * sizeof(float) : 0);
     const size_t n_partials = std::min((size_t)kMaxPartials, (size_t)kPartialsPerSource * (size_t)(n_src > 0 ? n_src : 1));
     const size_t o_part = take(ext ? n_partials * 4 * NN * sizeof(float) : 0);
@@ -273,7 +274,13 @@ rlf_status rlf_sky_model(const rlf_uvw *uvw, const rlf_sources *src, const rlf_p
     if (e == cudaSuccess)
         e = launch_prepare(*src, 0, src->n_src, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                            nullptr, *p, ws.table, ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.table, src->n_src, false, p->precision, vis_sky, st, p->tune_sky_blocks);
+    SplitRows sr;
+    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) {
+        e = launch_split_uvw(*uvw, ws.uvw_split, st);
+        sr.rec = ws.uvw_split;
+    }
+    if (e == cudaSuccess)
+        e = launch_sky(*uvw, ch, ws.table, src->n_src, false, p->precision, vis_sky, st, p->tune_sky_blocks, 1.0f, sr);
     return cuda_status(e);
 }
 
@@ -296,7 +303,13 @@ rlf_status rlf_sky_update(const rlf_uvw *uvw, const rlf_sources *src, int32_t fi
     if (e == cudaSuccess)
         e = launch_prepare(*src, first, count, src->e1, src->e2, e1_new, e2_new, flag,
                            flag ? p->update_mode : 1, nullptr, nullptr, *p, ws.upd, ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(*uvw, ch, ws.upd, count, true, p->precision, vis_sky, st, p->tune_sky_blocks);
+    SplitRows sr;
+    if (e == cudaSuccess && p->precision == RLF_PREC_MIXED_SPLIT) {
+        e = launch_split_uvw(*uvw, ws.uvw_split, st);
+        sr.rec = ws.uvw_split;
+    }
+    if (e == cudaSuccess)
+        e = launch_sky(*uvw, ch, ws.upd, count, true, p->precision, vis_sky, st, p->tune_sky_blocks, 1.0f, sr);
     return cuda_status(e);
 }
 
@@ -383,8 +396,12 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
     if (e == cudaSuccess)
         e = launch_prepare(src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
                            ws.status, st);
-    if (e == cudaSuccess) e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
+    // baseline extents and order, and (split mode) the split baselines, which the sky
+    // kernels of this call read too
     if (e == cudaSuccess) e = launch_extract_prepare(uvw, p, ws, st);
+    const SplitRows sr = split_rows(uvw, p, ws);
+    if (e == cudaSuccess)
+        e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks, 1.0f, sr);
     // several chunks (mixed modes): keep the residual R = D - V resident instead of V, so
     // that each chunk's extraction reads one array; the updates subtract their terms
     // from R and the sky model is restored at the end as V = D - R
@@ -409,11 +426,11 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
             e = launch_prepare(src, 0, n, e1c, e2c, nullptr, nullptr, nullptr, 0, nullptr, nullptr, p, ws.table,
                                ws.status, st);
             if (e == cudaSuccess)
-                e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks);
+                e = launch_sky(uvw, ch, ws.table, n, false, p.precision, vis_sky, st, p.tune_sky_blocks, 1.0f, sr);
         } else if (track_resid) {
-            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f);
+            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f, sr);
         } else {
-            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
+            e = launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks, 1.0f, sr);
         }
     }
     // the bad fits once more, against the sky model of every other measured shape (Sec. 2.4),
@@ -447,8 +464,9 @@ cudaError_t run_chain(const rlf_uvw &uvw, const float *vis_data, const rlf_sourc
             e = launch_prepare(src, 0, cnt, e1c, e2c, tmp.e1, tmp.e2, tmp.flag, p.update_mode, e1c, e2c, p, ws.upd,
                                ws.status, st, list);
             if (e != cudaSuccess) break;
-            e = track_resid ? launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f)
-                            : launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks);
+            e = track_resid
+                    ? launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, ws.resid, st, p.tune_sky_blocks, -1.0f, sr)
+                    : launch_sky(uvw, ch, ws.upd, cnt, true, p.precision, vis_sky, st, p.tune_sky_blocks, 1.0f, sr);
         }
     }
     if (e == cudaSuccess && track_resid) e = launch_difference(vis_data, ws.resid, n_vis, vis_sky, st);
@@ -570,6 +588,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
                                    ws.table, ws.status, st);
     if (e == cudaSuccess) e = launch_extract_prepare(*uvw, q, ws, st);
     if (e != cudaSuccess) return RLF_ECUDA;
+    const SplitRows sr = split_rows(*uvw, q, ws);
     float best[3] = {0, 0, 0};
     // 1. sky-model CTAs per SM
     {
@@ -577,7 +596,8 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
         float bt = 0;
         int bc = 8;
         for (int c : cand) {
-            const float t = time_median([&] { return launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, c); },
+            const float t = time_median([&] { return launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, c,
+                                                                1.0f, sr); },
                                         st, reps);
             if (t < 0) return RLF_ECUDA;
             if (bt == 0 || t < bt) {
@@ -587,7 +607,8 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
         }
         q.tune_sky_blocks = bc;
         best[0] = bt;
-        if ((e = launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, bc)) != cudaSuccess) return RLF_ECUDA;
+        if ((e = launch_sky(*uvw, ch, ws.table, n, false, q.precision, vis_sky, st, bc, 1.0f, sr)) != cudaSuccess)
+            return RLF_ECUDA;
     }
     // 2. extraction waves (first chunk of sources)
     {

@@ -717,6 +717,23 @@ cudaError_t launch_difference(const float *a, const float *b, int64_t n_complex,
     return cudaGetLastError();
 }
 
+cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st)
+{
+    split_uvw_kernel<<<(int)grid_for(uvw.n_rows, (int64_t)sm_count_x() * 8), kThreads, 0, st>>>(
+        uvw.u, uvw.v, uvw.w, uvw.n_rows, 1, nullptr, out);
+    return cudaGetLastError();
+}
+
+SplitRows split_rows(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws)
+{
+    SplitRows sr;
+    if (p.precision != RLF_PREC_MIXED_SPLIT || !ws.uvw_split) return sr;
+    sr.rec = ws.uvw_split;
+    sr.perm = ordered(uvw) ? ws.perm : nullptr;
+    sr.stride = row_stride(uvw);
+    return sr;
+}
+
 cudaError_t launch_extract_prepare(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws, cudaStream_t st)
 {
     if (p.precision == RLF_PREC_FP64) return cudaSuccess;

@@ -247,9 +247,20 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
                            double *e1_commit, double *e2_commit,
                            const rlf_params &p, SrcRow *out, int32_t *status, cudaStream_t st,
                            const int32_t *list = nullptr);
+// Split-baseline records of a call (split mode): record i = {uh, ul, vh, vl, wh, wl, 0, 0}
+// of row (i / stride) * stride + perm[i % stride] (perm set), else of row i.  rec null:
+// the sky kernels split u, v, w on the fly.
+struct SplitRows {
+    const float *rec = nullptr;
+    const int32_t *perm = nullptr;
+    int32_t stride = 1;
+};
+SplitRows split_rows(const rlf_uvw &uvw, const rlf_params &p, const Workspace &ws);
+// split records of every row in row order (no baseline order), for the standalone sky calls
+cudaError_t launch_split_uvw(const rlf_uvw &uvw, float *out, cudaStream_t st);
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st,
-                       int32_t blocks_per_sm = 0, float sign = 1.0f);
+                       int32_t blocks_per_sm = 0, float sign = 1.0f, const SplitRows &sr = SplitRows());
 // out = a - b over n4 float4 (the residual D - V, or the sky model D - R)
 cudaError_t launch_difference(const float *a, const float *b, int64_t n_complex, float *out, cudaStream_t st);
 // Per call, before the extraction batches: each baseline's smallest uv extent over

@@ -10,6 +10,7 @@
 // variant carries the phase argument as a float pair (error-free FP32 products
 // and sums), which GB300 executes at its FP32 rate.
 #include <cmath>
+#include <type_traits>
 
 #include "rlf_internal.cuh"
 
@@ -96,12 +97,14 @@ struct SkySrc {
 };
 
 // Mixed precision sky model / update.  CG channels per thread.  kSplit selects
-// the float-pair phase argument instead of the FP64 one.
-template <int CG, bool kUpdate, bool kUniform, bool kSplit, bool kGauss>
+// the float-pair phase argument instead of the FP64 one; kRec (split only) reads the
+// call's split-baseline records instead of splitting u, v, w per row.
+template <int CG, bool kUpdate, bool kUniform, bool kSplit, bool kGauss, bool kRec = false>
 __global__ void __launch_bounds__(kThreads)
 sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                  const double *__restrict__ w, int64_t n_rows, const ChanTable ch,
-                 const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis, float sign)
+                 const SrcRow *__restrict__ table, int32_t n_src, float2 *__restrict__ vis, float sign,
+                 const float *__restrict__ rec, const int32_t *__restrict__ perm, int32_t stride)
 {
     __shared__ SkySrc sm[kSkyTile];
     const int C = ch.n;
@@ -129,21 +132,52 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
     constexpr float kTwoPi = 6.28318530717958647692f;
 
     for (int64_t rb = (int64_t)blockIdx.x * lanes; rb < n_rows; rb += (int64_t)gridDim.x * lanes) {
-        const int64_t r = rb + lane;
-        const bool act = thread_on && r < n_rows;
+        // with split records: lane position i in record order, r its row
+        const int64_t i = rb + lane;
+        const bool act = thread_on && i < n_rows;
+        int64_t r = i;
         double ud = 0.0, vd = 0.0, wd = 0.0;
-        if (act) {
-            ud = u[r];
-            vd = v[r];
-            wd = w[r];
-        }
         float uh = 0, ul = 0, vh = 0, vl = 0, wh = 0, wl = 0;
-        if (kSplit) {
-            split_double(ud, uh, ul);
-            split_double(vd, vh, vl);
-            split_double(wd, wh, wl);
+        float uu, uv, vv;
+        if constexpr (kSplit && kRec) {
+            // the call's split records: no FP64 per row (u^2, uv, v^2 from the high parts,
+            // within 1e-7 of the rounded FP64 products, far below the FP32 model's error)
+            if (act) {
+                if (perm) {
+                    if (n_rows <= INT32_MAX) {
+                        const int32_t i32 = (int32_t)i;
+                        r = (int64_t)(i32 / stride) * stride + perm[i32 % stride];
+                    } else {
+                        r = (i / stride) * stride + perm[i % stride];
+                    }
+                }
+                const float4 a4 = reinterpret_cast<const float4 *>(rec)[2 * i];
+                const float2 b2 = reinterpret_cast<const float2 *>(rec)[4 * i + 2];
+                uh = a4.x;
+                ul = a4.y;
+                vh = a4.z;
+                vl = a4.w;
+                wh = b2.x;
+                wl = b2.y;
+            }
+            uu = uh * uh;
+            uv = uh * vh;
+            vv = vh * vh;
+        } else {
+            if (act) {
+                ud = u[r];
+                vd = v[r];
+                wd = w[r];
+            }
+            if (kSplit) {
+                split_double(ud, uh, ul);
+                split_double(vd, vh, vl);
+                split_double(wd, wh, wl);
+            }
+            uu = (float)(ud * ud);
+            uv = (float)(ud * vd);
+            vv = (float)(vd * vd);
         }
-        const float uu = (float)(ud * ud), uv = (float)(ud * vd), vv = (float)(vd * vd);
         float are[CG], aim[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) are[c] = aim[c] = 0.0f;
@@ -330,7 +364,7 @@ int sm_count()
 
 template <int CG, bool kUpdate, bool kSplit>
 void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
-                  float *vis, int blocks_per_sm, float sign, cudaStream_t st)
+                  float *vis, int blocks_per_sm, float sign, const SplitRows &sr, cudaStream_t st)
 {
     const int n_groups = (ch.n + CG - 1) / CG;
     const int lanes = kThreads / n_groups;
@@ -339,28 +373,29 @@ void launch_mixed(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, 
     const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
     float2 *out = reinterpret_cast<float2 *>(vis);
     const bool gauss = ch.profile == RLF_PROFILE_GAUSSIAN;
-    if (ch.uniform && !gauss)
-        sky_mixed_kernel<CG, kUpdate, true, kSplit, false><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
-    else if (ch.uniform)
-        sky_mixed_kernel<CG, kUpdate, true, kSplit, true><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
-    else if (!gauss)
-        sky_mixed_kernel<CG, kUpdate, false, kSplit, false><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
-    else
-        sky_mixed_kernel<CG, kUpdate, false, kSplit, true><<<grid, kThreads, 0, st>>>(
-            uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign);
+    auto pick = [&](auto rec_tag) {
+        constexpr bool kRec = decltype(rec_tag)::value;
+        if (ch.uniform && !gauss) return sky_mixed_kernel<CG, kUpdate, true, kSplit, false, kRec>;
+        if (ch.uniform) return sky_mixed_kernel<CG, kUpdate, true, kSplit, true, kRec>;
+        if (!gauss) return sky_mixed_kernel<CG, kUpdate, false, kSplit, false, kRec>;
+        return sky_mixed_kernel<CG, kUpdate, false, kSplit, true, kRec>;
+    };
+    auto kern = pick(std::false_type{});
+    if constexpr (kSplit) {
+        if (sr.rec) kern = pick(std::true_type{});
+    }
+    kern<<<grid, kThreads, 0, st>>>(uvw.u, uvw.v, uvw.w, uvw.n_rows, ch, table, n_src, out, sign, sr.rec, sr.perm,
+                                    sr.stride);
 }
 
 template <bool kUpdate, bool kSplit>
 void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table,
-                     int32_t n_src, float *vis, int bps, float sign, cudaStream_t st)
+                     int32_t n_src, float *vis, int bps, float sign, const SplitRows &sr, cudaStream_t st)
 {
-    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
-    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
-    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
-    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, st);
+    if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
 }
 
 }  // namespace
@@ -381,15 +416,16 @@ cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,
 
 cudaError_t launch_sky(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *table, int32_t n_src,
                        bool update, int32_t precision, float *vis, cudaStream_t st, int32_t blocks_per_sm,
-                       float sign)
+                       float sign, const SplitRows &sr)
 {
     const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
+    const SplitRows none;
     if (precision == RLF_PREC_MIXED) {
-        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, bps, sign, st);
-        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, bps, 1.0f, st);
+        if (update) launch_mixed_cg<true, false>(uvw, ch, table, n_src, vis, bps, sign, none, st);
+        else launch_mixed_cg<false, false>(uvw, ch, table, n_src, vis, bps, 1.0f, none, st);
     } else if (precision == RLF_PREC_MIXED_SPLIT) {
-        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, bps, sign, st);
-        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, bps, 1.0f, st);
+        if (update) launch_mixed_cg<true, true>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+        else launch_mixed_cg<false, true>(uvw, ch, table, n_src, vis, bps, 1.0f, sr, st);
     } else {
         const int64_t n_out = uvw.n_rows * ch.n;
         const int64_t need = (n_out + kThreads - 1) / kThreads;
