@@ -48,8 +48,8 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
         const int c = c0 + i;
         if (c < NN && f[2 * NN + c] > 0.0) {
             ++mine;
-            const double n = f[2 * NN + c];
-            const double dr = f[c] / n, di = f[NN + c] / n;
+            const double n = f[2 * NN + c], in = 1.0 / n;
+            const double dr = f[c] * in, di = f[NN + c] * in;
             cc += n * inv_sigma2 * (dr * dr + di * di);
         }
     }
@@ -79,9 +79,9 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
     for (int i = 0; i < per; ++i) {
         const int c = c0 + i;
         if (c < NN && f[2 * NN + c] > 0.0) {
-            const double n = f[2 * NN + c];
-            const double dr = f[c] / n;
-            const double sbar = f[3 * NN + c] / n;
+            const double n = f[2 * NN + c], in = 1.0 / n;
+            const double dr = f[c] * in;
+            const double sbar = f[3 * NN + c] * in;
             const double wc = n * inv_sigma2;
             const int iu = c % N, iv = c / N;
             const double cu = iu - N / 2 + 0.5, cv = iv - N / 2 + 0.5;
@@ -94,7 +94,7 @@ compact_kernel(const double *__restrict__ facets, const SrcRow *__restrict__ tab
             } else {
                 // B of offset x_j = (dl, dm): w s Re(D exp(-2 pi i k.x_j)), k = du (cu, cv); the
                 // cell's values side by side (zero padding)
-                const double di = f[NN + c] / n;
+                const double di = f[NN + c] * in;
                 const int nb = b_stride(nj);
                 T *row = cells + 4 * plane + ((size_t)s * NN + pos) * nb;
                 for (int j = nj; j < nb; ++j) row[j] = T(0);
@@ -384,7 +384,7 @@ __device__ double flux_marginal(double a, double b, double cc, int flux_prior)
 // estimate's time.
 __device__ double flux_marginal_mixed(double a, double b, double cc, int flux_prior)
 {
-    const float lg = 0.5f * logf((float)(kPi / (2.0 * a)));
+    const float lg = 0.5f * logf(3.14159265358979323846f / (2.0f * (float)a));
     if (flux_prior == 1) return -0.5 * cc + b * b / (2.0 * a) + (double)(lg + 0.5f * 1.38629436111989061883f);
     const float x = (float)(-b) * rsqrtf((float)(2.0 * a));
     if (x > 0.0f) return -0.5 * cc + (double)(lg + logf(erfcxf(x)));
