@@ -162,6 +162,20 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
     return d;
 }
 
+// brightness() of two channels: q broadcast, f2 per channel
+template <bool kGauss>
+__device__ __forceinline__ f32x2 brightness2(f32x2 q2, f32x2 f2)
+{
+    float x0, x1;
+    if (kGauss) {
+        up2(mul2(mul2(pk2(-0.25f, -0.25f), q2), f2), x0, x1);
+        return pk2(ex2_approx(x0), ex2_approx(x1));
+    }
+    up2(fma2(q2, f2, pk2(1.0f, 1.0f)), x0, x1);
+    const f32x2 r = pk2(rsqrtf(x0), rsqrtf(x1));
+    return mul2(mul2(r, r), r);
+}
+
 __device__ __forceinline__ void split_double(double x, float &hi, float &lo)
 {
     hi = (float)x;

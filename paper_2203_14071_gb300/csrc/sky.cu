@@ -127,6 +127,12 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
         shi[c] = k < C ? ch.s_hi[k] : 0.0f;
         slo[c] = k < C ? ch.s_lo[k] : 0.0f;
     }
+    // uniform channels in pairs: two channels per paired FP32 instruction
+    constexpr bool kPair = kUniform && CG >= 2 && CG % 2 == 0;
+    constexpr int NP2 = kPair ? CG / 2 : 1;
+    f32x2 F2[NP2];
+#pragma unroll
+    for (int j = 0; j < NP2; ++j) F2[j] = kPair ? pk2(f2[2 * j], f2[2 * j + 1]) : pk2(0.0f, 0.0f);
     const double s_k0 = sk[0];
     const double ds = ch.ds;
     constexpr float kTwoPi = 6.28318530717958647692f;
@@ -181,6 +187,9 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
         float are[CG], aim[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) are[c] = aim[c] = 0.0f;
+        f32x2 are2[NP2], aim2[NP2];
+#pragma unroll
+        for (int j = 0; j < NP2; ++j) are2[j] = aim2[j] = pk2(0.0f, 0.0f);
 
         for (int t0 = 0; t0 < n_src; t0 += kSkyTile) {
             const int nt = min(kSkyTile, n_src - t0);
@@ -234,6 +243,30 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                     __sincosf(f0 * kTwoPi, &sn, &cs);
                     if (CG > 1) __sincosf(fd * kTwoPi, &sd, &cd);
                 }
+                if constexpr (kPair) {
+                    // channel pairs (2j, 2j + 1): phasors z_2j and z_2j+1 = z_2j d, then both
+                    // turned by d^2 for the next pair; lane by lane the arithmetic of the
+                    // scalar loop below
+                    const float cs1 = cs * cd - sn * sd, sn1 = fmaf(cs, sd, sn * cd);
+                    f32x2 C2 = pk2(cs, cs1), S2 = pk2(sn, sn1);
+                    const float cdd = cd * cd - sd * sd, sdd = 2.0f * cd * sd;
+                    const f32x2 CD = pk2(cdd, cdd), SD = pk2(sdd, sdd), NSD = pk2(-sdd, -sdd);
+                    const f32x2 Q2 = pk2(q, q), QN2 = pk2(qn, qn), FL = pk2(S.flux, S.flux);
+#pragma unroll
+                    for (int pr = 0; pr < NP2; ++pr) {
+                        f32x2 M2 = brightness2<kGauss>(Q2, F2[pr]);
+                        if (kUpdate) M2 = fma2(M2, pk2(-1.0f, -1.0f), brightness2<kGauss>(QN2, F2[pr]));
+                        const f32x2 A2 = mul2(FL, M2);
+                        are2[pr] = fma2(A2, C2, are2[pr]);
+                        aim2[pr] = fma2(A2, S2, aim2[pr]);
+                        if (pr + 1 < NP2) {
+                            const f32x2 Cn = fma2(C2, CD, mul2(S2, NSD));
+                            S2 = fma2(C2, SD, mul2(S2, CD));
+                            C2 = Cn;
+                        }
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int c = 0; c < CG; ++c) {
                     if (!kUniform) {
@@ -257,6 +290,13 @@ sky_mixed_kernel(const double *__restrict__ u, const double *__restrict__ v,
                         cs = cn;
                     }
                 }
+            }
+        }
+        if constexpr (kPair) {
+#pragma unroll
+            for (int j = 0; j < NP2; ++j) {
+                up2(are2[j], are[2 * j], are[2 * j + 1]);
+                up2(aim2[j], aim[2 * j], aim[2 * j + 1]);
             }
         }
         if (act) {
