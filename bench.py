@@ -577,9 +577,9 @@ OPS = {
 # the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
 # files hash to the recorded value; otherwise the bench reports null.
 TRAFFIC = {
-    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "bb587427176a2dd2", 1024.94e6),
-    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "65f78dbb870b66c3", 391.56e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "4074ecfe14a9c221", 16.71e6),
+    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "de9e12d2b402154d", 1022.47e6),
+    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "70d743ed82f2f66f", 391.61e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "b9848c2ed1bbf6b3", 16.80e6),
 }
 
 
