@@ -181,7 +181,9 @@ typedef struct {
 
 /* Fill *p with the paper's defaults: ADD, ESP, K = 38, beta = -0.7, RMIN 0.3",
  * RMAX 3.5", R_STD 0.3136, 5% threshold, 5e-3 / 5e-5 cuts, 21 x 21 e nodes on
- * [-0.8, 0.8], 20 alpha nodes, 64 x 64 facets, RLF_PREC_MIXED, chunk = all. */
+ * [-0.8, 0.8], 20 alpha nodes, 64 x 64 facets, RLF_PREC_MIXED, chunk = all, the
+ * exponential profile, the grid estimator, no refit, position exact (n_pos = 1,
+ * pos_step_arcsec = 0.1). */
 void rlf_params_default(rlf_params *p);
 
 /* Bytes of workspace needed by entry point `which` (RLF_WS_*) for these sizes;
