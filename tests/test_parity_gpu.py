@@ -249,6 +249,31 @@ def test_run_small_pipeline(rlf, prec, chunk, update_mode):
     assert dv.max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum(), dv.max() / c.cat.flux_jy.sum()
 
 
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_run_rows_without_baseline_order(rlf, chunk):
+    # rows given without their baseline count (n_baselines = 0): no baseline order, the
+    # split baselines in row order for the extraction and the sky kernels; same results
+    torch = _torch()
+    c = small_case(True)
+    est, sky_ref = oracle.pipeline(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.cat.l, c.cat.m,
+                                   c.cat.flux_jy, None, c.oracle_params(chunk=chunk, update_mode=1), want_sky=True)
+    obs, cat = cases.to_device(c)
+    obs = rlf.Observation(obs.u, obs.v, obs.w, c.obs.freq_hz, 0)
+    p = rlf.params_default(precision=PRECS["split"], nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, chunk=chunk,
+                           update_mode=1)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
+    out = rlf.Results(cat.n_src, "cuda")
+    sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
+    rlf.run(obs, cases.vis_tensor(c.data), cat, p, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    got = out.numpy()
+    for i in range(c.cat.n_src):
+        assert cases.est_matches(got, i, est[i]) <= 1e-4, (i, got["e1"][i], est[i, oracle.E1])
+    g = sky.view(obs.n_rows, obs.n_chan, 2).cpu().numpy().astype(np.float64)
+    assert np.abs(g[..., 0] + 1j * g[..., 1] - sky_ref).max() <= (2e-5 + 1.5e-4) * c.cat.flux_jy.sum()
+
+
 @pytest.mark.parametrize("prec", ["split", "mixed", "fp64"])
 def test_gaussian_profile_sky_model_and_chain(rlf, prec):
     # the Gaussian source profile (footnote to Sec. 2.2) through the sky model and the whole
