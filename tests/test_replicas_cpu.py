@@ -4,7 +4,7 @@ The path shards by replica: every rank runs its own copy of the workload on its 
 GPU with no collective on the data path; the job's clock is the slowest rank's timed
 region and its throughput counts every rank's sources.  These tests run the
 aggregation across two gloo processes, and check that the reference arm prints only
-on rank 0.
+on rank 0; and the benchmark's roofline arithmetic (host logic, no GPU).
 """
 import json
 import os
@@ -71,3 +71,26 @@ def test_reference_arm_prints_on_rank_zero_only(tmp_path):
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
+
+
+def test_roofline_arithmetic_and_traffic_validity():
+    # the ALU roofline is the shorter of the FP32 and MUFU times for the stated op counts;
+    # the DRAM figure is the captured bytes over the measured time; the captured bytes are
+    # reported only while the kernel's sources hash to the captured version
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"fp32_fma_per_s": 3.0e13, "fp32x2_fma_per_s": 4.0e13, "mufu_rsqrt_per_s": 5.0e12,
+             "mufu_sin_per_s": 6.0e12}
+    r = bench.roofline_one("fit", 2.0, 1.0e10, 0.0, peaks)
+    t_fp32 = 6.0 * 1.0e10 / 4.0e13
+    t_mufu = 1.0 * 1.0e10 / 5.0e12
+    assert r["limiting_unit"] == "mufu" and r["frac"] == pytest.approx(max(t_fp32, t_mufu) / 2.0e-3)
+    assert r["achieved"] == pytest.approx(1.0e10 / 2.0e-3 / 1e9)
+    r5 = bench.roofline_one("fit", 2.0, 1.0e10, 0.0, peaks, fp32=30.0)
+    assert r5["limiting_unit"] == "fp32" and r5["frac"] == pytest.approx(30.0 * 1.0e10 / 4.0e13 / 2.0e-3)
+    for name, (files, digest, nbytes) in bench.TRAFFIC.items():
+        assert bench.traffic_of(name) in (None, nbytes)
+        if bench.source_hash(files) == digest:
+            assert bench.traffic_of(name) == nbytes
+    if bench.traffic_of("fit") is not None and bench.hbm_peak_gbs():
+        assert r["dram_gb_s"] == pytest.approx(bench.traffic_of("fit") / 2.0e-3 / 1e9)
