@@ -357,7 +357,7 @@ void rlf_graph_destroy(rlf_graph *graph);
 
 /*
  * Autotuner of the launch shapes (the tune_* fields of rlf_params) for this
- * workload: times the sky model over CTAs per SM {4, 8, 12, 16}, the extraction
+ * workload: times the sky model over CTAs per SM {8, 16, 32, 64}, the extraction
  * of the first chunk over {1, 2, 3, 4, 6, 8, 12, 16} CTA waves, and the persistent fit over
  * scalelength nodes per thread {2, 4, 8} x CTAs per SM {1, 2, 3} (median of 3
  * runs each, CUDA events on `stream`), and writes the fastest choices into *p.

@@ -343,7 +343,7 @@ def tuning_key(obs: Observation, n_src: int, params: Params) -> str:
 
 
 # bumped whenever rlf_autotune's candidate sets change, so that cached choices are redone
-TUNER_VERSION = 2
+TUNER_VERSION = 3
 
 
 def autotune(obs: Observation, vis_data, cat: Catalogue, params: Params, out: Results, vis_sky, workspace,

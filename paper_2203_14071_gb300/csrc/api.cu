@@ -592,7 +592,7 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
     float best[3] = {0, 0, 0};
     // 1. sky-model CTAs per SM
     {
-        const int cand[] = {4, 8, 12, 16};
+        const int cand[] = {8, 16, 32, 64};
         float bt = 0;
         int bc = 8;
         for (int c : cand) {

@@ -107,7 +107,7 @@ def test_autotune_and_cache(rlf, tmp_path):
     cache = str(tmp_path / "tune.json")
     r1 = rlf.autotune(obs, data, cat, p, out, sky, ws, cache_path=cache)
     assert not r1["cached"]
-    assert p.tune_sky_blocks in (4, 8, 12, 16) and p.tune_extract_waves in (1, 2, 3, 4, 6, 8, 12, 16)
+    assert p.tune_sky_blocks in (8, 16, 32, 64) and p.tune_extract_waves in (1, 2, 3, 4, 6, 8, 12, 16)
     assert p.tune_fit_ag in (2, 4, 8) and p.tune_fit_blocks in (1, 2, 3)
     assert all(t > 0 for t in r1["phase_ms"])
     p2 = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=c.sigma, precision=rlf.PREC_MIXED_SPLIT,
