@@ -126,3 +126,22 @@ def test_host_argument_checks(L):
     out = rlf.FitOut()
     h = L.rlf_fit_sources
     assert h(fac, ctypes.byref(src), 0, 2, ctypes.byref(p), ctypes.byref(out), ws, 1 << 40, None) == rlf.RLF_EINVAL
+
+
+def test_no_cpu_fallback_and_no_oracle_in_the_product():
+    # without the built library every compute call raises; the package never loads the oracle
+    code = ("import sys, paper_2203_14071_gb300 as r\n"
+            "assert 'oracle' not in sys.modules\n"
+            "r.LIB_PATH = '/nonexistent/librlf.so'\n"
+            "r._lib = None\n"
+            "try:\n"
+            "    r.lib()\n"
+            "except RuntimeError as e:\n"
+            "    assert 'not built' in str(e)\n"
+            "    print('raised')\n")
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "raised"
