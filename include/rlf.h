@@ -45,7 +45,8 @@ typedef enum {
     RLF_EINVAL = 1,        /* null pointer, non-positive size, bad parameter */
     RLF_ECUDA = 2,         /* a CUDA runtime call or kernel launch failed */
     RLF_ENOSPACE = 3,      /* workspace or facet buffer smaller than required */
-    RLF_ETIMEOUT = 4,      /* a bounded device wait gave up (status word) */
+    RLF_ETIMEOUT = 4,      /* a bounded device wait gave up (status word); reserved: no entry
+                              point of this version waits on the device */
     RLF_ENUMERIC = 5,      /* a non-finite likelihood was produced (status word) */
     RLF_EUNSUPPORTED = 6   /* valid request outside the implemented limits */
 } rlf_status;
@@ -92,7 +93,7 @@ enum {
 enum {
     RLF_DEV_INVALID_SOURCE = 1,
     RLF_DEV_NONFINITE = 2,
-    RLF_DEV_TIMEOUT = 4
+    RLF_DEV_TIMEOUT = 4    /* reserved (no kernel of this version waits) */
 };
 
 /* workspace users for rlf_workspace_size */
