@@ -315,7 +315,8 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
     }
 }
 
-// block reductions over kThreads threads (fixed tree order)
+// block reductions over NT threads (fixed tree order)
+template <int NT = kThreads>
 __device__ double block_sum(double x, double *scratch)
 {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -324,10 +325,11 @@ __device__ double block_sum(double x, double *scratch)
     if (lane == 0) scratch[wid] = x;
     __syncthreads();
     double t = 0.0;
-    for (int i = 0; i < kThreads / 32; ++i) t += scratch[i];
+    for (int i = 0; i < NT / 32; ++i) t += scratch[i];
     return t;
 }
 
+template <int NT = kThreads>
 __device__ double block_max(double x, double *scratch)
 {
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
@@ -336,11 +338,12 @@ __device__ double block_max(double x, double *scratch)
     if (lane == 0) scratch[wid] = x;
     __syncthreads();
     double t = -INFINITY;
-    for (int i = 0; i < kThreads / 32; ++i) t = fmax(t, scratch[i]);
+    for (int i = 0; i < NT / 32; ++i) t = fmax(t, scratch[i]);
     return t;
 }
 
 // argmax with ties to the lowest index
+template <int NT = kThreads>
 __device__ void block_argmax(double &v, long long &idx, double *sv, long long *si)
 {
     for (int o = 16; o > 0; o >>= 1) {
@@ -360,7 +363,7 @@ __device__ void block_argmax(double &v, long long &idx, double *sv, long long *s
     __syncthreads();
     v = -INFINITY;
     idx = 0x7fffffffffffffffLL;
-    for (int i = 0; i < kThreads / 32; ++i)
+    for (int i = 0; i < NT / 32; ++i)
         if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
             v = sv[i];
             idx = si[i];
@@ -874,6 +877,7 @@ fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict
 // the previous step, is sampled (|e| < 1, at most 17 per component around the MAP
 // sample).  The estimate is the last level's, by the rules of the grid estimate.
 constexpr int kAdaptSide = 17, kAdaptMax = kAdaptSide * kAdaptSide;
+constexpr int kAT = 512;   // threads of an adaptive-sampling CTA (one facet each)
 
 struct AdaptResult {
     double e1m, e2m, sd1, sd2, am, flux, e1s, e2s;
@@ -883,24 +887,25 @@ struct AdaptResult {
 
 // block-wide estimate over np samples (e of sample i: grid node i / n_e, i % n_e when
 // e1s is null); lg, a, b are [np][n_alpha]
+template <int NT>
 __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, const double *e2s,
                                       const double *__restrict__ lg, const double *__restrict__ a,
                                       const double *__restrict__ b, const GridConst &gc, const double *qp,
                                       const double *alph, const double *lnp, double *Ls, double *As,
                                       AdaptResult &res)
 {
-    __shared__ double red[kThreads / 32];
-    __shared__ long long redi[kThreads / 32];
+    __shared__ double red[NT / 32];
+    __shared__ long long redi[NT / 32];
     const int na = gc.n_alpha, ne = gc.n_e;
     const long long npa = (long long)np * na;
     auto e1_of = [&](int i) { return e1s ? e1s[i] : grid_e(gc, i / ne); };
     auto e2_of = [&](int i) { return e2s ? e2s[i] : grid_e(gc, i % ne); };
     double lmax = -INFINITY;
-    for (long long g = threadIdx.x; g < npa; g += kThreads) lmax = fmax(lmax, lg[g]);
-    lmax = block_max(lmax, red);
+    for (long long g = threadIdx.x; g < npa; g += NT) lmax = fmax(lmax, lg[g]);
+    lmax = block_max<NT>(lmax, red);
     __syncthreads();
     double Lm = 0.0;
-    for (int i = threadIdx.x; i < np; i += kThreads) {
+    for (int i = threadIdx.x; i < np; i += NT) {
         double sL = 0.0, sA = 0.0;
         for (int k = 0; k < na; ++k) {
             const double v = lg[(size_t)i * na + k];
@@ -913,11 +918,11 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
         As[i] = sA;
         Lm = fmax(Lm, sL);
     }
-    const double Lmax = block_max(Lm, red);
+    const double Lmax = block_max<NT>(Lm, red);
     __syncthreads();
     double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0, kept = 0;
     double lo1 = INFINITY, hi1 = -INFINITY, lo2 = INFINITY, hi2 = -INFINITY;
-    for (int i = threadIdx.x; i < np; i += kThreads) {
+    for (int i = threadIdx.x; i < np; i += NT) {
         const double L = Ls[i];
         if (!(L > 0.0)) continue;
         const double e1 = e1_of(i), e2 = e2_of(i);
@@ -936,21 +941,21 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
             hi2 = fmax(hi2, e2);
         }
     }
-    W = block_sum(W, red);
-    m1 = block_sum(m1, red);
-    m2 = block_sum(m2, red);
-    WA = block_sum(WA, red);
-    Ws = block_sum(Ws, red);
-    s1 = block_sum(s1, red);
-    s2 = block_sum(s2, red);
-    kept = block_sum(kept, red);
-    lo1 = -block_max(-lo1, red);
-    hi1 = block_max(hi1, red);
-    lo2 = -block_max(-lo2, red);
-    hi2 = block_max(hi2, red);
+    W = block_sum<NT>(W, red);
+    m1 = block_sum<NT>(m1, red);
+    m2 = block_sum<NT>(m2, red);
+    WA = block_sum<NT>(WA, red);
+    Ws = block_sum<NT>(Ws, red);
+    s1 = block_sum<NT>(s1, red);
+    s2 = block_sum<NT>(s2, red);
+    kept = block_sum<NT>(kept, red);
+    lo1 = -block_max<NT>(-lo1, red);
+    hi1 = block_max<NT>(hi1, red);
+    lo2 = -block_max<NT>(-lo2, red);
+    hi2 = block_max<NT>(hi2, red);
     const double e1m = W > 0 ? m1 / W : 0.0, e2m = W > 0 ? m2 / W : 0.0;
     double c11 = 0, c22 = 0, c12 = 0;
-    for (int i = threadIdx.x; i < np; i += kThreads) {
+    for (int i = threadIdx.x; i < np; i += NT) {
         const double L = Ls[i];
         if (!(L > 0.0) || L < gc.thresh_frac * Lmax) continue;
         const double d1 = e1_of(i) - e1m, d2 = e2_of(i) - e2m;
@@ -958,12 +963,12 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
         c22 += L * d2 * d2;
         c12 += L * d1 * d2;
     }
-    c11 = block_sum(c11, red);
-    c22 = block_sum(c22, red);
-    c12 = block_sum(c12, red);
+    c11 = block_sum<NT>(c11, red);
+    c22 = block_sum<NT>(c22, red);
+    c12 = block_sum<NT>(c12, red);
     double best = -INFINITY;
     long long gbest = 0x7fffffffffffffffLL;
-    for (long long g = threadIdx.x; g < npa; g += kThreads) {
+    for (long long g = threadIdx.x; g < npa; g += NT) {
         const double v = lg[g];
         if (v == -INFINITY) continue;
         const double lp = v + lnp[g % na];
@@ -972,7 +977,7 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
             gbest = g;
         }
     }
-    block_argmax(best, gbest, red, redi);
+    block_argmax<NT>(best, gbest, red, redi);
     if (threadIdx.x == 0) {
         if (W > 0) {
             c11 /= W;
@@ -1001,7 +1006,7 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
 }
 
 template <typename T, bool kGauss, int NJ>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kAT, 1)
 adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table,
                 size_t plane, int32_t NN, const GridConst gc, const double *__restrict__ ga,
                 const double *__restrict__ gb, const double *__restrict__ gl, const double *__restrict__ ccv,
@@ -1040,7 +1045,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
     }
     __syncthreads();
     // level 0: the grid
-    estimate_over_samples(mixed, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
+    estimate_over_samples<kAT>(mixed, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
                           lnp, Ls, As, res);
     double h = 2.0 * gc.e_max / (ne - 1);
     int level = 0;
@@ -1076,7 +1081,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
         __syncthreads();
         const int np = s_np;
         const T *cu = cells + (size_t)s * NN;
-        for (int base = 0; base < np * na; base += kThreads) {
+        for (int base = 0; base < np * na; base += kAT) {
             const int pr = base + threadIdx.x;
             const bool on = pr < np * na;
             const int i = on ? pr / na : 0, k = on ? pr % na : 0;
@@ -1098,13 +1103,13 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
             for (int c0 = 0; c0 < nc; c0 += kTA) {
                 const int nt = min(kTA, nc - c0);
                 __syncthreads();
-                for (int j = threadIdx.x; j < nt; j += kThreads) {
+                for (int j = threadIdx.x; j < nt; j += kAT) {
 #pragma unroll
                     for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
                 }
                 if constexpr (NJ > 1) {
                     const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
-                    for (int i = threadIdx.x; i < nt * NB; i += kThreads) (&sbr[0][0])[i] = brow[i];
+                    for (int i = threadIdx.x; i < nt * NB; i += kAT) (&sbr[0][0])[i] = brow[i];
                 }
                 __syncthreads();
                 if (!on) continue;
@@ -1162,7 +1167,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
         }
         __threadfence_block();
         __syncthreads();
-        estimate_over_samples(mixed, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
+        estimate_over_samples<kAT>(mixed, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
         h = hn;
         ++level;
     }
@@ -1264,7 +1269,7 @@ cudaError_t launch_adaptive_nj(const T *cells, const SrcRow *table, size_t plane
                                cudaStream_t st)
 {
     auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? adaptive_kernel<T, true, NJ> : adaptive_kernel<T, false, NJ>;
-    kern<<<count, kThreads, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc, ws.adapt, out,
+    kern<<<count, kAT, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc, ws.adapt, out,
                                      out_offset);
     return cudaGetLastError();
 }
