@@ -159,3 +159,38 @@ def test_unsupported_offset_grids_give_nan(n_pos):
     acc, _ = _complex_facet(N)
     lg, a, b, _ = oracle.like_grid(acc, 3.0e4, oracle.default_params(facet_n=N, n_e=3, n_alpha=2, n_pos=n_pos))
     assert np.all(np.isnan(lg[np.isfinite(lg) | np.isnan(lg)]))
+
+
+def test_adaptive_sampling_with_the_position_marginal():
+    # a noise-free source off the e grid and displaced by a grid offset: adaptive sampling
+    # with the position marginal closes in on the true shape, as it does for an undisplaced
+    # source without the marginal
+    N, nu = 16, 1.0e9
+    step = 0.5
+    p = oracle.default_params(facet_n=N, nu_ref_hz=nu, sigma_jy=1e-7, n_pos=3, pos_step_arcsec=step, estimator=1)
+    ga = oracle.grid_alpha(p)
+    flux = 1.2e-4
+    du = oracle.facet_du(flux, 0.0, p)
+    rng = np.random.default_rng(29)
+    iuv = sorted({(int(a), int(b)) for a, b in rng.integers(1, N - 1, size=(90, 2))})
+    u = np.array([(iu - N // 2 + 0.5) * du * C / nu for iu, iv in iuv])
+    v = np.array([(iv - N // 2 + 0.5) * du * C / nu for iu, iv in iuv])
+    w = np.zeros(len(iuv))
+    l0, m0 = 1.1e-3, 0.4e-3
+    e1, e2, al = 0.123, -0.057, ga[6] * ARC
+    data = np.array([[oracle.model_vis(u[r], v[r], w[r], nu, l0 - step * ARC, m0 + step * ARC, flux, al, e1, e2,
+                                       -0.7, nu)] for r in range(len(u))])
+    sky = np.array([[oracle.model_vis(u[r], v[r], w[r], nu, l0, m0, flux, al, 0.0, 0.0, -0.7, nu)]
+                    for r in range(len(u))])
+    d2 = np.stack([data.real, data.imag], -1)
+    s2 = np.stack([sky.real, sky.imag], -1)
+    acc = oracle.extract_facet(u, v, w, np.array([nu]), d2.astype(np.float32), s2, l0, m0, flux, al, 0.0, 0.0,
+                               du, p)
+    ad = oracle.fit_facet_adaptive(acc, du, flux, p)
+    assert ad[oracle.LEVELS] >= 1
+    assert abs(ad[oracle.E1] - e1) < p.e_res and abs(ad[oracle.E2] - e2) < p.e_res
+    assert abs(ad[oracle.FLUX] / flux - 1) < 1e-2
+    # without the marginal the displaced source's estimate is off by more than E_RES
+    p.n_pos = 1
+    ex = oracle.fit_facet_adaptive(acc, du, flux, p)
+    assert max(abs(ex[oracle.E1] - e1), abs(ex[oracle.E2] - e2)) > p.e_res
