@@ -579,7 +579,7 @@ OPS = {
 TRAFFIC = {
     "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "de9e12d2b402154d", 1022.47e6),
     "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "70d743ed82f2f66f", 391.61e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "2879bb8caa4ff564", 16.80e6),
+    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "ceb20818c2e625e9", 16.80e6),
 }
 
 

@@ -4,7 +4,8 @@
 //
 //   compact_kernel    one CTA per facet: the non-empty cells in increasing cell
 //                     order, as (uu, uv, vv) in units of du^2 (exact for the
-//                     half-integer cell centres), A = w s^2, B = w s Re D, and
+//                     half-integer cell centres), A = w s^2, B = w s Re D (with the
+//                     position marginal one B per offset, side by side), and
 //                     C = sum w |D|^2 in FP64.
 //   fit_persistent_kernel  one launch for every facet: CTAs take work items
 //                     (facet in largest-first order, tile of grid pairs) from an
@@ -19,6 +20,11 @@
 //                     scalelength nodes share each paired (f32x2) instruction.
 //   estimate_source   one CTA per facet, FP64 throughout: logL, alpha marginal,
 //                     threshold, moments, MAP point, flags.
+//   fit_persistent_pos_kernel / grid_tile_pos   the grid with the position
+//                     marginal (Sec. 2.4): one (e, alpha) point per thread, every
+//                     offset's b, the marginal over offsets in the tile's epilogue.
+//   adaptive_kernel   adaptive sampling around the maximum (Sec. 2.4): one CTA per
+//                     facet refines halved lattices after the grid fit.
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
