@@ -194,3 +194,21 @@ def test_adaptive_sampling_with_the_position_marginal():
     p.n_pos = 1
     ex = oracle.fit_facet_adaptive(acc, du, flux, p)
     assert max(abs(ex[oracle.E1] - e1), abs(ex[oracle.E2] - e2)) > p.e_res
+
+
+def test_flux_marginal_grows_with_b():
+    # the position marginal's best offset is the one with the largest b (S >= 0 prior) or
+    # the largest |b| (real-line prior): for fixed a and C, d ln L / d b is the posterior
+    # mean of S, positive when S >= 0, and with S on the real line ln L = b^2/(2a) + const;
+    # checked on random pairs
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        a = 10 ** rng.uniform(-2, 12)
+        scale = math.sqrt(a)
+        b1, b2 = np.sort(rng.normal(0.0, 1.0, 2) * scale * 10 ** rng.uniform(-3, 2))
+        if b1 == b2:
+            continue
+        cc = 1.0
+        assert oracle.flux_marginal(a, b2, cc, 0) >= oracle.flux_marginal(a, b1, cc, 0), (a, b1, b2)
+        l1, l2 = oracle.flux_marginal(a, b1, cc, 1), oracle.flux_marginal(a, b2, cc, 1)
+        assert (l2 >= l1) == (abs(b2) >= abs(b1)) or l1 == l2, (a, b1, b2)
