@@ -115,3 +115,39 @@ def test_simulated_noise_has_the_cell_variance():
             assert abs(part.mean() - mean) < 5 * math.sqrt(want / 20000)
             assert abs(part.var() / want - 1.0) < 0.05
     assert np.all(draws[:, 4:N * N] == 0.0)
+
+
+def test_forward_of_a_hand_computed_network():
+    # a 3-2-2-6 network with small exact weights, worked out by hand:
+    #   x = (1, -2, 1/2):  z1 = (1 - 1 + 1 + 1/4, 1/2 + 2 + 1/2 - 1/2) = (5/4, 5/2), h1 = z1
+    #                      z2 = (5/4 - 5/4 + 1/2, -5/4 + 5/8) = (1/2, -5/8), h2 = (1/2, 0)
+    #                      o  = (1/2)(1..6) + b3
+    #   x = (-1, 1, 1):    z1 = (-1 + 1/2 + 2 + 1/4, -1/2 - 1 + 1 - 1/2) = (7/4, -1), h1 = (7/4, 0)
+    #                      z2 = (7/4 + 1/2, -7/4) = (9/4, -7/4), h2 = (9/4, 0)
+    #                      o  = (9/4)(1..6) + b3
+    # Dropping either ReLU, or transposing W1 or W2, changes every output.
+    W1 = np.array([[1.0, 0.5], [0.5, -1.0], [2.0, 1.0]])
+    b1 = np.array([0.25, -0.5])
+    W2 = np.array([[1.0, -1.0], [-0.5, 0.25]])
+    b2 = np.array([0.5, 0.0])
+    W3 = np.array([[1.0, 2.0, 3.0, 4.0, 5.0, 6.0], [7.0, 8.0, 9.0, 10.0, 11.0, 12.0]])
+    b3 = np.array([0.0, 0.5, -1.0, 1.0, 0.0, -0.5])
+    x = np.array([[1.0, -2.0, 0.5], [-1.0, 1.0, 1.0]])
+    o, (_, z1, h1, z2, h2) = mlp.forward(x, W1, b1, W2, b2, W3, b3)
+    assert np.array_equal(z1, [[1.25, 2.5], [1.75, -1.0]])
+    assert np.array_equal(h1, [[1.25, 2.5], [1.75, 0.0]])
+    assert np.array_equal(z2, [[0.5, -0.625], [2.25, -1.75]])
+    assert np.array_equal(h2, [[0.5, 0.0], [2.25, 0.0]])
+    assert np.array_equal(o, [[0.5, 1.5, 0.5, 3.0, 2.5, 2.5], [2.25, 5.0, 5.75, 10.0, 11.25, 13.0]])
+
+
+def test_encode_of_a_hand_made_facet():
+    # a 2 x 2 window: cells 0..3 with counts (2, 0, 3, 1); x = [sum Re / n / S, sum Im / n / S],
+    # real parts first, the empty cell 0 (not 0/0)
+    S = 0.5
+    acc = np.array([[1.0, 0.0, -3.0, 0.25],     # sum Re x
+                    [0.5, 0.0, 1.5, -0.5],      # sum Im x
+                    [2.0, 0.0, 3.0, 1.0],       # count
+                    [2.0, 0.0, 3.3, 0.9]])      # sum of the spectral factor (unused)
+    x = mlp.encode(acc, S, N=2)
+    assert np.array_equal(x, [1.0, 0.0, -2.0, 0.5, 0.5, 0.0, 1.0, -1.0])
