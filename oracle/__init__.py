@@ -11,6 +11,7 @@ ctypes.  Functions and the passages they follow:
     model_vis        Eq. 1 + Eq. 2 (Sec. 2.2)
     alpha_med        Eq. 4 (Sec. 2.2)
     sky_model        sum of Eq. 1 over the catalogue (Sec. 2.2)
+    simulate_vis     the same sum arranged for speed (test data of large observations)
     extract_facet    Sec. 2.3 (residual, phase shift, facet of K * alpha)
     fit_facet        Sec. 2.4 (chi^2, flux, scalelength and position marginals,
                      estimate)
@@ -99,6 +100,9 @@ def lib():
             L.rlfo_sky_model.restype = None
             L.rlfo_sky_model.argtypes = [i64, i32, vp, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
                                          d, d, ctypes.c_int, vp, vp, ctypes.c_int]
+            L.rlfo_simulate_vis.restype = None
+            L.rlfo_simulate_vis.argtypes = [i64, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp,
+                                            d, d, ctypes.c_int, vp, ctypes.c_int]
             L.rlfo_extract_facet.restype = None
             L.rlfo_extract_facet.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp] + [d] * 8 + \
                                             [ctypes.c_int, d, i32, vp, vp]
@@ -174,6 +178,18 @@ def sky_model(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.
                          beta, nu_ref, profile, _p(out), _p(ab), n_threads)
     vis = out[..., 0] + 1j * out[..., 1]
     return (vis, ab) if with_abs else vis
+
+
+def simulate_vis(u, v, w, freq, l, m, flux, alpha_rad, e1, e2, beta=-0.7, nu_ref=1.0e9, profile: int = 0,
+                 n_threads=0) -> np.ndarray:
+    """Data visibilities of a synthetic observation, [n_rows, n_chan, 2] float64: the sum of
+    Eq. 1 over the catalogue (as sky_model), arranged for speed; test inputs only."""
+    u, v, w, freq = _f64(u), _f64(v), _f64(w), _f64(freq)
+    l, m, flux, alpha_rad, e1, e2 = map(_f64, (l, m, flux, alpha_rad, e1, e2))
+    out = np.empty((u.shape[0], freq.shape[0], 2), dtype=np.float64)
+    lib().rlfo_simulate_vis(u.shape[0], freq.shape[0], _p(u), _p(v), _p(w), _p(freq), l.shape[0], _p(l), _p(m),
+                            _p(flux), _p(alpha_rad), _p(e1), _p(e2), beta, nu_ref, profile, _p(out), n_threads)
+    return out
 
 
 def facet_du(flux_jy: float, alpha_cat_arcsec: float, params: Params) -> float:
