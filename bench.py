@@ -3,15 +3,16 @@
 
 One step is one pass of the whole chain over the workload: sky model of the
 catalogue, extraction of every facet, likelihood fit of every facet, sky-model
-update with the measured shapes (rlf_run).  Default workload: 197 antennas
-(19306 baselines) x 240 time steps x 8 channels = 37,067,520 visibilities and 200
-sources (chunk = all sources, mixed precision).  Inputs are synthetic and
-resident in HBM before the timed region (they exceed L2, so no flush is
+update with the measured shapes (rlf_run, captured as one CUDA graph).  Default
+workload: 197 antennas (19306 baselines) x 480 time steps x 16 channels =
+148,270,080 visibilities and 1000 sources (the paper's 9,266,880 uv points per
+channel), all sources in one chunk, split-phase precision.  Inputs are synthetic
+and resident in HBM before the timed region (they exceed L2, so no flush is
 needed); the data visibilities are made with the library's own sky-model call at
 the catalogue's true shapes and scalelengths plus seeded Gaussian noise.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+bounded sample of the same workload on every host core instead.
 """
 from __future__ import annotations
 
@@ -39,10 +40,10 @@ METRIC = "source fits/sec (end-to-end: sky model + facet extraction + likelihood
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--chunk", type=int, default=0, help="sources per extract/fit/update step (0: all)")
     ap.add_argument("--precision", default="split", choices=["split", "mixed", "fp64"])
     ap.add_argument("--update-mode", type=int, default=1)
@@ -61,7 +62,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time rlf_run calls instead of the captured graph")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
-    ap.add_argument("--no-batched", action="store_true", help="skip the extra 148M-visibility workload line")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra lines (the mid workload, and the FP64-phase precision form)")
+    ap.add_argument("--mlp-sigma", type=float, default=1e-2,
+                    help="noise per visibility component (Jy) of the learned-proposal comparison's data")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--n-src", type=int, default=0, help="use only the first N sources (profiling cases)")
@@ -159,37 +163,86 @@ def whole_job_value(n_src: int, world: int, ms: float) -> float:
 # CPU arm: the FP64 oracle on a bounded sample
 
 
-def oracle_sample_step(wl, obs, cat, params, rows_stride=2, n_threads=1):
-    """Per-source CPU cost of the chain, measured on one source (index 0).
+def oracle_chain_sample(wl, obs, cat, params, n_threads, sky_row_stride=194, ext_time_stride=16):
+    """CPU cost of the chain on this workload, from a bounded sample, on n_threads host threads.
 
-    Extraction and the sky-model/update passes are timed on every
-    `rows_stride`-th row and scaled by the row ratio; the fit runs on the full
-    facet of that subset.  Returns seconds per source at the full workload:
-        t_extract + t_fit + t_update + t_sky_model / n_src
-    """
+    The FP64 oracle as it stands (OpenMP over rows for the sky model, one source per
+    thread for extraction and fit):
+      - sky model of every source on every `sky_row_stride`-th row, scaled by the row ratio;
+      - extraction of n_threads sources (evenly spaced in the flux order) on every
+        `ext_time_stride`-th time step (all baselines), scaled by the step ratio, and the
+        fit of those facets, both scaled to all sources by n_src / n_threads;
+      - the sky update counted as two sky models (the new and the old shape of every source).
+    Returns (fits/s of the whole chain at full size, seconds of the full chain, wall
+    seconds of the sample, description)."""
+    import concurrent.futures as cf
+
     import oracle
-    rows = np.arange(0, obs.n_rows, rows_stride)
-    u, v, w = obs.u[rows], obs.v[rows], obs.w[rows]
-    scale = obs.n_rows / rows.size
-    rng = np.random.default_rng(5)
-    data = rng.standard_normal((rows.size, obs.n_chan, 2)).astype(np.float32) * np.float32(1e-5)
-    sky = np.zeros_like(data)
-    i = 0
-    al = oracle.alpha_med(cat.flux_jy[i]) * ARC
-    du = oracle.facet_du(cat.flux_jy[i], 0.0, params)
+    R, C, n = obs.n_rows, obs.n_chan, cat.n_src
+    al = np.array([oracle.alpha_med(f) for f in cat.flux_jy]) * ARC
+    z = np.zeros(n)
+    t_start = time.perf_counter()
+    rows = np.arange(0, R, sky_row_stride)
     t0 = time.perf_counter()
-    acc = oracle.extract_facet(u, v, w, obs.freq_hz, data, sky, cat.l[i], cat.m[i], cat.flux_jy[i], al,
-                               0.0, 0.0, du, params)
-    t1 = time.perf_counter()
-    oracle.fit_facet(acc, du, cat.flux_jy[i], params)
-    t2 = time.perf_counter()
-    # one source's sky-model term on the subset: the sky model costs n_src of these per pass,
-    # the update two of them (new and old shape) per source
-    oracle.sky_model(u, v, w, obs.freq_hz, cat.l[:1], cat.m[:1], cat.flux_jy[:1], np.array([al]),
-                     np.zeros(1), np.zeros(1), nu_ref=wl.nu_ref_hz, n_threads=n_threads)
-    t3 = time.perf_counter()
-    t_term = (t3 - t2) * scale
-    return (t1 - t0) * scale + (t2 - t1) + 2 * t_term + t_term
+    oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al, z, z, nu_ref=wl.nu_ref_hz,
+                     rows=rows, n_threads=n_threads)
+    t_sky = (time.perf_counter() - t0) * R / rows.size
+    n_bl = obs.n_bl if obs.n_bl > 0 and R % obs.n_bl == 0 else R
+    steps = np.arange(0, R // n_bl, ext_time_stride)
+    er = (steps[:, None] * n_bl + np.arange(n_bl)[None, :]).reshape(-1)
+    u, v, w = obs.u[er], obs.v[er], obs.w[er]
+    rng = np.random.default_rng(5)
+    data = rng.standard_normal((er.size, C, 2)).astype(np.float32) * np.float32(1e-5)
+    sky = np.zeros_like(data)
+    n_sample = max(1, min(n, n_threads))
+    picks = np.unique(np.linspace(0, n - 1, n_sample).round().astype(int))
+
+    def extract(i):
+        du = oracle.facet_du(cat.flux_jy[i], 0.0, params)
+        return oracle.extract_facet(u, v, w, obs.freq_hz, data, sky, cat.l[i], cat.m[i], cat.flux_jy[i], al[i],
+                                    0.0, 0.0, du, params), du
+
+    with cf.ThreadPoolExecutor(max_workers=n_threads) as ex:
+        t0 = time.perf_counter()
+        facets = list(ex.map(extract, picks))
+        t_ext = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        list(ex.map(lambda j: oracle.fit_facet(facets[j][0], facets[j][1], cat.flux_jy[picks[j]], params),
+                    range(len(picks))))
+        t_fit = time.perf_counter() - t0
+    wall = time.perf_counter() - t_start
+    scale = n / len(picks)
+    total = t_sky + (t_ext * (R / er.size) + t_fit) * scale + 2.0 * t_sky
+    desc = ("FP64 oracle on %d host threads: sky model of all %d sources on every %dth row (x%d), "
+            "extraction of %d sources evenly spaced in flux on every %dth time step (x%.0f) and their fits, "
+            "scaled to %d sources; sky update = 2 sky models; fits/s of the full chain"
+            % (n_threads, n, sky_row_stride, sky_row_stride, len(picks), ext_time_stride, R / er.size, n))
+    return n / total, total, wall, desc
+
+
+def oracle_small_full(n_threads):
+    """The whole chain of the 10-source, 120,960-visibility workload in full, FP64 oracle: fits/s."""
+    import oracle
+    wl = synth.workload("small")
+    obs, cat = synth.make_observation(wl), synth.make_catalogue(wl)
+    al = cat.alpha_arcsec * ARC
+    d = oracle.sky_model(obs.u, obs.v, obs.w, obs.freq_hz, cat.l, cat.m, cat.flux_jy, al, cat.e1, cat.e2,
+                         nu_ref=wl.nu_ref_hz, n_threads=n_threads)
+    data = (np.stack([d.real, d.imag], -1) + synth.noise(obs.n_rows, obs.n_chan, wl.sigma_jy, wl.seed,
+                                                          dtype=np.float64)).astype(np.float32)
+    p = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, chunk=0, update_mode=1)
+    t0 = time.perf_counter()
+    oracle.pipeline(obs.u, obs.v, obs.w, obs.freq_hz, data, cat.l, cat.m, cat.flux_jy, None, p, n_threads=n_threads)
+    wall = time.perf_counter() - t0
+    return {"workload": "small", "n_vis": obs.n_rows * obs.n_chan, "n_src": cat.n_src, "wall_s": wall,
+            "fits_per_s": cat.n_src / wall, "cores": n_threads}
+
+
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args, rank, world):
@@ -202,26 +255,25 @@ def run_reference(args, rank, world):
     params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, n_pos=args.n_pos,
                                    pos_step_arcsec=args.pos_step)
     oracle.build()
+    nt = host_threads()
     for _ in range(args.warmup):
-        oracle_sample_step(wl, obs, cat, params)
-    per = []
-    t0 = time.perf_counter()
+        oracle_chain_sample(wl, obs, cat, params, nt)
+    vals, walls, fulls = [], [], []
+    desc = ""
     for _ in range(args.steps):
-        per.append(oracle_sample_step(wl, obs, cat, params))
-    wall = time.perf_counter() - t0
-    sec_per_source = float(np.mean(per))
-    value = 1.0 / sec_per_source
-    sample = ("source 0 of %d: facet extraction and one-source sky-model term on every 2nd row (scaled x2), "
-              "fit of that facet; per-source cost = extract + fit + update (2 terms) + sky model (1 term)"
-              % cat.n_src)
+        v, full, wall, desc = oracle_chain_sample(wl, obs, cat, params, nt)
+        vals.append(v)
+        walls.append(wall)
+        fulls.append(full)
+    value = float(np.mean(vals))
     line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sec_per_source * cat.n_src * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "n_vis": obs.n_rows * obs.n_chan, "n_src": cat.n_src,
                        "n_pos": args.n_pos},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "fits/s", "cores": 1, "sample": sample,
-                             "wall_s": wall},
+            "step": "one bounded sample of the workload per step (ms_per_step is the sample's wall time)",
+            "full_chain_s_extrapolated": float(np.mean(fulls)),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "fits/s", "cores": nt, "sample": desc},
             "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -268,36 +320,75 @@ def setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=None):
             "params": params, "ws": ws, "data": data, "sky": sky, "out": out}
 
 
-def batched_line(rlf, torch, dev, args, prec, rank, stream):
-    """The 148M-visibility, 1000-source workload (all facets per step, one graph)."""
-    W = setup_workload(rlf, torch, dev, "batched", args, prec, rank, stream, n_src=0)
-    p = W["params"]
-    tune = rlf.autotune(W["obs"], W["data"], W["cat"], p, W["out"], W["sky"], W["ws"], TUNE_CACHE, stream)
-    g = rlf.Graph(W["obs"], W["data"], W["cat"], p, W["out"], W["sky"], W["ws"], stream)
+def graph_steps_ms(rlf, torch, dev, W, params, stream, steps):
+    """ms per step of the captured chain on a workload's resident inputs (after one launch)."""
+    g = rlf.Graph(W["obs"], W["data"], W["cat"], params, W["out"], W["sky"], W["ws"], stream)
     g.launch(stream)
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = 2
     a.record(stream)
     for _ in range(steps):
         g.launch(stream)
     b.record(stream)
     torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b) / steps
     g.close()
+    return a.elapsed_time(b) / steps
+
+
+def extra_workload_line(rlf, torch, dev, args, prec, rank, stream, name, steps=5):
+    """Another workload's whole chain (all facets per step, one graph, autotuned shapes)."""
+    W = setup_workload(rlf, torch, dev, name, args, prec, rank, stream, n_src=0)
+    p = W["params"]
+    rlf.autotune(W["obs"], W["data"], W["cat"], p, W["out"], W["sky"], W["ws"], TUNE_CACHE, stream)
+    ms = graph_steps_ms(rlf, torch, dev, W, p, stream, steps)
     n = W["cat_np"].n_src
     nv = W["obs_np"].n_rows * W["obs_np"].n_chan
-    return {"workload": "batched", "n_vis": nv, "n_src": n, "ms_per_step": ms, "fits_per_s": n / (ms * 1e-3),
+    return {"workload": name, "n_vis": nv, "n_src": n, "ms_per_step": ms, "fits_per_s": n / (ms * 1e-3),
             "tuning": {f: int(getattr(p, f)) for f in rlf.TUNE_FIELDS}, "steps": steps}
 
 
-def mlp_line(rlf, torch, dev, W, stream, train_steps=2000, batch=256, lr=1e-3, lr_min=5e-5, chunk=25, reps=5):
-    """The learned proposal on this workload: train the network on facets simulated from
-    the workload's own coverage (every source's facet as a template, random shapes,
-    scalelengths from the Eq. 4 prior; cosine learning-rate decay), then fit the real
-    facets with the narrowed grid and with the full grid, timed with CUDA events on the
-    same stream.  The random draws of `chunk` steps are made at once."""
-    obs, cat, p, ws, data, sky = (W[k] for k in ("obs", "cat", "params", "ws", "data", "sky"))
+def precision_line(rlf, torch, dev, W, stream, prec, steps=5):
+    """The same workload and inputs in another precision form (its own workspace and tuned
+    launch shapes): ms per step of the captured chain, and the fitted shapes' largest
+    difference from the headline run."""
+    p = rlf.Params.from_buffer_copy(W["params"])
+    p.precision = prec
+    R, C, n = W["obs_np"].n_rows, W["obs_np"].n_chan, W["cat_np"].n_src
+    ws = rlf.alloc_workspace(R, C, n, p, rlf.WS_RUN, device=dev)
+    out = rlf.Results(n, dev)
+    V = dict(W, ws=ws, out=out)
+    rlf.autotune(W["obs"], W["data"], W["cat"], p, out, W["sky"], ws, TUNE_CACHE, stream)
+    ms = graph_steps_ms(rlf, torch, dev, V, p, stream, steps)
+    a, b = out.numpy(), W["out"].numpy()
+    de = float(np.max(np.maximum(np.abs(a["e1"] - b["e1"]), np.abs(a["e2"] - b["e2"]))))
+    del ws
+    return {"precision": {0: "fp64", 1: "mixed", 2: "split"}[prec], "ms_per_step": ms,
+            "fits_per_s": n / (ms * 1e-3), "max_abs_de_vs_headline": de, "steps": steps,
+            "tuning": {f: int(getattr(p, f)) for f in rlf.TUNE_FIELDS}}
+
+
+def data_at(rlf, torch, dev, W, sigma, seed, stream):
+    """Data visibilities of the workload's true sky with noise sigma per component (device)."""
+    data = torch.empty_like(W["data"])
+    rlf.sky_model(W["obs"], W["truth"], W["params"], data, W["ws"], stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    data += torch.randn(data.numel(), generator=gen, device=dev, dtype=torch.float32) * sigma
+    return data
+
+
+def mlp_line(rlf, torch, dev, W, stream, sigma, train_steps=2000, batch=256, lr=1e-3, lr_min=5e-5, chunk=25,
+             reps=5):
+    """The learned proposal on this workload: data of the true sky with noise `sigma` per
+    component; train the network on facets simulated from the workload's own coverage
+    (every source's facet as a template, random shapes, scalelengths from the Eq. 4
+    prior; cosine learning-rate decay), then fit the real facets with the narrowed grid
+    and with the full grid, timed with CUDA events on the same stream.  The random draws
+    of `chunk` steps are made at once."""
+    obs, cat, ws, sky = (W[k] for k in ("obs", "cat", "ws", "sky"))
+    p = rlf.Params.from_buffer_copy(W["params"])
+    p.sigma_jy = sigma
+    data = data_at(rlf, torch, dev, W, sigma, 777, stream)
     n = W["cat_np"].n_src
     rlf.sky_model(obs, cat, p, sky, ws, stream)
     fac = torch.empty(rlf.facets_size(n, p) // 8, dtype=torch.float64, device=dev)
@@ -354,11 +445,16 @@ def mlp_line(rlf, torch, dev, W, stream, train_steps=2000, batch=256, lr=1e-3, l
     t_mlp = timed(lambda: rlf.fit_sources_mlp(fac, cat, 0, n, p, m, narrow, ws, nfb, stream))
     F, G = full.numpy(), narrow.numpy()
     de = np.maximum(np.abs(F["e1"] - G["e1"]), np.abs(F["e2"] - G["e2"]))
+    nv = W["obs_np"].n_rows * W["obs_np"].n_chan
+    snr = W["cat_np"].flux_jy * math.sqrt(nv) / sigma
+    del data, fac
     return {"train": {"steps": train_steps, "batch": batch, "lr": [lr, lr_min], "ms": train_ms,
                       "samples_per_s": train_steps * batch / (train_ms * 1e-3), "nll_last_100": tail},
+            "sigma_jy": sigma, "snr_range": [float(snr.min()), float(snr.max())],
             "fit_full_ms": t_full, "fit_mlp_ms": t_mlp, "fit_speedup": t_full / t_mlp,
+            "fits_per_s_full": n / (t_full * 1e-3), "fits_per_s_mlp": n / (t_mlp * 1e-3),
             "fallbacks": int(nfb.item()), "n_src": n, "agree_1e-4": float(np.mean(de <= 1e-4)),
-            "max_abs_de": float(de.max()), "box": [7, 7, 5]}
+            "max_abs_de": float(de.max()), "n_bad_full": int(np.sum(F["flag"] & 1)), "box": [7, 7, 5]}
 
 
 def main():
@@ -391,9 +487,10 @@ def main():
         "obs_np", "cat_np", "obs", "cat", "params", "ws", "data", "sky", "out"))
     n_src, R, C = cat_np.n_src, obs_np.n_rows, obs_np.n_chan
     n_vis = R * C
+    wl_head = W["wl"]
 
     if args.only == "mlp":
-        print(json.dumps({"only": "mlp", "mlp_proposal": mlp_line(rlf, torch, dev, W, stream,
+        print(json.dumps({"only": "mlp", "mlp_proposal": mlp_line(rlf, torch, dev, W, stream, args.mlp_sigma,
                                                                     train_steps=args.mlp_steps)}))
         return
     if args.only:
@@ -470,21 +567,24 @@ def main():
                  "refinements": np.bincount((res["flag"] >> 8) & 15, minlength=6).tolist(),
                  "n_refit": int(np.sum((res["flag"] & 8) != 0))},
     }
-    line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C)
+    line["roofline"], line["rooflines"] = roofline(comp, peaks, params, n_vis, n_src, R, C, workload=args.workload)
     line["launch"] = {"graph": graph is not None, "tuning": None if tuning is None else
                       {f: int(getattr(params, f)) for f in rlf.TUNE_FIELDS}}
     if graph is not None:
         graph.close()
+    if not args.no_extra and world == 1 and prec == rlf.PREC_MIXED_SPLIT:
+        # the FP64-phase form (FP64 phase argument, tile-sum accumulation and normalisation)
+        line["precision_mixed"] = precision_line(rlf, torch, dev, W, stream, rlf.PREC_MIXED)
     if not args.no_mlp and world == 1 and args.n_pos == 1:
-        line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream, train_steps=args.mlp_steps)
-    if not args.no_batched and world == 1:
-        del ws, data, sky
+        line["mlp_proposal"] = mlp_line(rlf, torch, dev, W, stream, args.mlp_sigma, train_steps=args.mlp_steps)
+    if not args.no_extra and world == 1 and args.workload != "mid":
+        del ws, data, sky, W
         torch.cuda.empty_cache()
-        line["batched_workload"] = batched_line(rlf, torch, dev, args, prec, rank, stream)
+        line["mid_workload"] = extra_workload_line(rlf, torch, dev, args, prec, rank, stream, "mid")
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(W["wl"], obs_np, cat_np, args.n_pos, args.pos_step)
+        line["cpu_baseline"] = cpu_baseline(wl_head, obs_np, cat_np, args.n_pos, args.pos_step)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -564,23 +664,24 @@ def component_times(rlf, torch, obs, data, cat, params, ws, sky, out, stream, de
 
 
 # Algorithmic operation counts per unit of work: FP32 ops and MUFU ops per unit, plus
-# per (row, source) overheads of the phase argument.
+# per (row, source) overheads of the phase argument (its float-pair form).  Per unit:
+#   sky-model term: 1 sin + 1 cos of the phase and 1 rsqrt of the profile (3 MUFU), ~10 FP32;
+#   update term: the new and the old model (2 rsqrt) and one phase (sin, cos): 4 MUFU, ~13 FP32;
+#   extraction pair (a visibility inside the source's window): the shift's sin + cos and
+#     the model's rsqrt (3 MUFU), ~16 FP32;
+#   likelihood evaluation (grid point x cell): 1 rsqrt, ~6 FP32.
 OPS = {
-    "sky_model": {"fp32": 10.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
-    "update": {"fp32": 13.0, "mufu": 2.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
-    "extract": {"fp32": 16.0, "mufu": 1.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gpair/s"},
+    "sky_model": {"fp32": 10.0, "mufu": 3.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
+    "update": {"fp32": 13.0, "mufu": 4.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gterm/s"},
+    "extract": {"fp32": 16.0, "mufu": 3.0, "fp32_rs": 50.0, "mufu_rs": 4.0, "unit": "Gpair/s"},
     "fit": {"fp32": 6.0, "mufu": 1.0, "fp32_rs": 0.0, "mufu_rs": 0.0, "unit": "Geval/s"},
 }
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the full-size launch (profiles/dram_traffic_mid_workload.md), valid while the kernel's source
-# files hash to the recorded value; otherwise the bench reports null.
-TRAFFIC = {
-    "extract": (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "de9e12d2b402154d", 1022.47e6),
-    "sky_model": (("csrc/sky.cu", "csrc/rlf_internal.cuh"), "70d743ed82f2f66f", 391.61e6),
-    "fit": (("csrc/fit.cu", "csrc/rlf_internal.cuh"), "ceb20818c2e625e9", 16.80e6),
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# per (kernel, workload), kept in the profile summaries; valid while the kernel's source files
+# hash to the recorded value, otherwise the bench reports null.
+TRAFFIC = {}
 
 
 def source_hash(files):
@@ -592,10 +693,11 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def traffic_of(name):
-    if name not in TRAFFIC:
+def traffic_of(name, workload=None):
+    key = (name, workload)
+    if key not in TRAFFIC:
         return None
-    files, digest, nbytes = TRAFFIC[name]
+    files, digest, nbytes = TRAFFIC[key]
     return nbytes if source_hash(files) == digest else None
 
 
@@ -618,7 +720,7 @@ def refit_launches(params, res, n_src):
     return launches
 
 
-def roofline_one(name, t_ms, units, row_src, peaks, fp32=None):
+def roofline_one(name, t_ms, units, row_src, peaks, fp32=None, workload=None):
     """ALU roofline: the shortest time the FP32 and MUFU budgets allow for the
     algorithmic op counts, against the measured unit rates."""
     o = dict(OPS[name])
@@ -630,7 +732,7 @@ def roofline_one(name, t_ms, units, row_src, peaks, fp32=None):
     t_mufu = (o["mufu"] * units + o["mufu_rs"] * row_src) / mufu_rate
     t_min = max(t_fp32, t_mufu)
     t = t_ms * 1e-3
-    traffic = traffic_of(name)
+    traffic = traffic_of(name, workload)
     line = {"kernel": name, "bound": "alu", "limiting_unit": "fp32" if t_fp32 >= t_mufu else "mufu",
             "unit": o["unit"], "achieved": units / t / 1e9, "peak": units / t_min / 1e9, "frac": t_min / t,
             "units_per_launch": units, "traffic": traffic,
@@ -652,19 +754,20 @@ def hbm_peak_gbs():
         return None
 
 
-def roofline(comp, peaks, params, n_vis, n_src, R, C):
+def roofline(comp, peaks, params, n_vis, n_src, R, C, workload=None):
     ph = comp["phases_ms"]
     out = {}
     for name in ("sky_model", "update"):
-        out[name] = roofline_one(name, ph[name], float(n_vis) * n_src, float(R) * n_src, peaks)
+        out[name] = roofline_one(name, ph[name], float(n_vis) * n_src, float(R) * n_src, peaks, workload=workload)
     # extraction: the algorithmic work is the terms that enter a facet (visibility-source pairs
     # inside the source's window); pairs outside need no arithmetic, and the (row, source)
     # phase work is counted in the same proportion
     frac_in = comp["in_window_pairs"] / (float(n_vis) * n_src)
-    out["extract"] = roofline_one("extract", ph["extract"], comp["in_window_pairs"], float(R) * n_src * frac_in, peaks)
+    out["extract"] = roofline_one("extract", ph["extract"], comp["in_window_pairs"], float(R) * n_src * frac_in, peaks,
+                                  workload=workload)
     # the fit's FP32 ops per evaluation: the brightness (3), a (2) and one b per position offset
     nj = params.n_pos * params.n_pos if params.n_pos > 1 else 1
-    out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks, fp32=5.0 + nj)
+    out["fit"] = roofline_one("fit", ph["fit"], float(comp["fit_evals"]), 0.0, peaks, fp32=5.0 + nj, workload=workload)
     dom = max(ph, key=ph.get)
     return out[dom], out
 
@@ -679,16 +782,20 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
     n = cat.n_src
     h_data = data.cpu().pin_memory()
     h_uvw = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (obs_np.u, obs_np.v, obs_np.w)]
+    # the catalogue (positions, fluxes, the initial circular shapes) is uploaded every step too
+    h_cat = [x.cpu().pin_memory() for x in (cat.l, cat.m, cat.flux_jy, cat.e1, cat.e2)]
     bufs = []
     for _ in range(2):
         d_uvw = [torch.empty_like(x, device=dev) for x in h_uvw]
         d_data = torch.empty_like(data)
-        bufs.append((d_uvw, d_data, rlf.Observation(d_uvw[0], d_uvw[1], d_uvw[2], obs_np.freq_hz, obs_np.n_bl)))
+        d_cat = [torch.empty_like(x, device=dev) for x in h_cat]
+        bufs.append((d_uvw, d_data, rlf.Observation(d_uvw[0], d_uvw[1], d_uvw[2], obs_np.freq_hz, obs_np.n_bl),
+                     d_cat, rlf.Catalogue(*d_cat)))
     h_out = torch.empty((2, n), dtype=torch.float64).pin_memory()
     # the chain of each input buffer as a captured graph (rlf_graph_*), else rlf_run calls
     graphs = None
     if not (args.no_graph or params.refit_bad):
-        graphs = [rlf.Graph(bf[2], bf[1], cat, params, out, sky, ws, stream) for bf in bufs]
+        graphs = [rlf.Graph(bf[2], bf[1], bf[4], params, out, sky, ws, stream) for bf in bufs]
     copy_stream = torch.cuda.Stream(dev)
     ev_copy = [torch.cuda.Event(), torch.cuda.Event()]
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
@@ -697,6 +804,8 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
         with torch.cuda.stream(copy_stream):
             copy_stream.wait_event(after)
             for h, d in zip(h_uvw, bufs[i][0]):
+                d.copy_(h, non_blocking=True)
+            for h, d in zip(h_cat, bufs[i][3]):
                 d.copy_(h, non_blocking=True)
             bufs[i][1].copy_(h_data, non_blocking=True)
             ev_copy[i].record(copy_stream)
@@ -711,7 +820,7 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
             if graphs:
                 graphs[i].launch(stream)
             else:
-                rlf.run(bufs[i][2], bufs[i][1], cat, params, out, sky, ws, stream)
+                rlf.run(bufs[i][2], bufs[i][1], bufs[i][4], params, out, sky, ws, stream)
             h_out[0].copy_(out.e1, non_blocking=True)
             h_out[1].copy_(out.e2, non_blocking=True)
             ev_done[i].record(stream)
@@ -731,9 +840,11 @@ def e2e_time(rlf, torch, obs_np, data, cat, params, ws, sky, out, stream, dev, a
     if graphs:
         for g in graphs:
             g.close()
-    h2d = h_data.numel() * 4 + sum(x.numel() * 8 for x in h_uvw)
+    h2d = h_data.numel() * 4 + sum(x.numel() * 8 for x in h_uvw) + sum(x.numel() * 8 for x in h_cat)
     return {"value": n / (ms * 1e-3), "unit": "fits/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": 2 * n * 8, "graph": graphs is not None,
+            "inputs": "data visibilities, u/v/w and the catalogue (l, m, flux, initial shapes) uploaded every "
+                      "step from pinned host memory; the fitted e1, e2 read back",
             "overlap": "uploads on a second stream, two input buffers"}
 
 
@@ -742,12 +853,10 @@ def cpu_baseline(wl, obs_np, cat_np, n_pos=1, pos_step=0.1):
     params = oracle.default_params(nu_ref_hz=wl.nu_ref_hz, sigma_jy=wl.sigma_jy, n_pos=n_pos,
                                    pos_step_arcsec=pos_step)
     oracle.build()
-    t0 = time.perf_counter()
-    sec = oracle_sample_step(wl, obs_np, cat_np, params, rows_stride=1)
-    wall = time.perf_counter() - t0
-    return {"value": 1.0 / sec, "unit": "fits/s", "cores": 1, "kind": "oracle", "wall_s": wall,
-            "sample": "source 0 on every row: facet extraction, fit of that facet, one-source sky-model "
-                      "term; per source = extract + fit + update (2 terms) + sky model (1 term)"}
+    nt = host_threads()
+    value, full, wall, desc = oracle_chain_sample(wl, obs_np, cat_np, params, nt)
+    return {"value": value, "unit": "fits/s", "cores": nt, "kind": "oracle", "wall_s": wall,
+            "full_chain_s_extrapolated": full, "sample": desc, "small_workload_in_full": oracle_small_full(nt)}
 
 
 if __name__ == "__main__":
