@@ -54,13 +54,22 @@ typedef enum {
 /* arithmetic of the path */
 enum {
     RLF_PREC_FP64 = 0,     /* every step in double precision */
-    RLF_PREC_MIXED = 1,    /* FP32 model and sums of products; FP64 phase argument and its
-                              range reduction, cell-index decisions, likelihood accumulation
-                              and the marginal normalisation */
-    RLF_PREC_MIXED_SPLIT = 2 /* as RLF_PREC_MIXED, but the phase argument and its range
-                              reduction are carried as pairs of floats with error-free FP32
-                              products and sums (about 48 significant bits), which GB300 runs
-                              at its FP32 rate instead of its much lower FP64 rate */
+    RLF_PREC_MIXED = 1,    /* FP32 model and FP32 sums of products over tiles of at most 128
+                              cells (likelihood) or one run of visibilities (facets); FP64 phase
+                              argument and its range reduction, cell-index decisions, the
+                              accumulation of the likelihood's tile sums a and b, the
+                              log-likelihood (logarithms, error functions) and the alpha
+                              marginal and its normalisation */
+    RLF_PREC_MIXED_SPLIT = 2 /* FP32 model and tile sums as in RLF_PREC_MIXED, but the phase
+                              argument and its range reduction, and the accumulation of the
+                              tile sums a and b, are carried as pairs of floats with error-free
+                              FP32 products and sums (about 48 significant bits), and the
+                              estimate takes its logarithms, error functions and exponentials
+                              (values of order one) in FP32 while the terms that cancel at high
+                              SNR, -C/2 + b^2/(2a), stay FP64; GB300 runs this at its FP32 rate
+                              instead of its much lower FP64 rate.  Measured against the FP64
+                              oracle on the 37M-visibility, 200-source workload: |de| <= 1e-6 at
+                              SNR 10 */
 };
 
 /* estimator of the ellipticity from the likelihood (Sec. 2.4) */
@@ -324,12 +333,32 @@ rlf_status rlf_mlp_forward(const void *weights, const void *x_f16, int32_t batch
 rlf_status rlf_mlp_encode(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
                           const rlf_params *p, void *x_f16, void *workspace, size_t ws_bytes, void *stream);
 /*
+ * The network's proposal alone: for the `count` facets [count][4][64*64] of sources
+ * [first, first + count), origin (device [count][3] int32) receives the (e1 node, e2
+ * node, alpha node) origin of the 7 x 7 x 5 box of grid nodes centred on the node
+ * nearest the predicted mean (clamped inside the grid), and wide (device [count]
+ * int32, may be NULL) 1 where the predicted spread of e1 or e2 exceeds three node
+ * spacings (the full grid is then needed), else 0.  Requires facet_n = 64, n_e >= 7
+ * and n_alpha >= 5.  Workspace: rlf_workspace_size(..., RLF_WS_FIT).  The paper has no
+ * counterpart (its fit searches the likelihood with Nelder-Mead, Sec. 2.4).
+ */
+rlf_status rlf_mlp_propose(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                           const rlf_params *p, const void *weights, int32_t *origin, int32_t *wide, void *workspace,
+                           size_t ws_bytes, void *stream);
+
+/*
  * rlf_fit_sources on a narrowed grid: the network proposes each facet's 7 x 7 x 5
  * box of grid nodes centred on the node nearest mu (clamped inside the grid); the
  * likelihood and the estimate are computed on the box only (alpha quadrature on the
  * box's nodes, points outside the box excluded).  A facet is refitted on the full
- * grid when the predicted spread of e1 or e2 exceeds three node spacings, or when
- * its box MAP point lies on a face of the box that is not a face of the grid.
+ * grid when the predicted spread of e1 or e2 exceeds three node spacings, when its
+ * box MAP point lies on a face of the box that is not a face of the grid (an inner
+ * face), or when a box point whose alpha marginal L(e) reaches half the estimate's
+ * threshold (thresh_frac max L / 2) lies on an inner e face or has, at an inner alpha
+ * face, an alpha-profile term above 1e-6 L(e).  The refitted facets' results are the
+ * full grid's; the others' thresholded estimate (e1, e2, sig1, sig2, alpha, flux, flag)
+ * is the full grid's up to the alpha tail so bounded, while e1_smooth/e2_smooth cover
+ * the box's points only.
  * n_fallback (device int32, may be NULL) receives the number of refitted facets.
  * Requires facet_n = 64, a mixed precision mode, n_e >= 7 and n_alpha >= 5.
  */
@@ -381,10 +410,15 @@ rlf_status rlf_autotune(const rlf_uvw *uvw, const float *vis_data, const rlf_sou
  * here in a fixed device array inside the library (about 460 KB on every GPU that
  * loads the library, held until the process exits).
  *   - At most RLF_STATIC_MAX_SRC sources; more returns RLF_ENOSPACE and enqueues
- *     nothing.  Other arguments as for rlf_sky_model.
+ *     nothing.  Other arguments as for rlf_sky_model, checked the same way.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any stream
- *     capture.
+ *     capture.  The address is kept for the life of the process: do not use this
+ *     entry point across a cudaDeviceReset.
+ *   - The launch shape follows p->tune_sky_blocks as in rlf_sky_model.  In
+ *     RLF_PREC_MIXED_SPLIT each row's float-pair phase is formed on the fly (there is
+ *     no workspace for the split-baseline records rlf_sky_model writes first); the
+ *     result is the same to FP32 rounding.
  *   - Calls share the array: calls that overlap on the GPU (other streams, or
  *     other host threads without ordering) race on it.  Each call rewrites what it
  *     reads, so earlier contents do not matter.

@@ -16,7 +16,10 @@ should be evaluated.  Everything here is the plain definition, in numpy float64:
               the facet model of the likelihood (Sec. 2.4) at the cell centres of a
               given coverage (counts n_c, mean spectral factors s_c)
   propose     the 7 x 7 x 5 sub-box of the grid centred on the node nearest mu,
-              clamped inside the grid, and the fallback rules
+              clamped inside the grid, and the fallback rules: the full grid when the
+              predicted spread is wide, when the box's MAP point lies on an inner face,
+              or when a point near the estimate's threshold touches an inner face
+              (box_needs_full_grid)
 """
 from __future__ import annotations
 
@@ -142,6 +145,37 @@ def on_inner_boundary(g, origin, box, ne, na):
         if idx == o and o > 0:
             return True
         if idx == o + b - 1 and o + b < n:
+            return True
+    return False
+
+
+def box_needs_full_grid(lg_box, qp, origin, box, thresh_frac, ne, na, alpha_tail=1e-6) -> bool:
+    """Whether a sub-box fit cannot stand for the full grid (the second fallback rule).
+
+    lg_box is the log-likelihood grid [ne, ne, na] with -inf outside the box, qp the
+    trapezoid weight times the prior density of each scalelength node.  With
+    t(e, k) = qp_k exp(lg(e, k) - max lg) and the alpha marginal L(e) = sum_k t(e, k), the
+    points that can enter the thresholded estimate are those with L(e) >= thresh_frac
+    max L / 2.  The box fails if one of them lies on a face of the box that is not a face
+    of the grid (e directions), or if its alpha profile at such a face is above
+    alpha_tail L(e) (alpha direction)."""
+    fin = np.isfinite(lg_box)
+    lmax = lg_box[fin].max()
+    t = np.where(fin, qp[None, None, :] * np.exp(np.where(fin, lg_box, lmax) - lmax), 0.0)
+    L = t.sum(axis=2)
+    near = (L > 0.0) & (L >= 0.5 * thresh_frac * L.max())
+    o1, o2, ok = origin
+    face = np.zeros((ne, ne), dtype=bool)
+    for o, b, axis in ((o1, box[0], 0), (o2, box[1], 1)):
+        for idx in ([o] if o > 0 else []) + ([o + b - 1] if o + b < ne else []):
+            if axis == 0:
+                face[idx, :] = True
+            else:
+                face[:, idx] = True
+    if np.any(near & face):
+        return True
+    for kf in ([ok] if ok > 0 else []) + ([ok + box[2] - 1] if ok + box[2] < na else []):
+        if np.any(near & (t[:, :, kf] > alpha_tail * L)):
             return True
     return False
 

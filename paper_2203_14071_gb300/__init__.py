@@ -134,10 +134,11 @@ def lib():
             L.rlf_mlp_train_step.argtypes = [_vp, _vp, _vp, i32, ctypes.c_float, i32, _vp, _vp, sz, _vp]
             L.rlf_mlp_forward.argtypes = [_vp, _vp, i32, _vp, _vp, sz, _vp]
             L.rlf_mlp_encode.argtypes = [_vp, P(Sources), i32, i32, P(Params), _vp, _vp, sz, _vp]
+            L.rlf_mlp_propose.argtypes = [_vp, P(Sources), i32, i32, P(Params), _vp, _vp, _vp, _vp, sz, _vp]
             L.rlf_fit_sources_mlp.argtypes = [_vp, P(Sources), i32, i32, P(Params), _vp, P(FitOut), _vp, _vp, sz,
                                               _vp]
             for f in ("rlf_mlp_init", "rlf_mlp_simulate", "rlf_mlp_train_step", "rlf_mlp_forward",
-                      "rlf_mlp_encode", "rlf_fit_sources_mlp"):
+                      "rlf_mlp_encode", "rlf_mlp_propose", "rlf_fit_sources_mlp"):
                 getattr(L, f).restype = ctypes.c_int
             L.rlf_sky_model_static.argtypes = [P(Uvw), P(Sources), P(Params), _vp, _vp]
             L.rlf_sky_model_static.restype = ctypes.c_int
@@ -477,6 +478,15 @@ def mlp_forward(mlp: Mlp, x16, out, workspace, stream=None):
 def mlp_encode(facets, cat: Catalogue, first: int, count: int, params: Params, x16, workspace, stream=None):
     _check(lib().rlf_mlp_encode(_ptr(facets), ctypes.byref(cat.struct), first, count, ctypes.byref(params),
                                 _ptr(x16), _ptr(workspace), workspace.numel(), _stream(stream)), "rlf_mlp_encode")
+
+
+def mlp_propose(facets, cat: Catalogue, first: int, count: int, params: Params, mlp: Mlp, origin, workspace,
+                wide=None, stream=None):
+    """rlf_mlp_propose: the network's 7 x 7 x 5 sub-box origin per facet (origin: int32 [count, 3])
+    and, optionally, its too-wide flag (wide: int32 [count])."""
+    _check(lib().rlf_mlp_propose(_ptr(facets), ctypes.byref(cat.struct), first, count, ctypes.byref(params),
+                                 _ptr(mlp.blob), _ptr(origin), _ptr(wide), _ptr(workspace), workspace.numel(),
+                                 _stream(stream)), "rlf_mlp_propose")
 
 
 def fit_sources_mlp(facets, cat: Catalogue, first: int, count: int, params: Params, mlp: Mlp, out: Results,

@@ -14,6 +14,8 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
 bool params_ok(const rlf_params &p)
 {
     if (!(p.facet_n >= 2 && p.facet_n <= RLF_MAX_FACET_N && p.facet_n % 2 == 0)) return false;
@@ -89,6 +91,8 @@ ChanTable make_chan_table(const rlf_uvw &uvw, const rlf_params &p)
         if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;
     return ch;
 }
+
+namespace {
 
 rlf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RLF_OK : RLF_ECUDA; }
 
@@ -740,6 +744,28 @@ rlf_status rlf_mlp_encode(const double *facets, const rlf_sources *src, int32_t 
     cudaError_t e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                                    nullptr, *p, ws.table, ws.status, st);
     if (e == cudaSuccess) e = mlp_encode(facets, ws.table, count, p->facet_n, static_cast<__half *>(x_f16), st);
+    return cuda_status(e);
+}
+
+rlf_status rlf_mlp_propose(const double *facets, const rlf_sources *src, int32_t first, int32_t count,
+                           const rlf_params *p, const void *weights, int32_t *origin, int32_t *wide, void *workspace,
+                           size_t ws_bytes, void *stream)
+{
+    if (!p || !params_ok(*p)) return RLF_EINVAL;
+    rlf_status s = check_src(src, first, count);
+    if (s != RLF_OK) return s;
+    if (!facets || !workspace || !weights || !origin) return RLF_EINVAL;
+    if (p->facet_n * p->facet_n * 2 != kMlpIn || p->n_e < kBoxE || p->n_alpha < kBoxA) return RLF_EUNSUPPORTED;
+    Workspace ws;
+    if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    __half *x = static_cast<__half *>(ws.mlp_x);
+    cudaError_t e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
+                                   nullptr, *p, ws.table, ws.status, st);
+    if (e == cudaSuccess) e = mlp_encode(facets, ws.table, count, p->facet_n, x, st);
+    if (e == cudaSuccess) e = mlp_forward(mlp_weights(const_cast<void *>(weights)), x, count, sc, st);
+    if (e == cudaSuccess) e = mlp_propose(sc.o, count, grid_const(*p), origin, wide ? wide : ws.wide, st);
     return cuda_status(e);
 }
 

@@ -477,6 +477,235 @@ extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
     }
 }
 
+// ---- lane-per-track extraction ------------------------------------------------------
+// A warp holds 32 / CL baselines x CL channels (CL = the channel count rounded up to a
+// power of two, at most 32; more channels are split into groups of 32): each lane walks
+// one (baseline, channel) track through time, sums runs of equal cells in registers and
+// appends a finished run to its own ring in shared memory.  The per-row work of a
+// baseline (float-pair phase argument, the channel group's phase f0 and step fd, the
+// source's quadratic form, u and v in FP32) is shared by its CL lanes: for a block of
+// CL time steps lane c computes row t0 + c and stores it in shared memory, then every
+// lane reads each row of the block (a broadcast).  One channel per thread keeps the
+// registers low enough for 512-thread CTAs, two per SM.
+constexpr int kLaneThreads = 512;
+constexpr int kLaneWarps = kLaneThreads / 32;
+constexpr int kLaneRing = 4;     // ring entries per lane: one append per row at most, drained every two rows
+constexpr int kRowWords = 8;     // per row: P, E (or the FP64 phase), f0, fd, q, u, v, valid
+
+__device__ __noinline__ void drain_lane_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
+                                             int *scnt, float *ssp, const float *dsp_s)
+{
+    for (int j = 0; j < n_entries; ++j) {
+        const int4 e = ring[j * kLaneThreads + tid];
+        const int cell = e.x & 0xfff;
+        atomicAdd(&sre[cell], __int_as_float(e.z));
+        atomicAdd(&sim[cell], __int_as_float(e.w));
+        atomicAdd(&scnt[cell], e.y);
+        atomicAdd(&ssp[cell], (float)e.y * dsp_s[e.x >> 12]);
+    }
+}
+
+template <bool kUniform, bool kSplit, bool kResid, bool kGauss>
+__global__ void __launch_bounds__(kLaneThreads, 2)
+extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ w,
+                    const float *__restrict__ us, int64_t n_rows, int32_t stride, int32_t n_parts, const ChanTable ch,
+                    const float2 *__restrict__ data, const float2 *__restrict__ sky, const SrcRow *__restrict__ table,
+                    int32_t N, const int32_t *__restrict__ perm, const int32_t *__restrict__ n_live,
+                    int32_t n_tslices, int32_t CL, float *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int NN = N * N;
+    int4 *ring = reinterpret_cast<int4 *>(smraw);                                   // [kLaneRing][threads]
+    float4 *rows = reinterpret_cast<float4 *>(ring + kLaneRing * kLaneThreads);     // [warps][32][2]
+    float *dsp_s = reinterpret_cast<float *>(rows + kLaneWarps * 32 * 2);           // [RLF_MAX_CHAN]
+    float *sre = dsp_s + RLF_MAX_CHAN;
+    float *sim = sre + NN;
+    int *scnt = reinterpret_cast<int *>(sim + NN);
+    float *ssp = reinterpret_cast<float *>(scnt + NN);
+    const int s = blockIdx.x;
+    const SrcRow S = table[s];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < NN; i += kLaneThreads) {
+        sre[i] = 0.0f;
+        sim[i] = 0.0f;
+        scnt[i] = 0;
+        ssp[i] = 0.0f;
+    }
+    const int C = ch.n;
+    for (int k = tid; k < C; k += kLaneThreads) dsp_s[k] = (float)(ch.spec[k] - ch.spec_off);
+    __syncthreads();
+    const int BW = 32 / CL;                    // baselines per warp
+    const int lb = lane / CL, lc = lane % CL;  // this lane's baseline in the warp, channel in the group
+    const int n_cg = (C + CL - 1) / CL;
+    const int bpc = kLaneWarps * BW;           // baselines per work unit
+    const double du = S.du;
+    const int half = N / 2;
+    constexpr float kTwoPi = 6.28318530717958647692f;
+    int cnt = 0;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring) + (uint32_t)tid * 16u;
+    float4 *my_rows = rows + (size_t)warp * 64;   // this warp's 32 rows x 2 float4
+
+    if (S.flux > 0.0) {
+        const float q0 = (float)S.q[0], q1 = (float)S.q[1], q2 = (float)S.q[2];
+        float lh, ll, mh, ml, nh, nl;
+        split_double(S.l, lh, ll);
+        split_double(S.m, mh, ml);
+        split_double(S.n1, nh, nl);
+        const int64_t n_time = (n_rows + stride - 1) / stride;
+        const int n_base = n_live[s];
+        const int n_blocks = (n_base + bpc - 1) / bpc;
+        const int n_units = n_blocks * n_cg * n_tslices;
+        for (int wk = blockIdx.y; wk < n_units; wk += n_parts) {
+            const int blk = wk % n_blocks;
+            const int g = (wk / n_blocks) % n_cg;
+            const int ts = wk / (n_blocks * n_cg);
+            const int64_t t_begin = n_time * ts / n_tslices, t_end = n_time * (ts + 1) / n_tslices;
+            const int j = blk * bpc + warp * BW + lb;         // position in the baseline order
+            const bool base_on = j < n_base;
+            const int bl = base_on ? (perm ? perm[j] : j) : 0;
+            const int k0 = g * CL;                            // the group's first channel
+            const int k = k0 + lc;                            // this lane's channel
+            const bool lane_on = base_on && k < C;
+            const int kk = k < C ? k : C - 1;
+            // per-channel constants
+            const float sdu = (float)(ch.s[kk] / du);
+            const float f2 = (float)(ch.s[kk] * ch.s[kk]);
+            const float fspec = (float)(S.flux * ch.spec[kk]);
+            const float cpos = (float)lc;
+            int run_cell = -1, run_n = 0;
+            float run_re = 0.0f, run_im = 0.0f;
+            for (int64_t t0 = t_begin; t0 < t_end; t0 += CL) {
+                // rows t0 .. t0 + CL - 1 of this lane's baseline: lane lc prepares row t0 + lc
+                {
+                    const int64_t tt = t0 + lc;
+                    const int64_t r = tt * stride + bl;
+                    const bool row_ok = base_on && tt < t_end && r < n_rows;
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (row_ok) {
+                        float uh, ul, vh, vl, wh, wl;
+                        float P = 0.0f, E = 0.0f, f0 = 0.0f, fd = 0.0f;
+                        if (kSplit) {
+                            const int64_t c0 = tt * stride + j;
+                            const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * c0];
+                            const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
+                            uh = a4.x; ul = a4.y; vh = a4.z; vl = a4.w; wh = b2.x; wl = b2.y;
+                            phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
+                            if (kUniform) {
+                                f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
+                                fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
+                            }
+                        } else {
+                            const double ud = u[r], vd = v[r], wd = w[r];
+                            const double ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
+                            uh = (float)ud;
+                            vh = (float)vd;
+                            // the FP64 phase (metres) kept in the two words P, E
+                            P = __int_as_float(__double2hiint(ph));
+                            E = __int_as_float(__double2loint(ph));
+                            if (kUniform) {
+                                const double t1 = ph * ch.s[k0];
+                                f0 = (float)(t1 - rint(t1));
+                                const double t2 = ph * ch.ds;
+                                fd = (float)(t2 - rint(t2));
+                            }
+                            (void)ul; (void)vl; (void)wh; (void)wl;
+                        }
+                        const float q = fmaf(q2, vh * vh, fmaf(q1, uh * vh, q0 * (uh * uh)));
+                        a = make_float4(P, E, f0, fd);
+                        b = make_float4(q, uh, vh, 1.0f);
+                    }
+                    my_rows[2 * lane] = a;
+                    my_rows[2 * lane + 1] = b;
+                }
+                __syncwarp();
+                const int nt = (int)min((int64_t)CL, t_end - t0);
+                for (int tau = 0; tau < nt; ++tau) {
+                    // two rows append at most two runs: make room every other row
+                    if ((tau & 1) == 0 && __any_sync(0xffffffffu, cnt > kLaneRing - 2)) {
+                        drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+                        cnt = 0;
+                    }
+                    const float4 ra = my_rows[2 * (lb * CL + tau)];
+                    const float4 rb = my_rows[2 * (lb * CL + tau) + 1];
+                    const bool on = lane_on && rb.w != 0.0f;
+                    const int64_t r = (t0 + tau) * stride + bl;
+                    float rr = 0.0f, ri = 0.0f;
+                    if (on) {
+                        const float2 dv = data[r * C + k];
+                        rr = dv.x;
+                        ri = dv.y;
+                        if (!kResid) {
+                            const float2 sv = sky[r * C + k];
+                            rr -= sv.x;
+                            ri -= sv.y;
+                        }
+                    }
+                    float f;
+                    if (kUniform) {
+                        f = fmaf(cpos, ra.w, ra.z);
+                    } else if (kSplit) {
+                        f = frac_cycles(ra.x, ra.y, ch.s_hi[kk], ch.s_lo[kk]);
+                    } else {
+                        const double ph = __hiloint2double(__float_as_int(ra.x), __float_as_int(ra.y));
+                        const double tt = ph * ch.s[kk];
+                        f = (float)(tt - rint(tt));
+                    }
+                    f -= rintf(f);
+                    float sn, cs;
+                    __sincosf(f * kTwoPi, &sn, &cs);
+                    int cell = -1;
+                    if (on) {
+                        int iu, iv;
+                        bool edge;
+                        cell_floor2(rb.y, rb.z, sdu, iu, iv, edge);
+                        if (edge) {
+                            iu = (int)floor((u[r] * ch.s[k]) / du);
+                            iv = (int)floor((v[r] * ch.s[k]) / du);
+                        }
+                        iu += half;
+                        iv += half;
+                        if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
+                    }
+                    // (rr + i ri) exp(-2 pi i f) plus the source's model S s M
+                    float xr = fmaf(rr, cs, ri * sn);
+                    const float xi = fmaf(ri, cs, -rr * sn);
+                    xr = fmaf(fspec, brightness<kGauss>(rb.x, f2), xr);
+                    const bool change = cell != run_cell;
+                    const bool app = change && run_cell >= 0;
+                    st_shared_v4_if(ring_s + (uint32_t)cnt * (kLaneThreads * 16u), app, run_cell | (k << 12), run_n,
+                                    __float_as_int(run_re), __float_as_int(run_im));
+                    cnt += app ? 1 : 0;
+                    const float keep = change ? 0.0f : 1.0f;
+                    run_re = fmaf(run_re, keep, xr);
+                    run_im = fmaf(run_im, keep, xi);
+                    run_n = change ? 1 : run_n + 1;
+                    run_cell = cell;
+                }
+                __syncwarp();
+            }
+            // the unit's last run
+            if (__any_sync(0xffffffffu, cnt > kLaneRing - 1)) {
+                drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+                cnt = 0;
+            }
+            if (run_cell >= 0) {
+                ring[cnt * kLaneThreads + tid] = make_int4(run_cell | (k << 12), run_n, __float_as_int(run_re),
+                                                           __float_as_int(run_im));
+                ++cnt;
+            }
+        }
+    }
+    drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+    __syncthreads();
+    float *o = partial + ((size_t)s * n_parts + blockIdx.y) * 4 * NN;
+    for (int i = tid; i < NN; i += kLaneThreads) {
+        o[i] = sre[i];
+        o[NN + i] = sim[i];
+        o[2 * NN + i] = __int_as_float(scnt[i]);
+        o[3 * NN + i] = ssp[i];
+    }
+}
+
 // Sum of the parts of every cell in FP64: a CTA takes 32 cells of one facet and
 // eight groups of threads sum every eighth part each; the groups' sums are then
 // added in group order (the result does not depend on timing).
@@ -668,6 +897,78 @@ cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *d
     return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
 }
 
+// channel lanes of the lane-per-track kernel: the channel count rounded up to a power of
+// two, at most 32
+int lane_cl(int n_chan)
+{
+    int cl = 1;
+    while (cl < n_chan && cl < 32) cl *= 2;
+    return cl;
+}
+
+size_t lane_smem(int N)
+{
+    return (size_t)kLaneRing * kLaneThreads * sizeof(int4) + (size_t)kLaneWarps * 64 * sizeof(float4) +
+           RLF_MAX_CHAN * sizeof(float) + 4 * (size_t)N * N * sizeof(float);
+}
+
+template <bool kSplit>
+cudaError_t launch_lane(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
+                        const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
+                        float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
+{
+    const size_t smem = lane_smem(N);
+    const bool resid = sky == nullptr;
+    decltype(&extract_lane_kernel<true, kSplit, true, false>) kern;
+    if (ch.profile == RLF_PROFILE_GAUSSIAN)
+        kern = ch.uniform ? (resid ? extract_lane_kernel<true, kSplit, true, true> : extract_lane_kernel<true, kSplit, false, true>)
+                          : (resid ? extract_lane_kernel<false, kSplit, true, true> : extract_lane_kernel<false, kSplit, false, true>);
+    else
+        kern = ch.uniform ? (resid ? extract_lane_kernel<true, kSplit, true, false> : extract_lane_kernel<true, kSplit, false, false>)
+                          : (resid ? extract_lane_kernel<false, kSplit, true, false> : extract_lane_kernel<false, kSplit, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLaneThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int32_t stride = uvw.n_baselines > 0 ? uvw.n_baselines : 1024;
+    const int CL = lane_cl(ch.n);
+    const int n_cg = (ch.n + CL - 1) / CL;
+    const int bpc = kLaneWarps * (32 / CL);
+    const int64_t n_blocks = ((int64_t)stride + bpc - 1) / bpc * n_cg;   // (baseline block, channel group) units
+    const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
+    const int NN = N * N;
+    const int64_t slots = (int64_t)sm_count_x() * per_sm;
+    for (int32_t first = 0; first < count; first += max_partials) {
+        const int32_t cnt = count - first < max_partials ? count - first : max_partials;
+        // parts per source: about `waves` waves of CTAs; beyond one part per unit (few
+        // sources) the time series are split too, into slices of at least 16 steps
+        int64_t parts = ((int64_t)waves * slots + cnt - 1) / cnt;
+        int64_t slices = 1;
+        if (parts > n_blocks) {
+            slices = (parts + n_blocks - 1) / n_blocks;
+            const int64_t max_slices = n_time / 16 > 1 ? n_time / 16 : 1;
+            if (slices > max_slices) slices = max_slices;
+            if (slices > 32) slices = 32;
+        }
+        if (parts > n_blocks * slices) parts = n_blocks * slices;
+        if (parts > max_partials / cnt) parts = max_partials / cnt;
+        if (parts < 1) parts = 1;
+        dim3 grid(cnt, (unsigned)parts);
+        kern<<<grid, kLaneThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
+                                               reinterpret_cast<const float2 *>(data),
+                                               reinterpret_cast<const float2 *>(sky), table + first, N, ord.perm,
+                                               ord.n_live + first, (int32_t)slices, CL, partial);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dim3 rgrid((NN + kReduceCells - 1) / kReduceCells, cnt);
+        facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
+                                                        facets + (size_t)first * 4 * NN);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_fp64(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
                         const SrcRow *table, int32_t count, int32_t N, double *facets, cudaStream_t st)
 {
@@ -789,10 +1090,10 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int waves = p.tune_extract_waves > 0 ? p.tune_extract_waves : 2;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_rl_cg<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, ws.n_partials, facets,
-                                   waves, st);
-    return launch_rl_cg<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, ws.n_partials, facets,
-                              waves, st);
+        return launch_lane<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, ws.n_partials,
+                                  facets, waves, st);
+    return launch_lane<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, ws.n_partials,
+                             facets, waves, st);
 }
 
 }  // namespace rlf

@@ -16,10 +16,12 @@
 //                     alpha nodes for every cell: one quadratic form per cell,
 //                     then per alpha one FMA, one rsqrt and the a, b products.
 //                     Mixed precision sums the products in FP32 over a tile of
-//                     cells and adds the tile sums to FP64 accumulators; two
+//                     cells and adds the tile sums to FP64 accumulators
+//                     (RLF_PREC_MIXED) or float pairs (RLF_PREC_MIXED_SPLIT); two
 //                     scalelength nodes share each paired (f32x2) instruction.
-//   estimate_source   one CTA per facet, FP64 throughout: logL, alpha marginal,
-//                     threshold, moments, MAP point, flags.
+//   estimate_source   one CTA per facet: logL, alpha marginal, threshold,
+//                     moments, MAP point, flags; FP64 throughout except the
+//                     logarithms, error functions and exponentials of split mode.
 //   fit_persistent_pos_kernel / grid_tile_pos   the grid with the position
 //                     marginal (Sec. 2.4): one (e, alpha) point per thread, every
 //                     offset's b, the marginal over offsets in the tile's epilogue.
@@ -205,7 +207,8 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
         }
     }
     // FP64 path: FP64 accumulators; FP32 path: the 128-cell tile sums are added to
-    // float pairs (hi + lo, exact two-sum), about 48 significant bits, at FP32 speed
+    // float pairs (hi + lo, exact two-sum, about 48 significant bits, at FP32 speed) in
+    // split mode, and in FP64 (a double held in the same two registers) otherwise
     double da[AG], db[AG];
     float ah[AG], al[AG], bh[AG], bl[AG];
 #pragma unroll
@@ -213,16 +216,16 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
         da[j] = db[j] = 0.0;
         ah[j] = al[j] = bh[j] = bl[j] = 0.0f;
     }
-    auto ff_add = [](float &hi, float &lo, float x) {
-        float sum, err;
-        two_sum(hi, x, sum, err);
-        hi = sum;
-        lo = __fadd_rn(lo, err);
-    };
+    const bool split = gc.split != 0;
+    auto ff_add = [split](float &hi, float &lo, float x) { acc_add(split, hi, lo, x); };
 
+    // the parts split the facet's 128-cell tiles, not its cells: every tile is summed the
+    // same way however many parts the launch uses (a fit split over CTAs and one that is
+    // not then differ only in how the float-pair tile sums are added, ~1e-14 relative)
     const int nc_all = ncell[s];
-    const int c_begin = (int)((int64_t)nc_all * part / n_parts);
-    const int nc = (int)((int64_t)nc_all * (part + 1) / n_parts);
+    const int n_tiles = (nc_all + kCellTile - 1) / kCellTile;
+    const int c_begin = (int)((int64_t)n_tiles * part / n_parts) * kCellTile;
+    const int nc = min(nc_all, (int)((int64_t)n_tiles * (part + 1) / n_parts) * kCellTile);
     const T *cu = cells + (size_t)s * NN;
     for (int c0 = c_begin; c0 < nc; c0 += kCellTile) {
         const int nt = min(kCellTile, nc - c0);
@@ -308,8 +311,8 @@ __device__ void grid_tile(int s, int tile, int part, int n_parts, const T *__res
     if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
         for (int j = 0; j < AG; ++j) {
-            da[j] = (double)ah[j] + (double)al[j];
-            db[j] = (double)bh[j] + (double)bl[j];
+            da[j] = acc_value(split, ah[j], al[j]);
+            db[j] = acc_value(split, bh[j], bl[j]);
         }
     }
     if (e_idx < ne2) {
@@ -515,12 +518,8 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
         db[j] = 0.0;
         bh[j] = bl[j] = 0.0f;
     }
-    auto ff_add = [](float &hi, float &lo, float x) {
-        float sum, err;
-        two_sum(hi, x, sum, err);
-        hi = sum;
-        lo = __fadd_rn(lo, err);
-    };
+    const bool split = gc.split != 0;
+    auto ff_add = [split](float &hi, float &lo, float x) { acc_add(split, hi, lo, x); };
     const int nc = ncell[s];
     const T *cu = cells + (size_t)s * NN;
     for (int c0 = 0; c0 < nc; c0 += kT) {
@@ -588,8 +587,14 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
     if (on && nc > 0) {
         double bb;
         if constexpr (f32) {
-            da = (double)ah + (double)al;
-            gl[g] = position_marginal_ff<NJ>(da, bh, bl, ccv[s], gc.flux_prior, bb);
+            da = acc_value(split, ah, al);
+            if (split) {
+                gl[g] = position_marginal_ff<NJ>(da, bh, bl, ccv[s], gc.flux_prior, bb);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) db[j] = pair_as_double(bh[j], bl[j]);
+                gl[g] = position_marginal<NJ>(da, db, ccv[s], gc.flux_prior, bb);
+            }
         } else {
             gl[g] = position_marginal<NJ>(da, db, ccv[s], gc.flux_prior, bb);
         }
@@ -679,6 +684,34 @@ __device__ void estimate_source(bool mixed, bool logl_ready, int s, const double
     }
     const double Lmax = block_max(Lm, red);
     __syncthreads();
+    // Sub-box fit: the box stands for the full grid only when nothing near the threshold
+    // touches a face of the box that is not a face of the grid.  Every e point with
+    // L(e) >= thresh_frac Lmax / 2 must lie off the inner e faces, and its alpha profile at
+    // an inner alpha face must be below 1e-6 L(e) (the alpha marginal over the box's nodes
+    // then misses at most ~1e-5 of the full grid's).  Otherwise the facet is fitted again
+    // on the full grid.
+    if (gc.box && gc.box_fail) {
+        const int o1 = gc.box[s * 3 + 0], o2 = gc.box[s * 3 + 1], ok = gc.box[s * 3 + 2];
+        const double cut = 0.5 * gc.thresh_frac * Lmax;
+        bool fail = false;
+        for (int e = threadIdx.x; e < ne2; e += kThreads) {
+            const double L = Le[e];
+            if (!(L > 0.0) || L < cut) continue;
+            const int i1 = e / ne, i2 = e % ne;
+            if ((i1 == o1 && o1 > 0) || (i1 == o1 + kBoxE - 1 && o1 + kBoxE < ne) || (i2 == o2 && o2 > 0) ||
+                (i2 == o2 + kBoxE - 1 && o2 + kBoxE < ne))
+                fail = true;
+            const int kf[2] = {ok > 0 ? ok : -1, ok + kBoxA < na ? ok + kBoxA - 1 : -1};
+            for (int f = 0; f < 2; ++f) {
+                if (kf[f] < 0) continue;
+                const double v = lg[(size_t)e * na + kf[f]];
+                if (v == -INFINITY) continue;
+                const double t = qp[kf[f]] * (mixed ? (double)expf((float)(v - lmax)) : exp(v - lmax));
+                if (t > 1.0e-6 * L) fail = true;
+            }
+        }
+        if (fail) gc.box_fail[s] = 1;
+    }
     // moments above the threshold and over every point
     double W = 0, m1 = 0, m2 = 0, WA = 0, Ws = 0, s1 = 0, s2 = 0;
     for (int e = threadIdx.x; e < ne2; e += kThreads) {
@@ -834,8 +867,8 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
                 }
                 __syncthreads();
             }
-            estimate_source(std::is_same<T, float>::value, false, s, ga, gb, gl, ncell, ccv, table, gc, out,
-                            out_offset, status, map_out);
+            estimate_source(std::is_same<T, float>::value && gc.split, false, s, ga, gb, gl, ncell, ccv, table, gc,
+                            out, out_offset, status, map_out);
         }
         __syncthreads();
     }
@@ -868,7 +901,7 @@ fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict
         __syncthreads();
         if (s_last) {
             __threadfence();
-            estimate_source(std::is_same<T, float>::value, true, s, ga, gb, gl, ncell, ccv, table, gc, out,
+            estimate_source(std::is_same<T, float>::value && gc.split, true, s, ga, gb, gl, ncell, ccv, table, gc, out,
                             out_offset, status, nullptr);
         }
         __syncthreads();
@@ -1019,6 +1052,8 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                 double *__restrict__ scratch, rlf_fit_out out, int32_t out_offset)
 {
     constexpr bool mixed = std::is_same<T, float>::value;
+    const bool split = gc.split != 0;
+    const bool fp32_norm = mixed && split;   // FP32 logarithms, error functions and exponentials
     // cells per staged tile: uu, uv, vv, A and NJ B planes (B per position offset)
     constexpr int kTA = (NJ > 1 && !mixed) ? kCellTile / 2 : kCellTile;
     constexpr int NB = NJ > 1 ? (NJ + 3) / 4 * 4 : 1;   // B values per cell (b_stride)
@@ -1051,7 +1086,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
     }
     __syncthreads();
     // level 0: the grid
-    estimate_over_samples<kAT>(mixed, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
+    estimate_over_samples<kAT>(fp32_norm, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
                           lnp, Ls, As, res);
     double h = 2.0 * gc.e_max / (ne - 1);
     int level = 0;
@@ -1136,16 +1171,9 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
                     }
                 }
                 if constexpr (mixed) {
-                    float sum, err;
-                    two_sum(ah, pa, sum, err);
-                    ah = sum;
-                    al = __fadd_rn(al, err);
+                    acc_add(split, ah, al, pa);
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) {
-                        two_sum(bh[j], pb[j], sum, err);
-                        bh[j] = sum;
-                        bl[j] = __fadd_rn(bl[j], err);
-                    }
+                    for (int j = 0; j < NJ; ++j) acc_add(split, bh[j], bl[j], pb[j]);
                 } else {
                     da += (double)pa;
 #pragma unroll
@@ -1154,18 +1182,18 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
             }
             if (on) {
                 if constexpr (mixed) {
-                    da = (double)ah + (double)al;
+                    da = acc_value(split, ah, al);
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) db[j] = (double)bh[j] + (double)bl[j];
+                    for (int j = 0; j < NJ; ++j) db[j] = acc_value(split, bh[j], bl[j]);
                 }
                 sa[pr] = da;
                 if constexpr (NJ == 1) {
                     sb[pr] = db[0];
-                    slg[pr] = mixed ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
-                                    : flux_marginal(da, db[0], cc, gc.flux_prior);
+                    slg[pr] = fp32_norm ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
+                                        : flux_marginal(da, db[0], cc, gc.flux_prior);
                 } else {
                     double bb;
-                    if constexpr (mixed) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
+                    if (fp32_norm) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
                     else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
                     sb[pr] = bb;
                 }
@@ -1173,7 +1201,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
         }
         __threadfence_block();
         __syncthreads();
-        estimate_over_samples<kAT>(mixed, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
+        estimate_over_samples<kAT>(fp32_norm, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
         h = hn;
         ++level;
     }
@@ -1198,7 +1226,8 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
 namespace {
 
 // Facets whose sub-box fit must be redone on the full grid: the proposal was too
-// wide, or the MAP point lies on a face of the box that is not a face of the grid.
+// wide or the box's estimate found mass near the threshold on an inner face (both
+// in `wide`), or the MAP point lies on a face of the box that is not a face of the grid.
 __global__ void refit_list_kernel(const int32_t *__restrict__ box, const int32_t *__restrict__ wide,
                                   const int32_t *__restrict__ map_index, int32_t count, int32_t ne, int32_t na,
                                   int32_t *__restrict__ refit)
@@ -1424,6 +1453,9 @@ GridConst grid_const(const rlf_params &p)
     gc.thresh_frac = p.thresh_frac;
     gc.var_sigma_min = p.var_sigma_min;
     gc.var_det_min = p.var_det_min;
+    gc.split = p.precision == RLF_PREC_MIXED_SPLIT ? 1 : 0;
+    gc.pad_ = 0;
+    gc.box_fail = nullptr;
     return gc;
 }
 
@@ -1468,8 +1500,10 @@ cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t co
     if (e == cudaSuccess) e = mlp_forward(W, x, count, sc, st);
     if (e == cudaSuccess) e = mlp_propose(sc.o, count, gc, ws.box, ws.wide, st);
     // the likelihood on every facet's sub-box
-    // one scalelength node per thread: 7 x 7 x 5 = 245 of the CTA's 256 threads busy
+    // one scalelength node per thread: 7 x 7 x 5 = 245 of the CTA's 256 threads busy;
+    // the estimate marks the boxes that cannot stand for the full grid in ws.wide
     gc.box = ws.box;
+    gc.box_fail = ws.wide;
     if (e == cudaSuccess)
         e = launch_persistent<float, 1>(cells, table, plane, NN, count, nullptr, nullptr, gc, p, ws, out, 0,
                                         ws.map_index, st);
@@ -1481,6 +1515,7 @@ cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t co
         e = cudaGetLastError();
     }
     gc.box = nullptr;
+    gc.box_fail = nullptr;
     if (e == cudaSuccess)
         e = launch_persistent_ag<float>(cells, table, plane, NN, count, ws.refit, ws.refit + 1, gc, p, ws, out, 0,
                                         nullptr, st);

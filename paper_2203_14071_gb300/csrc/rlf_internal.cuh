@@ -212,7 +212,44 @@ struct GridConst {
     double r_std;
     double inv_sigma2;      // 1 / sigma^2
     double thresh_frac, var_sigma_min, var_det_min;
+    int32_t split;          // RLF_PREC_MIXED_SPLIT: FP32 tile sums added to float pairs, FP32 logarithms,
+                            // error functions and exponentials in the estimate; otherwise (FP32 kernels of
+                            // RLF_PREC_MIXED) tile sums added in FP64 and the estimate in FP64
+    int32_t pad_;
+    int32_t *box_fail;      // sub-box fits: set to 1 for a facet whose box cannot stand for the full grid
 };
+
+// FP64 accumulation in the registers of a float pair: the pair holds the two 32-bit halves
+// of a double (no extra registers beside the float-pair form of the same kernels).
+__device__ __forceinline__ double pair_as_double(float hi, float lo)
+{
+    return __hiloint2double(__float_as_int(hi), __float_as_int(lo));
+}
+
+__device__ __forceinline__ void double_to_pair(double d, float &hi, float &lo)
+{
+    hi = __int_as_float(__double2hiint(d));
+    lo = __int_as_float(__double2loint(d));
+}
+
+// Add x to an accumulator held in (hi, lo): a float pair (hi + lo, error-free two-sum,
+// about 48 significant bits) when `split`, else a double stored in the two registers.
+__device__ __forceinline__ void acc_add(bool split, float &hi, float &lo, float x)
+{
+    if (split) {
+        float sum, err;
+        two_sum(hi, x, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, err);
+    } else {
+        double_to_pair(pair_as_double(hi, lo) + (double)x, hi, lo);
+    }
+}
+
+__device__ __forceinline__ double acc_value(bool split, float hi, float lo)
+{
+    return split ? (double)hi + (double)lo : pair_as_double(hi, lo);
+}
 
 // Carve-up of the caller's workspace.
 struct Workspace {
@@ -253,6 +290,13 @@ struct Workspace {
 
 size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf_params &p,
                         int32_t which, void *base, Workspace *ws);
+
+// Host-side argument checks shared by every entry point (api.cu): the parameters, the
+// observation and a source range; and the channel table of a call.
+bool params_ok(const rlf_params &p);
+rlf_status check_uvw(const rlf_uvw *uvw);
+rlf_status check_src(const rlf_sources *src, int32_t first, int32_t count);
+ChanTable make_chan_table(const rlf_uvw &uvw, const rlf_params &p);
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_prepare(const rlf_sources &src, int32_t first, int32_t count,

@@ -13,12 +13,13 @@
 // name is only a host-side stand-in, so the device address is looked up with
 // cudaGetSymbolAddress, once per device, with that device current, on the first
 // call made on the device.  That first call should therefore come before any
-// stream capture.  Every call on a device shares the array: calls that overlap on
-// the GPU (different streams, or different host threads without ordering) race
-// on it.  Each call clears the status word it uses before its kernels run; the
-// per-source table is fully rewritten by every call.
-#include <cmath>
-#include <cstring>
+// stream capture.  The address is kept per device ordinal for the life of the
+// process, so the entry point must not be used across a cudaDeviceReset (which
+// reloads the module and moves the array).  Every call on a device shares the
+// array: calls that overlap on the GPU (different streams, or different host
+// threads without ordering) race on it.  Each call clears the status word it uses
+// before its kernels run; the per-source table is fully rewritten by every call.
+// Arguments are checked exactly as rlf_sky_model checks them.
 #include <mutex>
 
 #include "rlf_internal.cuh"
@@ -51,70 +52,32 @@ rlf_status scratch_address(void **out)
     return RLF_OK;
 }
 
-bool params_valid(const rlf_params &p)
-{
-    return p.facet_n >= 2 && p.facet_n <= RLF_MAX_FACET_N && p.facet_n % 2 == 0 && p.n_e >= 2 &&
-           p.n_e <= rlf::kMaxNe && p.n_alpha >= 1 && p.n_alpha <= 64 && p.sigma_jy > 0 && p.psf_nat > 0 &&
-           std::isfinite(p.psf_nat) && p.r_min_arcsec > 0 && p.r_max_arcsec >= p.r_min_arcsec && p.r_std > 0 &&
-           p.thresh_frac > 0 && p.thresh_frac <= 1 && p.e_max > 0 && p.e_max <= 1 && p.nu_ref_hz > 0 &&
-           std::isfinite(p.nu_ref_hz) && std::isfinite(p.beta) && std::isfinite(p.add) && std::isfinite(p.esp) &&
-           (p.precision == RLF_PREC_FP64 || p.precision == RLF_PREC_MIXED || p.precision == RLF_PREC_MIXED_SPLIT) &&
-           (p.flux_prior == 0 || p.flux_prior == 1) && (p.update_mode == 0 || p.update_mode == 1);
-}
-
-rlf::ChanTable channel_table(const rlf_uvw &uvw, const rlf_params &p)
-{
-    rlf::ChanTable ch;
-    std::memset(&ch, 0, sizeof(ch));
-    ch.n = uvw.n_chan;
-    double mean = 0.0;
-    for (int k = 0; k < ch.n; ++k) {
-        ch.s[k] = uvw.freq_hz[k] / rlf::kC;
-        ch.spec[k] = std::pow(uvw.freq_hz[k] / p.nu_ref_hz, p.beta);
-        ch.s_hi[k] = (float)ch.s[k];
-        ch.s_lo[k] = (float)(ch.s[k] - (double)ch.s_hi[k]);
-        mean += ch.spec[k];
-    }
-    ch.spec_off = mean / ch.n;
-    ch.s0 = ch.s[0];
-    ch.ds = ch.n > 1 ? (ch.s[ch.n - 1] - ch.s[0]) / (ch.n - 1) : 0.0;
-    ch.ds_hi = (float)ch.ds;
-    ch.ds_lo = (float)(ch.ds - (double)ch.ds_hi);
-    ch.profile = p.profile;
-    ch.pad = 0;
-    ch.uniform = 1;
-    for (int k = 0; k < ch.n; ++k)
-        if (std::fabs(ch.s[k] - (ch.s0 + k * ch.ds)) > 1e-12 * ch.s0) ch.uniform = 0;
-    return ch;
-}
-
 }  // namespace
 
 extern "C" rlf_status rlf_sky_model_static(const rlf_uvw *uvw, const rlf_sources *src,
                                            const rlf_params *p, float *vis_sky, void *stream)
 {
-    if (!uvw || !uvw->u || !uvw->v || !uvw->w || !uvw->freq_hz || uvw->n_rows <= 0 || uvw->n_chan <= 0 ||
-        uvw->n_baselines < 0)
-        return RLF_EINVAL;
-    if (uvw->n_chan > RLF_MAX_CHAN) return RLF_EUNSUPPORTED;
-    for (int k = 0; k < uvw->n_chan; ++k)
-        if (!(uvw->freq_hz[k] > 0 && std::isfinite(uvw->freq_hz[k])) ||
-            (k > 0 && !(uvw->freq_hz[k] > uvw->freq_hz[k - 1])))
-            return RLF_EINVAL;
-    if (!src || !src->l || !src->m || !src->flux_jy || !src->e1 || !src->e2 || src->n_src <= 0) return RLF_EINVAL;
-    if (!p || !params_valid(*p) || !vis_sky) return RLF_EINVAL;
+    // the same argument checks as rlf_sky_model
+    rlf_status s = rlf::check_uvw(uvw);
+    if (s != RLF_OK) return s;
+    if (!src) return RLF_EINVAL;
+    if ((s = rlf::check_src(src, 0, src->n_src)) != RLF_OK) return s;
+    if (!p || !rlf::params_ok(*p) || !vis_sky) return RLF_EINVAL;
     if (src->n_src > RLF_STATIC_MAX_SRC) return RLF_ENOSPACE;   // the fixed table holds RLF_STATIC_MAX_SRC
     void *base = nullptr;
-    rlf_status s = scratch_address(&base);
-    if (s != RLF_OK) return s;
+    if ((s = scratch_address(&base)) != RLF_OK) return s;
     int32_t *status = static_cast<int32_t *>(base);
     rlf::SrcRow *table = reinterpret_cast<rlf::SrcRow *>(static_cast<unsigned char *>(base) + kStatusBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const rlf::ChanTable ch = channel_table(*uvw, *p);
+    const rlf::ChanTable ch = rlf::make_chan_table(*uvw, *p);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess)
         e = rlf::launch_prepare(*src, 0, src->n_src, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                                 nullptr, *p, table, status, st);
-    if (e == cudaSuccess) e = rlf::launch_sky(*uvw, ch, table, src->n_src, false, p->precision, vis_sky, st);
+    // the caller's launch shape; no split-baseline records (there is no workspace to hold
+    // them): in split mode each row's float-pair phase is formed on the fly
+    if (e == cudaSuccess)
+        e = rlf::launch_sky(*uvw, ch, table, src->n_src, false, p->precision, vis_sky, st, p->tune_sky_blocks, 1.0f,
+                            rlf::SplitRows());
     return e == cudaSuccess ? RLF_OK : RLF_ECUDA;
 }

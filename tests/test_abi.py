@@ -145,3 +145,20 @@ def test_no_cpu_fallback_and_no_oracle_in_the_product():
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "raised"
+
+
+def test_static_sky_model_checks_arguments_as_the_workspace_entry_point(L):
+    # an out-of-range profile (or estimator) is rejected by both sky-model entry points before
+    # anything is enqueued
+    fake = 0x1000
+    freq = np.array([1.0e9], dtype=np.float64)
+    uvw = rlf.Uvw(n_rows=4, n_chan=1, n_baselines=0, u=fake, v=fake, w=fake,
+                  freq_hz=freq.ctypes.data_as(ctypes.c_void_p).value)
+    src = rlf.Sources(n_src=3, reserved=0, l=fake, m=fake, flux_jy=fake, alpha_arcsec=None, e1=fake, e2=fake)
+    for field, bad in (("profile", 7), ("estimator", 9), ("n_pos", 4), ("tune_sky_blocks", -1)):
+        p = rlf.params_default()
+        setattr(p, field, bad)
+        assert L.rlf_sky_model_static(ctypes.byref(uvw), ctypes.byref(src), ctypes.byref(p), fake, None) == \
+            rlf.RLF_EINVAL, field
+        assert L.rlf_sky_model(ctypes.byref(uvw), ctypes.byref(src), ctypes.byref(p), fake, fake, 1 << 40,
+                               None) == rlf.RLF_EINVAL, field

@@ -192,6 +192,9 @@ def _oracle_narrowed(acc, du, flux, p, o_row):
     est, _ = oracle.estimate(lgm, a, b, flux, p, nc)
     refit = wide or (est[oracle.MAP_INDEX] >= 0 and omlp.on_inner_boundary(int(est[oracle.MAP_INDEX]), origin,
                                                                             (7, 7, 5), p.n_e, p.n_alpha))
+    if not refit and nc > 0:
+        refit = omlp.box_needs_full_grid(lgm, oracle.alpha_weight(p, flux), origin, (7, 7, 5), p.thresh_frac,
+                                         p.n_e, p.n_alpha)
     if refit:
         est, _ = oracle.estimate(lg, a, b, flux, p, nc)
     return est, origin, refit
@@ -221,6 +224,42 @@ def test_narrowed_fit_matches_oracle(rlf, small):
         n_refit += refit
         assert cases.est_matches(got, i, est) <= 1e-4, (i, origin, refit)
     assert int(nfb.item()) == n_refit
+
+
+def test_propose_matches_oracle(rlf, small):
+    # rlf_mlp_propose alone: the sub-box origin and the too-wide flag of every facet, from
+    # the oracle's own forward pass of the same (f16-rounded) weights and inputs; a node
+    # choice within 1e-3 of a tie between two nodes may go either way
+    import torch
+    c = small
+    n = c.cat.n_src
+    T = _oracle_facets(c, range(n))
+    P = _host_weights(7, scale=0.3)
+    m, R = _load(rlf, P)
+    obs, cat = cases.to_device(c)
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, precision=rlf.PREC_MIXED_SPLIT)
+    ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, n, p, rlf.WS_FIT)
+    origin = torch.full((n, 3), -1, dtype=torch.int32, device="cuda")
+    wide = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    rlf.mlp_propose(torch.from_numpy(T).cuda(), cat, 0, n, p, m, origin, ws, wide)
+    og, wg = origin.cpu().numpy(), wide.cpu().numpy()
+    po = c.oracle_params()
+    ge, ga = oracle.grid_e(po), oracle.grid_alpha(po)
+    X = np.stack([omlp.encode(T[i], c.cat.flux_jy[i]) for i in range(n)]).astype(np.float16).astype(np.float64)
+    O, _ = omlp.forward(X, *R)
+    de = ge[1] - ge[0]
+
+    def near_tie(x, nodes):
+        d = np.sort(np.abs(nodes - x))
+        return d[1] - d[0] < 1e-3 * (nodes[1] - nodes[0] if nodes.size > 1 else 1.0)
+    for i in range(n):
+        (o1, o2, ok), wide_o = omlp.propose(O[i, :3], O[i, 3:6], ge, ga)
+        ties = (near_tie(O[i, 0], ge), near_tie(O[i, 1], ge), near_tie(math.exp(O[i, 2]), ga))
+        for d, (want, tie) in enumerate(zip((o1, o2, ok), ties)):
+            assert tie or og[i, d] == want, (i, d, og[i], (o1, o2, ok))
+        sig = np.exp(0.5 * O[i, 3:5])
+        if np.all(np.abs(sig - 3.0 * de) > 1e-3 * de):
+            assert wg[i] == int(wide_o), (i, sig, wg[i])
 
 
 def test_training_reduces_loss_and_narrowed_fit_gains(rlf):
@@ -289,5 +328,6 @@ def test_training_reduces_loss_and_narrowed_fit_gains(rlf):
     agree = float(np.mean(de <= 1e-4))
     print(f"\nfull grid {t_full:.3f} ms, narrowed {t_mlp:.3f} ms ({t_full / t_mlp:.1f}x), "
           f"fallbacks {int(nfb.item())}/{n}, agreement within 1e-4: {agree:.2%}, losses {losses}")
+    # every narrowed fit either agrees with the full grid or was refitted on it
+    assert agree == 1.0, (agree, float(de.max()))
     assert t_mlp < t_full
-    assert agree >= 0.9

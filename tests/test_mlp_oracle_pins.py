@@ -151,3 +151,34 @@ def test_encode_of_a_hand_made_facet():
                     [2.0, 0.0, 3.3, 0.9]])      # sum of the spectral factor (unused)
     x = mlp.encode(acc, S, N=2)
     assert np.array_equal(x, [1.0, 0.0, -2.0, 0.5, 0.5, 0.0, 1.0, -1.0])
+
+
+def test_box_fallback_rule_on_hand_made_grids():
+    # a 7 x 7 x 5 box at origin (7, 7, 7) of a 21 x 21 x 20 grid, flat prior weights; the
+    # log-likelihood is a narrow bump at a chosen (e1, e2, alpha) node, -inf outside the box
+    ne, na, box, origin = 21, 20, (7, 7, 5), (7, 7, 7)
+    qp = np.ones(na)
+    m = mlp.box_mask(origin, box, ne, na)
+    i1, i2, k = np.meshgrid(np.arange(ne), np.arange(ne), np.arange(na), indexing="ij")
+
+    def grid(c1, c2, ck, w_e, w_a):
+        lg = -0.5 * (((i1 - c1) / w_e) ** 2 + ((i2 - c2) / w_e) ** 2 + ((k - ck) / w_a) ** 2)
+        return np.where(m, lg, -np.inf)
+    fb = lambda lg: mlp.box_needs_full_grid(lg, qp, origin, box, 0.05, ne, na)
+    # centred and narrow in every direction: the box stands for the grid
+    assert not fb(grid(10, 10, 9, 0.7, 0.3))
+    # wide in e: the inner e faces (3 nodes off the centre) carry L above 2.5 % of the maximum
+    assert fb(grid(10, 10, 9, 2.0, 0.3))
+    # narrow in e but wide in alpha: the alpha faces carry more than 1e-6 of L(e)
+    assert fb(grid(10, 10, 9, 0.7, 1.5))
+    # at the grid's own edge a box face is not an inner face: a bump on e1 node 0 with the box
+    # at origin 0 does not fail on that face
+    o0 = (0, 7, 7)
+    m0 = mlp.box_mask(o0, box, ne, na)
+    lg0 = np.where(m0, -0.5 * ((i1 / 0.7) ** 2 + ((i2 - 10) / 0.7) ** 2 + ((k - 9) / 0.3) ** 2), -np.inf)
+    assert not mlp.box_needs_full_grid(lg0, qp, o0, box, 0.05, ne, na)
+    # the same bump against an inner face (box at origin 1: e1 node 1 is its lower face)
+    o1 = (1, 7, 7)
+    m1 = mlp.box_mask(o1, box, ne, na)
+    lg1 = np.where(m1, -0.5 * (((i1 - 1) / 0.7) ** 2 + ((i2 - 10) / 0.7) ** 2 + ((k - 9) / 0.3) ** 2), -np.inf)
+    assert mlp.box_needs_full_grid(lg1, qp, o1, box, 0.05, ne, na)

@@ -173,6 +173,35 @@ def test_extract_multichannel_ragged(rlf, prec):
         _check_facet(got[t], ref, ab, FACET_TOL[prec])
 
 
+@pytest.mark.parametrize("prec", ["split", "mixed"])
+@pytest.mark.parametrize("n_chan,uniform", [(2, True), (5, False), (16, True), (40, True)])
+@pytest.mark.parametrize("count", [1, 3])
+def test_extract_channel_lanes(rlf, prec, n_chan, uniform, count):
+    # every channel-lane layout of the extraction: 2 and 16 channels fill their lanes, 5 leaves
+    # three of eight idle (uneven spacing: no phase step), 40 splits into groups of 32 and 8;
+    # one source reads data and sky model separately, three the formed residual
+    wl = synth.tiny(seed=60 + n_chan, n_ant=20, n_time=37, n_chan=n_chan, n_src=4, r_max_m=5000.0)
+    c = cases.build(wl, snr10=True)
+    if not uniform:
+        c.obs.freq_hz = c.obs.freq_hz * (1 + 0.02 * np.arange(n_chan) ** 2 / n_chan ** 2)
+        c = cases.Case(c.wl, c.obs, c.cat, c.sigma)
+        c.data = cases.data_from(cases.true_sky(c), c.sigma, wl.seed)
+        z = np.zeros(c.cat.n_src)
+        s0 = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                              c.alpha_med_rad(), z, z, nu_ref=wl.nu_ref_hz)
+        c.sky0 = np.stack([s0.real, s0.imag], -1).astype(np.float32)
+    got = _extract_gpu(rlf, c, prec, None, None, c.data, c.sky0, first=1, count=count, facet_n=32)
+    p = c.oracle_params(facet_n=32)
+    al = c.alpha_med_rad()
+    for t in range(count):
+        i = 1 + t
+        du = oracle.facet_du(c.cat.flux_jy[i], 0.0, p)
+        ref, ab = oracle.extract_facet(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.data, c.sky0, c.cat.l[i],
+                                       c.cat.m[i], c.cat.flux_jy[i], al[i], 0.0, 0.0, du, p, with_abs=True)
+        assert ref[2].sum() > 100
+        _check_facet(got[t], ref, ab, FACET_TOL[prec])
+
+
 def _fit_gpu(rlf, case, prec, facets_np, first=0, **pk):
     torch = _torch()
     count = facets_np.shape[0]

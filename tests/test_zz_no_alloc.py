@@ -5,14 +5,16 @@ must not allocate after start-up, a plugin handed only input and output buffers)
 cannot supply the workspace rlf_sky_model needs; this entry point keeps its
 per-source table in a fixed device array inside the library instead.  The test
 calls it twice in a row through the C ABI, with different catalogues, and checks
-each result against rlf_sky_model's within the visibility tolerance of the
-parity tests.  This file is collected last on purpose.
+each result against rlf_sky_model's and against the FP64 oracle with the
+per-visibility bound of the parity tests (1e-5 of the summed moduli of the terms,
+plus the complex64 rounding of the output).  This file is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from tests import cases
 
@@ -44,10 +46,16 @@ def test_static_sky_model_matches_workspace_entry_point():
         torch.cuda.synchronize()
         g = got.view(-1, 2).cpu().numpy().astype(np.float64)
         r = ref.view(-1, 2).cpu().numpy().astype(np.float64)
-        err = np.hypot(g[:, 0] - r[:, 0], g[:, 1] - r[:, 1])
-        scale = np.abs(c.cat.flux_jy).sum()
         assert np.all(np.isfinite(g)), call
-        assert np.max(err) <= 1e-5 * scale, (call, float(np.max(err)))
+        orc, ab = oracle.sky_model(c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l, c.cat.m, c.cat.flux_jy,
+                                   c.alpha_med_rad(), e1, e2, nu_ref=wl.nu_ref_hz, with_abs=True)
+        orc, ab = orc.reshape(-1), ab.reshape(-1)
+        gz, rz = g[:, 0] + 1j * g[:, 1], r[:, 0] + 1j * r[:, 1]
+        rnd = 2.0 ** -24 * np.sqrt(2.0) * np.abs(orc)
+        # against the workspace entry point: both within the parity bound of the oracle
+        assert np.all(np.abs(gz - rz) <= 2e-5 * ab + 2 * rnd + 1e-30), (call, float(np.max(np.abs(gz - rz) / ab)))
+        # against the FP64 oracle, as the parity tests bound rlf_sky_model
+        assert np.all(np.abs(gz - orc) <= 1e-5 * ab + rnd + 1e-30), (call, float(np.max(np.abs(gz - orc) / ab)))
 
 
 def test_static_sky_model_rejects_too_many_sources():
