@@ -6,18 +6,21 @@
 // exp(+2 pi i phi_i), so after the shift it is the real number S s M(k) and
 // x = (D - V_sky) exp(-2 pi i phi_i) + S s M(k).
 //
-// Mixed-precision kernel (extract_rl_kernel).  A CTA owns (source, part) and
-// keeps a private copy of the facet in shared memory; the part is an
-// interleaved share of the blocks of baselines.  Each thread walks one
-// baseline's whole time series for a group of channels.  A baseline's uv track
-// moves slowly (a few per cent of a cell per 60 s step at the facet sizes of the
-// method), so consecutive visibilities of one channel usually fall in the same
-// cell: the thread sums that run in registers and adds it to shared memory only
-// when the cell changes.  At the end the CTA stores its partial facet with
-// plain coalesced stores, and facet_reduce_kernel sums the parts of each cell in
-// FP64 in a fixed order (no global atomics).  Inside a CTA the warps' shared-memory
-// additions land in varying order, so repeated runs agree to FP32 rounding.  blockIdx.x runs over the sources, so the CTAs reading the same
-// baselines run together and share them through L2.
+// Mixed-precision kernel (extract_pair_kernel).  The residual D - V_sky is formed
+// once per call (one streaming pass) and every source of the batch reads it.  A CTA
+// owns (source, part) and keeps a private copy of the facet in shared memory; the
+// part is an interleaved share of (block of baselines, channel group, time slice)
+// units.  A lane walks one baseline's time series for two adjacent channels.  A
+// baseline's uv track moves slowly (a few per cent of a cell per 60 s step at the
+// facet sizes of the method), so consecutive visibilities of one channel usually
+// fall in the same cell: the lane sums that run in registers and appends it to its
+// own ring in shared memory only when the cell changes; the rings are drained into
+// the facet with shared-memory atomics.  At the end the CTA stores its partial facet
+// with plain coalesced stores, and facet_reduce_kernel sums the parts of each cell
+// in FP64 in a fixed order (no global atomics).  Inside a CTA the drains land in
+// varying order, so repeated runs agree to FP32 rounding.  blockIdx.x runs over the
+// sources, so the CTAs reading the same baselines run together and share them
+// through L2.
 //
 // Shared-memory planes: sum Re x, sum Im x (FP32), count (int32), and the sum of
 // spec - spec_off (FP32, spec_off the band mean; the flush adds count * spec_off
@@ -152,48 +155,25 @@ __global__ void live_count_kernel(const float *__restrict__ extent, const int32_
     }
 }
 
-// Run rings: a lane whose run of equal cells ends appends the run to its own
-// ring of kRing entries in shared memory (slot-major, so a warp's appends are
-// consecutive 16-byte words); no warp vote per visibility.  Once per row the warp
-// checks whether any ring could overflow during the row (at most CG appends) and,
-// if so, every lane adds its own entries to the shared-memory facet.
-constexpr int kRing = 12;    // entries per lane
-
-// Add lane `tid`'s n_entries ring entries to the facet; entry = {cell | k << 12
-// (cell < 4096, channel k < 128), count, sum Re, sum Im}; the spectral sum of a
-// run is count * (spec_k - spec_off).
-__device__ __noinline__ void drain_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
-                                        int *scnt, float *ssp, const float *dsp_s)
+// Cell of both coordinates from one paired FMA.  With off = 320 + N/2, m = fl(u) fl(s/du) +
+// off, rounded once to the 2^-15 grid of [256, 512); a window coordinate t = u s / du in
+// [-N/2, N/2) lands in [320, 320 + N), whose integer part minus 320 is the cell, and
+// d = bits(m) - bits(320) holds it as d >> 15 with the fraction in the low 15 bits.  The
+// product's error is below 2^-23 |t| < 4e-6 for |t| <= 33 (the window and one cell
+// beyond), under half the grid step 2^-16, so away from an integer m rounds to the same
+// side as the exact value and floor(t) is the definition's.  `edge` marks m on an
+// integer (a zero fraction: t within ~2e-5 of a cell edge, including the window's own
+// edges at 320 and 320 + N), where the caller takes the FP64 decision; `in` marks both
+// coordinates inside the window.
+__device__ __forceinline__ void cell_index2(float uh, float vh, float sdu, float off, int N, int &cell, bool &edge,
+                                            bool &in)
 {
-    for (int j = 0; j < n_entries; ++j) {
-        const int4 e = ring[j * kThreads + tid];
-        const int cell = e.x & 0xfff;
-        atomicAdd(&sre[cell], __int_as_float(e.z));
-        atomicAdd(&sim[cell], __int_as_float(e.w));
-        atomicAdd(&scnt[cell], e.y);
-        atomicAdd(&ssp[cell], (float)e.y * dsp_s[e.x >> 12]);
-    }
-}
-
-// Cell index of both coordinates, with paired FP32 instructions: floor(t) for
-// |t| < 2^22 as round(t - 1/2), where the rounding to an integer is done by adding
-// 1.5 * 2^23 (the integer lands in the low mantissa bits) and d = y - round(y) is
-// exact.  Away from a cell edge round(t - 1/2) = floor(t).  With t = fl(u) *
-// fl(nu/c/du) formed by one FMA, |error of t| <= 3 * 2^-24 |t| < 6e-6 for
-// |t| <= 33 (every facet window here); `edge` flags values within 1e-5 of a
-// cell edge, where the caller takes the FP64 decision instead.
-__device__ __forceinline__ void cell_floor2(float uh, float vh, float sdu, int &iu, int &iv, bool &edge)
-{
-    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-    const f32x2 y = fma2(pk2(uh, vh), pk2(sdu, sdu), pk2(-0.5f, -0.5f));
-    const f32x2 m = add2(y, pk2(kMagic, kMagic));
-    const f32x2 d = add2(y, add2(m, pk2(-kMagic, -kMagic)) ^ 0x8000000080000000ull);
-    float du_, dv_, mu_, mv_;
-    up2(d, du_, dv_);
-    up2(m, mu_, mv_);
-    edge = fmaxf(fabsf(du_), fabsf(dv_)) > 0.5f - 1.0e-5f;
-    iu = __float_as_int(mu_) - 0x4B400000;
-    iv = __float_as_int(mv_) - 0x4B400000;
+    float mu, mv;
+    up2(fma2(pk2(uh, vh), pk2(sdu, sdu), pk2(off, off)), mu, mv);
+    const int du = __float_as_int(mu) - 0x43A00000, dv = __float_as_int(mv) - 0x43A00000;  // bits(320.0f)
+    edge = ((du & 0x7fff) == 0) | ((dv & 0x7fff) == 0);
+    in = max((unsigned)du, (unsigned)dv) < ((unsigned)N << 15);
+    cell = (dv >> 15) * N + (du >> 15);
 }
 
 // A 16-byte shared-memory store under a predicate: the append of a finished run
@@ -205,319 +185,50 @@ __device__ __forceinline__ void st_shared_v4_if(uint32_t addr, bool p, int a, in
                  :: "r"((int)p), "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-// kResid: `data` already holds D - V_sky (one load per visibility), `sky` is unused.
-// kGauss: the Gaussian source profile instead of the exponential one.
-template <int CG, bool kUniform, bool kSplit, bool kResid, bool kGauss>
-__global__ void __launch_bounds__(kThreads, CG >= 8 ? 2 : 3)
-extract_rl_kernel(const double *__restrict__ u, const double *__restrict__ v,
-                  const double *__restrict__ w, const float *__restrict__ us, int64_t n_rows,
-                  int32_t stride, int32_t n_parts, const ChanTable ch,
-                  const float2 *__restrict__ data, const float2 *__restrict__ sky,
-                  const SrcRow *__restrict__ table, int32_t N, const int32_t *__restrict__ perm,
-                  const int32_t *__restrict__ n_live, int32_t n_tslices, float *__restrict__ partial)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int NN = N * N;
-    (void)sky;
-    int4 *ring = reinterpret_cast<int4 *>(smraw);                       // [kRing][kThreads]
-    float *dsp_s = reinterpret_cast<float *>(ring + kRing * kThreads);  // [RLF_MAX_CHAN]
-    float *sre = dsp_s + RLF_MAX_CHAN;
-    float *sim = sre + NN;
-    int *scnt = reinterpret_cast<int *>(sim + NN);
-    float *ssp = reinterpret_cast<float *>(scnt + NN);
-    const int s = blockIdx.x;
-    const SrcRow S = table[s];
-    const int tid = threadIdx.x;
+// ---- extraction by channel-pair lanes -------------------------------------------------
+// A warp holds 32 / CL baselines x CL lanes; lane lc of a baseline walks two adjacent
+// channels, k0 + 2 lc and k0 + 2 lc + 1 (k0 = the first channel of the lane group; more
+// than 2 CL channels are split into groups), through time.  Each lane sums runs of equal
+// cells of its two channels in registers (paired FP32 instructions: two channels per
+// instruction for the phase, the rotation, the model and the run sums) and appends a
+// finished run to its own ring in shared memory.  The per-row work of a baseline
+// (float-pair phase argument, the group's phase f0 and step fd, the source's quadratic
+// form, u and v in FP32) is shared by its CL lanes: for a block of CL time steps lane lc
+// computes row t0 + lc and stores it in shared memory, and every lane then reads each
+// row of the block (a broadcast).  The next row's residual is loaded one row ahead.
+constexpr int kPairThreads = 384;
+constexpr int kPairWarps = kPairThreads / 32;
+constexpr int kPairRing = 6;     // ring entries per lane: a row appends at most two runs, checked every two rows
 
-    for (int i = tid; i < NN; i += kThreads) {
-        sre[i] = 0.0f;
-        sim[i] = 0.0f;
-        scnt[i] = 0;
-        ssp[i] = 0.0f;
-    }
-    const int C = ch.n;
-    const int n_groups = (C + CG - 1) / CG;
-    const int bpc = kThreads / n_groups;           // baselines per block
-    const int g = tid / bpc;
-    const int lane_b = tid % bpc;
-    const bool group_on = g < n_groups;
-    const int k0 = group_on ? g * CG : 0;
-    for (int k = tid; k < C; k += kThreads) dsp_s[k] = (float)(ch.spec[k] - ch.spec_off);
-    __syncthreads();
-    const int half = N / 2;
-    const double du = S.du;
-    constexpr float kTwoPi = 6.28318530717958647692f;
-    int cnt = 0;                                   // entries in this lane's ring
-    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
-
-    auto append = [&](int cell, int k, int n, float re, float im) {
-        ring[cnt * kThreads + tid] = make_int4(cell | (k << 12), n, __float_as_int(re), __float_as_int(im));
-        ++cnt;
-    };
-
-    if (S.flux > 0.0) {
-        // per-channel constants used for every visibility stay in registers
-        float sdu[CG], f2[CG], fspec[CG];
-#pragma unroll
-        for (int c = 0; c < CG; ++c) {
-            const int k = min(k0 + c, C - 1);
-            sdu[c] = (float)(ch.s[k] / du);
-            f2[c] = (float)(ch.s[k] * ch.s[k]);
-            fspec[c] = (float)(S.flux * ch.spec[k]);
-        }
-        const float q0 = (float)S.q[0], q1 = (float)S.q[1], q2 = (float)S.q[2];
-        float lh, ll, mh, ml, nh, nl;
-        split_double(S.l, lh, ll);
-        split_double(S.m, mh, ml);
-        split_double(S.n1, nh, nl);
-        const int64_t n_time = (n_rows + stride - 1) / stride;
-        // the source's baselines, in extent order, that can reach its window
-        const int n_base = n_live[s];
-        const int n_blocks = (n_base + bpc - 1) / bpc;
-        // the residual of a row's channel group is read as float4 pairs when the
-        // layout allows (even channel count, groups of >= 2 channels)
-        const bool vec = kResid && CG >= 2 && (C % 2 == 0);
-
-        int run_cell[CG], run_n[CG];
-        float run_re[CG], run_im[CG];
-        // every lane runs every iteration (the per-row ring check is a warp vote);
-        // lanes without a visibility carry cell = -1, whose runs are never appended
-        // work units: (block of baselines, slice of the time series); a few sources at a
-        // time also split each baseline's time series so that the grid fills the GPU
-        for (int wk = blockIdx.y; wk < n_blocks * n_tslices; wk += n_parts) {
-            const int blk = wk % n_blocks, ts = wk / n_blocks;
-            const int64_t t_begin = n_time * ts / n_tslices, t_end = n_time * (ts + 1) / n_tslices;
-            // lane position j in the order; bl the baseline (data rows bl + t * stride);
-            // the split baselines are stored in order, at column j
-            const int j = blk * bpc + lane_b;
-            const bool lane_on = group_on && j < n_base;
-            const int bl = lane_on ? (perm ? perm[j] : j) : 0;
-#pragma unroll
-            for (int c = 0; c < CG; ++c) {
-                run_cell[c] = -1;
-                run_n[c] = 0;
-                run_re[c] = run_im[c] = 0.0f;
-            }
-            // split baselines of the next row are fetched one iteration ahead
-            float nuh = 0, nul = 0, nvh = 0, nvl = 0, nwh = 0, nwl = 0;
-            if (kSplit && lane_on && t_begin < t_end && t_begin * stride + bl < n_rows) {
-                const int64_t c0 = t_begin * stride + j;
-                const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * c0];
-                const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
-                nuh = a4.x;
-                nul = a4.y;
-                nvh = a4.z;
-                nvl = a4.w;
-                nwh = b2.x;
-                nwl = b2.y;
-            }
-            for (int64_t t = t_begin; t < t_end; ++t) {
-                // a row appends at most CG runs: make room first
-                if (__any_sync(0xffffffffu, cnt > kRing - CG)) {
-                    drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
-                    cnt = 0;
-                }
-                const int64_t r = t * stride + bl;
-                const bool row_on = lane_on && r < n_rows;
-                float2 rv[CG];
-#pragma unroll
-                for (int c = 0; c < CG; ++c) rv[c] = make_float2(0.0f, 0.0f);
-                if (vec && row_on) {
-                    const float4 *src4 = reinterpret_cast<const float4 *>(data + (r * C + k0));
-#pragma unroll
-                    for (int j = 0; j < CG / 2; ++j) {
-                        if (k0 + 2 * j < C) {
-                            const float4 q4 = src4[j];
-                            rv[2 * j] = make_float2(q4.x, q4.y);
-                            rv[2 * j + 1] = make_float2(q4.z, q4.w);
-                        }
-                    }
-                }
-                float uh = 0, ul = 0, vh = 0, vl = 0, wh = 0, wl = 0;
-                double ph = 0.0;
-                if (kSplit) {
-                    uh = nuh;
-                    ul = nul;
-                    vh = nvh;
-                    vl = nvl;
-                    wh = nwh;
-                    wl = nwl;
-                    const int64_t rn = r + stride;
-                    const int64_t cn = (t + 1) * stride + j;
-                    if (lane_on && t + 1 < t_end && rn < n_rows) {
-                        const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * cn];
-                        const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * cn + 2];
-                        nuh = a4.x;
-                        nul = a4.y;
-                        nvh = a4.z;
-                        nvl = a4.w;
-                        nwh = b2.x;
-                        nwl = b2.y;
-                    }
-                } else if (row_on) {
-                    const double ud = u[r], vd = v[r], wd = w[r];
-                    ph = fma(wd, S.n1, fma(vd, S.m, ud * S.l));
-                    uh = (float)ud;
-                    vh = (float)vd;
-                }
-                const float uu = uh * uh, uv = uh * vh, vv = vh * vh;
-                const float q = fmaf(q2, vv, fmaf(q1, uv, q0 * uu));
-                float P = 0.0f, E = 0.0f;
-                if (kSplit) phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
-                // uniform channels: the phase of channel c is frac(f0 + c fd) cycles, each
-                // channel's sincos independent of the others (f0 + c fd in FP32 is within
-                // 2^-24 * CG cycles of the exact value)
-                float sn = 0.0f, cs = 1.0f;
-                float f0_keep = 0.0f, fd_keep = 0.0f;
-                if (kUniform) {
-                    float f0, fd = 0.0f;
-                    if (kSplit) {
-                        f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
-                        if (CG > 1) fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
-                    } else {
-                        const double tt = ph * ch.s[k0];
-                        f0 = (float)(tt - rint(tt));
-                        if (CG > 1) {
-                            const double td = ph * ch.ds;
-                            fd = (float)(td - rint(td));
-                        }
-                    }
-                    f0_keep = f0;
-                    fd_keep = fd;
-                }
-#pragma unroll
-                for (int c = 0; c < CG; ++c) {
-                    const int k = k0 + c;
-                    if (kUniform) {
-                        float fk = fmaf((float)c, fd_keep, f0_keep);
-                        fk -= rintf(fk);
-                        __sincosf(fk * kTwoPi, &sn, &cs);
-                    }
-                    if (!kUniform) {
-                        const int kk = min(k, C - 1);
-                        float f;
-                        if (kSplit) {
-                            f = frac_cycles(P, E, ch.s_hi[kk], ch.s_lo[kk]);
-                        } else {
-                            const double tt = ph * ch.s[kk];
-                            f = (float)(tt - rint(tt));
-                        }
-                        __sincosf(f * kTwoPi, &sn, &cs);
-                    }
-                    int cell = -1;
-                    if (row_on && k < C) {
-                        int iu, iv;
-                        bool edge;
-                        cell_floor2(uh, vh, sdu[c], iu, iv, edge);
-                        if (edge) {
-                            iu = (int)floor((u[r] * ch.s[k]) / du);
-                            iv = (int)floor((v[r] * ch.s[k]) / du);
-                        }
-                        iu += half;
-                        iv += half;
-                        if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
-                    }
-                    float rr, ri;
-                    if (vec) {
-                        rr = rv[c].x;
-                        ri = rv[c].y;
-                    } else {
-                        rr = ri = 0.0f;
-                        if (cell >= 0) {
-                            const float2 dv = data[r * C + k];
-                            rr = dv.x;
-                            ri = dv.y;
-                            if (!kResid) {
-                                const float2 sv = sky[r * C + k];
-                                rr -= sv.x;
-                                ri -= sv.y;
-                            }
-                        }
-                    }
-                    // (rr + i ri) exp(-2 pi i f) = (rr + i ri)(cs - i sn), plus the source's model
-                    float xr = fmaf(rr, cs, ri * sn);
-                    const float xi = fmaf(ri, cs, -rr * sn);
-                    xr = fmaf(fspec[c], brightness<kGauss>(q, f2[c]), xr);
-                    // a run ends when the cell changes; runs of cell -1 are dropped
-                    const bool change = cell != run_cell[c];
-                    {
-                        const bool app = change && run_cell[c] >= 0;
-                        st_shared_v4_if(ring_s + (uint32_t)(cnt * kThreads + tid) * 16u, app,
-                                        run_cell[c] | ((k0 + c) << 12), run_n[c], __float_as_int(run_re[c]),
-                                        __float_as_int(run_im[c]));
-                        cnt += app ? 1 : 0;
-                    }
-                    const float keep = change ? 0.0f : 1.0f;
-                    run_re[c] = fmaf(run_re[c], keep, xr);
-                    run_im[c] = fmaf(run_im[c], keep, xi);
-                    run_n[c] = change ? 1 : run_n[c] + 1;
-                    run_cell[c] = cell;
-
-                }
-            }
-            if (__any_sync(0xffffffffu, cnt > kRing - CG)) {
-                drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
-                cnt = 0;
-            }
-#pragma unroll
-            for (int c = 0; c < CG; ++c)
-                if (run_cell[c] >= 0) append(run_cell[c], k0 + c, run_n[c], run_re[c], run_im[c]);
-        }
-    }
-    // the rings' remainders
-    drain_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
-    __syncthreads();
-    // this CTA's partial facet: plain stores; planes Re, Im, count (int bits), spec - spec_off
-    float *o = partial + ((size_t)s * n_parts + blockIdx.y) * 4 * NN;
-    for (int i = tid; i < NN; i += kThreads) {
-        o[i] = sre[i];
-        o[NN + i] = sim[i];
-        o[2 * NN + i] = __int_as_float(scnt[i]);
-        o[3 * NN + i] = ssp[i];
-    }
-}
-
-// ---- lane-per-track extraction ------------------------------------------------------
-// A warp holds 32 / CL baselines x CL channels (CL = the channel count rounded up to a
-// power of two, at most 32; more channels are split into groups of 32): each lane walks
-// one (baseline, channel) track through time, sums runs of equal cells in registers and
-// appends a finished run to its own ring in shared memory.  The per-row work of a
-// baseline (float-pair phase argument, the channel group's phase f0 and step fd, the
-// source's quadratic form, u and v in FP32) is shared by its CL lanes: for a block of
-// CL time steps lane c computes row t0 + c and stores it in shared memory, then every
-// lane reads each row of the block (a broadcast).  One channel per thread keeps the
-// registers low enough for 512-thread CTAs, two per SM.
-constexpr int kLaneThreads = 512;
-constexpr int kLaneWarps = kLaneThreads / 32;
-constexpr int kLaneRing = 4;     // ring entries per lane: one append per row at most, drained every two rows
-constexpr int kRowWords = 8;     // per row: P, E (or the FP64 phase), f0, fd, q, u, v, valid
-
-__device__ __noinline__ void drain_lane_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
+// entry = {cell | k << 12, count (as a float), sum Re, sum Im}
+__device__ __noinline__ void drain_pair_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
                                              int *scnt, float *ssp, const float *dsp_s)
 {
     for (int j = 0; j < n_entries; ++j) {
-        const int4 e = ring[j * kLaneThreads + tid];
+        const int4 e = ring[j * kPairThreads + tid];
         const int cell = e.x & 0xfff;
+        const float n = __int_as_float(e.y);
         atomicAdd(&sre[cell], __int_as_float(e.z));
         atomicAdd(&sim[cell], __int_as_float(e.w));
-        atomicAdd(&scnt[cell], e.y);
-        atomicAdd(&ssp[cell], (float)e.y * dsp_s[e.x >> 12]);
+        atomicAdd(&scnt[cell], (int)n);
+        atomicAdd(&ssp[cell], n * dsp_s[e.x >> 12]);
     }
 }
 
-template <bool kUniform, bool kSplit, bool kResid, bool kGauss>
-__global__ void __launch_bounds__(kLaneThreads, 2)
-extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ w,
+template <int CL, bool kUniform, bool kSplit, bool kGauss>
+__global__ void __launch_bounds__(kPairThreads, 2)
+extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ w,
                     const float *__restrict__ us, int64_t n_rows, int32_t stride, int32_t n_parts, const ChanTable ch,
-                    const float2 *__restrict__ data, const float2 *__restrict__ sky, const SrcRow *__restrict__ table,
-                    int32_t N, const int32_t *__restrict__ perm, const int32_t *__restrict__ n_live,
-                    int32_t n_tslices, int32_t CL, float *__restrict__ partial)
+                    const float2 *__restrict__ resid, const SrcRow *__restrict__ table, int32_t N,
+                    const int32_t *__restrict__ perm, const int32_t *__restrict__ n_live, int32_t n_tslices,
+                    float *__restrict__ partial)
 {
+    constexpr int BW = 32 / CL;                // baselines per warp
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NN = N * N;
-    int4 *ring = reinterpret_cast<int4 *>(smraw);                                   // [kLaneRing][threads]
-    float4 *rows = reinterpret_cast<float4 *>(ring + kLaneRing * kLaneThreads);     // [warps][32][2]
-    float *dsp_s = reinterpret_cast<float *>(rows + kLaneWarps * 32 * 2);           // [RLF_MAX_CHAN]
+    int4 *ring = reinterpret_cast<int4 *>(smraw);                                   // [kPairRing][threads]
+    float4 *rows = reinterpret_cast<float4 *>(ring + kPairRing * kPairThreads);     // [warps][32][2]
+    float *dsp_s = reinterpret_cast<float *>(rows + kPairWarps * 32 * 2);           // [RLF_MAX_CHAN]
     float *sre = dsp_s + RLF_MAX_CHAN;
     float *sim = sre + NN;
     int *scnt = reinterpret_cast<int *>(sim + NN);
@@ -525,22 +236,24 @@ extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, 
     const int s = blockIdx.x;
     const SrcRow S = table[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < NN; i += kLaneThreads) {
+    for (int i = tid; i < NN; i += kPairThreads) {
         sre[i] = 0.0f;
         sim[i] = 0.0f;
         scnt[i] = 0;
         ssp[i] = 0.0f;
     }
     const int C = ch.n;
-    for (int k = tid; k < C; k += kLaneThreads) dsp_s[k] = (float)(ch.spec[k] - ch.spec_off);
+    for (int k = tid; k < C; k += kPairThreads) dsp_s[k] = (float)(ch.spec[k] - ch.spec_off);
     __syncthreads();
-    const int BW = 32 / CL;                    // baselines per warp
-    const int lb = lane / CL, lc = lane % CL;  // this lane's baseline in the warp, channel in the group
-    const int n_cg = (C + CL - 1) / CL;
-    const int bpc = kLaneWarps * BW;           // baselines per work unit
+    const int lb = lane / CL, lc = lane % CL;  // this lane's baseline in the warp, lane in the group
+    const int n_cg = (C + 2 * CL - 1) / (2 * CL);
+    const int bpc = kPairWarps * BW;           // baselines per work unit
+    const bool vec = (C & 1) == 0;             // channel pairs load as one 16-byte vector
     const double du = S.du;
     const int half = N / 2;
-    constexpr float kTwoPi = 6.28318530717958647692f;
+    const float coff = 320.0f + (float)half;
+    const f32x2 two_pi2 = pk2(6.28318530717958647692f, 6.28318530717958647692f);
+    const f32x2 one2 = pk2(1.0f, 1.0f);
     int cnt = 0;
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring) + (uint32_t)tid * 16u;
     float4 *my_rows = rows + (size_t)warp * 64;   // this warp's 32 rows x 2 float4
@@ -563,17 +276,29 @@ extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, 
             const int j = blk * bpc + warp * BW + lb;         // position in the baseline order
             const bool base_on = j < n_base;
             const int bl = base_on ? (perm ? perm[j] : j) : 0;
-            const int k0 = g * CL;                            // the group's first channel
-            const int k = k0 + lc;                            // this lane's channel
-            const bool lane_on = base_on && k < C;
-            const int kk = k < C ? k : C - 1;
-            // per-channel constants
-            const float sdu = (float)(ch.s[kk] / du);
-            const float f2 = (float)(ch.s[kk] * ch.s[kk]);
-            const float fspec = (float)(S.flux * ch.spec[kk]);
-            const float cpos = (float)lc;
-            int run_cell = -1, run_n = 0;
-            float run_re = 0.0f, run_im = 0.0f;
+            const int k0 = g * 2 * CL;                        // the group's first channel
+            const int ka = k0 + 2 * lc, kb = ka + 1;          // this lane's channels
+            const bool on_a = base_on && ka < C, on_b = base_on && kb < C;
+            const int kac = on_a ? ka : 0, kbc = on_b ? kb : 0;
+            // per-channel constants (pairs: channel a, channel b)
+            const float sdu_a = (float)(ch.s[kac] / du), sdu_b = (float)(ch.s[kbc] / du);
+            const f32x2 f2 = pk2((float)(ch.s[kac] * ch.s[kac]), (float)(ch.s[kbc] * ch.s[kbc]));
+            const f32x2 fspec = pk2((float)(S.flux * ch.spec[kac]), (float)(S.flux * ch.spec[kbc]));
+            const f32x2 cpos = pk2((float)(2 * lc), (float)(2 * lc + 1));
+            const int kbits_a = ka << 12, kbits_b = kb << 12;
+            int cell_a = -1, cell_b = -1;
+            f32x2 run_re = pk2(0.0f, 0.0f), run_im = pk2(0.0f, 0.0f), run_n = pk2(0.0f, 0.0f);
+            // split-baseline record of this lane's row of the next block, fetched a block ahead
+            float4 rec_a = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 rec_b = make_float2(0.f, 0.f);
+            auto fetch_record = [&](int64_t tt) {
+                if (kSplit && base_on && tt < t_end && tt * stride + bl < n_rows) {
+                    const int64_t c0 = tt * stride + j;
+                    rec_a = reinterpret_cast<const float4 *>(us)[2 * c0];
+                    rec_b = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
+                }
+            };
+            fetch_record(t_begin + lc);
             for (int64_t t0 = t_begin; t0 < t_end; t0 += CL) {
                 // rows t0 .. t0 + CL - 1 of this lane's baseline: lane lc prepares row t0 + lc
                 {
@@ -581,15 +306,16 @@ extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                     const int64_t r = tt * stride + bl;
                     const bool row_ok = base_on && tt < t_end && r < n_rows;
                     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 a4 = rec_a;
+                    const float2 b2 = rec_b;
+                    fetch_record(tt + CL);
                     if (row_ok) {
-                        float uh, ul, vh, vl, wh, wl;
+                        float uh, vh;
                         float P = 0.0f, E = 0.0f, f0 = 0.0f, fd = 0.0f;
                         if (kSplit) {
-                            const int64_t c0 = tt * stride + j;
-                            const float4 a4 = reinterpret_cast<const float4 *>(us)[2 * c0];
-                            const float2 b2 = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
-                            uh = a4.x; ul = a4.y; vh = a4.z; vl = a4.w; wh = b2.x; wl = b2.y;
-                            phase_metres(uh, ul, vh, vl, wh, wl, lh, ll, mh, ml, nh, nl, P, E);
+                            uh = a4.x;
+                            vh = a4.z;
+                            phase_metres(a4.x, a4.y, a4.z, a4.w, b2.x, b2.y, lh, ll, mh, ml, nh, nl, P, E);
                             if (kUniform) {
                                 f0 = frac_cycles(P, E, ch.s_hi[k0], ch.s_lo[k0]);
                                 fd = frac_cycles(P, E, ch.ds_hi, ch.ds_lo);
@@ -608,97 +334,151 @@ extract_lane_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                                 const double t2 = ph * ch.ds;
                                 fd = (float)(t2 - rint(t2));
                             }
-                            (void)ul; (void)vl; (void)wh; (void)wl;
                         }
                         const float q = fmaf(q2, vh * vh, fmaf(q1, uh * vh, q0 * (uh * uh)));
                         a = make_float4(P, E, f0, fd);
-                        b = make_float4(q, uh, vh, 1.0f);
+                        b = make_float4(uh, vh, q, 1.0f);
                     }
                     my_rows[2 * lane] = a;
                     my_rows[2 * lane + 1] = b;
                 }
                 __syncwarp();
                 const int nt = (int)min((int64_t)CL, t_end - t0);
-                for (int tau = 0; tau < nt; ++tau) {
-                    // two rows append at most two runs: make room every other row
-                    if ((tau & 1) == 0 && __any_sync(0xffffffffu, cnt > kLaneRing - 2)) {
-                        drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
-                        cnt = 0;
-                    }
-                    const float4 ra = my_rows[2 * (lb * CL + tau)];
-                    const float4 rb = my_rows[2 * (lb * CL + tau) + 1];
-                    const bool on = lane_on && rb.w != 0.0f;
-                    const int64_t r = (t0 + tau) * stride + bl;
-                    float rr = 0.0f, ri = 0.0f;
-                    if (on) {
-                        const float2 dv = data[r * C + k];
-                        rr = dv.x;
-                        ri = dv.y;
-                        if (!kResid) {
-                            const float2 sv = sky[r * C + k];
-                            rr -= sv.x;
-                            ri -= sv.y;
-                        }
-                    }
-                    float f;
-                    if (kUniform) {
-                        f = fmaf(cpos, ra.w, ra.z);
-                    } else if (kSplit) {
-                        f = frac_cycles(ra.x, ra.y, ch.s_hi[kk], ch.s_lo[kk]);
+                int64_t r = t0 * stride + bl;
+                const float2 *dp = resid + (r * C + kac);
+                const size_t vstep = (size_t)stride * C;
+                float4 dnext = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < n_rows) {
+                    if (vec) {
+                        dnext = *reinterpret_cast<const float4 *>(dp);
                     } else {
-                        const double ph = __hiloint2double(__float_as_int(ra.x), __float_as_int(ra.y));
-                        const double tt = ph * ch.s[kk];
-                        f = (float)(tt - rint(tt));
+                        const float2 x = dp[0];
+                        const float2 y = on_b ? dp[1] : make_float2(0.f, 0.f);
+                        dnext = make_float4(x.x, x.y, y.x, y.y);
                     }
-                    f -= rintf(f);
-                    float sn, cs;
-                    __sincosf(f * kTwoPi, &sn, &cs);
-                    int cell = -1;
-                    if (on) {
-                        int iu, iv;
-                        bool edge;
-                        cell_floor2(rb.y, rb.z, sdu, iu, iv, edge);
-                        if (edge) {
-                            iu = (int)floor((u[r] * ch.s[k]) / du);
-                            iv = (int)floor((v[r] * ch.s[k]) / du);
+                }
+#pragma unroll 2
+                for (int tau = 0; tau < CL; ++tau) {
+                    if (tau < nt) {
+                        // two rows append at most four runs: make room every other row
+                        if ((tau & 1) == 0 && __any_sync(0xffffffffu, cnt > kPairRing - 4)) {
+                            drain_pair_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+                            cnt = 0;
                         }
-                        iu += half;
-                        iv += half;
-                        if ((unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N) cell = iv * N + iu;
+                        const float4 d = dnext;
+                        {
+                            // the next row of the block, or this row again past its end (always in bounds)
+                            const float2 *np = (tau + 1 < nt && r + stride < n_rows) ? dp + vstep : dp;
+                            if (vec) {
+                                dnext = *reinterpret_cast<const float4 *>(np);
+                            } else {
+                                const float2 x = np[0];
+                                const float2 y = on_b ? np[1] : make_float2(0.f, 0.f);
+                                dnext = make_float4(x.x, x.y, y.x, y.y);
+                            }
+                        }
+                        const float4 ra = my_rows[2 * (lb * CL + tau)];
+                        const float4 rb = my_rows[2 * (lb * CL + tau) + 1];
+                        const bool row_on = rb.w != 0.0f;
+                        // phases of the two channels, in cycles, reduced to [-1/2, 1/2]
+                        float fa, fb;
+                        if (kUniform) {
+                            up2(fma2(cpos, pk2(ra.w, ra.w), pk2(ra.z, ra.z)), fa, fb);
+                        } else if (kSplit) {
+                            fa = frac_cycles(ra.x, ra.y, ch.s_hi[kac], ch.s_lo[kac]);
+                            fb = frac_cycles(ra.x, ra.y, ch.s_hi[kbc], ch.s_lo[kbc]);
+                        } else {
+                            const double ph = __hiloint2double(__float_as_int(ra.x), __float_as_int(ra.y));
+                            const double ta = ph * ch.s[kac], tb = ph * ch.s[kbc];
+                            fa = (float)(ta - rint(ta));
+                            fb = (float)(tb - rint(tb));
+                        }
+                        float xa, xb;
+                        up2(mul2(add2(pk2(fa, fb), pk2(-rintf(fa), -rintf(fb))), two_pi2), xa, xb);
+                        float sa, ca, sb, cb;
+                        __sincosf(xa, &sa, &ca);
+                        __sincosf(xb, &sb, &cb);
+                        // cells of the two channels (FP64 decision within the FP32 error of an edge)
+                        int ia, ib;
+                        bool ea, eb, ina, inb;
+                        cell_index2(rb.x, rb.y, sdu_a, coff, N, ia, ea, ina);
+                        cell_index2(rb.x, rb.y, sdu_b, coff, N, ib, eb, inb);
+                        // rows past the baseline list or the time slice hold u = v = 0: not edges
+                        ea = ea && row_on && on_a;
+                        eb = eb && row_on && on_b;
+                        if (ea || eb) {
+                            const double ku = u[r], kv = v[r];
+                            if (ea) {
+                                const int iu = (int)floor((ku * ch.s[kac]) / du) + half;
+                                const int iv = (int)floor((kv * ch.s[kac]) / du) + half;
+                                ina = (unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N;
+                                ia = iv * N + iu;
+                            }
+                            if (eb) {
+                                const int iu = (int)floor((ku * ch.s[kbc]) / du) + half;
+                                const int iv = (int)floor((kv * ch.s[kbc]) / du) + half;
+                                inb = (unsigned)iu < (unsigned)N && (unsigned)iv < (unsigned)N;
+                                ib = iv * N + iu;
+                            }
+                        }
+                        ia = (row_on && on_a && ina) ? ia : -1;
+                        ib = (row_on && on_b && inb) ? ib : -1;
+                        // (rr + i ri) exp(-2 pi i f) plus the source's model S s M, two channels
+                        const f32x2 rr = pk2(d.x, d.z), ri = pk2(d.y, d.w);
+                        const f32x2 cs = pk2(ca, cb), sn = pk2(sa, sb), nsn = pk2(-sa, -sb);
+                        f32x2 xr = fma2(rr, cs, mul2(ri, sn));
+                        const f32x2 xi = fma2(ri, cs, mul2(rr, nsn));
+                        xr = fma2(fspec, brightness2<kGauss>(pk2(rb.z, rb.z), f2), xr);
+                        // runs: a run ends when the cell changes; runs of cell -1 are dropped
+                        const bool cha = ia != cell_a, chb = ib != cell_b;
+                        float re_a, re_b, im_a, im_b, n_a, n_b;
+                        up2(run_re, re_a, re_b);
+                        up2(run_im, im_a, im_b);
+                        up2(run_n, n_a, n_b);
+                        const bool app_a = cha && cell_a >= 0, app_b = chb && cell_b >= 0;
+                        st_shared_v4_if(ring_s + (uint32_t)cnt * (kPairThreads * 16u), app_a, cell_a | kbits_a,
+                                        __float_as_int(n_a), __float_as_int(re_a), __float_as_int(im_a));
+                        cnt += app_a ? 1 : 0;
+                        st_shared_v4_if(ring_s + (uint32_t)cnt * (kPairThreads * 16u), app_b, cell_b | kbits_b,
+                                        __float_as_int(n_b), __float_as_int(re_b), __float_as_int(im_b));
+                        cnt += app_b ? 1 : 0;
+                        const f32x2 keep = pk2(cha ? 0.0f : 1.0f, chb ? 0.0f : 1.0f);
+                        run_re = fma2(run_re, keep, xr);
+                        run_im = fma2(run_im, keep, xi);
+                        run_n = fma2(run_n, keep, one2);
+                        cell_a = ia;
+                        cell_b = ib;
+                        r += stride;
+                        dp += vstep;
                     }
-                    // (rr + i ri) exp(-2 pi i f) plus the source's model S s M
-                    float xr = fmaf(rr, cs, ri * sn);
-                    const float xi = fmaf(ri, cs, -rr * sn);
-                    xr = fmaf(fspec, brightness<kGauss>(rb.x, f2), xr);
-                    const bool change = cell != run_cell;
-                    const bool app = change && run_cell >= 0;
-                    st_shared_v4_if(ring_s + (uint32_t)cnt * (kLaneThreads * 16u), app, run_cell | (k << 12), run_n,
-                                    __float_as_int(run_re), __float_as_int(run_im));
-                    cnt += app ? 1 : 0;
-                    const float keep = change ? 0.0f : 1.0f;
-                    run_re = fmaf(run_re, keep, xr);
-                    run_im = fmaf(run_im, keep, xi);
-                    run_n = change ? 1 : run_n + 1;
-                    run_cell = cell;
                 }
                 __syncwarp();
             }
-            // the unit's last run
-            if (__any_sync(0xffffffffu, cnt > kLaneRing - 1)) {
-                drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+            // the unit's last runs
+            if (__any_sync(0xffffffffu, cnt > kPairRing - 2)) {
+                drain_pair_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
                 cnt = 0;
             }
-            if (run_cell >= 0) {
-                ring[cnt * kLaneThreads + tid] = make_int4(run_cell | (k << 12), run_n, __float_as_int(run_re),
-                                                           __float_as_int(run_im));
+            float re_a, re_b, im_a, im_b, n_a, n_b;
+            up2(run_re, re_a, re_b);
+            up2(run_im, im_a, im_b);
+            up2(run_n, n_a, n_b);
+            if (cell_a >= 0) {
+                ring[cnt * kPairThreads + tid] = make_int4(cell_a | kbits_a, __float_as_int(n_a), __float_as_int(re_a),
+                                                           __float_as_int(im_a));
+                ++cnt;
+            }
+            if (cell_b >= 0) {
+                ring[cnt * kPairThreads + tid] = make_int4(cell_b | kbits_b, __float_as_int(n_b), __float_as_int(re_b),
+                                                           __float_as_int(im_b));
                 ++cnt;
             }
         }
     }
-    drain_lane_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
+    drain_pair_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
     __syncthreads();
     float *o = partial + ((size_t)s * n_parts + blockIdx.y) * 4 * NN;
-    for (int i = tid; i < NN; i += kLaneThreads) {
+    for (int i = tid; i < NN; i += kPairThreads) {
         o[i] = sre[i];
         o[NN + i] = sim[i];
         o[2 * NN + i] = __int_as_float(scnt[i]);
@@ -827,115 +607,54 @@ struct Order {
     const int32_t *n_live;
 };
 
-template <int CG, bool kSplit>
-cudaError_t launch_rl(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                      const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
-                      float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
-{
-    const size_t smem = (size_t)kRing * kThreads * sizeof(int4) + RLF_MAX_CHAN * sizeof(float) +
-                        4 * (size_t)N * N * sizeof(float);
-    const bool resid = sky == nullptr;
-    decltype(&extract_rl_kernel<CG, true, kSplit, true, false>) kern;
-    if (ch.profile == RLF_PROFILE_GAUSSIAN)
-        kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true, true> : extract_rl_kernel<CG, true, kSplit, false, true>)
-                          : (resid ? extract_rl_kernel<CG, false, kSplit, true, true> : extract_rl_kernel<CG, false, kSplit, false, true>);
-    else
-        kern = ch.uniform ? (resid ? extract_rl_kernel<CG, true, kSplit, true, false> : extract_rl_kernel<CG, true, kSplit, false, false>)
-                          : (resid ? extract_rl_kernel<CG, false, kSplit, true, false> : extract_rl_kernel<CG, false, kSplit, false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    // rows are walked as [time][stride]; stride = baselines per time step when known
-    const int32_t stride = uvw.n_baselines > 0 ? uvw.n_baselines : 1024;
-    const int n_groups = (ch.n + CG - 1) / CG;
-    const int bpc = kThreads / n_groups;
-    const int64_t n_blocks = (stride + bpc - 1) / bpc;
-    const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
-    const int NN = N * N;
-    const int64_t slots = (int64_t)sm_count_x() * per_sm;
-    // sources are handled in batches whose partial facets fit the workspace
-    for (int32_t first = 0; first < count; first += max_partials) {
-        const int32_t cnt = count - first < max_partials ? count - first : max_partials;
-        // parts per source: about `waves` waves of CTAs; beyond one part per baseline block
-        // (few sources) the time series are split too, into slices of at least 16 steps
-        int64_t parts = ((int64_t)waves * slots + cnt - 1) / cnt;
-        int64_t slices = 1;
-        if (parts > n_blocks) {
-            slices = (parts + n_blocks - 1) / n_blocks;
-            const int64_t max_slices = n_time / 16 > 1 ? n_time / 16 : 1;
-            if (slices > max_slices) slices = max_slices;
-            if (slices > 32) slices = 32;
-        }
-        if (parts > n_blocks * slices) parts = n_blocks * slices;
-        if (parts > max_partials / cnt) parts = max_partials / cnt;
-        if (parts < 1) parts = 1;
-        dim3 grid(cnt, (unsigned)parts);
-        kern<<<grid, kThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
-                                           reinterpret_cast<const float2 *>(data),
-                                           reinterpret_cast<const float2 *>(sky), table + first, N, ord.perm,
-                                           ord.n_live + first, (int32_t)slices, partial);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        dim3 rgrid((NN + kReduceCells - 1) / kReduceCells, cnt);
-        facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
-                                                        facets + (size_t)first * 4 * NN);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-template <bool kSplit>
-cudaError_t launch_rl_cg(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                         const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
-                         float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
-{
-    if (ch.n == 1) return launch_rl<1, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
-    if (ch.n == 2) return launch_rl<2, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
-    if (ch.n <= 4) return launch_rl<4, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
-    return launch_rl<8, kSplit>(uvw, ch, data, sky, table, count, N, us, ord, partial, max_partials, facets, waves, st);
-}
-
-// channel lanes of the lane-per-track kernel: the channel count rounded up to a power of
-// two, at most 32
-int lane_cl(int n_chan)
+// lanes per baseline of the channel-pair kernel: half the channel count rounded up to a
+// power of two, at most 32 (more channels form groups of 64)
+int pair_cl(int n_chan)
 {
     int cl = 1;
-    while (cl < n_chan && cl < 32) cl *= 2;
+    while (2 * cl < n_chan && cl < 32) cl *= 2;
     return cl;
 }
 
-size_t lane_smem(int N)
+size_t pair_smem(int N)
 {
-    return (size_t)kLaneRing * kLaneThreads * sizeof(int4) + (size_t)kLaneWarps * 64 * sizeof(float4) +
+    return (size_t)kPairRing * kPairThreads * sizeof(int4) + (size_t)kPairWarps * 64 * sizeof(float4) +
            RLF_MAX_CHAN * sizeof(float) + 4 * (size_t)N * N * sizeof(float);
 }
 
-template <bool kSplit>
-cudaError_t launch_lane(const rlf_uvw &uvw, const ChanTable &ch, const float *data, const float *sky,
-                        const SrcRow *table, int32_t count, int32_t N, const float *us, const Order &ord,
-                        float *partial, int32_t max_partials, double *facets, int waves, cudaStream_t st)
+template <int CL, bool kSplit>
+auto pick_pair_kernel(const ChanTable &ch)
 {
-    const size_t smem = lane_smem(N);
-    const bool resid = sky == nullptr;
-    decltype(&extract_lane_kernel<true, kSplit, true, false>) kern;
     if (ch.profile == RLF_PROFILE_GAUSSIAN)
-        kern = ch.uniform ? (resid ? extract_lane_kernel<true, kSplit, true, true> : extract_lane_kernel<true, kSplit, false, true>)
-                          : (resid ? extract_lane_kernel<false, kSplit, true, true> : extract_lane_kernel<false, kSplit, false, true>);
-    else
-        kern = ch.uniform ? (resid ? extract_lane_kernel<true, kSplit, true, false> : extract_lane_kernel<true, kSplit, false, false>)
-                          : (resid ? extract_lane_kernel<false, kSplit, true, false> : extract_lane_kernel<false, kSplit, false, false>);
+        return ch.uniform ? extract_pair_kernel<CL, true, kSplit, true> : extract_pair_kernel<CL, false, kSplit, true>;
+    return ch.uniform ? extract_pair_kernel<CL, true, kSplit, false> : extract_pair_kernel<CL, false, kSplit, false>;
+}
+
+template <bool kSplit>
+cudaError_t launch_pair(const rlf_uvw &uvw, const ChanTable &ch, const float *resid, const SrcRow *table,
+                        int32_t count, int32_t N, const float *us, const Order &ord, float *partial,
+                        int32_t max_partials, double *facets, int waves, cudaStream_t st)
+{
+    const size_t smem = pair_smem(N);
+    const int CL = pair_cl(ch.n);
+    decltype(&extract_pair_kernel<1, true, kSplit, false>) kern;
+    switch (CL) {
+    case 1: kern = pick_pair_kernel<1, kSplit>(ch); break;
+    case 2: kern = pick_pair_kernel<2, kSplit>(ch); break;
+    case 4: kern = pick_pair_kernel<4, kSplit>(ch); break;
+    case 8: kern = pick_pair_kernel<8, kSplit>(ch); break;
+    case 16: kern = pick_pair_kernel<16, kSplit>(ch); break;
+    default: kern = pick_pair_kernel<32, kSplit>(ch); break;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLaneThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int32_t stride = uvw.n_baselines > 0 ? uvw.n_baselines : 1024;
-    const int CL = lane_cl(ch.n);
-    const int n_cg = (ch.n + CL - 1) / CL;
-    const int bpc = kLaneWarps * (32 / CL);
+    const int n_cg = (ch.n + 2 * CL - 1) / (2 * CL);
+    const int bpc = kPairWarps * (32 / CL);
     const int64_t n_blocks = ((int64_t)stride + bpc - 1) / bpc * n_cg;   // (baseline block, channel group) units
     const int64_t n_time = (uvw.n_rows + stride - 1) / stride;
     const int NN = N * N;
@@ -956,10 +675,9 @@ cudaError_t launch_lane(const rlf_uvw &uvw, const ChanTable &ch, const float *da
         if (parts > max_partials / cnt) parts = max_partials / cnt;
         if (parts < 1) parts = 1;
         dim3 grid(cnt, (unsigned)parts);
-        kern<<<grid, kLaneThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
-                                               reinterpret_cast<const float2 *>(data),
-                                               reinterpret_cast<const float2 *>(sky), table + first, N, ord.perm,
-                                               ord.n_live + first, (int32_t)slices, CL, partial);
+        kern<<<grid, kPairThreads, smem, st>>>(uvw.u, uvw.v, uvw.w, us, uvw.n_rows, stride, (int32_t)parts, ch,
+                                               reinterpret_cast<const float2 *>(resid), table + first, N, ord.perm,
+                                               ord.n_live + first, (int32_t)slices, partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         dim3 rgrid((NN + kReduceCells - 1) / kReduceCells, cnt);
         facet_reduce_kernel<<<rgrid, kThreads, 0, st>>>(partial, (int32_t)parts, NN, ch.spec_off,
@@ -1008,6 +726,32 @@ int64_t grid_for(int64_t n, int64_t cap)
 }
 
 }  // namespace
+
+// out = a - b over n_complex complex values of any count (float4 pairs, then the odd one)
+__global__ void difference_tail_kernel(const float2 *__restrict__ a, const float2 *__restrict__ b, int64_t i,
+                                       float2 *__restrict__ out)
+{
+    const float2 x = a[i], y = b[i];
+    out[i] = make_float2(x.x - y.x, x.y - y.y);
+}
+
+cudaError_t launch_difference_any(const float *a, const float *b, int64_t n_complex, float *out, cudaStream_t st)
+{
+    const int64_t n4 = n_complex / 2;
+    if (n4 > 0) {
+        residual_kernel<<<(int)grid_for(n4, (int64_t)sm_count_x() * 16), kThreads, 0, st>>>(
+            reinterpret_cast<const float4 *>(a), reinterpret_cast<const float4 *>(b), n4,
+            reinterpret_cast<float4 *>(out));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_complex % 2 != 0) {
+        difference_tail_kernel<<<1, 1, 0, st>>>(reinterpret_cast<const float2 *>(a), reinterpret_cast<const float2 *>(b),
+                                                n_complex - 1, reinterpret_cast<float2 *>(out));
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_difference(const float *a, const float *b, int64_t n_complex, float *out, cudaStream_t st)
 {
@@ -1067,18 +811,13 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
         if (e != cudaSuccess) return e;
         return launch_fp64(uvw, ch, data, sky, table, count, p.facet_n, facets, st);
     }
-    // several sources read every visibility: form D - V_sky once (one streaming pass)
-    if (sky && ws.resid && count >= 3) {
+    // the extraction reads R = D - V_sky: formed here in one streaming pass (every source
+    // of the batch reads it), unless the caller passes the residual itself (sky null)
+    if (sky) {
+        if (!ws.resid) return cudaErrorInvalidValue;
         const int64_t n2 = uvw.n_rows * uvw.n_chan;   // complex values
-        if (n2 % 2 == 0) {
-            const int64_t n4 = n2 / 2;
-            residual_kernel<<<(int)grid_for(n4, (int64_t)sm_count_x() * 16), kThreads, 0, st>>>(
-                reinterpret_cast<const float4 *>(data), reinterpret_cast<const float4 *>(sky), n4,
-                reinterpret_cast<float4 *>(ws.resid));
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            data = ws.resid;
-            sky = nullptr;
-        }
+        if ((e = launch_difference_any(data, sky, n2, ws.resid, st)) != cudaSuccess) return e;
+        data = ws.resid;
     }
     // per source, how far along the baseline order its window can be reached
     const int32_t stride = row_stride(uvw);
@@ -1090,9 +829,9 @@ cudaError_t launch_extract(const rlf_uvw &uvw, const ChanTable &ch, const float 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int waves = p.tune_extract_waves > 0 ? p.tune_extract_waves : 2;
     if (p.precision == RLF_PREC_MIXED)
-        return launch_lane<false>(uvw, ch, data, sky, table, count, p.facet_n, nullptr, ord, ws.partial, ws.n_partials,
+        return launch_pair<false>(uvw, ch, data, table, count, p.facet_n, nullptr, ord, ws.partial, ws.n_partials,
                                   facets, waves, st);
-    return launch_lane<true>(uvw, ch, data, sky, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, ws.n_partials,
+    return launch_pair<true>(uvw, ch, data, table, count, p.facet_n, ws.uvw_split, ord, ws.partial, ws.n_partials,
                              facets, waves, st);
 }
 
