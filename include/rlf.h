@@ -108,15 +108,16 @@ enum {
 /* workspace users for rlf_workspace_size */
 enum { RLF_WS_SKY = 0, RLF_WS_EXTRACT = 1, RLF_WS_FIT = 2, RLF_WS_RUN = 3 };
 
-/* Largest channel count and facet side handled by one call. */
+/* Largest channel count, row count and facet side handled by one call. */
 #define RLF_MAX_CHAN 128
+#define RLF_MAX_ROWS 2147483647
 #define RLF_MAX_FACET_N 64
 /* Largest position-offset grid side (rlf_params.n_pos). */
 #define RLF_MAX_POS 5
 
 /* Observation: baselines in metres (Sec. 2.2: (u, v, w) with w towards the phase centre). */
 typedef struct {
-    int64_t n_rows;          /* number of (baseline, time) rows, > 0 */
+    int64_t n_rows;          /* number of (baseline, time) rows, 1 .. RLF_MAX_ROWS */
     int32_t n_chan;          /* channels, 1 .. RLF_MAX_CHAN */
     int32_t n_baselines;     /* rows are time-major with this many baselines per time step
                                 (the Measurement Set order); 0 if unknown.  Only speed

@@ -49,7 +49,7 @@ rlf_status check_uvw(const rlf_uvw *uvw)
 {
     if (!uvw || !uvw->u || !uvw->v || !uvw->w || !uvw->freq_hz) return RLF_EINVAL;
     if (uvw->n_rows <= 0 || uvw->n_chan <= 0 || uvw->n_baselines < 0) return RLF_EINVAL;
-    if (uvw->n_chan > RLF_MAX_CHAN) return RLF_EUNSUPPORTED;
+    if (uvw->n_chan > RLF_MAX_CHAN || uvw->n_rows > RLF_MAX_ROWS) return RLF_EUNSUPPORTED;
     for (int k = 0; k < uvw->n_chan; ++k) {
         if (!(uvw->freq_hz[k] > 0 && std::isfinite(uvw->freq_hz[k]))) return RLF_EINVAL;
         if (k > 0 && !(uvw->freq_hz[k] > uvw->freq_hz[k - 1])) return RLF_EINVAL;

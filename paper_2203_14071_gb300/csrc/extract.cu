@@ -196,9 +196,9 @@ __device__ __forceinline__ void st_shared_v4_if(uint32_t addr, bool p, int a, in
 // form, u and v in FP32) is shared by its CL lanes: for a block of CL time steps lane lc
 // computes row t0 + lc and stores it in shared memory, and every lane then reads each
 // row of the block (a broadcast).  The next row's residual is loaded one row ahead.
-constexpr int kPairThreads = 384;
+constexpr int kPairThreads = 512;
 constexpr int kPairWarps = kPairThreads / 32;
-constexpr int kPairRing = 6;     // ring entries per lane: a row appends at most two runs, checked every two rows
+constexpr int kPairRing = 4;     // ring entries per lane: a row appends at most two runs, checked every row
 
 // entry = {cell | k << 12, count (as a float), sum Re, sum Im}
 __device__ __noinline__ void drain_pair_ring(const int4 *ring, int n_entries, int tid, float *sre, float *sim,
@@ -298,7 +298,6 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                     rec_b = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
                 }
             };
-            fetch_record(t_begin + lc);
             for (int64_t t0 = t_begin; t0 < t_end; t0 += CL) {
                 // rows t0 .. t0 + CL - 1 of this lane's baseline: lane lc prepares row t0 + lc
                 {
@@ -306,9 +305,9 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                     const int64_t r = tt * stride + bl;
                     const bool row_ok = base_on && tt < t_end && r < n_rows;
                     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    fetch_record(tt);
                     const float4 a4 = rec_a;
                     const float2 b2 = rec_b;
-                    fetch_record(tt + CL);
                     if (row_ok) {
                         float uh, vh;
                         float P = 0.0f, E = 0.0f, f0 = 0.0f, fd = 0.0f;
@@ -344,11 +343,12 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                 }
                 __syncwarp();
                 const int nt = (int)min((int64_t)CL, t_end - t0);
-                int64_t r = t0 * stride + bl;
-                const float2 *dp = resid + (r * C + kac);
-                const size_t vstep = (size_t)stride * C;
+                int r = (int)(t0 * stride + bl);
+                const int nr32 = (int)n_rows;
+                const float2 *dp = resid + ((int64_t)r * C + kac);
+                const int vstep = stride * C;
                 float4 dnext = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < n_rows) {
+                if (r < nr32) {
                     if (vec) {
                         dnext = *reinterpret_cast<const float4 *>(dp);
                     } else {
@@ -360,15 +360,15 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
 #pragma unroll 2
                 for (int tau = 0; tau < CL; ++tau) {
                     if (tau < nt) {
-                        // two rows append at most four runs: make room every other row
-                        if ((tau & 1) == 0 && __any_sync(0xffffffffu, cnt > kPairRing - 4)) {
+                        // a row appends at most two runs: make room first
+                        if (__any_sync(0xffffffffu, cnt > kPairRing - 2)) {
                             drain_pair_ring(ring, cnt, tid, sre, sim, scnt, ssp, dsp_s);
                             cnt = 0;
                         }
                         const float4 d = dnext;
                         {
                             // the next row of the block, or this row again past its end (always in bounds)
-                            const float2 *np = (tau + 1 < nt && r + stride < n_rows) ? dp + vstep : dp;
+                            const float2 *np = (tau + 1 < nt && r + stride < nr32) ? dp + vstep : dp;
                             if (vec) {
                                 dnext = *reinterpret_cast<const float4 *>(np);
                             } else {
