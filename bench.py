@@ -681,7 +681,9 @@ OPS = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # per (kernel, workload), kept in the profile summaries; valid while the kernel's source files
 # hash to the recorded value, otherwise the bench reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("extract", "batched"): (("csrc/extract.cu", "csrc/rlf_internal.cuh"), "d9a2fee7d9d3e5f4", 17.07e9 + 103.74e6),
+}
 
 
 def source_hash(files):
