@@ -88,9 +88,12 @@ def test_roofline_arithmetic_and_traffic_validity():
     assert r["achieved"] == pytest.approx(1.0e10 / 2.0e-3 / 1e9)
     r5 = bench.roofline_one("fit", 2.0, 1.0e10, 0.0, peaks, fp32=30.0)
     assert r5["limiting_unit"] == "fp32" and r5["frac"] == pytest.approx(30.0 * 1.0e10 / 4.0e13 / 2.0e-3)
-    for name, (files, digest, nbytes) in bench.TRAFFIC.items():
-        assert bench.traffic_of(name) in (None, nbytes)
+    for (name, workload), (files, digest, nbytes) in bench.TRAFFIC.items():
+        assert bench.traffic_of(name, workload) in (None, nbytes)
+        assert bench.traffic_of(name, "another workload") is None
         if bench.source_hash(files) == digest:
-            assert bench.traffic_of(name) == nbytes
-    if bench.traffic_of("fit") is not None and bench.hbm_peak_gbs():
-        assert r["dram_gb_s"] == pytest.approx(bench.traffic_of("fit") / 2.0e-3 / 1e9)
+            assert bench.traffic_of(name, workload) == nbytes
+            rw = bench.roofline_one(name, 2.0, 1.0e10, 0.0, peaks, workload=workload)
+            assert rw["traffic"] == nbytes
+            if bench.hbm_peak_gbs():
+                assert rw["dram_gb_s"] == pytest.approx(nbytes / 2.0e-3 / 1e9)
