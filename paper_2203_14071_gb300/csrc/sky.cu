@@ -96,7 +96,8 @@ struct SkySrc {
     float flux, q0, q1, q2, qn0, qn1, qn2, pad;
 };
 
-// Mixed precision sky model / update.  CG channels per thread.  kSplit selects
+// Mixed precision sky model / update.  CG channels per thread (up to 16: the per-(row,
+// source) phase work, about 40 instructions in split mode, is shared by CG terms).  kSplit selects
 // the float-pair phase argument instead of the FP64 one; kRec (split only) reads the
 // call's split-baseline records instead of splitting u, v, w per row.
 template <int CG, bool kUpdate, bool kUniform, bool kSplit, bool kGauss, bool kRec = false>
@@ -435,7 +436,8 @@ void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *tabl
     if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
     else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
     else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
-    else launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    else if (ch.n <= 8) launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    else launch_mixed<16, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
 }
 
 }  // namespace
