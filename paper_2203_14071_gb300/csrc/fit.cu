@@ -1122,80 +1122,164 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
         __syncthreads();
         const int np = s_np;
         const T *cu = cells + (size_t)s * NN;
-        for (int base = 0; base < np * na; base += kAT) {
-            const int pr = base + threadIdx.x;
-            const bool on = pr < np * na;
-            const int i = on ? pr / na : 0, k = on ? pr % na : 0;
-            const double e1 = e1s[i], e2 = e2s[i];
-            const double det = 1.0 - e1 * e1 - e2 * e2;
-            const double id2 = 1.0 / (det * det);
-            const T p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
-            const T p12 = (T)(4.0 * e2 * id2);
-            const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
-            const double alr = alph[k] * kArcsec * S.du;
-            const T ca = (T)(4.0 * kPi * kPi * alr * alr);
-            float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
-            double da = 0.0, db[NJ];
+        if constexpr (NJ == 1 && mixed) {
+            // four scalelength nodes per thread, as the grid's tiles: the quadratic form of a
+            // cell once for them, two nodes per paired FP32 instruction
+            constexpr int kAG = 4;
+            const int n_ag = (na + kAG - 1) / kAG;
+            const bool split = gc.split != 0;
+            const f32x2 one2 = pk2(1.0f, 1.0f);
+            for (int base = 0; base < np * n_ag; base += kAT) {
+                const int it = base + threadIdx.x;
+                const bool on = it < np * n_ag;
+                const int i = on ? it / n_ag : 0, g = on ? it % n_ag : 0;
+                const double e1 = e1s[i], e2 = e2s[i];
+                const double det = 1.0 - e1 * e1 - e2 * e2;
+                const double id2 = 1.0 / (det * det);
+                const float p11 = (float)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+                const float p12 = (float)(4.0 * e2 * id2);
+                const float p22 = (float)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+                float cak[kAG];
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                bh[j] = bl[j] = 0.0f;
-                db[j] = 0.0;
-            }
-            for (int c0 = 0; c0 < nc; c0 += kTA) {
-                const int nt = min(kTA, nc - c0);
-                __syncthreads();
-                for (int j = threadIdx.x; j < nt; j += kAT) {
-#pragma unroll
-                    for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
+                for (int j = 0; j < kAG; ++j) {
+                    const int k = g * kAG + j;
+                    const double alr = (k < na ? alph[k] : 0.0) * kArcsec * S.du;
+                    cak[j] = (float)(4.0 * kPi * kPi * alr * alr) * (kGauss ? -0.25f : 1.0f);
                 }
-                if constexpr (NJ > 1) {
-                    const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
-                    for (int i = threadIdx.x; i < nt * NB; i += kAT) (&sbr[0][0])[i] = brow[i];
-                }
-                __syncthreads();
-                if (!on) continue;
-                T pa = T(0), pb[NJ];
+                const f32x2 c2[2] = {pk2(cak[0], cak[1]), pk2(cak[2], cak[3])};
+                float ah[kAG], al[kAG], bh[kAG], bl[kAG];
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) pb[j] = T(0);
-                for (int c = 0; c < nt; ++c) {
-                    const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
-                    T M;
-                    if constexpr (mixed) M = brightness<kGauss>(ca, Q);
-                    else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
-                    pa += sm[3][c] * M * M;
-                    if constexpr (NJ == 1) {
-                        pb[0] += sm[4][c] * M;
-                    } else {
+                for (int j = 0; j < kAG; ++j) ah[j] = al[j] = bh[j] = bl[j] = 0.0f;
+                for (int c0 = 0; c0 < nc; c0 += kTA) {
+                    const int nt = min(kTA, nc - c0);
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < nt; j += kAT) {
 #pragma unroll
-                        for (int j = 0; j < NJ; ++j) pb[j] += sbr[c][j] * M;
+                        for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
+                    }
+                    __syncthreads();
+                    if (!on) continue;
+                    f32x2 pa2[2] = {pk2(0.0f, 0.0f), pk2(0.0f, 0.0f)}, pb2[2] = {pk2(0.0f, 0.0f), pk2(0.0f, 0.0f)};
+                    for (int c = 0; c < nt; ++c) {
+                        const float Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                        const f32x2 Q2 = pk2(Q, Q), A2 = pk2(sm[3][c], sm[3][c]), B2 = pk2(sm[4][c], sm[4][c]);
+#pragma unroll
+                        for (int j2 = 0; j2 < 2; ++j2) {
+                            float x0, x1;
+                            f32x2 M2;
+                            if (kGauss) {
+                                up2(mul2(c2[j2], Q2), x0, x1);
+                                M2 = pk2(ex2_approx(x0), ex2_approx(x1));
+                            } else {
+                                up2(fma2(c2[j2], Q2, one2), x0, x1);
+                                const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
+                                M2 = mul2(mul2(r2, r2), r2);
+                            }
+                            pa2[j2] = fma2(mul2(A2, M2), M2, pa2[j2]);
+                            pb2[j2] = fma2(B2, M2, pb2[j2]);
+                        }
+                    }
+#pragma unroll
+                    for (int j2 = 0; j2 < 2; ++j2) {
+                        float a0, a1, b0, b1;
+                        up2(pa2[j2], a0, a1);
+                        up2(pb2[j2], b0, b1);
+                        acc_add(split, ah[2 * j2], al[2 * j2], a0);
+                        acc_add(split, ah[2 * j2 + 1], al[2 * j2 + 1], a1);
+                        acc_add(split, bh[2 * j2], bl[2 * j2], b0);
+                        acc_add(split, bh[2 * j2 + 1], bl[2 * j2 + 1], b1);
                     }
                 }
-                if constexpr (mixed) {
-                    acc_add(split, ah, al, pa);
+                if (on) {
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) acc_add(split, bh[j], bl[j], pb[j]);
-                } else {
-                    da += (double)pa;
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
+                    for (int j = 0; j < kAG; ++j) {
+                        const int k = g * kAG + j;
+                        if (k >= na) break;
+                        const int pr = i * na + k;
+                        const double da = acc_value(split, ah[j], al[j]), db = acc_value(split, bh[j], bl[j]);
+                        sa[pr] = da;
+                        sb[pr] = db;
+                        slg[pr] = fp32_norm ? flux_marginal_mixed(da, db, cc, gc.flux_prior)
+                                            : flux_marginal(da, db, cc, gc.flux_prior);
+                    }
                 }
             }
-            if (on) {
-                if constexpr (mixed) {
-                    da = acc_value(split, ah, al);
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) db[j] = acc_value(split, bh[j], bl[j]);
+        } else {
+            for (int base = 0; base < np * na; base += kAT) {
+                const int pr = base + threadIdx.x;
+                const bool on = pr < np * na;
+                const int i = on ? pr / na : 0, k = on ? pr % na : 0;
+                const double e1 = e1s[i], e2 = e2s[i];
+                const double det = 1.0 - e1 * e1 - e2 * e2;
+                const double id2 = 1.0 / (det * det);
+                const T p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+                const T p12 = (T)(4.0 * e2 * id2);
+                const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+                const double alr = alph[k] * kArcsec * S.du;
+                const T ca = (T)(4.0 * kPi * kPi * alr * alr);
+                float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
+                double da = 0.0, db[NJ];
+    #pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    bh[j] = bl[j] = 0.0f;
+                    db[j] = 0.0;
                 }
-                sa[pr] = da;
-                if constexpr (NJ == 1) {
-                    sb[pr] = db[0];
-                    slg[pr] = fp32_norm ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
-                                        : flux_marginal(da, db[0], cc, gc.flux_prior);
-                } else {
-                    double bb;
-                    if (fp32_norm) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
-                    else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
-                    sb[pr] = bb;
+                for (int c0 = 0; c0 < nc; c0 += kTA) {
+                    const int nt = min(kTA, nc - c0);
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < nt; j += kAT) {
+    #pragma unroll
+                        for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
+                    }
+                    if constexpr (NJ > 1) {
+                        const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
+                        for (int i = threadIdx.x; i < nt * NB; i += kAT) (&sbr[0][0])[i] = brow[i];
+                    }
+                    __syncthreads();
+                    if (!on) continue;
+                    T pa = T(0), pb[NJ];
+    #pragma unroll
+                    for (int j = 0; j < NJ; ++j) pb[j] = T(0);
+                    for (int c = 0; c < nt; ++c) {
+                        const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                        T M;
+                        if constexpr (mixed) M = brightness<kGauss>(ca, Q);
+                        else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
+                        pa += sm[3][c] * M * M;
+                        if constexpr (NJ == 1) {
+                            pb[0] += sm[4][c] * M;
+                        } else {
+    #pragma unroll
+                            for (int j = 0; j < NJ; ++j) pb[j] += sbr[c][j] * M;
+                        }
+                    }
+                    if constexpr (mixed) {
+                        acc_add(split, ah, al, pa);
+    #pragma unroll
+                        for (int j = 0; j < NJ; ++j) acc_add(split, bh[j], bl[j], pb[j]);
+                    } else {
+                        da += (double)pa;
+    #pragma unroll
+                        for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
+                    }
+                }
+                if (on) {
+                    if constexpr (mixed) {
+                        da = acc_value(split, ah, al);
+    #pragma unroll
+                        for (int j = 0; j < NJ; ++j) db[j] = acc_value(split, bh[j], bl[j]);
+                    }
+                    sa[pr] = da;
+                    if constexpr (NJ == 1) {
+                        sb[pr] = db[0];
+                        slg[pr] = fp32_norm ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
+                                            : flux_marginal(da, db[0], cc, gc.flux_prior);
+                    } else {
+                        double bb;
+                        if (fp32_norm) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
+                        else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
+                        sb[pr] = bb;
+                    }
                 }
             }
         }
