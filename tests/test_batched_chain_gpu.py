@@ -1,0 +1,120 @@
+"""The whole chain on the 148,270,080-visibility, 1000-source workload (9,266,880 rows x 16
+channels), on the GPU against the FP64 oracle, in the launch configuration the benchmark
+times: split-phase precision, all sources in one chunk, update mode 1, launch shapes from
+the autotuner, the chain run as rlf_run and as a captured graph.
+
+Expected values come from tests/golden/batched_chain_oracle.json, written by
+make_batched_chain.py beside it (oracle only): every source's estimate and the final sky
+model at 300 sampled rows, for sigma = 1 uJy and for sigma at which the faintest source has
+SNR 10.  The data are rebuilt here the same way (the oracle's simulate_vis of the true sky
+plus seeded noise, rounded to complex64) and checked against the stored fingerprint.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import cases
+from tests.golden import make_batched_chain as mk
+
+pytestmark = pytest.mark.gpu
+
+GOLD_PATH = os.path.join(os.path.dirname(__file__), "golden", "batched_chain_oracle.json")
+TUNE_CACHE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2203_14071_gb300", "_build",
+                          "tune_cache.json")
+
+
+@pytest.fixture(scope="module")
+def rlf():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2203_14071_gb300 as m
+    from paper_2203_14071_gb300 import build_ext
+    build_ext.build()
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLD_PATH) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def batched():
+    c = cases.build(synth.workload("batched"), with_data=False)
+    return c, mk.true_data(c)
+
+
+def _check_estimates(res, est, n):
+    de = np.array([cases.est_matches(res, i, est[i]) for i in range(n)])
+    assert np.all(de <= 1e-4), (int(np.argmax(de)), float(de.max()))
+    # the bad-fit flag, except where the oracle's spread sits within 1e-6 of a cut
+    sd1, sd2 = est[:, oracle.SIG1], est[:, oracle.SIG2]
+    near = (np.abs(sd1 - 5e-3) < 1e-6 * 5e-3) | (np.abs(sd2 - 5e-3) < 1e-6 * 5e-3)
+    same = ((res["flag"] & 1) != 0) == (est[:, oracle.FLAG] != 0)
+    assert np.all(same | near), np.flatnonzero(~(same | near))[:10]
+    return float(de.max())
+
+
+def _check_sky(sky_dev, rows, g, n_chan, max_de):
+    import torch
+    got = sky_dev.view(-1, n_chan, 2)[torch.from_numpy(np.asarray(rows)).cuda()].cpu().numpy().astype(np.float64)
+    ref = np.array(g["sky_final_re"]) + 1j * np.array(g["sky_final_im"])
+    ab = np.array(g["sky_final_abs"])
+    err = np.abs(got[..., 0] + 1j * got[..., 1] - ref)
+    # FP32 model (1e-5 of the summed moduli, cancellation-aware), the complex64 output, and the
+    # two sides' fitted shapes differing by max_de: a term moves by at most ~10 |term| per unit e
+    bound = (2e-5 + 10.0 * max_de) * ab + 2.0 ** -24 * math.sqrt(2.0) * np.abs(ref) + 1e-30
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("variant", ["snr10"])
+def test_batched_chain_matches_oracle(rlf, gold, batched, variant):
+    import torch
+    c, true = batched
+    g = gold["variants"][variant]
+    sigma = g["sigma_jy"]
+    data = mk.data_from_true(true, sigma, c.wl.seed)
+    fp, gfp = cases.fingerprint(data), g["fingerprint"]
+    assert fp["values"] == gfp["values"]
+    assert math.isclose(fp["sum"], gfp["sum"], rel_tol=1e-9, abs_tol=1e-9)
+    assert math.isclose(fp["sum_sq"], gfp["sum_sq"], rel_tol=1e-9)
+    est = np.array(g["est"])
+    R, C, n = c.obs.n_rows, c.obs.n_chan, c.cat.n_src
+    obs, cat = cases.to_device(c)
+    d = cases.vis_tensor(data)
+    del data
+    p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=sigma, precision=rlf.PREC_MIXED_SPLIT, chunk=0,
+                           update_mode=1)
+    ws = rlf.alloc_workspace(R, C, n, p, rlf.WS_RUN)
+    out = rlf.Results(n, "cuda")
+    sky = torch.empty(R * C * 2, dtype=torch.float32, device="cuda")
+    rlf.autotune(obs, d, cat, p, out, sky, ws, TUNE_CACHE)
+    # rlf_run
+    rlf.run(obs, d, cat, p, out, sky, ws)
+    code, status = rlf.read_status(ws)
+    assert code == rlf.RLF_OK, status
+    res = out.numpy()
+    max_de = _check_estimates(res, est, n)
+    _check_sky(sky, gold["rows"], g, C, max_de)
+    # one replay of the captured chain on the same buffers
+    out.e1.zero_()
+    out.e2.zero_()
+    sky.zero_()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        graph = rlf.Graph(obs, d, cat, p, out, sky, ws, stream)
+        graph.launch(stream)
+    stream.synchronize()
+    graph.close()
+    res = out.numpy()
+    max_de = _check_estimates(res, est, n)
+    _check_sky(sky, gold["rows"], g, C, max_de)
+    print(f"\n{variant}: sigma {sigma:.4g} Jy, max |de| {max_de:.3g}, bad fits {int(np.sum(res['flag'] & 1))}/{n}, "
+          f"tuning {[int(getattr(p, f)) for f in rlf.TUNE_FIELDS]}")
