@@ -436,7 +436,10 @@ void launch_mixed_cg(const rlf_uvw &uvw, const ChanTable &ch, const SrcRow *tabl
     if (ch.n == 1) launch_mixed<1, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
     else if (ch.n == 2) launch_mixed<2, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
     else if (ch.n <= 4) launch_mixed<4, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
-    else if (ch.n <= 8) launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
+    // 16 channels per thread share the per-(row, source) phase work when there are enough
+    // sources to make the kernel compute bound; a few sources (the serial order's updates)
+    // stream the visibilities, where 8 channels per thread (more warps) go faster
+    else if (ch.n <= 8 || n_src < 32) launch_mixed<8, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
     else launch_mixed<16, kUpdate, kSplit>(uvw, ch, table, n_src, vis, bps, sign, sr, st);
 }
 
