@@ -102,7 +102,10 @@ enum {
 enum {
     RLF_DEV_INVALID_SOURCE = 1,
     RLF_DEV_NONFINITE = 2,
-    RLF_DEV_TIMEOUT = 4    /* reserved (no kernel of this version waits) */
+    RLF_DEV_TIMEOUT = 4    /* a bounded wait ran out: the proposal network's tensor-core GEMM
+                              (rlf_mlp_propose, rlf_fit_sources_mlp; the results of the call
+                              are then invalid; rlf_mlp_forward and rlf_mlp_train_step keep
+                              the flag in their own scratch and do not report it) */
 };
 
 /* workspace users for rlf_workspace_size */
@@ -298,7 +301,8 @@ rlf_status rlf_run(const rlf_uvw *uvw, const float *vis_data, const rlf_sources 
  * P = rlf_mlp_n_params() and the parameter order W1 [8192][256], b1 [256],
  * W2 [256][256], b2 [256], W3 [256][8], b3 [8] (row-major, columns 6 and 7 of W3
  * zero): f32 params [P] | f32 Adam m [P] | f32 Adam v [P] | f32 gradients [P] |
- * f16 copies of W1, W2, W3 (used by the tensor-core GEMMs).
+ * f16 copies of W1, W2, W3 (used by the tensor-core GEMMs; the first layer's GEMM
+ * transposes W1 into its scratch on every call).
  */
 #define RLF_MLP_IN 8192
 #define RLF_MLP_OUT 8
@@ -321,12 +325,14 @@ rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux
                             const int32_t *tidx, const double *e1, const double *e2, const double *alpha_arcsec,
                             const float *normals, int32_t batch, const rlf_params *p, void *x_f16, float *y,
                             void *stream);
-/* One Adam step on a batch (x_f16 [batch][8192], y [batch][3]); step >= 1 is the Adam time
+/* One Adam step on a batch (x_f16 [batch][8192], 16-byte aligned; y [batch][3]); step >= 1 is the Adam time
  * step (bias correction); step = 0 computes the gradients into the blob and leaves the
  * parameters unchanged.  loss (device f32, may be NULL) receives the batch NLL. */
 rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,
                               int32_t step, float *loss, void *workspace, size_t ws_bytes, void *stream);
-/* out (device [batch][8] f32): the network's outputs for x_f16. */
+/* out (device [batch][8] f32): the network's outputs for x_f16 (16-byte aligned, else
+ * RLF_EINVAL).  The first layer runs on tcgen05 (TMA-staged f16 operands, f32
+ * accumulators in TMEM), the others on mma.sync. */
 rlf_status rlf_mlp_forward(const void *weights, const void *x_f16, int32_t batch, float *out, void *workspace,
                            size_t ws_bytes, void *stream);
 /* Network inputs (device [count][8192] f16) of facets [count][4][64*64] of sources

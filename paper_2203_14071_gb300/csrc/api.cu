@@ -680,6 +680,8 @@ size_t rlf_mlp_workspace_size(int32_t max_batch)
     return mlp_scratch(nullptr, max_batch).bytes + 256;
 }
 
+static bool aligned16(const void *p) { return (reinterpret_cast<size_t>(p) & 15u) == 0; }
+
 static void *align256(void *p) { return reinterpret_cast<void *>((reinterpret_cast<size_t>(p) + 255) / 256 * 256); }
 
 rlf_status rlf_mlp_init(void *weights, const float *normals, void *stream)
@@ -705,26 +707,28 @@ rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux
 rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,
                               int32_t step, float *loss, void *workspace, size_t ws_bytes, void *stream)
 {
-    if (!weights || !x_f16 || !y || !workspace || batch <= 0) return RLF_EINVAL;
+    if (!weights || !x_f16 || !y || !workspace || batch <= 0 || !aligned16(x_f16)) return RLF_EINVAL;
     if (ws_bytes < rlf_mlp_workspace_size(batch)) return RLF_ENOSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
+    const MlpScratch sc = mlp_scratch(align256(workspace), batch);
     if (loss) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess)
-        e = mlp_train_step(mlp_weights(weights), static_cast<const __half *>(x_f16), y, batch, lr, step, loss,
-                           mlp_scratch(align256(workspace), batch), st);
+        e = mlp_train_step(mlp_weights(weights), static_cast<const __half *>(x_f16), y, batch, lr, step, loss, sc, st);
     return cuda_status(e);
 }
 
 rlf_status rlf_mlp_forward(const void *weights, const void *x_f16, int32_t batch, float *out, void *workspace,
                            size_t ws_bytes, void *stream)
 {
-    if (!weights || !x_f16 || !out || !workspace || batch <= 0) return RLF_EINVAL;
+    if (!weights || !x_f16 || !out || !workspace || batch <= 0 || !aligned16(x_f16)) return RLF_EINVAL;
     if (ws_bytes < rlf_mlp_workspace_size(batch)) return RLF_ENOSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const MlpScratch sc = mlp_scratch(align256(workspace), batch);
-    cudaError_t e = mlp_forward(mlp_weights(const_cast<void *>(weights)), static_cast<const __half *>(x_f16), batch,
-                                sc, st);
+    cudaError_t e = cudaMemsetAsync(sc.status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = mlp_forward(mlp_weights(const_cast<void *>(weights)), static_cast<const __half *>(x_f16), batch, sc, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, sc.o, (size_t)batch * kMlpOutPad * sizeof(float), cudaMemcpyDeviceToDevice, st);
     return cuda_status(e);
@@ -759,7 +763,8 @@ rlf_status rlf_mlp_propose(const double *facets, const rlf_sources *src, int32_t
     Workspace ws;
     if (workspace_layout(0, 1, src->n_src, *p, RLF_WS_FIT, workspace, &ws) > ws_bytes) return RLF_ENOSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    sc.status = ws.status;
     __half *x = static_cast<__half *>(ws.mlp_x);
     cudaError_t e = launch_prepare(*src, first, count, src->e1, src->e2, nullptr, nullptr, nullptr, 0, nullptr,
                                    nullptr, *p, ws.table, ws.status, st);

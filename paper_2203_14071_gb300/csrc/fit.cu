@@ -1578,7 +1578,8 @@ cudaError_t launch_fit_mlp(const double *facets, const SrcRow *table, int32_t co
     cudaError_t e = cudaGetLastError();
     // the network's proposal of each facet's sub-box
     const MlpWeights W = mlp_weights(const_cast<void *>(weights));
-    const MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    MlpScratch sc = mlp_scratch(ws.mlp_scratch, count);
+    sc.status = ws.status;
     __half *x = static_cast<__half *>(ws.mlp_x);
     if (e == cudaSuccess) e = mlp_encode(facets, table, count, N, x, st);
     if (e == cudaSuccess) e = mlp_forward(W, x, count, sc, st);

@@ -3,7 +3,8 @@
 // predicts the mean and log-variance of (e1, e2, ln alpha); the fit then
 // evaluates only a 7 x 7 x 5 box of the grid around the prediction.
 //
-// Kernels: tensor-core GEMMs (mma.sync m16n8k16, f16 inputs, f32 accumulation)
+// Kernels: the first layer's forward GEMM on tcgen05 (mlp_umma.cu); the other
+// GEMMs on mma.sync m16n8k16 (f16 inputs, f32 accumulation; K = 256 or the batch)
 // with fused epilogues for the forward and backward passes, the Gaussian NLL and
 // its gradient, bias-gradient column sums, Adam, the facet encoder, the training
 // facet simulator and the proposal rule.  Weights: f32 masters + f16 copies.
@@ -442,6 +443,8 @@ MlpScratch mlp_scratch(void *base, int32_t max_batch)
     s.dz2 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
     s.dz1 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
     s.part = reinterpret_cast<float *>(take((size_t)kL1Slices * max_batch * kMlpHidden * sizeof(float)));
+    s.w1t = reinterpret_cast<__half *>(take((size_t)kMlpIn * kMlpHidden * sizeof(__half)));
+    s.status = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
     s.bytes = (size_t)(b - static_cast<char *>(base));
     return s;
 }
@@ -450,9 +453,8 @@ cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const M
 {
     const MlpOffsets o = mlp_offsets();
     const __half *W1h = W.h, *W2h = W.h + o.W1h_n, *W3h = W.h + o.W1h_n + o.W2h_n;
-    // layer 1 (K = 8192): split over K so that the small batch still fills the GPU
-    cudaError_t e = gemm<false, false, EPI_F32>(B, kMlpHidden, kMlpIn, x, kMlpIn, W1h, kMlpHidden, nullptr, nullptr, 0,
-                                                s.part, nullptr, kMlpHidden, st, kL1Slices);
+    // layer 1 (K = 8192) on tcgen05, split over K so that a small batch still fills the GPU
+    cudaError_t e = mlp_layer1_umma(x, B, W1h, s.w1t, s.part, kL1Slices, s.status, st);
     if (e == cudaSuccess) {
         const int64_t mn = (int64_t)B * kMlpHidden;
         splitk_reduce_kernel<<<(int)((mn + 255) / 256 < 1024 ? (mn + 255) / 256 : 1024), 256, 0, st>>>(

@@ -354,6 +354,8 @@ struct MlpScratch {
     __half *h1, *h2, *g16, *dz2, *dz1;
     float *o, *g32;
     float *part;            // split-K partial sums of the first layer
+    __half *w1t;            // W1 transposed, [256][8192] (the tensor-core GEMM's K-major B)
+    int32_t *status;        // RLF_DEV_TIMEOUT from the tensor-core GEMM's bounded waits
     size_t bytes;
 };
 MlpOffsets mlp_offsets();
@@ -361,6 +363,11 @@ MlpWeights mlp_weights(void *blob);
 size_t mlp_weights_bytes();
 MlpScratch mlp_scratch(void *base, int32_t max_batch);
 cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const MlpScratch &s, cudaStream_t st);
+// first layer on tcgen05 (mlp_umma.cu): part[z][m][n] over n_slices K slices; x and W1t
+// 16-byte aligned; cudaErrorNotSupported, launching nothing, when the driver cannot
+// encode their tensor maps
+cudaError_t mlp_layer1_umma(const __half *x, int32_t M, const __half *W1h, __half *W1t, float *part, int32_t n_slices,
+                            int32_t *status, cudaStream_t st);
 cudaError_t mlp_train_step(const MlpWeights &W, const __half *x, const float *y, int32_t B, float lr, int32_t step,
                            float *loss, const MlpScratch &s, cudaStream_t st);
 cudaError_t mlp_init(const MlpWeights &W, const float *z, cudaStream_t st);

@@ -91,6 +91,37 @@ def test_forward_and_gradients_match_oracle(rlf):
     assert np.array_equal(m.section(m.w, "b2").cpu().numpy(), P[3].astype(np.float32))
 
 
+@pytest.mark.parametrize("B", [1, 96, 129, 1000])
+def test_first_layer_tcgen05_matches_oracle(rlf, B):
+    """The first layer's activations h1 = relu(x W1 + b1) (the tcgen05 GEMM over 16 K
+    slices, the slices' sum with the bias, f16) element by element against the oracle's
+    FP64 forward of the same f16 inputs and weights.  h1 is the first buffer of the
+    forward's scratch (at the workspace pointer rounded up to 256 bytes).  Bound per
+    element: the f16 rounding of the result (2^-11 relative) plus 1e-4 of sum_k |x_k W_kn|
+    for the f32 accumulation; a wrong operand layout misses by about 1e-2 of that sum.
+    B = 1, 129 and 1000 leave ragged 128-row tiles (rows past B read as zeros)."""
+    import torch
+    P = _host_weights(11)
+    m, R = _load(rlf, P)
+    rng = np.random.default_rng(12 + B)
+    x = rng.normal(0.1, 0.5, (B, 8192)).astype(np.float16)
+    ws = rlf.mlp_workspace(B)
+    out = torch.zeros(B, 8, device="cuda")
+    rlf.mlp_forward(m, torch.from_numpy(x).cuda(), out, ws)
+    torch.cuda.synchronize()
+    off = (-ws.data_ptr()) % 256
+    h1 = ws[off:off + B * 256 * 2].view(torch.float16).view(B, 256).cpu().numpy().astype(np.float64)
+    x64 = x.astype(np.float64)
+    _, (_, z1, h1_ref, _, _) = omlp.forward(x64, *R)
+    scale = np.abs(x64) @ np.abs(R[0])
+    bound = 2.0 ** -11 * np.abs(h1_ref) + 1e-4 * scale + 6e-8
+    err = np.abs(h1 - h1_ref)
+    assert np.all(err <= bound), (float(np.max(err / bound)), np.unravel_index(np.argmax(err / bound), err.shape))
+    # the layer is not degenerate: about half the units active, values well above the bound
+    assert 0.3 < np.mean(h1_ref > 0) < 0.7
+    assert np.median(bound[h1_ref > 0] / h1_ref[h1_ref > 0]) < 0.05
+
+
 def test_adam_step_matches_oracle(rlf):
     import torch
     P = _host_weights(3)
