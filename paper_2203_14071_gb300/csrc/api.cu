@@ -139,7 +139,7 @@ size_t workspace_layout(int64_t n_rows, int32_t n_chan, int32_t n_src, const rlf
     const size_t o_gb = take(fit ? fit_parts * cap * ng * sizeof(double) : 0);
     const size_t o_gl = take(fit ? cap * ng * sizeof(double) : 0);
     const bool adapt = fit && p.estimator == RLF_ESTIMATOR_ADAPTIVE;
-    const size_t o_ad = take(adapt ? cap * 289 * (size_t)p.n_alpha * 3 * sizeof(double) : 0);
+    const size_t o_ad = take(adapt ? cap * adapt_doubles_per_facet(p.n_alpha) * sizeof(double) : 0);
     const size_t o_ecur = take(run ? 2 * (size_t)n_src * sizeof(double) : 0);
     const size_t o_bad = take(run ? ((size_t)n_src + 1) * sizeof(int32_t) : 0);
     const size_t o_ftmp = take(run ? 8 * cap * sizeof(double) : 0);

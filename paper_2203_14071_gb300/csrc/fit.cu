@@ -25,8 +25,11 @@
 //   fit_persistent_pos_kernel / grid_tile_pos   the grid with the position
 //                     marginal (Sec. 2.4): one (e, alpha) point per thread, every
 //                     offset's b, the marginal over offsets in the tile's epilogue.
-//   adaptive_kernel   adaptive sampling around the maximum (Sec. 2.4): one CTA per
-//                     facet refines halved lattices after the grid fit.
+//   adaptive_cluster_kernel / adaptive_kernel   adaptive sampling around the maximum
+//                     (Sec. 2.4) after the grid fit: halved lattices, a cluster of four
+//                     CTAs per facet (FP32, one position) or one CTA per facet.
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
@@ -1061,8 +1064,10 @@ fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict
 // step is halved and every multiple of it in the box of the kept samples, widened by
 // the previous step, is sampled (|e| < 1, at most 17 per component around the MAP
 // sample).  The estimate is the last level's, by the rules of the grid estimate.
-constexpr int kAdaptSide = 17, kAdaptMax = kAdaptSide * kAdaptSide;
-constexpr int kAT = 512;   // threads of an adaptive-sampling CTA (one facet each)
+constexpr int kAT = 512;    // threads of an adaptive-sampling CTA (one facet each)
+constexpr int kATc = 128;   // threads of a CTA of the cluster form
+constexpr int kAdaptR = 4;  // CTAs per facet in the cluster form
+static_assert(kAdaptR <= kAdaptRanks && kAdaptR <= 8, "a portable cluster, within the partials' scratch");
 
 struct AdaptResult {
     double e1m, e2m, sd1, sd2, am, flux, e1s, e2s;
@@ -1190,6 +1195,77 @@ __device__ void estimate_over_samples(bool mixed, int np, const double *e1s, con
     __syncthreads();
 }
 
+// quadrature weights qp_k (trapezoid in alpha times the lognormal prior of Eq. 4), the
+// nodes alpha_k and the log prior lnp_k of the scalelength grid (threads k < n_alpha)
+__device__ void alpha_weights(const GridConst &gc, const SrcRow &S, double *qp, double *alph, double *lnp)
+{
+    const int na = gc.n_alpha;
+    if (threadIdx.x < na) {
+        const int k = threadIdx.x;
+        const double ak = grid_alpha(gc, k);
+        double q;
+        if (na == 1) q = 1.0;
+        else if (k == 0) q = 0.5 * (grid_alpha(gc, 1) - ak);
+        else if (k == na - 1) q = 0.5 * (ak - grid_alpha(gc, na - 2));
+        else q = 0.5 * (grid_alpha(gc, k + 1) - grid_alpha(gc, k - 1));
+        const double z = (log(ak) - S.mu) / gc.r_std;
+        qp[k] = q * exp(-0.5 * z * z) / (ak * gc.r_std * sqrt(2.0 * kPi));
+        alph[k] = ak;
+        lnp[k] = -0.5 * z * z - log(ak);
+    }
+}
+
+// The next lattice (one thread): every multiple of hn = h / 2 in the box of the kept
+// samples widened by h, |e| < 1, at most kAdaptSide per component around the MAP
+// sample; returns the number of samples written to e1s, e2s.
+__device__ int plan_lattice(const GridConst &gc, const AdaptResult &res, int level, double h, double *e1s, double *e2s)
+{
+    const int ne = gc.n_e;
+    const double hn = 0.5 * h;
+    const double cen[2] = {level == 0 ? grid_e(gc, res.map_i / ne) : e1s[res.map_i],
+                           level == 0 ? grid_e(gc, res.map_i % ne) : e2s[res.map_i]};
+    int lo[2], hi[2];
+    for (int d = 0; d < 2; ++d) {
+        lo[d] = (int)ceil((res.box[2 * d] - h) / hn - 1e-9);
+        hi[d] = (int)floor((res.box[2 * d + 1] + h) / hn + 1e-9);
+        if (hi[d] - lo[d] + 1 > kAdaptSide) {
+            const int c = (int)llround(cen[d] / hn);
+            lo[d] = c - kAdaptSide / 2;
+            hi[d] = c + kAdaptSide / 2;
+        }
+    }
+    int np = 0;
+    for (int i1 = lo[0]; i1 <= hi[0]; ++i1)
+        for (int i2 = lo[1]; i2 <= hi[1]; ++i2) {
+            const double a1 = i1 * hn, a2 = i2 * hn;
+            if (!(a1 * a1 + a2 * a2 < 1.0)) continue;
+            e1s[np] = a1;
+            e2s[np] = a2;
+            ++np;
+        }
+    return np;
+}
+
+// the last level's estimate as the fit result of facet s (one thread)
+__device__ void write_adapt_result(const AdaptResult &res, const SrcRow &S, int level, int s, const rlf_fit_out &out,
+                                   int32_t out_offset)
+{
+    int flag = res.bad ? RLF_FLAG_BAD : 0;
+    if (S.invalid) flag |= RLF_FLAG_INVALID;
+    const int o = out_offset + s;
+    out.e1[o] = res.e1m;
+    out.e2[o] = res.e2m;
+    out.sig1[o] = res.sd1;
+    out.sig2[o] = res.sd2;
+    out.alpha_arcsec[o] = res.am;
+    out.flux_jy[o] = res.flux;
+    out.e1_smooth[o] = res.e1s;
+    out.e2_smooth[o] = res.e2s;
+    out.flag[o] = flag | (level << RLF_FLAG_LEVELS_SHIFT);
+}
+
+// One CTA per facet (the position marginal and the FP64 form): each thread one
+// (sample, alpha) pair over all of the facet's cells, level after level.
 template <typename T, bool kGauss, int NJ>
 __global__ void __launch_bounds__(kAT, 1)
 adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, const SrcRow *__restrict__ table,
@@ -1217,215 +1293,96 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
     const SrcRow S = table[s];
     const int nc = ncell[s];
     const double cc = ccv[s];
-    if (threadIdx.x < na) {
-        const int k = threadIdx.x;
-        const double ak = grid_alpha(gc, k);
-        double q;
-        if (na == 1) q = 1.0;
-        else if (k == 0) q = 0.5 * (grid_alpha(gc, 1) - ak);
-        else if (k == na - 1) q = 0.5 * (ak - grid_alpha(gc, na - 2));
-        else q = 0.5 * (grid_alpha(gc, k + 1) - grid_alpha(gc, k - 1));
-        const double z = (log(ak) - S.mu) / gc.r_std;
-        qp[k] = q * exp(-0.5 * z * z) / (ak * gc.r_std * sqrt(2.0 * kPi));
-        alph[k] = ak;
-        lnp[k] = -0.5 * z * z - log(ak);
-    }
+    alpha_weights(gc, S, qp, alph, lnp);
     __syncthreads();
     // level 0: the grid
     estimate_over_samples<kAT>(fp32_norm, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp, alph,
                           lnp, Ls, As, res);
     double h = 2.0 * gc.e_max / (ne - 1);
     int level = 0;
-    double *slg = scratch + (size_t)s * kAdaptMax * na * 3;
+    double *slg = scratch + (size_t)s * adapt_doubles_per_facet(na);
     double *sa = slg + (size_t)kAdaptMax * na, *sb = sa + (size_t)kAdaptMax * na;
     while (res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0) {
         // the next lattice (thread 0), then every (sample, alpha) pair over the cells
         const double hn = 0.5 * h;
-        if (threadIdx.x == 0) {
-            const double cen[2] = {level == 0 ? grid_e(gc, res.map_i / ne) : e1s[res.map_i],
-                                   level == 0 ? grid_e(gc, res.map_i % ne) : e2s[res.map_i]};
-            int lo[2], hi[2];
-            for (int d = 0; d < 2; ++d) {
-                lo[d] = (int)ceil((res.box[2 * d] - h) / hn - 1e-9);
-                hi[d] = (int)floor((res.box[2 * d + 1] + h) / hn + 1e-9);
-                if (hi[d] - lo[d] + 1 > kAdaptSide) {
-                    const int c = (int)llround(cen[d] / hn);
-                    lo[d] = c - kAdaptSide / 2;
-                    hi[d] = c + kAdaptSide / 2;
-                }
-            }
-            int np = 0;
-            for (int i1 = lo[0]; i1 <= hi[0]; ++i1)
-                for (int i2 = lo[1]; i2 <= hi[1]; ++i2) {
-                    const double a1 = i1 * hn, a2 = i2 * hn;
-                    if (!(a1 * a1 + a2 * a2 < 1.0)) continue;
-                    e1s[np] = a1;
-                    e2s[np] = a2;
-                    ++np;
-                }
-            s_np = np;
-        }
+        if (threadIdx.x == 0) s_np = plan_lattice(gc, res, level, h, e1s, e2s);
         __syncthreads();
         const int np = s_np;
         const T *cu = cells + (size_t)s * NN;
-        if constexpr (NJ == 1 && mixed) {
-            // four scalelength nodes per thread, as the grid's tiles: the quadratic form of a
-            // cell once for them, two nodes per paired FP32 instruction
-            constexpr int kAG = 4;
-            const int n_ag = (na + kAG - 1) / kAG;
-            const bool split = gc.split != 0;
-            const f32x2 one2 = pk2(1.0f, 1.0f);
-            for (int base = 0; base < np * n_ag; base += kAT) {
-                const int it = base + threadIdx.x;
-                const bool on = it < np * n_ag;
-                const int i = on ? it / n_ag : 0, g = on ? it % n_ag : 0;
-                const double e1 = e1s[i], e2 = e2s[i];
-                const double det = 1.0 - e1 * e1 - e2 * e2;
-                const double id2 = 1.0 / (det * det);
-                const float p11 = (float)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
-                const float p12 = (float)(4.0 * e2 * id2);
-                const float p22 = (float)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
-                float cak[kAG];
+        for (int base = 0; base < np * na; base += kAT) {
+            const int pr = base + threadIdx.x;
+            const bool on = pr < np * na;
+            const int i = on ? pr / na : 0, k = on ? pr % na : 0;
+            const double e1 = e1s[i], e2 = e2s[i];
+            const double det = 1.0 - e1 * e1 - e2 * e2;
+            const double id2 = 1.0 / (det * det);
+            const T p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+            const T p12 = (T)(4.0 * e2 * id2);
+            const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+            const double alr = alph[k] * kArcsec * S.du;
+            const T ca = (T)(4.0 * kPi * kPi * alr * alr);
+            float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
+            double da = 0.0, db[NJ];
 #pragma unroll
-                for (int j = 0; j < kAG; ++j) {
-                    const int k = g * kAG + j;
-                    const double alr = (k < na ? alph[k] : 0.0) * kArcsec * S.du;
-                    cak[j] = (float)(4.0 * kPi * kPi * alr * alr) * (kGauss ? -0.25f : 1.0f);
+            for (int j = 0; j < NJ; ++j) {
+                bh[j] = bl[j] = 0.0f;
+                db[j] = 0.0;
+            }
+            for (int c0 = 0; c0 < nc; c0 += kTA) {
+                const int nt = min(kTA, nc - c0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < nt; j += kAT) {
+#pragma unroll
+                    for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
                 }
-                const f32x2 c2[2] = {pk2(cak[0], cak[1]), pk2(cak[2], cak[3])};
-                float ah[kAG], al[kAG], bh[kAG], bl[kAG];
+                if constexpr (NJ > 1) {
+                    const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
+                    for (int i = threadIdx.x; i < nt * NB; i += kAT) (&sbr[0][0])[i] = brow[i];
+                }
+                __syncthreads();
+                if (!on) continue;
+                T pa = T(0), pb[NJ];
 #pragma unroll
-                for (int j = 0; j < kAG; ++j) ah[j] = al[j] = bh[j] = bl[j] = 0.0f;
-                for (int c0 = 0; c0 < nc; c0 += kTA) {
-                    const int nt = min(kTA, nc - c0);
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < nt; j += kAT) {
+                for (int j = 0; j < NJ; ++j) pb[j] = T(0);
+                for (int c = 0; c < nt; ++c) {
+                    const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                    T M;
+                    if constexpr (mixed) M = brightness<kGauss>(ca, Q);
+                    else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
+                    pa += sm[3][c] * M * M;
+                    if constexpr (NJ == 1) {
+                        pb[0] += sm[4][c] * M;
+                    } else {
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
-                    }
-                    __syncthreads();
-                    if (!on) continue;
-                    f32x2 pa2[2] = {pk2(0.0f, 0.0f), pk2(0.0f, 0.0f)}, pb2[2] = {pk2(0.0f, 0.0f), pk2(0.0f, 0.0f)};
-                    for (int c = 0; c < nt; ++c) {
-                        const float Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
-                        const f32x2 Q2 = pk2(Q, Q), A2 = pk2(sm[3][c], sm[3][c]), B2 = pk2(sm[4][c], sm[4][c]);
-#pragma unroll
-                        for (int j2 = 0; j2 < 2; ++j2) {
-                            float x0, x1;
-                            f32x2 M2;
-                            if (kGauss) {
-                                up2(mul2(c2[j2], Q2), x0, x1);
-                                M2 = pk2(ex2_approx(x0), ex2_approx(x1));
-                            } else {
-                                up2(fma2(c2[j2], Q2, one2), x0, x1);
-                                const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
-                                M2 = mul2(mul2(r2, r2), r2);
-                            }
-                            pa2[j2] = fma2(mul2(A2, M2), M2, pa2[j2]);
-                            pb2[j2] = fma2(B2, M2, pb2[j2]);
-                        }
-                    }
-#pragma unroll
-                    for (int j2 = 0; j2 < 2; ++j2) {
-                        float a0, a1, b0, b1;
-                        up2(pa2[j2], a0, a1);
-                        up2(pb2[j2], b0, b1);
-                        acc_add(split, ah[2 * j2], al[2 * j2], a0);
-                        acc_add(split, ah[2 * j2 + 1], al[2 * j2 + 1], a1);
-                        acc_add(split, bh[2 * j2], bl[2 * j2], b0);
-                        acc_add(split, bh[2 * j2 + 1], bl[2 * j2 + 1], b1);
+                        for (int j = 0; j < NJ; ++j) pb[j] += sbr[c][j] * M;
                     }
                 }
-                if (on) {
+                if constexpr (mixed) {
+                    acc_add(split, ah, al, pa);
 #pragma unroll
-                    for (int j = 0; j < kAG; ++j) {
-                        const int k = g * kAG + j;
-                        if (k >= na) break;
-                        const int pr = i * na + k;
-                        const double da = acc_value(split, ah[j], al[j]), db = acc_value(split, bh[j], bl[j]);
-                        sa[pr] = da;
-                        sb[pr] = db;
-                        slg[pr] = fp32_norm ? flux_marginal_mixed(da, db, cc, gc.flux_prior)
-                                            : flux_marginal(da, db, cc, gc.flux_prior);
-                    }
+                    for (int j = 0; j < NJ; ++j) acc_add(split, bh[j], bl[j], pb[j]);
+                } else {
+                    da += (double)pa;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
                 }
             }
-        } else {
-            for (int base = 0; base < np * na; base += kAT) {
-                const int pr = base + threadIdx.x;
-                const bool on = pr < np * na;
-                const int i = on ? pr / na : 0, k = on ? pr % na : 0;
-                const double e1 = e1s[i], e2 = e2s[i];
-                const double det = 1.0 - e1 * e1 - e2 * e2;
-                const double id2 = 1.0 / (det * det);
-                const T p11 = (T)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
-                const T p12 = (T)(4.0 * e2 * id2);
-                const T p22 = (T)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
-                const double alr = alph[k] * kArcsec * S.du;
-                const T ca = (T)(4.0 * kPi * kPi * alr * alr);
-                float ah = 0.0f, al = 0.0f, bh[NJ], bl[NJ];
-                double da = 0.0, db[NJ];
-    #pragma unroll
-                for (int j = 0; j < NJ; ++j) {
-                    bh[j] = bl[j] = 0.0f;
-                    db[j] = 0.0;
+            if (on) {
+                if constexpr (mixed) {
+                    da = acc_value(split, ah, al);
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) db[j] = acc_value(split, bh[j], bl[j]);
                 }
-                for (int c0 = 0; c0 < nc; c0 += kTA) {
-                    const int nt = min(kTA, nc - c0);
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < nt; j += kAT) {
-    #pragma unroll
-                        for (int q = 0; q < (NJ > 1 ? 4 : 5); ++q) sm[q][j] = cu[q * plane + c0 + j];
-                    }
-                    if constexpr (NJ > 1) {
-                        const T *brow = cells + 4 * plane + ((size_t)s * NN + c0) * NB;
-                        for (int i = threadIdx.x; i < nt * NB; i += kAT) (&sbr[0][0])[i] = brow[i];
-                    }
-                    __syncthreads();
-                    if (!on) continue;
-                    T pa = T(0), pb[NJ];
-    #pragma unroll
-                    for (int j = 0; j < NJ; ++j) pb[j] = T(0);
-                    for (int c = 0; c < nt; ++c) {
-                        const T Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
-                        T M;
-                        if constexpr (mixed) M = brightness<kGauss>(ca, Q);
-                        else M = brightness64(ca * Q, kGauss ? RLF_PROFILE_GAUSSIAN : RLF_PROFILE_EXPONENTIAL);
-                        pa += sm[3][c] * M * M;
-                        if constexpr (NJ == 1) {
-                            pb[0] += sm[4][c] * M;
-                        } else {
-    #pragma unroll
-                            for (int j = 0; j < NJ; ++j) pb[j] += sbr[c][j] * M;
-                        }
-                    }
-                    if constexpr (mixed) {
-                        acc_add(split, ah, al, pa);
-    #pragma unroll
-                        for (int j = 0; j < NJ; ++j) acc_add(split, bh[j], bl[j], pb[j]);
-                    } else {
-                        da += (double)pa;
-    #pragma unroll
-                        for (int j = 0; j < NJ; ++j) db[j] += (double)pb[j];
-                    }
-                }
-                if (on) {
-                    if constexpr (mixed) {
-                        da = acc_value(split, ah, al);
-    #pragma unroll
-                        for (int j = 0; j < NJ; ++j) db[j] = acc_value(split, bh[j], bl[j]);
-                    }
-                    sa[pr] = da;
-                    if constexpr (NJ == 1) {
-                        sb[pr] = db[0];
-                        slg[pr] = fp32_norm ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
-                                            : flux_marginal(da, db[0], cc, gc.flux_prior);
-                    } else {
-                        double bb;
-                        if (fp32_norm) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
-                        else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
-                        sb[pr] = bb;
-                    }
+                sa[pr] = da;
+                if constexpr (NJ == 1) {
+                    sb[pr] = db[0];
+                    slg[pr] = fp32_norm ? flux_marginal_mixed(da, db[0], cc, gc.flux_prior)
+                                        : flux_marginal(da, db[0], cc, gc.flux_prior);
+                } else {
+                    double bb;
+                    if (fp32_norm) slg[pr] = position_marginal_ff<NJ>(da, bh, bl, cc, gc.flux_prior, bb);
+                    else slg[pr] = position_marginal<NJ>(da, db, cc, gc.flux_prior, bb);
+                    sb[pr] = bb;
                 }
             }
         }
@@ -1435,20 +1392,195 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
         h = hn;
         ++level;
     }
-    if (level > 0 && threadIdx.x == 0) {
-        int flag = res.bad ? RLF_FLAG_BAD : 0;
-        if (S.invalid) flag |= RLF_FLAG_INVALID;
-        const int o = out_offset + s;
-        out.e1[o] = res.e1m;
-        out.e2[o] = res.e2m;
-        out.sig1[o] = res.sd1;
-        out.sig2[o] = res.sd2;
-        out.alpha_arcsec[o] = res.am;
-        out.flux_jy[o] = res.flux;
-        out.e1_smooth[o] = res.e1s;
-        out.e2_smooth[o] = res.e2s;
-        out.flag[o] = flag | (level << RLF_FLAG_LEVELS_SHIFT);
+    if (level > 0 && threadIdx.x == 0) write_adapt_result(res, S, level, s, out, out_offset);
+}
+
+// The FP32 form with one position (the common case) as a cluster of kAdaptR CTAs per
+// facet (facets in the grid fit's order, most cells first), so that the serial levels of a facet with many cells spread over several
+// SMs.  Rank r sums the (sample, alpha) pairs of the current lattice over its share of
+// the facet's 128-cell tiles (the tiles cut as in the grid's parts), four scalelength
+// nodes per thread with the quadratic form of a cell once for them (two nodes per
+// paired FP32 instruction; tile sums added to float pairs), and stores its partial a,
+// b per pair (FP64) in the facet's scratch.  The leader (rank 0) runs the estimate: it
+// adds the ranks' partials in rank order, forms ln L, estimates over the samples and
+// writes the next lattice to the scratch.  Hardware cluster barriers order the steps
+// (no polling).  Scratch per facet (adapt_doubles_per_facet): ln L, a, b [kAdaptMax][na];
+// partial a, b [kAdaptRanks >= kAdaptR][kAdaptMax][na][2]; lattice e1, e2 [kAdaptMax]; control words.
+template <bool kGauss>
+__global__ void __cluster_dims__(kAdaptR, 1, 1) __launch_bounds__(kATc, 2048 / kATc / 4)
+adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restrict__ ncell,
+                        const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst gc,
+                        const double *__restrict__ ga, const double *__restrict__ gb, const double *__restrict__ gl,
+                        const double *__restrict__ ccv, const int32_t *__restrict__ order,
+                        double *__restrict__ scratch, rlf_fit_out out, int32_t out_offset)
+{
+    namespace cg = cooperative_groups;
+    const cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const bool leader = rank == 0;
+    const bool split = gc.split != 0;   // FP32 logarithms, error functions and exponentials in split mode
+    __shared__ float sm[5][kCellTile];
+    __shared__ double qp[64], alph[64], lnp[64];
+    __shared__ double Ls[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
+    __shared__ double As[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
+    __shared__ double e1s[kAdaptMax], e2s[kAdaptMax];
+    __shared__ AdaptResult res;
+    const int s = order[blockIdx.x / kAdaptR];   // facets with the most cells first
+    const int ne = gc.n_e, na = gc.n_alpha;
+    const size_t ng = (size_t)ne * ne * na;
+    const SrcRow S = table[s];
+    const int nc = ncell[s];
+    const double cc = ccv[s];
+    double *slg = scratch + (size_t)s * adapt_doubles_per_facet(na);
+    double *sa = slg + (size_t)kAdaptMax * na, *sb = sa + (size_t)kAdaptMax * na;
+    double *part = sb + (size_t)kAdaptMax * na;                      // [rank][pair][2]
+    double *lat = part + (size_t)kAdaptRanks * kAdaptMax * na * 2;   // e1 [kAdaptMax], e2 [kAdaptMax]
+    int *ctl = reinterpret_cast<int *>(lat + 2 * kAdaptMax);         // samples of the next lattice (0: done)
+    // this rank's tiles of the facet's cells
+    const int n_tiles = (nc + kCellTile - 1) / kCellTile;
+    const int c_begin = (int)((int64_t)n_tiles * rank / kAdaptR) * kCellTile;
+    const int c_end = min(nc, (int)((int64_t)n_tiles * (rank + 1) / kAdaptR) * kCellTile);
+    alpha_weights(gc, S, qp, alph, lnp);
+    __syncthreads();
+    double h = 2.0 * gc.e_max / (ne - 1);
+    int level = 0;
+    if (leader) {
+        // level 0: the grid
+        estimate_over_samples<kATc>(split, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp,
+                                    alph, lnp, Ls, As, res);
+        if (threadIdx.x == 0) {
+            const bool more = res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0;
+            const int np = more ? plan_lattice(gc, res, level, h, e1s, e2s) : 0;
+            for (int i = 0; i < np; ++i) {
+                lat[i] = e1s[i];
+                lat[kAdaptMax + i] = e2s[i];
+            }
+            ctl[0] = np;
+        }
     }
+    constexpr int kAG = 4;
+    const int n_ag = (na + kAG - 1) / kAG;
+    const f32x2 one2 = pk2(1.0f, 1.0f), zero2 = pk2(0.0f, 0.0f);
+    const float *cu = cells + (size_t)s * NN;
+    for (;;) {
+        __threadfence();
+        cluster.sync();
+        const int np = *reinterpret_cast<volatile int *>(ctl);
+        if (np == 0) break;
+        if (!leader) {
+            for (int i = threadIdx.x; i < np; i += kATc) {
+                e1s[i] = lat[i];
+                e2s[i] = lat[kAdaptMax + i];
+            }
+            __syncthreads();
+        }
+        // this rank's partial sums of every (sample, alpha) pair
+        for (int base = 0; base < np * n_ag; base += kATc) {
+            const int it = base + threadIdx.x;
+            const bool on = it < np * n_ag;
+            const int i = on ? it / n_ag : 0, g = on ? it % n_ag : 0;
+            const double e1 = e1s[i], e2 = e2s[i];
+            const double det = 1.0 - e1 * e1 - e2 * e2;
+            const double id2 = 1.0 / (det * det);
+            const float p11 = (float)(((1.0 + e1) * (1.0 + e1) + e2 * e2) * id2);
+            const float p12 = (float)(4.0 * e2 * id2);
+            const float p22 = (float)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
+            float cak[kAG];
+#pragma unroll
+            for (int j = 0; j < kAG; ++j) {
+                const int k = g * kAG + j;
+                const double alr = (k < na ? alph[k] : 0.0) * kArcsec * S.du;
+                cak[j] = (float)(4.0 * kPi * kPi * alr * alr) * (kGauss ? -0.25f : 1.0f);
+            }
+            const f32x2 c2[2] = {pk2(cak[0], cak[1]), pk2(cak[2], cak[3])};
+            float ah[kAG], al[kAG], bh[kAG], bl[kAG];
+#pragma unroll
+            for (int j = 0; j < kAG; ++j) ah[j] = al[j] = bh[j] = bl[j] = 0.0f;
+            for (int c0 = c_begin; c0 < c_end; c0 += kCellTile) {
+                const int nt = min(kCellTile, c_end - c0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < nt; j += kATc) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) sm[q][j] = cu[q * plane + c0 + j];
+                }
+                __syncthreads();
+                if (!on) continue;
+                f32x2 pa2[2] = {zero2, zero2}, pb2[2] = {zero2, zero2};
+                for (int c = 0; c < nt; ++c) {
+                    const float Q = p11 * sm[0][c] + p12 * sm[1][c] + p22 * sm[2][c];
+                    const f32x2 Q2 = pk2(Q, Q), A2 = pk2(sm[3][c], sm[3][c]), B2 = pk2(sm[4][c], sm[4][c]);
+#pragma unroll
+                    for (int j2 = 0; j2 < 2; ++j2) {
+                        float x0, x1;
+                        f32x2 M2;
+                        if (kGauss) {
+                            up2(mul2(c2[j2], Q2), x0, x1);
+                            M2 = pk2(ex2_approx(x0), ex2_approx(x1));
+                        } else {
+                            up2(fma2(c2[j2], Q2, one2), x0, x1);
+                            const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
+                            M2 = mul2(mul2(r2, r2), r2);
+                        }
+                        pa2[j2] = fma2(mul2(A2, M2), M2, pa2[j2]);
+                        pb2[j2] = fma2(B2, M2, pb2[j2]);
+                    }
+                }
+#pragma unroll
+                for (int j2 = 0; j2 < 2; ++j2) {
+                    float a0, a1, b0, b1;
+                    up2(pa2[j2], a0, a1);
+                    up2(pb2[j2], b0, b1);
+                    acc_add(split, ah[2 * j2], al[2 * j2], a0);
+                    acc_add(split, ah[2 * j2 + 1], al[2 * j2 + 1], a1);
+                    acc_add(split, bh[2 * j2], bl[2 * j2], b0);
+                    acc_add(split, bh[2 * j2 + 1], bl[2 * j2 + 1], b1);
+                }
+            }
+            if (on) {
+#pragma unroll
+                for (int j = 0; j < kAG; ++j) {
+                    const int k = g * kAG + j;
+                    if (k >= na) break;
+                    double *pp = part + ((size_t)rank * kAdaptMax * na + (size_t)i * na + k) * 2;
+                    pp[0] = acc_value(split, ah[j], al[j]);
+                    pp[1] = acc_value(split, bh[j], bl[j]);
+                }
+            }
+        }
+        __threadfence();
+        cluster.sync();
+        if (leader) {
+            // the pairs' a and b (partials added in rank order) and ln L, then the estimate
+            for (int pr = threadIdx.x; pr < np * na; pr += kATc) {
+                double da = 0.0, db = 0.0;
+#pragma unroll
+                for (int r = 0; r < kAdaptR; ++r) {
+                    const double *pp = part + ((size_t)r * kAdaptMax * na + pr) * 2;
+                    da += pp[0];
+                    db += pp[1];
+                }
+                sa[pr] = da;
+                sb[pr] = db;
+                slg[pr] = split ? flux_marginal_mixed(da, db, cc, gc.flux_prior)
+                                : flux_marginal(da, db, cc, gc.flux_prior);
+            }
+            __threadfence_block();
+            __syncthreads();
+            estimate_over_samples<kATc>(split, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
+            ++level;
+            if (threadIdx.x == 0) {
+                const bool more = res.kept < gc.np_max && 0.5 * h > gc.e_res && res.map_i >= 0;
+                const int np2 = more ? plan_lattice(gc, res, level, 0.5 * h, e1s, e2s) : 0;
+                for (int i = 0; i < np2; ++i) {
+                    lat[i] = e1s[i];
+                    lat[kAdaptMax + i] = e2s[i];
+                }
+                ctl[0] = np2;
+            }
+            h *= 0.5;
+        }
+    }
+    if (leader && level > 0 && threadIdx.x == 0) write_adapt_result(res, S, level, s, out, out_offset);
 }
 
 }  // namespace
@@ -1533,9 +1665,15 @@ cudaError_t launch_adaptive_nj(const T *cells, const SrcRow *table, size_t plane
                                const GridConst &gc, const Workspace &ws, const rlf_fit_out &out, int32_t out_offset,
                                cudaStream_t st)
 {
-    auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? adaptive_kernel<T, true, NJ> : adaptive_kernel<T, false, NJ>;
-    kern<<<count, kAT, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc, ws.adapt, out,
-                                     out_offset);
+    if constexpr (std::is_same<T, float>::value && NJ == 1) {
+        auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? adaptive_cluster_kernel<true> : adaptive_cluster_kernel<false>;
+        kern<<<count * kAdaptR, kATc, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc,
+                                               ws.order, ws.adapt, out, out_offset);
+    } else {
+        auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? adaptive_kernel<T, true, NJ> : adaptive_kernel<T, false, NJ>;
+        kern<<<count, kAT, 0, st>>>(cells, ws.ncell, table, plane, NN, gc, ws.ga, ws.gb, ws.gl, ws.cc, ws.adapt, out,
+                                    out_offset);
+    }
     return cudaGetLastError();
 }
 
