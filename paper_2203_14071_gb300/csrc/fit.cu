@@ -1218,7 +1218,8 @@ __device__ void alpha_weights(const GridConst &gc, const SrcRow &S, double *qp, 
 // The next lattice (one thread): every multiple of hn = h / 2 in the box of the kept
 // samples widened by h, |e| < 1, at most kAdaptSide per component around the MAP
 // sample; returns the number of samples written to e1s, e2s.
-__device__ int plan_lattice(const GridConst &gc, const AdaptResult &res, int level, double h, double *e1s, double *e2s)
+__device__ int plan_lattice(const GridConst &gc, const AdaptResult &res, int level, double h, double *e1s, double *e2s,
+                            short *i1s = nullptr, short *i2s = nullptr, int *lo_out = nullptr, int *hi_out = nullptr)
 {
     const int ne = gc.n_e;
     const double hn = 0.5 * h;
@@ -1241,8 +1242,18 @@ __device__ int plan_lattice(const GridConst &gc, const AdaptResult &res, int lev
             if (!(a1 * a1 + a2 * a2 < 1.0)) continue;
             e1s[np] = a1;
             e2s[np] = a2;
+            if (i1s) {
+                i1s[np] = (short)i1;
+                i2s[np] = (short)i2;
+            }
             ++np;
         }
+    if (lo_out) {
+        lo_out[0] = lo[0];
+        lo_out[1] = lo[1];
+        hi_out[0] = hi[0];
+        hi_out[1] = hi[1];
+    }
     return np;
 }
 
@@ -1396,16 +1407,20 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
 }
 
 // The FP32 form with one position (the common case) as a cluster of kAdaptR CTAs per
-// facet (facets in the grid fit's order, most cells first), so that the serial levels of a facet with many cells spread over several
-// SMs.  Rank r sums the (sample, alpha) pairs of the current lattice over its share of
-// the facet's 128-cell tiles (the tiles cut as in the grid's parts), four scalelength
-// nodes per thread with the quadratic form of a cell once for them (two nodes per
-// paired FP32 instruction; tile sums added to float pairs), and stores its partial a,
-// b per pair (FP64) in the facet's scratch.  The leader (rank 0) runs the estimate: it
-// adds the ranks' partials in rank order, forms ln L, estimates over the samples and
-// writes the next lattice to the scratch.  Hardware cluster barriers order the steps
-// (no polling).  Scratch per facet (adapt_doubles_per_facet): ln L, a, b [kAdaptMax][na];
-// partial a, b [kAdaptRanks >= kAdaptR][kAdaptMax][na][2]; lattice e1, e2 [kAdaptMax]; control words.
+// facet (facets in the grid fit's order, most cells first), so that the serial levels
+// of a facet with many cells spread over several SMs.  Rank r sums the lattice's new
+// (sample, alpha) pairs over its share of the facet's 128-cell tiles (the tiles cut as
+// in the grid's parts), four scalelength nodes per thread with the quadratic form of
+// a cell once for them (two nodes per paired FP32 instruction; tile sums added to
+// float pairs), and stores its partial a, b per pair (FP64) in the facet's scratch.
+// The leader (rank 0) runs the estimate: it adds the ranks' partials in rank order,
+// forms ln L, estimates over the samples and writes the next lattice.  A sample the
+// lattice shares with the previous one (even multiples of the new step: the same e
+// bit for bit, hence the same sums) is not evaluated again; the leader copies its a,
+// b and ln L.  Hardware cluster barriers order the steps (no polling).  Scratch per
+// facet (adapt_doubles_per_facet): ln L, a, b [2 levels][kAdaptMax][na]; partial a, b
+// [kAdaptRanks >= kAdaptR][kAdaptMax][na][2]; lattice e1, e2 [kAdaptMax]; the samples
+// to evaluate [kAdaptMax] (int); control words.
 template <bool kGauss>
 __global__ void __cluster_dims__(kAdaptR, 1, 1) __launch_bounds__(kATc, 2048 / kATc / 4)
 adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restrict__ ncell,
@@ -1424,18 +1439,23 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
     __shared__ double Ls[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
     __shared__ double As[kMaxNe * kMaxNe > kAdaptMax ? kMaxNe * kMaxNe : kAdaptMax];
     __shared__ double e1s[kAdaptMax], e2s[kAdaptMax];
+    __shared__ int elist[kAdaptMax];                 // samples to evaluate
+    __shared__ short li1[kAdaptMax], li2[kAdaptMax];   // leader: integer coordinates of the samples
+    __shared__ short src[kAdaptMax];                 // leader: the previous lattice's sample, or -1
+    __shared__ short pmap[kAdaptMax];                // leader: the lattice's box -> sample (-1: |e| >= 1)
+    __shared__ int plo[2], pw;                       // leader: that box's origin and e2 width
     __shared__ AdaptResult res;
     const int s = order[blockIdx.x / kAdaptR];   // facets with the most cells first
     const int ne = gc.n_e, na = gc.n_alpha;
-    const size_t ng = (size_t)ne * ne * na;
+    const size_t ng = (size_t)ne * ne * na, nsa = (size_t)kAdaptMax * na;
     const SrcRow S = table[s];
     const int nc = ncell[s];
     const double cc = ccv[s];
-    double *slg = scratch + (size_t)s * adapt_doubles_per_facet(na);
-    double *sa = slg + (size_t)kAdaptMax * na, *sb = sa + (size_t)kAdaptMax * na;
-    double *part = sb + (size_t)kAdaptMax * na;                      // [rank][pair][2]
-    double *lat = part + (size_t)kAdaptRanks * kAdaptMax * na * 2;   // e1 [kAdaptMax], e2 [kAdaptMax]
-    int *ctl = reinterpret_cast<int *>(lat + 2 * kAdaptMax);         // samples of the next lattice (0: done)
+    double *base = scratch + (size_t)s * adapt_doubles_per_facet(na);   // ln L, a, b of two levels
+    double *part = base + 6 * nsa;                                      // [rank][pair][2]
+    double *lat = part + (size_t)kAdaptRanks * nsa * 2;                 // e1 [kAdaptMax], e2 [kAdaptMax]
+    int *glist = reinterpret_cast<int *>(lat + 2 * kAdaptMax);          // samples to evaluate [kAdaptMax]
+    int *ctl = glist + kAdaptMax;                                       // samples, samples to evaluate
     // this rank's tiles of the facet's cells
     const int n_tiles = (nc + kCellTile - 1) / kCellTile;
     const int c_begin = (int)((int64_t)n_tiles * rank / kAdaptR) * kCellTile;
@@ -1444,19 +1464,43 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
     __syncthreads();
     double h = 2.0 * gc.e_max / (ne - 1);
     int level = 0;
+    // the next lattice from the estimate `res` of level `level` at step h (leader, one
+    // thread): samples, which of them the previous lattice holds, the list to evaluate
+    auto plan = [&](bool more) {
+        int lo[2] = {0, 0}, hi[2] = {-1, -1};
+        const int np = more ? plan_lattice(gc, res, level, h, e1s, e2s, li1, li2, lo, hi) : 0;
+        int n_eval = 0;
+        for (int i = 0; i < np; ++i) {
+            int from = -1;
+            if (level >= 1 && (li1[i] & 1) == 0 && (li2[i] & 1) == 0) {
+                const int j1 = li1[i] / 2 - plo[0], j2 = li2[i] / 2 - plo[1];
+                if (j1 >= 0 && j2 >= 0 && j2 < pw && j1 * pw + j2 < kAdaptMax && (j1 + 1) * pw <= kAdaptMax)
+                    from = pmap[j1 * pw + j2];
+            }
+            src[i] = (short)from;
+            if (from < 0) elist[n_eval++] = i;
+            lat[i] = e1s[i];
+            lat[kAdaptMax + i] = e2s[i];
+        }
+        for (int i = 0; i < n_eval; ++i) glist[i] = elist[i];
+        // this lattice's box -> sample map, for the next level (at most kAdaptSide per side)
+        plo[0] = lo[0];
+        plo[1] = lo[1];
+        pw = hi[1] - lo[1] + 1;
+        const int cells_box = (hi[0] - lo[0] + 1) * pw;
+        for (int i = 0; i < kAdaptMax; ++i) pmap[i] = -1;
+        if (cells_box <= kAdaptMax)
+            for (int i = 0; i < np; ++i) pmap[(li1[i] - lo[0]) * pw + (li2[i] - lo[1])] = (short)i;
+        else
+            pw = 0;   // no map (cannot happen: both sides are at most kAdaptSide)
+        ctl[0] = np;
+        ctl[1] = n_eval;
+    };
     if (leader) {
         // level 0: the grid
         estimate_over_samples<kATc>(split, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp,
                                     alph, lnp, Ls, As, res);
-        if (threadIdx.x == 0) {
-            const bool more = res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0;
-            const int np = more ? plan_lattice(gc, res, level, h, e1s, e2s) : 0;
-            for (int i = 0; i < np; ++i) {
-                lat[i] = e1s[i];
-                lat[kAdaptMax + i] = e2s[i];
-            }
-            ctl[0] = np;
-        }
+        if (threadIdx.x == 0) plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0);
     }
     constexpr int kAG = 4;
     const int n_ag = (na + kAG - 1) / kAG;
@@ -1465,20 +1509,22 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
     for (;;) {
         __threadfence();
         cluster.sync();
-        const int np = *reinterpret_cast<volatile int *>(ctl);
+        const int np = reinterpret_cast<volatile int *>(ctl)[0];
+        const int n_eval = reinterpret_cast<volatile int *>(ctl)[1];
         if (np == 0) break;
         if (!leader) {
             for (int i = threadIdx.x; i < np; i += kATc) {
                 e1s[i] = lat[i];
                 e2s[i] = lat[kAdaptMax + i];
             }
-            __syncthreads();
+            for (int i = threadIdx.x; i < n_eval; i += kATc) elist[i] = glist[i];
         }
-        // this rank's partial sums of every (sample, alpha) pair
-        for (int base = 0; base < np * n_ag; base += kATc) {
-            const int it = base + threadIdx.x;
-            const bool on = it < np * n_ag;
-            const int i = on ? it / n_ag : 0, g = on ? it % n_ag : 0;
+        __syncthreads();
+        // this rank's partial sums of every new (sample, alpha) pair
+        for (int b0 = 0; b0 < n_eval * n_ag; b0 += kATc) {
+            const int it = b0 + threadIdx.x;
+            const bool on = it < n_eval * n_ag;
+            const int i = on ? elist[it / n_ag] : 0, g = on ? it % n_ag : 0;
             const double e1 = e1s[i], e2 = e2s[i];
             const double det = 1.0 - e1 * e1 - e2 * e2;
             const double id2 = 1.0 / (det * det);
@@ -1527,13 +1573,13 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
                 }
 #pragma unroll
                 for (int j2 = 0; j2 < 2; ++j2) {
-                    float a0, a1, b0, b1;
+                    float a0, a1, b0v, b1v;
                     up2(pa2[j2], a0, a1);
-                    up2(pb2[j2], b0, b1);
+                    up2(pb2[j2], b0v, b1v);
                     acc_add(split, ah[2 * j2], al[2 * j2], a0);
                     acc_add(split, ah[2 * j2 + 1], al[2 * j2 + 1], a1);
-                    acc_add(split, bh[2 * j2], bl[2 * j2], b0);
-                    acc_add(split, bh[2 * j2 + 1], bl[2 * j2 + 1], b1);
+                    acc_add(split, bh[2 * j2], bl[2 * j2], b0v);
+                    acc_add(split, bh[2 * j2 + 1], bl[2 * j2 + 1], b1v);
                 }
             }
             if (on) {
@@ -1541,7 +1587,7 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
                 for (int j = 0; j < kAG; ++j) {
                     const int k = g * kAG + j;
                     if (k >= na) break;
-                    double *pp = part + ((size_t)rank * kAdaptMax * na + (size_t)i * na + k) * 2;
+                    double *pp = part + ((size_t)rank * nsa + (size_t)i * na + k) * 2;
                     pp[0] = acc_value(split, ah[j], al[j]);
                     pp[1] = acc_value(split, bh[j], bl[j]);
                 }
@@ -1550,12 +1596,25 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
         __threadfence();
         cluster.sync();
         if (leader) {
-            // the pairs' a and b (partials added in rank order) and ln L, then the estimate
+            // the pairs' a and b (partials added in rank order, or the previous level's
+            // values of a shared sample) and ln L, then the estimate
+            const int cur = (level + 1) & 1;
+            double *slg = base + (size_t)cur * 3 * nsa, *sa = slg + nsa, *sb = sa + nsa;
+            const double *plg = base + (size_t)(cur ^ 1) * 3 * nsa, *pa = plg + nsa, *pb = pa + nsa;
             for (int pr = threadIdx.x; pr < np * na; pr += kATc) {
+                const int i = pr / na, k = pr % na;
+                const int from = src[i];
+                if (from >= 0) {
+                    const size_t q = (size_t)from * na + k;
+                    slg[pr] = plg[q];
+                    sa[pr] = pa[q];
+                    sb[pr] = pb[q];
+                    continue;
+                }
                 double da = 0.0, db = 0.0;
 #pragma unroll
                 for (int r = 0; r < kAdaptR; ++r) {
-                    const double *pp = part + ((size_t)r * kAdaptMax * na + pr) * 2;
+                    const double *pp = part + ((size_t)r * nsa + pr) * 2;
                     da += pp[0];
                     db += pp[1];
                 }
@@ -1568,16 +1627,8 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
             __syncthreads();
             estimate_over_samples<kATc>(split, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
             ++level;
-            if (threadIdx.x == 0) {
-                const bool more = res.kept < gc.np_max && 0.5 * h > gc.e_res && res.map_i >= 0;
-                const int np2 = more ? plan_lattice(gc, res, level, 0.5 * h, e1s, e2s) : 0;
-                for (int i = 0; i < np2; ++i) {
-                    lat[i] = e1s[i];
-                    lat[kAdaptMax + i] = e2s[i];
-                }
-                ctl[0] = np2;
-            }
             h *= 0.5;
+            if (threadIdx.x == 0) plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0);
         }
     }
     if (leader && level > 0 && threadIdx.x == 0) write_adapt_result(res, S, level, s, out, out_offset);

@@ -23,11 +23,12 @@ constexpr int kCellTile = 128;                           // facet cells staged p
 constexpr int kMaxNe = 32;                               // grid nodes per e component (estimator smem)
 constexpr int kAdaptSide = 17, kAdaptMax = kAdaptSide * kAdaptSide;  // adaptive lattice: per component, samples
 constexpr int kAdaptRanks = 4;                           // partial sums per sample in the clustered adaptive sampler
-// adaptive-sampling scratch per facet (doubles): ln L, a, b per (sample, alpha); the
-// cluster ranks' partial a, b; the lattice; control words
+// adaptive-sampling scratch per facet (doubles): ln L, a, b per (sample, alpha) of two
+// levels; the cluster ranks' partial a, b; the lattice; the samples to evaluate (int);
+// control words
 __host__ __device__ inline size_t adapt_doubles_per_facet(int n_alpha)
 {
-    return (size_t)kAdaptMax * n_alpha * (3 + 2 * kAdaptRanks) + 2 * kAdaptMax + 8;
+    return (size_t)kAdaptMax * n_alpha * (6 + 2 * kAdaptRanks) + 2 * kAdaptMax + (kAdaptMax + 1) / 2 + 8;
 }
 constexpr int kMaxPartials = 8192;                       // (source, part) partial facets per extraction batch
 constexpr int kPartialsPerSource = 64;                  // workspace partials per source below kMaxPartials
