@@ -1215,6 +1215,29 @@ __device__ void alpha_weights(const GridConst &gc, const SrcRow &S, double *qp, 
     }
 }
 
+// exclusive prefix sum over the NT threads of a block, in thread order; *total gets
+// the sum (scratch: NT / 32 + 1 ints)
+template <int NT>
+__device__ int block_exclusive_scan(int x, int *scratch, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[wid] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+        if (w < wid) before += scratch[w];
+        all += scratch[w];
+    }
+    *total = all;
+    return before + incl - x;
+}
+
 // The next lattice (one thread): every multiple of hn = h / 2 in the box of the kept
 // samples widened by h, |e| < 1, at most kAdaptSide per component around the MAP
 // sample; returns the number of samples written to e1s, e2s.
@@ -1444,6 +1467,7 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
     __shared__ short src[kAdaptMax];                 // leader: the previous lattice's sample, or -1
     __shared__ short pmap[kAdaptMax];                // leader: the lattice's box -> sample (-1: |e| >= 1)
     __shared__ int plo[2], pw;                       // leader: that box's origin and e2 width
+    __shared__ int box_lo[2], box_hi[2], scan_tmp[kATc / 32 + 1];
     __shared__ AdaptResult res;
     const int s = order[blockIdx.x / kAdaptR];   // facets with the most cells first
     const int ne = gc.n_e, na = gc.n_alpha;
@@ -1464,43 +1488,109 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
     __syncthreads();
     double h = 2.0 * gc.e_max / (ne - 1);
     int level = 0;
-    // the next lattice from the estimate `res` of level `level` at step h (leader, one
-    // thread): samples, which of them the previous lattice holds, the list to evaluate
+    // The next lattice from the estimate `res` of level `level` at step h (every thread
+    // of the leader): the samples of plan_lattice in its order (e1 outer, e2 inner), which
+    // of them the previous lattice holds, the list to evaluate.  Candidates of the box
+    // are split over the threads in order and placed by a prefix sum.
+    constexpr int kPer = (kAdaptMax + kATc - 1) / kATc;   // candidates per thread
     auto plan = [&](bool more) {
-        int lo[2] = {0, 0}, hi[2] = {-1, -1};
-        const int np = more ? plan_lattice(gc, res, level, h, e1s, e2s, li1, li2, lo, hi) : 0;
-        int n_eval = 0;
-        for (int i = 0; i < np; ++i) {
-            int from = -1;
-            if (level >= 1 && (li1[i] & 1) == 0 && (li2[i] & 1) == 0) {
-                const int j1 = li1[i] / 2 - plo[0], j2 = li2[i] / 2 - plo[1];
-                if (j1 >= 0 && j2 >= 0 && j2 < pw && j1 * pw + j2 < kAdaptMax && (j1 + 1) * pw <= kAdaptMax)
-                    from = pmap[j1 * pw + j2];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int lo[2] = {0, 0}, hi[2] = {-1, -1};
+            if (more) {
+                // the box as plan_lattice makes it (the centre read before e1s, e2s change)
+                const double hn = 0.5 * h;
+                const double cen[2] = {level == 0 ? grid_e(gc, res.map_i / ne) : e1s[res.map_i],
+                                       level == 0 ? grid_e(gc, res.map_i % ne) : e2s[res.map_i]};
+                for (int d = 0; d < 2; ++d) {
+                    lo[d] = (int)ceil((res.box[2 * d] - h) / hn - 1e-9);
+                    hi[d] = (int)floor((res.box[2 * d + 1] + h) / hn + 1e-9);
+                    if (hi[d] - lo[d] + 1 > kAdaptSide) {
+                        const int c = (int)llround(cen[d] / hn);
+                        lo[d] = c - kAdaptSide / 2;
+                        hi[d] = c + kAdaptSide / 2;
+                    }
+                }
             }
-            src[i] = (short)from;
-            if (from < 0) elist[n_eval++] = i;
-            lat[i] = e1s[i];
-            lat[kAdaptMax + i] = e2s[i];
+            box_lo[0] = lo[0];
+            box_lo[1] = lo[1];
+            box_hi[0] = hi[0];
+            box_hi[1] = hi[1];
         }
-        for (int i = 0; i < n_eval; ++i) glist[i] = elist[i];
-        // this lattice's box -> sample map, for the next level (at most kAdaptSide per side)
-        plo[0] = lo[0];
-        plo[1] = lo[1];
-        pw = hi[1] - lo[1] + 1;
-        const int cells_box = (hi[0] - lo[0] + 1) * pw;
-        for (int i = 0; i < kAdaptMax; ++i) pmap[i] = -1;
-        if (cells_box <= kAdaptMax)
-            for (int i = 0; i < np; ++i) pmap[(li1[i] - lo[0]) * pw + (li2[i] - lo[1])] = (short)i;
-        else
-            pw = 0;   // no map (cannot happen: both sides are at most kAdaptSide)
-        ctl[0] = np;
-        ctl[1] = n_eval;
+        __syncthreads();
+        const double hn = 0.5 * h;
+        const int w2 = box_hi[1] - box_lo[1] + 1;
+        const int total = (box_hi[0] - box_lo[0] + 1) * w2;   // at most kAdaptMax
+        // this thread's candidates, kept when |e| < 1
+        bool keep[kPer];
+        int n_keep = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int c = threadIdx.x * kPer + q;
+            keep[q] = false;
+            if (c < total) {
+                const double a1 = (box_lo[0] + c / w2) * hn, a2 = (box_lo[1] + c % w2) * hn;
+                keep[q] = a1 * a1 + a2 * a2 < 1.0;
+            }
+            n_keep += keep[q] ? 1 : 0;
+        }
+        int np;
+        int pos = block_exclusive_scan<kATc>(n_keep, scan_tmp, &np);
+        // place the samples; find each one in the previous lattice's map
+        int n_new = 0;
+        int from_q[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            from_q[q] = -1;
+            if (!keep[q]) continue;
+            const int c = threadIdx.x * kPer + q;
+            const int i1 = box_lo[0] + c / w2, i2 = box_lo[1] + c % w2;
+            e1s[pos] = i1 * hn;
+            e2s[pos] = i2 * hn;
+            li1[pos] = (short)i1;
+            li2[pos] = (short)i2;
+            if (level >= 1 && (i1 & 1) == 0 && (i2 & 1) == 0) {
+                const int j1 = i1 / 2 - plo[0], j2 = i2 / 2 - plo[1];
+                if (j1 >= 0 && j2 >= 0 && j2 < pw && (j1 + 1) * pw <= kAdaptMax) from_q[q] = pmap[j1 * pw + j2];
+            }
+            src[pos] = (short)from_q[q];
+            n_new += from_q[q] < 0 ? 1 : 0;
+            ++pos;
+        }
+        int n_eval;
+        int epos = block_exclusive_scan<kATc>(n_new, scan_tmp, &n_eval);
+        pos -= n_keep;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            if (!keep[q]) continue;
+            if (from_q[q] < 0) {
+                elist[epos] = pos;
+                glist[epos] = pos;
+                ++epos;
+            }
+            lat[pos] = e1s[pos];
+            lat[kAdaptMax + pos] = e2s[pos];
+            ++pos;
+        }
+        __syncthreads();
+        // this lattice's box -> sample map, for the next level (the box is at most
+        // kAdaptSide per side, so it fits)
+        for (int i = threadIdx.x; i < kAdaptMax; i += kATc) pmap[i] = -1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < np; i += kATc) pmap[(li1[i] - box_lo[0]) * w2 + (li2[i] - box_lo[1])] = (short)i;
+        if (threadIdx.x == 0) {
+            plo[0] = box_lo[0];
+            plo[1] = box_lo[1];
+            pw = w2;
+            ctl[0] = np;
+            ctl[1] = n_eval;
+        }
     };
     if (leader) {
         // level 0: the grid
         estimate_over_samples<kATc>(split, ne * ne, nullptr, nullptr, gl + s * ng, ga + s * ng, gb + s * ng, gc, qp,
                                     alph, lnp, Ls, As, res);
-        if (threadIdx.x == 0) plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0);
+        plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0 && nc > 0);
     }
     constexpr int kAG = 4;
     const int n_ag = (na + kAG - 1) / kAG;
@@ -1628,7 +1718,7 @@ adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restri
             estimate_over_samples<kATc>(split, np, e1s, e2s, slg, sa, sb, gc, qp, alph, lnp, Ls, As, res);
             ++level;
             h *= 0.5;
-            if (threadIdx.x == 0) plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0);
+            plan(res.kept < gc.np_max && h > gc.e_res && res.map_i >= 0);
         }
     }
     if (leader && level > 0 && threadIdx.x == 0) write_adapt_result(res, S, level, s, out, out_offset);
