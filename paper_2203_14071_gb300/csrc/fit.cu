@@ -610,27 +610,28 @@ __device__ void grid_tile_pos(int s, int tile, const T *__restrict__ cells, cons
     }
 }
 
-// grid_tile_pos in FP32 with two scalelength nodes per thread (n_pos <= 3): item
-// tile * kThreads + threadIdx.x is (e point, alpha nodes 2g and 2g + 1).  Each staged
-// cell's quadratic form, A and B_j row are read from shared memory once for both nodes,
-// which halves the shared-memory reads per evaluation (the broadcasts of the B rows
-// bound the one-node form); the two brightness values and every b_j update are paired
-// FP32 instructions.  The arithmetic of each node is the one-node form's, operation
-// for operation, so the results are the same bit for bit.
-template <int NJ, bool kGauss>
-__device__ void grid_tile_pos2(int s, int tile, const float *__restrict__ cells, const int32_t *__restrict__ ncell,
+// grid_tile_pos in FP32 with NODES scalelength nodes per thread (n_pos <= 3): item
+// tile * kThreads + threadIdx.x is (e point, alpha nodes NODES g .. NODES g + NODES - 1).
+// Each staged cell's quadratic form, A and B_j row are read from shared memory once for
+// all the nodes, which divides the shared-memory reads per evaluation by NODES (the
+// broadcasts of the B rows bound the one-node form); the brightness values and every
+// b_j update are paired FP32 instructions.  The arithmetic of each node is the one-node
+// form's, operation for operation, so the results are the same bit for bit.
+template <int NJ, int NODES, bool kGauss>
+__device__ void grid_tile_posn(int s, int tile, const float *__restrict__ cells, const int32_t *__restrict__ ncell,
                                const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst &gc,
                                const double *__restrict__ ccv, double *__restrict__ ga, double *__restrict__ gb,
                                double *__restrict__ gl)
 {
     constexpr int NB = (NJ + 3) / 4 * 4;            // B values per cell (b_stride)
     constexpr int NP = (NJ + 1) / 2;                // offset pairs
+    constexpr int NM = (NODES + 1) / 2;             // node pairs (the last one half used when NODES is odd)
     __shared__ __align__(16) float sg[kCellTile][4];
     __shared__ __align__(16) float sb[kCellTile][NB];
     const int item = tile * kThreads + threadIdx.x;
-    const int ne2 = gc.n_e * gc.n_e, na = gc.n_alpha, nag = (na + 1) / 2;
-    const int e_idx = item / nag, k0 = 2 * (item % nag);
-    const int nk = k0 + 1 < na ? 2 : 1;
+    const int ne2 = gc.n_e * gc.n_e, na = gc.n_alpha, nag = (na + NODES - 1) / NODES;
+    const int e_idx = item / nag, k0 = NODES * (item % nag);
+    const int nk = min(NODES, na - k0);
     const int i1 = e_idx / gc.n_e, i2 = e_idx % gc.n_e;
     bool on = e_idx < ne2;
     double e1 = 0.0, e2 = 0.0;
@@ -640,7 +641,9 @@ __device__ void grid_tile_pos2(int s, int tile, const float *__restrict__ cells,
         on = e1 * e1 + e2 * e2 < 1.0;
     }
     const double du = table[s].du;
-    float p11 = 0.0f, p12 = 0.0f, p22 = 0.0f, ca[2] = {0.0f, 0.0f};
+    float p11 = 0.0f, p12 = 0.0f, p22 = 0.0f, ca[2 * NM];
+#pragma unroll
+    for (int j = 0; j < 2 * NM; ++j) ca[j] = 0.0f;
     if (on) {
         const double det = 1.0 - e1 * e1 - e2 * e2;
         const double id2 = 1.0 / (det * det);
@@ -648,17 +651,24 @@ __device__ void grid_tile_pos2(int s, int tile, const float *__restrict__ cells,
         p12 = (float)(4.0 * e2 * id2);
         p22 = (float)(((1.0 - e1) * (1.0 - e1) + e2 * e2) * id2);
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < 2 * NM; ++j) {
             const double al = grid_alpha(gc, j < nk ? k0 + j : k0) * kArcsec * du;
             ca[j] = (float)(4.0 * kPi * kPi * al * al);
         }
     }
     // Gaussian profile: c2 carries -alpha-coefficient / 4 and M = 2^(c2 Q)
     const float cs = kGauss ? -0.25f : 1.0f;
-    const f32x2 c2 = pk2(cs * ca[0], cs * ca[1]), one2 = pk2(1.0f, 1.0f), zero2 = pk2(0.0f, 0.0f);
-    float ah[2] = {0.0f, 0.0f}, al[2] = {0.0f, 0.0f}, bh[2][NJ], bl[2][NJ];
+    f32x2 c2[NM];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) bh[0][j] = bl[0][j] = bh[1][j] = bl[1][j] = 0.0f;
+    for (int m = 0; m < NM; ++m) c2[m] = pk2(cs * ca[2 * m], cs * ca[2 * m + 1]);
+    const f32x2 one2 = pk2(1.0f, 1.0f), zero2 = pk2(0.0f, 0.0f);
+    float ah[NODES], al[NODES], bh[NODES][NJ], bl[NODES][NJ];
+#pragma unroll
+    for (int n = 0; n < NODES; ++n) {
+        ah[n] = al[n] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) bh[n][j] = bl[n][j] = 0.0f;
+    }
     const bool split = gc.split != 0;
     const int nc = ncell[s];
     const float *cu = cells + (size_t)s * NN;
@@ -673,58 +683,68 @@ __device__ void grid_tile_pos2(int s, int tile, const float *__restrict__ cells,
         }
         __syncthreads();
         if (!on) continue;
-        f32x2 pa2 = zero2, pb0[NP], pb1[NP];
+        f32x2 pa2[NM], pb[NODES][NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) pb0[q] = pb1[q] = zero2;
+        for (int m = 0; m < NM; ++m) pa2[m] = zero2;
+#pragma unroll
+        for (int n = 0; n < NODES; ++n)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) pb[n][q] = zero2;
 #pragma unroll 2
         for (int c = 0; c < nt; ++c) {
             const float4 g4 = *reinterpret_cast<const float4 *>(&sg[c][0]);
             const float Q = p11 * g4.x + p12 * g4.y + p22 * g4.z;
-            const f32x2 Q2 = pk2(Q, Q);
-            float x0, x1;
-            f32x2 M2;
-            if (kGauss) {
-                up2(mul2(c2, Q2), x0, x1);
-                M2 = pk2(ex2_approx(x0), ex2_approx(x1));
-            } else {
-                up2(fma2(c2, Q2, one2), x0, x1);
-                const f32x2 r2 = pk2(rsqrtf(x0), rsqrtf(x1));
-                M2 = mul2(mul2(r2, r2), r2);
+            const f32x2 Q2 = pk2(Q, Q), A2 = pk2(g4.w, g4.w);
+            f32x2 Mn[NODES];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                float x0, x1;
+                f32x2 M2;
+                if (kGauss) {
+                    up2(mul2(c2[m], Q2), x0, x1);
+                    M2 = pk2(ex2_approx(x0), 2 * m + 1 < NODES ? ex2_approx(x1) : 0.0f);
+                } else {
+                    up2(fma2(c2[m], Q2, one2), x0, x1);
+                    const f32x2 r2 = pk2(rsqrtf(x0), 2 * m + 1 < NODES ? rsqrtf(x1) : 0.0f);
+                    M2 = mul2(mul2(r2, r2), r2);
+                }
+                pa2[m] = fma2(mul2(A2, M2), M2, pa2[m]);
+                float m0, m1;
+                up2(M2, m0, m1);
+                Mn[2 * m] = pk2(m0, m0);
+                if (2 * m + 1 < NODES) Mn[2 * m + 1] = pk2(m1, m1);
             }
-            pa2 = fma2(mul2(pk2(g4.w, g4.w), M2), M2, pa2);
-            float m0, m1;
-            up2(M2, m0, m1);
-            const f32x2 M0 = pk2(m0, m0), M1 = pk2(m1, m1);
             const ulonglong2 *row = reinterpret_cast<const ulonglong2 *>(&sb[c][0]);
 #pragma unroll
             for (int q = 0; q < NB / 4; ++q) {
                 const ulonglong2 v = row[q];
-                pb0[2 * q] = fma2(v.x, M0, pb0[2 * q]);
-                pb1[2 * q] = fma2(v.x, M1, pb1[2 * q]);
-                if (2 * q + 1 < NP) {
-                    pb0[2 * q + 1] = fma2(v.y, M0, pb0[2 * q + 1]);
-                    pb1[2 * q + 1] = fma2(v.y, M1, pb1[2 * q + 1]);
+#pragma unroll
+                for (int n = 0; n < NODES; ++n) {
+                    pb[n][2 * q] = fma2(v.x, Mn[n], pb[n][2 * q]);
+                    if (2 * q + 1 < NP) pb[n][2 * q + 1] = fma2(v.y, Mn[n], pb[n][2 * q + 1]);
                 }
             }
         }
-        float a0, a1;
-        up2(pa2, a0, a1);
-        acc_add(split, ah[0], al[0], a0);
-        acc_add(split, ah[1], al[1], a1);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float b0, b1;
-            up2(pb0[q], b0, b1);
-            acc_add(split, bh[0][2 * q], bl[0][2 * q], b0);
-            if (2 * q + 1 < NJ) acc_add(split, bh[0][2 * q + 1], bl[0][2 * q + 1], b1);
-            up2(pb1[q], b0, b1);
-            acc_add(split, bh[1][2 * q], bl[1][2 * q], b0);
-            if (2 * q + 1 < NJ) acc_add(split, bh[1][2 * q + 1], bl[1][2 * q + 1], b1);
+        for (int m = 0; m < NM; ++m) {
+            float a0, a1;
+            up2(pa2[m], a0, a1);
+            acc_add(split, ah[2 * m], al[2 * m], a0);
+            if (2 * m + 1 < NODES) acc_add(split, ah[2 * m + 1], al[2 * m + 1], a1);
         }
+#pragma unroll
+        for (int n = 0; n < NODES; ++n)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float b0, b1;
+                up2(pb[n][q], b0, b1);
+                acc_add(split, bh[n][2 * q], bl[n][2 * q], b0);
+                if (2 * q + 1 < NJ) acc_add(split, bh[n][2 * q + 1], bl[n][2 * q + 1], b1);
+            }
     }
     if (e_idx >= ne2) return;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NODES; ++j) {
         if (j >= nk) break;
         const size_t g = ((size_t)s * ne2 + e_idx) * na + k0 + j;
         if (on && nc > 0) {
@@ -1021,6 +1041,7 @@ fit_persistent_kernel(const T *__restrict__ cells, const int32_t *__restrict__ n
 // on the marginal logL the tiles wrote.
 template <typename T, int NJ>
 constexpr bool kPos2 = std::is_same<T, float>::value && NJ <= 9;
+constexpr int kPosNodes = 3;   // scalelength nodes per thread in that form
 
 template <typename T, int NJ, bool kGauss>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -1040,7 +1061,8 @@ fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict
         if (item >= total) break;
         const int s = order[item / tiles_per_src];
         if constexpr (kPos2<T, NJ>)
-            grid_tile_pos2<NJ, kGauss>(s, item % tiles_per_src, cells, ncell, table, plane, NN, gc, ccv, ga, gb, gl);
+            grid_tile_posn<NJ, kPosNodes, kGauss>(s, item % tiles_per_src, cells, ncell, table, plane, NN, gc, ccv,
+                                                  ga, gb, gl);
         else
             grid_tile_pos<T, NJ, kGauss>(s, item % tiles_per_src, cells, ncell, table, plane, NN, gc, ccv, ga, gb,
                                          gl);
@@ -1835,7 +1857,7 @@ cudaError_t launch_persistent_pos(const T *cells, const SrcRow *table, size_t pl
                                   const GridConst &gc, const rlf_params &p, const Workspace &ws,
                                   const rlf_fit_out &out, int32_t out_offset, cudaStream_t st)
 {
-    const int pairs = gc.n_e * gc.n_e * (kPos2<T, NJ> ? (gc.n_alpha + 1) / 2 : gc.n_alpha);
+    const int pairs = gc.n_e * gc.n_e * (kPos2<T, NJ> ? (gc.n_alpha + kPosNodes - 1) / kPosNodes : gc.n_alpha);
     const int tiles = (pairs + kThreads - 1) / kThreads;
     auto kern = gc.profile == RLF_PROFILE_GAUSSIAN ? fit_persistent_pos_kernel<T, NJ, true>
                                                    : fit_persistent_pos_kernel<T, NJ, false>;
