@@ -6,7 +6,7 @@ the autotuner, the chain run as rlf_run and as a captured graph.
 Expected values come from tests/golden/batched_chain_oracle.json, written by
 make_batched_chain.py beside it (oracle only): every source's estimate and the final sky
 model at 300 sampled rows, for sigma = 1 uJy and for sigma at which the faintest source has
-SNR 10.  The data are rebuilt here the same way (the oracle's simulate_vis of the true sky
+SNR 10; at 1 uJy also each source's two best e nodes and their ln L gap, for near-ties.  The data are rebuilt here the same way (the oracle's simulate_vis of the true sky
 plus seeded noise, rounded to complex64) and checked against the stored fingerprint.
 """
 import json
@@ -51,22 +51,46 @@ def batched():
     return c, mk.true_data(c)
 
 
-def _check_estimates(res, est, n):
+def _check_estimates(res, est, n, top2=None, ge=None):
+    """Every source's estimate within 1e-4 of the oracle's, except a near-tie: at the
+    benchmark's noise (source SNR ~1e5) the posterior sits on one e node, and where the
+    two best nodes' ln L differ by less than the FP32 model's error (2e-6 of b^2/2a, the
+    scale of ln L) the GPU may take the second; it must then be exactly that node.
+    Returns the largest |de| of the others and the near-tie sources."""
     de = np.array([cases.est_matches(res, i, est[i]) for i in range(n)])
-    assert np.all(de <= 1e-4), (int(np.argmax(de)), float(de.max()))
+    ties = []
+    for i in np.flatnonzero(de > 1e-4):
+        assert top2 is not None, (int(i), float(de[i]))
+        best, second, gap, scale = top2[i]
+        j = int(second)
+        assert j >= 0 and gap <= 2e-6 * scale, (int(i), float(de[i]), gap, scale)
+        e1n, e2n = ge[j // len(ge)], ge[j % len(ge)]
+        assert abs(res["e1"][i] - e1n) < 1e-9 and abs(res["e2"][i] - e2n) < 1e-9, (int(i), res["e1"][i], e1n)
+        ties.append(int(i))
+    rest = np.delete(de, ties)
     # the bad-fit flag, except where the oracle's spread sits within 1e-6 of a cut
     sd1, sd2 = est[:, oracle.SIG1], est[:, oracle.SIG2]
     near = (np.abs(sd1 - 5e-3) < 1e-6 * 5e-3) | (np.abs(sd2 - 5e-3) < 1e-6 * 5e-3)
     same = ((res["flag"] & 1) != 0) == (est[:, oracle.FLAG] != 0)
     assert np.all(same | near), np.flatnonzero(~(same | near))[:10]
-    return float(de.max())
+    return float(rest.max()), ties
 
 
-def _check_sky(sky_dev, rows, g, n_chan, max_de):
+def _check_sky(sky_dev, rows, g, n_chan, max_de, c=None, est=None, res=None, ties=()):
     import torch
     got = sky_dev.view(-1, n_chan, 2)[torch.from_numpy(np.asarray(rows)).cuda()].cpu().numpy().astype(np.float64)
     ref = np.array(g["sky_final_re"]) + 1j * np.array(g["sky_final_im"])
     ab = np.array(g["sky_final_abs"])
+    # a near-tie source holds the GPU's node in the sky model: the oracle's model terms
+    # of that source at the two shapes move the reference
+    for i in ties:
+        sl = slice(i, i + 1)
+        al = c.alpha_med_rad()[sl]
+        args = (c.obs.u, c.obs.v, c.obs.w, c.obs.freq_hz, c.cat.l[sl], c.cat.m[sl], c.cat.flux_jy[sl], al)
+        new = oracle.sky_model(*args, np.array([res["e1"][i]]), np.array([res["e2"][i]]), nu_ref=c.wl.nu_ref_hz,
+                               rows=rows)
+        old = oracle.sky_model(*args, est[sl, oracle.E1], est[sl, oracle.E2], nu_ref=c.wl.nu_ref_hz, rows=rows)
+        ref = ref + (new - old)
     err = np.abs(got[..., 0] + 1j * got[..., 1] - ref)
     # FP32 model (1e-5 of the summed moduli, cancellation-aware), the complex64 output, and the
     # two sides' fitted shapes differing by max_de: a term moves by at most ~10 |term| per unit e
@@ -74,7 +98,7 @@ def _check_sky(sky_dev, rows, g, n_chan, max_de):
     assert np.all(err <= bound), float(np.max(err / bound))
 
 
-@pytest.mark.parametrize("variant", ["snr10"])
+@pytest.mark.parametrize("variant", ["snr10", "sigma_1uJy"])
 def test_batched_chain_matches_oracle(rlf, gold, batched, variant):
     import torch
     c, true = batched
@@ -100,9 +124,11 @@ def test_batched_chain_matches_oracle(rlf, gold, batched, variant):
     rlf.run(obs, d, cat, p, out, sky, ws)
     code, status = rlf.read_status(ws)
     assert code == rlf.RLF_OK, status
+    top2 = np.array(g["top2"]) if "top2" in g else None
+    ge = oracle.grid_e(c.oracle_params(sigma_jy=sigma, chunk=0, update_mode=1))
     res = out.numpy()
-    max_de = _check_estimates(res, est, n)
-    _check_sky(sky, gold["rows"], g, C, max_de)
+    max_de, ties = _check_estimates(res, est, n, top2, ge)
+    _check_sky(sky, gold["rows"], g, C, max_de, c, est, res, ties)
     # one replay of the captured chain on the same buffers
     out.e1.zero_()
     out.e2.zero_()
@@ -114,7 +140,7 @@ def test_batched_chain_matches_oracle(rlf, gold, batched, variant):
     stream.synchronize()
     graph.close()
     res = out.numpy()
-    max_de = _check_estimates(res, est, n)
-    _check_sky(sky, gold["rows"], g, C, max_de)
-    print(f"\n{variant}: sigma {sigma:.4g} Jy, max |de| {max_de:.3g}, bad fits {int(np.sum(res['flag'] & 1))}/{n}, "
-          f"tuning {[int(getattr(p, f)) for f in rlf.TUNE_FIELDS]}")
+    max_de, ties = _check_estimates(res, est, n, top2, ge)
+    _check_sky(sky, gold["rows"], g, C, max_de, c, est, res, ties)
+    print(f"\n{variant}: sigma {sigma:.4g} Jy, max |de| {max_de:.3g} (near-ties {ties}), "
+          f"bad fits {int(np.sum(res['flag'] & 1))}/{n}, tuning {[int(getattr(p, f)) for f in rlf.TUNE_FIELDS]}")
