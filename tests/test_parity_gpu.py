@@ -345,15 +345,17 @@ def test_gaussian_profile_sky_model_and_chain(rlf, prec):
     assert np.max(np.abs(r0["alpha_arcsec"] - res["alpha_arcsec"])) > 0.05
 
 
-@pytest.mark.parametrize("prec", ["split", "mixed", "fp64"])
-def test_adaptive_estimator_matches_oracle(rlf, prec):
+@pytest.mark.parametrize("prec,profile", [("split", 0), ("mixed", 0), ("fp64", 0), ("split", 1)])
+def test_adaptive_estimator_matches_oracle(rlf, prec, profile):
     # adaptive sampling around the maximum (Sec. 2.4) on facets whose posteriors are
     # narrower than the grid: the brightest source at SNR ~100; the oracle's facets in,
-    # the number of halvings and the estimates compared with the oracle's
+    # the number of halvings and the estimates compared with the oracle's (profile 1:
+    # the Gaussian source profile, data and fit)
     torch = _torch()
     c0 = cases.build(synth.workload("small"), with_data=False)
     snr_max = c0.cat.flux_jy.max() * math.sqrt(c0.obs.n_rows * c0.obs.n_chan) / c0.cat.flux_jy.min()
-    c = cases.build(synth.workload("small"), sigma=cases.snr10_sigma(c0.obs, c0.cat) * snr_max / 100.0)
+    c = cases.build(synth.workload("small"), sigma=cases.snr10_sigma(c0.obs, c0.cat) * snr_max / 100.0,
+                    profile=profile)
     po = c.oracle_params(estimator=1)
     al = c.alpha_med_rad()
     facets, ests = [], []
@@ -367,12 +369,19 @@ def test_adaptive_estimator_matches_oracle(rlf, prec):
     assert levels.max() >= 2 and levels.min() == 0        # both kinds of posterior are present
     obs, cat = cases.to_device(c)
     p = rlf.params_default(nu_ref_hz=c.wl.nu_ref_hz, sigma_jy=c.sigma, precision=PRECS[prec],
-                           estimator=rlf.ESTIMATOR_ADAPTIVE)
+                           estimator=rlf.ESTIMATOR_ADAPTIVE, profile=profile)
     ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_FIT)
     out = rlf.Results(cat.n_src, "cuda")
     rlf.fit_sources(torch.from_numpy(np.stack(facets)).cuda(), cat, 0, cat.n_src, p, out, ws)
     got = out.numpy()
     for i, est in enumerate(ests):
+        if est[oracle.NKEPT] == 0:
+            # no estimate: the likelihood vanishes on the oracle's last lattice (a posterior
+            # pushed against |e| = 1, where the Gaussian brightness underflows FP32 on the
+            # GPU a halving or two before FP64 does); both sides flag the fit bad
+            assert int(got["flag"][i]) & rlf.FLAG_BAD, i
+            assert cases.est_matches(got, i, est) <= 1e-4, (i, got["e1"][i], got["e2"][i])   # (0, 0): no samples kept
+            continue
         assert (int(got["flag"][i]) >> rlf.FLAG_LEVELS_SHIFT) & 15 == levels[i], i
         assert cases.est_matches(got, i, est) <= 1e-4, (i, levels[i], got["e1"][i], est[oracle.E1])
         assert abs(got["sig1"][i] - est[oracle.SIG1]) <= 1e-4 + 1e-3 * est[oracle.SIG1]
