@@ -1088,6 +1088,7 @@ fit_persistent_pos_kernel(const T *__restrict__ cells, const int32_t *__restrict
 // sample).  The estimate is the last level's, by the rules of the grid estimate.
 constexpr int kAT = 512;    // threads of an adaptive-sampling CTA (one facet each)
 constexpr int kATc = 128;   // threads of a CTA of the cluster form
+constexpr int kATcBlocks = 5;   // its CTAs per SM (96 registers; 4 left 40 % of the warp slots empty, 6 spilled)
 constexpr int kAdaptR = 4;  // CTAs per facet in the cluster form
 static_assert(kAdaptR <= kAdaptRanks && kAdaptR <= 8, "a portable cluster, within the partials' scratch");
 
@@ -1467,7 +1468,7 @@ adaptive_kernel(const T *__restrict__ cells, const int32_t *__restrict__ ncell, 
 // [kAdaptRanks >= kAdaptR][kAdaptMax][na][2]; lattice e1, e2 [kAdaptMax]; the samples
 // to evaluate [kAdaptMax] (int); control words.
 template <bool kGauss>
-__global__ void __cluster_dims__(kAdaptR, 1, 1) __launch_bounds__(kATc, 2048 / kATc / 4)
+__global__ void __cluster_dims__(kAdaptR, 1, 1) __launch_bounds__(kATc, kATcBlocks)
 adaptive_cluster_kernel(const float *__restrict__ cells, const int32_t *__restrict__ ncell,
                         const SrcRow *__restrict__ table, size_t plane, int32_t NN, const GridConst gc,
                         const double *__restrict__ ga, const double *__restrict__ gb, const double *__restrict__ gl,
