@@ -22,9 +22,10 @@
 //   estimate_source   one CTA per facet: logL, alpha marginal, threshold,
 //                     moments, MAP point, flags; FP64 throughout except the
 //                     logarithms, error functions and exponentials of split mode.
-//   fit_persistent_pos_kernel / grid_tile_pos   the grid with the position
-//                     marginal (Sec. 2.4): one (e, alpha) point per thread, every
-//                     offset's b, the marginal over offsets in the tile's epilogue.
+//   fit_persistent_pos_kernel / grid_tile_pos, grid_tile_posn   the grid with the
+//                     position marginal (Sec. 2.4): one (e, alpha) point per thread
+//                     (FP64, n_pos 5) or three alpha nodes of one e point (FP32, n_pos
+//                     3), every offset's b, the marginal over offsets in the epilogue.
 //   adaptive_cluster_kernel / adaptive_kernel   adaptive sampling around the maximum
 //                     (Sec. 2.4) after the grid fit: halved lattices, a cluster of four
 //                     CTAs per facet (FP32, one position) or one CTA per facet.
