@@ -417,8 +417,10 @@ def test_refit_pass_matches_oracle(rlf, chunk, update_mode):
         rlf.Graph(obs, data, cat, p, out, sky, ws, torch.cuda.Stream())
 
 
-@pytest.mark.parametrize("n_pos", [1, 3])
-def test_invalid_and_empty_sources_are_flagged(rlf, n_pos):
+@pytest.mark.parametrize("n_pos,estimator", [(1, 0), (3, 0), (1, 1), (3, 1)])
+def test_invalid_and_empty_sources_are_flagged(rlf, n_pos, estimator):
+    # estimator 1: adaptive sampling after the grid (the cluster form at n_pos 1, one CTA
+    # per facet at n_pos 3): an empty facet is not refined
     torch = _torch()
     wl = synth.tiny(seed=61, n_ant=12, n_time=9, n_chan=2, n_src=4, r_max_m=3000.0)
     c = cases.build(wl, snr10=True)
@@ -427,7 +429,8 @@ def test_invalid_and_empty_sources_are_flagged(rlf, n_pos):
     cat.e1[2] = 0.9
     cat.e2[2] = 0.6                       # |e| >= 1
     # K = 1e6 makes the cells ~0.1 wavelength wide: no baseline falls in the facet window
-    p = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=c.sigma, facet_n=8, psf_nat=1.0e6, n_pos=n_pos)
+    p = rlf.params_default(nu_ref_hz=wl.nu_ref_hz, sigma_jy=c.sigma, facet_n=8, psf_nat=1.0e6, n_pos=n_pos,
+                           estimator=estimator)
     ws = rlf.alloc_workspace(obs.n_rows, obs.n_chan, cat.n_src, p, rlf.WS_RUN)
     out = rlf.Results(cat.n_src, "cuda")
     sky = torch.empty(obs.n_rows * obs.n_chan * 2, dtype=torch.float32, device="cuda")
@@ -438,6 +441,7 @@ def test_invalid_and_empty_sources_are_flagged(rlf, n_pos):
     assert f[1] & rlf.FLAG_INVALID and f[2] & rlf.FLAG_INVALID
     for i in (0, 3):
         assert not (f[i] & rlf.FLAG_INVALID) and f[i] & rlf.FLAG_EMPTY
+        assert (int(f[i]) >> rlf.FLAG_LEVELS_SHIFT) & 15 == 0   # no lattice refinement of an empty facet
     # an empty facet is not a numerical failure (no non-finite likelihood reported)
     assert not (status & rlf.DEV_NONFINITE)
 
