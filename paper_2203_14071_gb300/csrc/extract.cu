@@ -195,7 +195,8 @@ __device__ __forceinline__ void st_shared_v4_if(uint32_t addr, bool p, int a, in
 // (float-pair phase argument, the group's phase f0 and step fd, the source's quadratic
 // form, u and v in FP32) is shared by its CL lanes: for a block of CL time steps lane lc
 // computes row t0 + lc and stores it in shared memory, and every lane then reads each
-// row of the block (a broadcast).  The next row's residual is loaded one row ahead.
+// row of the block (a broadcast).  The next row's residual is loaded one row ahead,
+// across block boundaries.
 constexpr int kPairThreads = 512;
 constexpr int kPairWarps = kPairThreads / 32;
 constexpr int kPairRing = 4;     // ring entries per lane: a row appends at most two runs, checked every row
@@ -298,6 +299,9 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                     rec_b = reinterpret_cast<const float2 *>(us)[4 * c0 + 2];
                 }
             };
+            const int nr32 = (int)n_rows;
+            const int vstep = stride * C;
+            float4 dnext = make_float4(0.f, 0.f, 0.f, 0.f);   // the residual of the lane's next row
             for (int64_t t0 = t_begin; t0 < t_end; t0 += CL) {
                 // rows t0 .. t0 + CL - 1 of this lane's baseline: lane lc prepares row t0 + lc
                 {
@@ -344,11 +348,10 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                 __syncwarp();
                 const int nt = (int)min((int64_t)CL, t_end - t0);
                 int r = (int)(t0 * stride + bl);
-                const int nr32 = (int)n_rows;
                 const float2 *dp = resid + ((int64_t)r * C + kac);
-                const int vstep = stride * C;
-                float4 dnext = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < nr32) {
+                if (t0 == t_begin && r < nr32) {
+                    // the unit's first row; later blocks start on the row the previous
+                    // block's last iteration fetched
                     if (vec) {
                         dnext = *reinterpret_cast<const float4 *>(dp);
                     } else {
@@ -367,8 +370,9 @@ extract_pair_kernel(const double *__restrict__ u, const double *__restrict__ v, 
                         }
                         const float4 d = dnext;
                         {
-                            // the next row of the block, or this row again past its end (always in bounds)
-                            const float2 *np = (tau + 1 < nt && r + stride < nr32) ? dp + vstep : dp;
+                            // the next row (the next block's first after a block's last), or this
+                            // row again past the last row (always in bounds)
+                            const float2 *np = r + stride < nr32 ? dp + vstep : dp;
                             if (vec) {
                                 dnext = *reinterpret_cast<const float4 *>(np);
                             } else {
