@@ -17,7 +17,8 @@
 // writes W1 transposed into the caller's scratch first (4 MB, a few microseconds).
 //
 // Every mbarrier wait has a time limit (about 2 s); a wait that runs out sets
-// RLF_DEV_TIMEOUT in *status, and the CTA still frees its TMEM and returns.
+// RLF_DEV_TIMEOUT in *status, and the CTA still waits (bounded) for the copies it
+// issued, frees its TMEM and returns.
 #include <cuda.h>
 
 #include <cstdint>
@@ -150,6 +151,7 @@ l1_umma_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ C
     bool ok = true;
     if (threadIdx.x == 0) {
         // loader: stage s is free again once the MMAs that read it have committed
+        int issued = 0;
         for (int kb = 0; kb < kb_per; ++kb) {
             const int s = kb % UST;
             if (kb >= UST && !mbar_wait(smem_u32(&bar_empty[s]), ((kb / UST) - 1) & 1)) {
@@ -160,7 +162,12 @@ l1_umma_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ C
             mbar_expect_tx(full, kStageBytes);
             tma_load_2d(dst, &tx, full, k_first + kb * UK, m0);
             tma_load_2d(dst + kTileA, &tw, full, k_first + kb * UK, 0);
+            issued = kb + 1;
         }
+        // the copies of the last stages this thread issued have landed before the CTA can
+        // leave (bounded; they have in any run whose MMAs completed)
+        for (int kb = issued > UST ? issued - UST : 0; kb < issued; ++kb)
+            if (!mbar_wait(smem_u32(&bar_full[kb % UST]), (kb / UST) & 1)) ok = false;
     } else if (threadIdx.x == 32) {
         // MMA issuer: four K-steps of 16 per stage, accumulating after the first
         for (int kb = 0; kb < kb_per; ++kb) {
