@@ -325,7 +325,9 @@ rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux
                             const int32_t *tidx, const double *e1, const double *e2, const double *alpha_arcsec,
                             const float *normals, int32_t batch, const rlf_params *p, void *x_f16, float *y,
                             void *stream);
-/* One Adam step on a batch (x_f16 [batch][8192], 16-byte aligned; y [batch][3]); step >= 1 is the Adam time
+/* One Adam step on a batch (x_f16 [batch][8192] and the weights blob 16-byte aligned, else
+ * RLF_EINVAL; y [batch][3]); the first layer's forward GEMM and its weight gradient run
+ * on tcgen05; step >= 1 is the Adam time
  * step (bias correction); step = 0 computes the gradients into the blob and leaves the
  * parameters unchanged.  loss (device f32, may be NULL) receives the batch NLL. */
 rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,

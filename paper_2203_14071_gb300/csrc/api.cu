@@ -707,7 +707,8 @@ rlf_status rlf_mlp_simulate(const double *templates, const double *template_flux
 rlf_status rlf_mlp_train_step(void *weights, const void *x_f16, const float *y, int32_t batch, float lr,
                               int32_t step, float *loss, void *workspace, size_t ws_bytes, void *stream)
 {
-    if (!weights || !x_f16 || !y || !workspace || batch <= 0 || !aligned16(x_f16)) return RLF_EINVAL;
+    if (!weights || !x_f16 || !y || !workspace || batch <= 0 || !aligned16(x_f16) || !aligned16(weights))
+        return RLF_EINVAL;
     if (ws_bytes < rlf_mlp_workspace_size(batch)) return RLF_ENOSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;

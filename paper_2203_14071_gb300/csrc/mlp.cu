@@ -3,8 +3,9 @@
 // predicts the mean and log-variance of (e1, e2, ln alpha); the fit then
 // evaluates only a 7 x 7 x 5 box of the grid around the prediction.
 //
-// Kernels: the first layer's forward GEMM on tcgen05 (mlp_umma.cu); the other
-// GEMMs on mma.sync m16n8k16 (f16 inputs, f32 accumulation; K = 256 or the batch)
+// Kernels: the first layer's forward GEMM and its weight gradient on tcgen05
+// (mlp_umma.cu); the other GEMMs on mma.sync m16n8k16 (f16 inputs, f32
+// accumulation; K = 256 or the batch)
 // with fused epilogues for the forward and backward passes, the Gaussian NLL and
 // its gradient, bias-gradient column sums, Adam, the facet encoder, the training
 // facet simulator and the proposal rule.  Weights: f32 masters + f16 copies.
@@ -444,6 +445,8 @@ MlpScratch mlp_scratch(void *base, int32_t max_batch)
     s.dz1 = reinterpret_cast<__half *>(take((size_t)max_batch * kMlpHidden * sizeof(__half)));
     s.part = reinterpret_cast<float *>(take((size_t)kL1Slices * max_batch * kMlpHidden * sizeof(float)));
     s.w1t = reinterpret_cast<__half *>(take((size_t)kMlpIn * kMlpHidden * sizeof(__half)));
+    s.xT = reinterpret_cast<__half *>(take((size_t)kMlpIn * mlp_batch_pad(max_batch) * sizeof(__half)));
+    s.dzT = reinterpret_cast<__half *>(take((size_t)kMlpHidden * mlp_batch_pad(max_batch) * sizeof(__half)));
     s.status = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
     s.bytes = (size_t)(b - static_cast<char *>(base));
     return s;
@@ -500,10 +503,8 @@ cudaError_t mlp_train_step(const MlpWeights &W, const __half *x, const float *y,
     if (e == cudaSuccess)
         e = gemm<false, true, EPI_F16_MASK>(B, kMlpHidden, kMlpHidden, s.dz2, kMlpHidden, W2h, kMlpHidden, nullptr,
                                             s.h1, kMlpHidden, nullptr, s.dz1, kMlpHidden, st);
-    // layer 1: dW1 = x^T dz1, db1 = sum dz1
-    if (e == cudaSuccess)
-        e = gemm<true, false, EPI_F32>(kMlpIn, kMlpHidden, B, x, kMlpIn, s.dz1, kMlpHidden, nullptr, nullptr, 0,
-                                       W.g + o.W1, nullptr, kMlpHidden, st);
+    // layer 1: dW1 = x^T dz1 (on tcgen05), db1 = sum dz1
+    if (e == cudaSuccess) e = mlp_dw1_umma(x, B, s.dz1, s.xT, s.dzT, W.g + o.W1, s.status, st);
     if (e == cudaSuccess) {
         colsum_kernel<__half><<<(kMlpHidden + 127) / 128, 128, 0, st>>>(s.dz1, B, kMlpHidden, W.g + o.b1);
         e = cudaGetLastError();
@@ -534,7 +535,6 @@ cudaError_t mlp_simulate(const double *tmpl, int32_t n_tmpl, const rlf_params &p
                          const int32_t *tidx, const double *e1, const double *e2, const double *alpha_as,
                          const float *z, int32_t B, int32_t N, double sigma, __half *x, float *y, cudaStream_t st)
 {
-    const int NN = N * N;
     dim3 grid(4, B);
     simulate_kernel<<<grid, 256, 0, st>>>(tmpl, n_tmpl, p.profile, p.add, p.esp, p.psf_nat, tflux, tidx, e1, e2, alpha_as, z, N,
                                           sigma, x, y);

@@ -13,8 +13,11 @@
 // and store their rows of the slice.  Rows past M read as zeros (TMA fills out of
 // bounds) and are not stored.
 //
-// The MMA wants B as [n][k] (K-major); W1 is stored [k][n], so transpose_w1_kernel
+// The MMA wants B as [n][k] (K-major); W1 is stored [k][n], so transpose_pad_kernel
 // writes W1 transposed into the caller's scratch first (4 MB, a few microseconds).
+// The same kernel computes the training's first-layer weight gradient
+// dW1 = x^T dz1 (M = 8192, K = the batch): both operands are transposed first into
+// zero-padded K-major copies (mlp_dw1_umma).
 //
 // Every mbarrier wait has a time limit (about 2 s); a wait that runs out sets
 // RLF_DEV_TIMEOUT in *status, and the CTA still waits (bounded) for the copies it
@@ -214,15 +217,24 @@ l1_umma_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ C
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
 }
 
-// wt[n][k] = w[k][n] for the [8192][256] f16 matrix, through 32 x 32 shared tiles
-__global__ void transpose_w1_kernel(const __half *__restrict__ w, __half *__restrict__ wt)
+// out[c][r] = in[r][c] (r < rows), 0 (rows <= r < ld_out), for an f16 matrix in
+// [rows][cols] (cols and ld_out multiples of 32), through 32 x 32 shared tiles
+__global__ void transpose_pad_kernel(const __half *__restrict__ in, int rows, int cols, __half *__restrict__ out,
+                                     int ld_out)
 {
     __shared__ __half t[32][33];
-    const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int j = ty; j < 32; j += 8) t[j][tx] = w[(size_t)(k0 + j) * kMlpHidden + n0 + tx];
+    for (int j = ty; j < 32; j += 8)
+        t[j][tx] = r0 + j < rows ? in[(size_t)(r0 + j) * cols + c0 + tx] : __float2half(0.0f);
     __syncthreads();
-    for (int j = ty; j < 32; j += 8) wt[(size_t)(n0 + j) * kMlpIn + k0 + tx] = t[tx][j];
+    for (int j = ty; j < 32; j += 8) out[(size_t)(c0 + j) * ld_out + r0 + tx] = t[tx][j];
+}
+
+cudaError_t transpose_pad(const __half *in, int rows, int cols, __half *out, int ld_out, cudaStream_t st)
+{
+    transpose_pad_kernel<<<dim3(cols / 32, ld_out / 32), dim3(32, 8), 0, st>>>(in, rows, cols, out, ld_out);
+    return cudaGetLastError();
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -257,25 +269,47 @@ bool tensor_map_2d(CUtensorMap *map, const __half *base, uint64_t inner, uint64_
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// part[z][m][n] = sum over k in slice z of A[m][k] Bt[n][k], m < M, n < 256: A
+// [M][K] and Bt [256][K] f16, K-major, 16-byte aligned, K a multiple of 64 n_slices
+cudaError_t umma_gemm_nt(const __half *A, int32_t M, int32_t K, const __half *Bt, float *part, int32_t n_slices,
+                         int32_t *status, cudaStream_t st)
+{
+    if (M <= 0 || K <= 0 || n_slices <= 0 || K % (n_slices * UK) != 0 || (reinterpret_cast<uintptr_t>(A) & 15u) != 0 ||
+        (reinterpret_cast<uintptr_t>(Bt) & 15u) != 0)
+        return cudaErrorInvalidValue;
+    CUtensorMap ta, tb;
+    if (!tensor_map_2d(&ta, A, (uint64_t)K, (uint64_t)M, UK, UM) || !tensor_map_2d(&tb, Bt, (uint64_t)K, UN, UK, UN))
+        return cudaErrorNotSupported;
+    const cudaError_t e =
+        cudaFuncSetAttribute(l1_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+    if (e != cudaSuccess) return e;
+    l1_umma_kernel<<<dim3((M + UM - 1) / UM, n_slices), UTHREADS, kUmmaSmem, st>>>(ta, tb, M, K / (n_slices * UK),
+                                                                                  part, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t mlp_layer1_umma(const __half *x, int32_t M, const __half *W1h, __half *W1t, float *part, int32_t n_slices,
                             int32_t *status, cudaStream_t st)
 {
-    // TMA reads from 16-byte aligned bases
-    if (M <= 0 || n_slices <= 0 || kMlpIn % (n_slices * UK) != 0 || (reinterpret_cast<uintptr_t>(x) & 15u) != 0 ||
-        (reinterpret_cast<uintptr_t>(W1t) & 15u) != 0)
-        return cudaErrorInvalidValue;
-    CUtensorMap tx, tw;
-    if (!tensor_map_2d(&tx, x, kMlpIn, (uint64_t)M, UK, UM) || !tensor_map_2d(&tw, W1t, kMlpIn, kMlpHidden, UK, UN))
-        return cudaErrorNotSupported;
-    cudaError_t e = cudaFuncSetAttribute(l1_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
-    if (e != cudaSuccess) return e;
-    transpose_w1_kernel<<<dim3(kMlpIn / 32, kMlpHidden / 32), dim3(32, 8), 0, st>>>(W1h, W1t);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    l1_umma_kernel<<<dim3((M + UM - 1) / UM, n_slices), UTHREADS, kUmmaSmem, st>>>(
-        tx, tw, M, kMlpIn / (n_slices * UK), part, status);
-    return cudaGetLastError();
+    // B operand: W1 [8192][256] transposed to [256][8192]
+    cudaError_t e = transpose_pad(W1h, kMlpIn, kMlpHidden, W1t, kMlpIn, st);
+    if (e == cudaSuccess) e = umma_gemm_nt(x, M, kMlpIn, W1t, part, n_slices, status, st);
+    return e;
+}
+
+cudaError_t mlp_dw1_umma(const __half *x, int32_t B, const __half *dz1, __half *xT, __half *dzT, float *dW1,
+                         int32_t *status, cudaStream_t st)
+{
+    // dW1[k][n] = sum over b of x[b][k] dz1[b][n]: both operands transposed to K-major
+    // ([8192][Bp] and [256][Bp], the batch zero-padded to Bp, a multiple of 64)
+    const int Bp = mlp_batch_pad(B);
+    if (B <= 0 || (reinterpret_cast<uintptr_t>(dW1) & 15u) != 0) return cudaErrorInvalidValue;   // 16-byte stores
+    cudaError_t e = transpose_pad(x, B, kMlpIn, xT, Bp, st);
+    if (e == cudaSuccess) e = transpose_pad(dz1, B, kMlpHidden, dzT, Bp, st);
+    if (e == cudaSuccess) e = umma_gemm_nt(xT, kMlpIn, Bp, dzT, dW1, 1, status, st);
+    return e;
 }
 
 }  // namespace rlf

@@ -364,6 +364,7 @@ struct MlpScratch {
     float *o, *g32;
     float *part;            // split-K partial sums of the first layer
     __half *w1t;            // W1 transposed, [256][8192] (the tensor-core GEMM's K-major B)
+    __half *xT, *dzT;       // x and dz1 transposed, [8192][Bp] and [256][Bp] (the weight gradient's operands)
     int32_t *status;        // RLF_DEV_TIMEOUT from the tensor-core GEMM's bounded waits
     size_t bytes;
 };
@@ -377,6 +378,11 @@ cudaError_t mlp_forward(const MlpWeights &W, const __half *x, int32_t B, const M
 // encode their tensor maps
 cudaError_t mlp_layer1_umma(const __half *x, int32_t M, const __half *W1h, __half *W1t, float *part, int32_t n_slices,
                             int32_t *status, cudaStream_t st);
+// the batch padded for the weight-gradient GEMM's K (a multiple of 64)
+inline int32_t mlp_batch_pad(int32_t B) { return (B + 63) / 64 * 64; }
+// dW1 = x^T dz1 on tcgen05 (mlp_umma.cu), through transposed, zero-padded copies xT, dzT
+cudaError_t mlp_dw1_umma(const __half *x, int32_t B, const __half *dz1, __half *xT, __half *dzT, float *dW1,
+                         int32_t *status, cudaStream_t st);
 cudaError_t mlp_train_step(const MlpWeights &W, const __half *x, const float *y, int32_t B, float lr, int32_t step,
                            float *loss, const MlpScratch &s, cudaStream_t st);
 cudaError_t mlp_init(const MlpWeights &W, const float *z, cudaStream_t st);
