@@ -413,6 +413,18 @@ def mlp_line(rlf, torch, dev, W, stream, sigma, train_steps=2000, batch=256, lr=
         z = torch.randn(k, batch, 2, 4096, generator=gen, device=dev)
         return tidx, e[..., 0].contiguous(), e[..., 1].contiguous(), al, z
 
+    # untimed warm-up on a throwaway network: the first use of the sampling ops and of
+    # the training kernels in a fresh process carries one-time costs (seconds) that the
+    # timed run must not include
+    m_w = rlf.Mlp(dev)
+    m_w.init(torch.randn(m_w.P, generator=torch.Generator(device=dev).manual_seed(1), device=dev), stream)
+    gen_state = gen.get_state()
+    tw, e1w, e2w, alw, zw = draws(2)
+    gen.set_state(gen_state)   # the timed run draws what it drew without the warm-up
+    for j in range(2):
+        rlf.mlp_simulate(fac, flux, tw[j], e1w[j], e2w[j], alw[j], zw[j], p, x16, y, stream)
+        rlf.mlp_train_step(m_w, x16, y, lr, j + 1, None, ws_t, stream)
+    del m_w
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)

@@ -24,6 +24,7 @@
 // issued, frees its TMEM and returns.
 #include <cuda.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "rlf_internal.cuh"
@@ -33,6 +34,7 @@ namespace rlf {
 namespace {
 
 constexpr int UM = 128, UN = 256, UK = 64, UST = 4, UTHREADS = 128;
+constexpr int kMaxDevices = 64;
 constexpr uint32_t kTileA = UM * UK * 2, kTileB = UN * UK * 2, kStageBytes = kTileA + kTileB;
 constexpr size_t kUmmaSmem = (size_t)UST * kStageBytes + 1024;   // + room to put the ring on a 1 KB boundary
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s of SM clock: the limit of every mbarrier wait
@@ -280,9 +282,18 @@ cudaError_t umma_gemm_nt(const __half *A, int32_t M, int32_t K, const __half *Bt
     CUtensorMap ta, tb;
     if (!tensor_map_2d(&ta, A, (uint64_t)K, (uint64_t)M, UK, UM) || !tensor_map_2d(&tb, Bt, (uint64_t)K, UN, UK, UN))
         return cudaErrorNotSupported;
-    const cudaError_t e =
-        cudaFuncSetAttribute(l1_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+    // the kernel's shared-memory limit, raised once per device (setting a function
+    // attribute on every launch can stall the host behind the kernel's running launches)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    static std::atomic<bool> smem_set[kMaxDevices];
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!smem_set[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(l1_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+        if (e != cudaSuccess) return e;
+        smem_set[dev].store(true, std::memory_order_release);
+    }
     l1_umma_kernel<<<dim3((M + UM - 1) / UM, n_slices), UTHREADS, kUmmaSmem, st>>>(ta, tb, M, K / (n_slices * UK),
                                                                                   part, status);
     return cudaGetLastError();
